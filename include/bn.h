@@ -1,0 +1,146 @@
+/*
+ * bn.h - batched exact addition and multiplication of midsize unsigned
+ * integers (1K to about 256K bits) on one NVIDIA GB300 (sm_103a) GPU.
+ *
+ * Method: Oancea & Watt, "GPU Implementations for Midsize Integer Addition
+ * and Multiplication" (arXiv 2405.14642).  Each integer is handled by one CTA
+ * (or by part of a CTA for small sizes), as in the paper.
+ *
+ * Representation (Section 2): an integer is an array of little-endian u32
+ * limbs, a = a_0 + a_1 x + ... + a_{n-1} x^{n-1} with x = 2^32.  A batch of
+ * `batch` integers of n limbs is one contiguous array: instance i starts at
+ * limb i*n.  Results are full width (the paper keeps the input length; its
+ * result is the low limbs of the result here):
+ *     add: max(na, nb) + 1 limbs      mul: na + nb limbs
+ * The shorter operand of an addition is zero-extended.
+ *
+ * Ownership and memory: every a/b/c pointer of the device entry points is
+ * caller-owned DEVICE memory that stays valid until the enqueued work has
+ * finished.  Plans own their tables and scratch until bn_plan_destroy.
+ * c must not overlap a or b (BN_EINVAL).  No alignment is required; 16-byte
+ * aligned rows (base 16-byte aligned and a limb count that is a multiple of 4)
+ * take the vectorised load path.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream).  Device entry points only enqueue work and return; results
+ * are ready when the stream reaches that point.  Errors from the work itself
+ * surface as BN_ECUDA on a later call or on stream synchronisation.
+ *
+ * Errors: every entry point returns a bn_status and throws nothing.  On
+ * BN_ECUDA the CUDA error text is available from bn_last_error().
+ * batch == 0 is a no-op returning BN_OK (pointers are not checked then).
+ *
+ * Thread safety: distinct plans may be used from different host threads.  One
+ * plan must not be executed concurrently from two host threads.  The one-shot
+ * forms keep an internal, mutex-protected cache of plans per size.
+ */
+#ifndef BN_GB300_H
+#define BN_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bn_status {
+    BN_OK = 0,
+    BN_EINVAL = 1,        /* null pointer, zero size, overlap, bad option */
+    BN_ENOMEM = 2,        /* a device or host allocation failed */
+    BN_ECUDA = 3,         /* a CUDA runtime call or launch failed */
+    BN_EUNSUPPORTED = 4,  /* size outside what the variant holds */
+    BN_ETIMEOUT = 5       /* a bounded device-side wait gave up */
+} bn_status;
+
+typedef enum bn_op {
+    /* Section 2: three-step addition, carries by an exclusive scan with the
+     * carry operator (here a warp-ballot carry-lookahead plus a cross-warp
+     * step through shared memory).  na, nb <= BN_ADD_MAX_LIMBS. */
+    BN_OP_ADD = 0,
+    /* Section 3: classical product, Eq. (1), each thread owning whole result
+     * windows under the load-balanced partition of Fig. 3 (extended to full,
+     * unequal-length products), per-thread windows recombined by the L/H
+     * addition of Fig. 4/5.  na, nb <= BN_MUL_MAX_LIMBS. */
+    BN_OP_MUL_QUAD = 1,
+    /* Section 4: product through a number-theoretic transform over the
+     * prime field PrimeField64 (p = 29*2^57 + 1, Section 4.1) with 16-bit
+     * digits, transform length the next power of two >= 2(na + nb). */
+    BN_OP_MUL_NTT64 = 2,
+    /* Section 4 with 32-bit digits over two primes (29*2^57 + 1 and
+     * 2^64 - 2^32 + 1), recombined by the Chinese remainder theorem. */
+    BN_OP_MUL_NTT_CRT = 3
+} bn_op;
+
+/* Largest limb counts per operand (256K bits for the products, 512K bits for
+ * the sum). */
+#define BN_ADD_MAX_LIMBS 16384u
+#define BN_MUL_MAX_LIMBS 8192u
+
+/* Optional launch tuning; a zero field takes the built-in default. */
+typedef struct bn_tuning {
+    uint32_t limbs_per_thread;  /* add: limbs per thread (multiple of the vector width);
+                                   quad: result limbs per window (2..16) */
+    uint32_t cta_threads;       /* threads per CTA (multiple of 32, <= 1024) */
+    uint32_t reserved[2];       /* must be zero */
+} bn_tuning;
+
+typedef struct bn_plan_s *bn_plan;
+
+/* Create a plan for `batch` instances of an na-limb by nb-limb operation.
+ * NTT plans build their twiddle tables and device scratch here (the only
+ * place the library allocates device memory besides the host-buffer staging
+ * of bn_plan_execute_host).  tuning may be NULL.
+ * Errors: BN_EINVAL (null out, zero size, bad tuning), BN_EUNSUPPORTED (size
+ * above the op's limit), BN_ENOMEM, BN_ECUDA. */
+bn_status bn_plan_create(bn_plan *out, bn_op op, uint32_t na, uint32_t nb,
+                         uint64_t batch, const bn_tuning *tuning);
+
+/* Enqueue the plan on `stream` over device arrays a (batch x na), b (batch x nb)
+ * and c (batch x bn_plan_out_limbs).  Errors: BN_EINVAL, BN_ECUDA. */
+bn_status bn_plan_execute(bn_plan plan, const uint32_t *a, const uint32_t *b,
+                          uint32_t *c, void *stream);
+
+/* Same over HOST arrays: copies a and b to plan-owned device staging buffers
+ * (allocated on first use), runs the plan, copies c back and synchronises
+ * `stream` before returning, so c is filled on BN_OK.  Pinned host memory
+ * makes the copies asynchronous and faster; pageable memory also works. */
+bn_status bn_plan_execute_host(bn_plan plan, const uint32_t *a, const uint32_t *b,
+                               uint32_t *c, void *stream);
+
+/* Free the plan's device resources (synchronises the device first). */
+bn_status bn_plan_destroy(bn_plan plan);
+
+/* Result limbs per instance: max(na,nb)+1 for add, na+nb for products. */
+uint32_t bn_plan_out_limbs(bn_plan plan);
+
+/* Device scratch the plan holds (bytes; 0 for add and quad). */
+size_t bn_plan_scratch_bytes(bn_plan plan);
+
+/* Transform length N of an NTT plan (0 for other ops). */
+uint32_t bn_plan_transform_length(bn_plan plan);
+
+/* One-shot forms over device arrays: create (or reuse a cached) plan for the
+ * size, enqueue on `stream`, return.  bn_mul_ntt: crt == 0 selects
+ * BN_OP_MUL_NTT64, crt != 0 selects BN_OP_MUL_NTT_CRT. */
+bn_status bn_add(const uint32_t *a, const uint32_t *b, uint32_t *c,
+                 uint32_t na, uint32_t nb, uint64_t batch, void *stream);
+bn_status bn_mul_quad(const uint32_t *a, const uint32_t *b, uint32_t *c,
+                      uint32_t na, uint32_t nb, uint64_t batch, void *stream);
+bn_status bn_mul_ntt(const uint32_t *a, const uint32_t *b, uint32_t *c,
+                     uint32_t na, uint32_t nb, uint64_t batch, int crt, void *stream);
+
+/* Static description of a status code. */
+const char *bn_status_str(bn_status s);
+
+/* Text of the last error recorded on this host thread ("" if none). */
+const char *bn_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int bn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BN_GB300_H */

@@ -1,0 +1,22 @@
+"""Batched exact addition and multiplication of midsize unsigned integers on
+one NVIDIA GB300 (sm_103a), after Oancea & Watt, "GPU Implementations for
+Midsize Integer Addition and Multiplication" (arXiv 2405.14642).
+
+The compute path is the CUDA library built from ``csrc/`` (C ABI in
+``include/bn.h``); this package is its thin ctypes binding.  Operations:
+
+* :func:`bn_add` - addition by a carry-propagation scan (Section 2);
+* :func:`bn_mul_quad` - classical multiplication with a load-balanced
+  per-thread partition of the result (Section 3);
+* :func:`bn_mul_ntt` - multiplication through a number-theoretic transform
+  over "good" primes, one 64-bit prime with 16-bit digits or two primes with
+  32-bit digits and CRT recombination (Section 4);
+* :class:`Plan` - the plan object of the C ABI (device and host-buffer forms).
+"""
+from ._binding import (BN_ADD_MAX_LIMBS, BN_MUL_MAX_LIMBS, BN_OP_ADD, BN_OP_MUL_NTT64,
+                       BN_OP_MUL_NTT_CRT, BN_OP_MUL_QUAD, BnError, Plan, bn_add, bn_mul_ntt,
+                       bn_mul_quad, library_path, load)
+
+__all__ = ["bn_add", "bn_mul_quad", "bn_mul_ntt", "Plan", "BnError", "load", "library_path",
+           "BN_OP_ADD", "BN_OP_MUL_QUAD", "BN_OP_MUL_NTT64", "BN_OP_MUL_NTT_CRT",
+           "BN_ADD_MAX_LIMBS", "BN_MUL_MAX_LIMBS"]

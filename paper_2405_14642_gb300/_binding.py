@@ -1,0 +1,235 @@
+"""Thin ctypes binding over the C ABI of ``include/bn.h``.
+
+Argument marshalling only: every step of every operation runs in the CUDA
+library.  There is no CPU fallback; if the library is missing or fails to
+load, every entry point raises.  Operands are torch CUDA tensors of dtype
+int32 or uint32 (limb bit patterns), shaped (batch, limbs) and contiguous;
+results come back as int32 tensors holding u32 bit patterns.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+BN_OK, BN_EINVAL, BN_ENOMEM, BN_ECUDA, BN_EUNSUPPORTED, BN_ETIMEOUT = range(6)
+BN_OP_ADD, BN_OP_MUL_QUAD, BN_OP_MUL_NTT64, BN_OP_MUL_NTT_CRT = range(4)
+BN_ADD_MAX_LIMBS = 16384
+BN_MUL_MAX_LIMBS = 8192
+
+_lib = None
+
+
+class BnError(RuntimeError):
+    """A non-OK bn_status, with the library's error text."""
+
+    def __init__(self, status: int, where: str):
+        self.status = status
+        lib = _lib
+        text = lib.bn_status_str(status).decode() if lib else str(status)
+        detail = lib.bn_last_error().decode() if lib else ""
+        super().__init__(f"{where}: {text}" + (f" ({detail})" if detail else ""))
+
+
+class bn_tuning(ctypes.Structure):
+    _fields_ = [("limbs_per_thread", ctypes.c_uint32), ("cta_threads", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
+
+
+def library_path():
+    return _build.library_path()
+
+
+def load(build_if_missing: bool = False):
+    """Load the library (once).  Raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.library_path()
+    if build_if_missing and not _build.is_current():
+        _build.build()
+    if not path.exists():
+        raise RuntimeError(f"CUDA library {path} is not built; run __graft_entry__.build()")
+    lib = ctypes.CDLL(str(path))
+    u32p, vp, u32, u64 = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+    st = ctypes.c_int
+    sigs = {
+        "bn_plan_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, u32, u32, u64,
+                            ctypes.POINTER(bn_tuning)], st),
+        "bn_plan_execute": ([vp, u32p, u32p, u32p, vp], st),
+        "bn_plan_execute_host": ([vp, u32p, u32p, u32p, vp], st),
+        "bn_plan_destroy": ([vp], st),
+        "bn_plan_out_limbs": ([vp], u32),
+        "bn_plan_scratch_bytes": ([vp], ctypes.c_size_t),
+        "bn_plan_transform_length": ([vp], u32),
+        "bn_add": ([u32p, u32p, u32p, u32, u32, u64, vp], st),
+        "bn_mul_quad": ([u32p, u32p, u32p, u32, u32, u64, vp], st),
+        "bn_mul_ntt": ([u32p, u32p, u32p, u32, u32, u64, ctypes.c_int, vp], st),
+        "bn_status_str": ([ctypes.c_int], ctypes.c_char_p),
+        "bn_last_error": ([], ctypes.c_char_p),
+        "bn_version": ([], ctypes.c_int),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != BN_OK:
+        raise BnError(status, where)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _operand(x, name):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        raise TypeError(f"{name} must hold 32-bit limbs (int32 or uint32)")
+    if x.dim() != 2 or not x.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous (batch, limbs) tensor")
+    return x
+
+
+def _stream_handle(stream, device):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _out(out, batch, limbs, like):
+    torch = _torch()
+    if out is None:
+        return torch.empty((batch, limbs), dtype=torch.int32, device=like.device)
+    out = _operand(out, "out")
+    if tuple(out.shape) != (batch, limbs):
+        raise ValueError(f"out must have shape {(batch, limbs)}")
+    return out
+
+
+def _pair(a, b):
+    a, b = _operand(a, "a"), _operand(b, "b")
+    if a.shape[0] != b.shape[0] or a.device != b.device:
+        raise ValueError("a and b need the same batch size and device")
+    return a, b
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def bn_add(a, b, out=None, stream=None):
+    """c = a + b per row (Section 2); result has max(na, nb) + 1 limbs."""
+    lib = load()
+    a, b = _pair(a, b)
+    batch, na, nb = a.shape[0], a.shape[1], b.shape[1]
+    out = _out(out, batch, max(na, nb) + 1, a)
+    _check(lib.bn_add(_ptr(a), _ptr(b), _ptr(out), na, nb, batch, _stream_handle(stream, a.device)),
+           "bn_add")
+    return out
+
+
+def bn_mul_quad(a, b, out=None, stream=None):
+    """c = a * b per row by the classical method (Section 3); na + nb limbs."""
+    lib = load()
+    a, b = _pair(a, b)
+    batch, na, nb = a.shape[0], a.shape[1], b.shape[1]
+    out = _out(out, batch, na + nb, a)
+    _check(lib.bn_mul_quad(_ptr(a), _ptr(b), _ptr(out), na, nb, batch,
+                           _stream_handle(stream, a.device)), "bn_mul_quad")
+    return out
+
+
+def bn_mul_ntt(a, b, crt: bool = False, out=None, stream=None):
+    """c = a * b per row through a number-theoretic transform (Section 4)."""
+    lib = load()
+    a, b = _pair(a, b)
+    batch, na, nb = a.shape[0], a.shape[1], b.shape[1]
+    out = _out(out, batch, na + nb, a)
+    _check(lib.bn_mul_ntt(_ptr(a), _ptr(b), _ptr(out), na, nb, batch, int(bool(crt)),
+                          _stream_handle(stream, a.device)), "bn_mul_ntt")
+    return out
+
+
+class Plan:
+    """A bn_plan: fixed op, sizes and batch; reusable across calls."""
+
+    def __init__(self, op: int, na: int, nb: int, batch: int,
+                 limbs_per_thread: int = 0, cta_threads: int = 0):
+        lib = load()
+        self._lib = lib
+        self._h = ctypes.c_void_p()
+        tun = bn_tuning(limbs_per_thread, cta_threads)
+        _check(lib.bn_plan_create(ctypes.byref(self._h), op, na, nb, batch, ctypes.byref(tun)),
+               "bn_plan_create")
+        self.op, self.na, self.nb, self.batch = op, na, nb, batch
+        self.out_limbs = lib.bn_plan_out_limbs(self._h)
+
+    @property
+    def scratch_bytes(self) -> int:
+        return self._lib.bn_plan_scratch_bytes(self._h)
+
+    @property
+    def transform_length(self) -> int:
+        return self._lib.bn_plan_transform_length(self._h)
+
+    def execute(self, a, b, out=None, stream=None):
+        """Run on device tensors a (batch, na), b (batch, nb)."""
+        a, b = _pair(a, b)
+        if tuple(a.shape) != (self.batch, self.na) or tuple(b.shape) != (self.batch, self.nb):
+            raise ValueError("operand shapes do not match the plan")
+        out = _out(out, self.batch, self.out_limbs, a)
+        _check(self._lib.bn_plan_execute(self._h, _ptr(a), _ptr(b), _ptr(out),
+                                         _stream_handle(stream, a.device)), "bn_plan_execute")
+        return out
+
+    def execute_host(self, a: np.ndarray, b: np.ndarray, out: Optional[np.ndarray] = None,
+                     stream=None) -> np.ndarray:
+        """Run on host arrays (numpy uint32, or pinned torch CPU tensors); the
+        library copies in, computes, copies out and synchronises."""
+        def host_ptr(x, shape, name):
+            if hasattr(x, "data_ptr"):  # torch CPU tensor (possibly pinned)
+                if tuple(x.shape) != shape or not x.is_contiguous() or x.element_size() != 4:
+                    raise ValueError(f"{name} must be a contiguous 32-bit {shape} tensor")
+                return ctypes.c_void_p(x.data_ptr()), x
+            arr = np.ascontiguousarray(x, dtype=np.uint32)
+            if arr.shape != shape:
+                raise ValueError(f"{name} must have shape {shape}")
+            return ctypes.c_void_p(arr.ctypes.data), arr
+        pa, ka = host_ptr(a, (self.batch, self.na), "a")
+        pb, kb = host_ptr(b, (self.batch, self.nb), "b")
+        if out is None:
+            out = np.empty((self.batch, self.out_limbs), np.uint32)
+        pc, kc = host_ptr(out, (self.batch, self.out_limbs), "out")
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(self._lib.bn_plan_execute_host(self._h, pa, pb, pc, ctypes.c_void_p(s.cuda_stream)),
+               "bn_plan_execute_host")
+        return kc
+
+    def close(self):
+        if self._h:
+            _check(self._lib.bn_plan_destroy(self._h), "bn_plan_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,381 @@
+// Batched classical multiplication c = a * b (Section 3, Eq. (1)).
+//
+// Partition (Section 3.1, Fig. 3, extended to full products of unequal
+// lengths).  With na >= nb (operands are swapped otherwise) the result columns
+// C_k = sum_{i+j=k} A_i B_j form a trapezoid: a rising region (columns
+// [0, nb), k+1 terms), a plateau (nb terms) and a falling region.  Columns are
+// grouped into windows of Q consecutive columns.  A thread owns one "unit":
+//   * a rising pair: window r and its mirror R-1-r of the rising region,
+//   * a plateau window, or
+//   * a falling pair, mirrored the same way.
+// Every unit then costs the same Q*(nb + Q) word products (the paper's
+// mirror pairing of C_t with C_{M-1-t}, applied to each sloped region), so
+// threads finish together and no update is atomic.
+//
+// Window accumulation.  A thread keeps the window value
+//     S = sum_{q<Q} C_{k+q} 2^{32q}
+// in Q+2 registers (it stays below 2^{32(Q+2)} since nb < 2^32) and adds
+// A_i * (B_{k-i}, ..., B_{k-i+Q-1}) for each i with one mad.lo carry chain
+// and one mad.hi carry chain: about two multiply-adds per word product.
+// Operands are read from shared memory as 16-byte vectors, Q at a time; the
+// B window slides down one word per step and is assembled from two
+// consecutive Q-word chunks held in registers.
+//
+// Recombination (Fig. 4/5).  Each window's low Q words go to L (the result
+// range [k, k+Q)), its two high words to H at k+Q and k+Q+1; windows are Q
+// apart, so L and H are each written once per word.  c = L + H is then an
+// ordinary addition done with the Section 2 carry scan over threads in
+// memory order (2Q words per thread), and the result is copied out.
+#include "bn_device.cuh"
+#include "bn_internal.h"
+
+namespace bn {
+namespace {
+
+constexpr uint32_t kQuadMaxThreads = 1024;
+
+// Shared-memory word index for logical index x: a 16-byte pad after every 32
+// words, which keeps 16-byte vector accesses at a stride of Q words free of
+// bank conflicts.  x must be a multiple of 4 for vector accesses.
+__device__ __forceinline__ uint32_t phys(uint32_t x) { return x + 4u * (x >> 5); }
+__host__ __device__ constexpr uint32_t phys_size(uint32_t x) { return x + 4u * ((x + 31) >> 5); }
+
+struct QuadArgs {
+    const uint32_t *a, *b;  // a is the longer operand (na >= nb)
+    uint32_t *c;
+    uint32_t na, nb;        // true limb counts
+    uint32_t nap, nbp;      // padded: nbp = roundup(nb, 2Q), nap = max(roundup(na, Q), nbp)
+    uint32_t nout;          // na + nb
+    uint32_t units;         // nap / Q
+    uint32_t group;         // threads per instance (power of two <= 32 or multiple of 32)
+    uint32_t ipb;           // instances per CTA
+    uint32_t inst_words;    // shared words per instance
+    uint32_t ab_words;      // A region (B region follows at ab_words)
+    uint32_t hc_offset;     // H spill words (2 per window)
+    uint32_t vec_a, vec_b, vec_c;  // 16-byte aligned rows
+    uint64_t batch;
+};
+
+// acc += a * (w[0] + w[1] 2^32 + ... + w[Q-1] 2^{32(Q-1)}), acc has Q+2 words.
+template <int Q>
+__device__ __forceinline__ void mac(uint32_t (&acc)[Q + 2], uint32_t a, const uint32_t (&w)[Q]);
+
+template <>
+__device__ __forceinline__ void mac<4>(uint32_t (&acc)[6], uint32_t a, const uint32_t (&w)[4]) {
+    asm("mad.lo.cc.u32  %0, %6, %7,  %0;\n\t"
+        "madc.lo.cc.u32 %1, %6, %8,  %1;\n\t"
+        "madc.lo.cc.u32 %2, %6, %9,  %2;\n\t"
+        "madc.lo.cc.u32 %3, %6, %10, %3;\n\t"
+        "addc.cc.u32    %4, %4, 0;\n\t"
+        "addc.u32       %5, %5, 0;\n\t"
+        "mad.hi.cc.u32  %1, %6, %7,  %1;\n\t"
+        "madc.hi.cc.u32 %2, %6, %8,  %2;\n\t"
+        "madc.hi.cc.u32 %3, %6, %9,  %3;\n\t"
+        "madc.hi.cc.u32 %4, %6, %10, %4;\n\t"
+        "addc.u32       %5, %5, 0;"
+        : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3]), "+r"(acc[4]), "+r"(acc[5])
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]));
+}
+
+template <>
+__device__ __forceinline__ void mac<8>(uint32_t (&acc)[10], uint32_t a, const uint32_t (&w)[8]) {
+    asm("mad.lo.cc.u32  %0, %10, %11, %0;\n\t"
+        "madc.lo.cc.u32 %1, %10, %12, %1;\n\t"
+        "madc.lo.cc.u32 %2, %10, %13, %2;\n\t"
+        "madc.lo.cc.u32 %3, %10, %14, %3;\n\t"
+        "madc.lo.cc.u32 %4, %10, %15, %4;\n\t"
+        "madc.lo.cc.u32 %5, %10, %16, %5;\n\t"
+        "madc.lo.cc.u32 %6, %10, %17, %6;\n\t"
+        "madc.lo.cc.u32 %7, %10, %18, %7;\n\t"
+        "addc.cc.u32    %8, %8, 0;\n\t"
+        "addc.u32       %9, %9, 0;\n\t"
+        "mad.hi.cc.u32  %1, %10, %11, %1;\n\t"
+        "madc.hi.cc.u32 %2, %10, %12, %2;\n\t"
+        "madc.hi.cc.u32 %3, %10, %13, %3;\n\t"
+        "madc.hi.cc.u32 %4, %10, %14, %4;\n\t"
+        "madc.hi.cc.u32 %5, %10, %15, %5;\n\t"
+        "madc.hi.cc.u32 %6, %10, %16, %6;\n\t"
+        "madc.hi.cc.u32 %7, %10, %17, %7;\n\t"
+        "madc.hi.cc.u32 %8, %10, %18, %8;\n\t"
+        "addc.u32       %9, %9, 0;"
+        : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3]), "+r"(acc[4]), "+r"(acc[5]),
+          "+r"(acc[6]), "+r"(acc[7]), "+r"(acc[8]), "+r"(acc[9])
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]),
+          "r"(w[7]));
+}
+
+template <int Q>
+__device__ __forceinline__ void ld_words(const uint32_t *S, uint32_t x, uint32_t (&v)[Q]) {
+#pragma unroll
+    for (int j = 0; j < Q / 4; ++j) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(S + phys(x + 4 * j));
+        v[4 * j] = t.x; v[4 * j + 1] = t.y; v[4 * j + 2] = t.z; v[4 * j + 3] = t.w;
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void st_words(uint32_t *S, uint32_t x, const uint32_t *v) {
+#pragma unroll
+    for (int j = 0; j < Q / 4; ++j)
+        *reinterpret_cast<uint4 *>(S + phys(x + 4 * j)) =
+            make_uint4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+}
+
+// Window starting at column k: sum over i in [ilo, ilo + steps) of
+// A_i * B[k-i .. k-i+Q).  B's logical index x lives at phys(x + Q).
+// ilo, k and steps are multiples of Q.
+template <int Q>
+__device__ __forceinline__ void conv_window(const uint32_t *As, const uint32_t *Bs, uint32_t k,
+                                            uint32_t ilo, uint32_t steps, uint32_t (&acc)[Q + 2]) {
+#pragma unroll
+    for (int q = 0; q < Q + 2; ++q) acc[q] = 0;
+    // x0 + Q = (k - i0) + Q: the offset-Q index of the upper B chunk of the block.
+    uint32_t xb = k - ilo + Q;
+    uint32_t bhi[Q], blo[Q], av[Q];
+    ld_words<Q>(Bs, xb, bhi);
+    for (uint32_t i0 = ilo; i0 < ilo + steps; i0 += Q, xb -= Q) {
+        ld_words<Q>(As, i0, av);
+        ld_words<Q>(Bs, xb - Q, blo);
+#pragma unroll
+        for (int s = 0; s < Q; ++s) {
+            uint32_t w[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int idx = Q - s + q;  // into (blo, bhi): B[k - i0 - s + q]
+                w[q] = idx < Q ? blo[idx] : bhi[idx - Q];
+            }
+            mac<Q>(acc, av[s], w);
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) bhi[q] = blo[q];
+    }
+}
+
+// Copies n words of a global row into shared memory at logical offset `off`
+// (layout phys), zero-filling logical [off + n, off + n_pad).
+__device__ __forceinline__ void stage_row(uint32_t *S, const uint32_t *row, uint32_t n,
+                                          uint32_t off, uint32_t n_pad, bool vec, bool live,
+                                          uint32_t t, uint32_t group) {
+    if (vec && live) {
+        for (uint32_t x = 4 * t; x < n; x += 4 * group) {
+            const uint4 v = ld_stream_v4(row + x);
+            *reinterpret_cast<uint4 *>(S + phys(off + x)) = v;
+        }
+        for (uint32_t x = n + t; x < n_pad; x += group) S[phys(off + x)] = 0;
+    } else {
+        for (uint32_t x = t; x < n_pad; x += group)
+            S[phys(off + x)] = (live && x < n) ? ld_stream(row + x) : 0u;
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kQuadMaxThreads) k_mul_quad(QuadArgs p) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    const uint32_t slot = threadIdx.x / p.group, t = threadIdx.x - slot * p.group;
+    const uint64_t inst = (uint64_t)blockIdx.x * p.ipb + slot;
+    const bool live = inst < p.batch;
+    uint32_t *As = smem + slot * p.inst_words;
+    uint32_t *Bs = As + p.ab_words;
+    uint32_t *Ls = As;                  // L reuses the operand region after the products
+    uint32_t *Hc = As + p.hc_offset;
+    uint32_t *flags = smem + p.ipb * p.inst_words;
+
+    // q1: stage the operands, zero-padded (B also below 0: logical [-Q, nbp + Q)).
+    stage_row(As, p.a + inst * p.na, p.na, 0, p.nap, p.vec_a, live, t, p.group);
+    for (uint32_t x = t; x < Q; x += p.group) Bs[phys(x)] = 0;
+    stage_row(Bs, p.b + inst * p.nb, p.nb, Q, p.nbp + Q, p.vec_b, live, t, p.group);
+    __syncthreads();
+
+    // q2: the products of this thread's unit (one or two windows).
+    const uint32_t R = p.nbp / Q;               // windows in each sloped region
+    const uint32_t plateau = (p.nap - p.nbp) / Q;
+    uint32_t k0 = 0, k1 = 0, nwin = 0;
+    uint32_t acc0[Q + 2], acc1[Q + 2];
+    if (t < p.units) {
+        if (t < R / 2) {                        // rising pair
+            k0 = t * Q;
+            k1 = (R - 1 - t) * Q;
+            nwin = 2;
+            conv_window<Q>(As, Bs, k0, 0, k0 + Q, acc0);
+            conv_window<Q>(As, Bs, k1, 0, k1 + Q, acc1);
+        } else if (t < R / 2 + plateau) {       // plateau window
+            k0 = p.nbp + (t - R / 2) * Q;
+            nwin = 1;
+            conv_window<Q>(As, Bs, k0, k0 - p.nbp, p.nbp + Q, acc0);
+        } else {                                // falling pair
+            const uint32_t r = t - R / 2 - plateau;
+            k0 = p.nap + r * Q;
+            k1 = p.nap + (R - 1 - r) * Q;
+            nwin = 2;
+            conv_window<Q>(As, Bs, k0, k0 - p.nbp, p.nap - (k0 - p.nbp), acc0);
+            conv_window<Q>(As, Bs, k1, k1 - p.nbp, p.nap - (k1 - p.nbp), acc1);
+        }
+    }
+    __syncthreads();
+    // q3: publish low words to L and the two spill words to H (Fig. 5).
+    if (nwin >= 1) {
+        st_words<Q>(Ls, k0, acc0);
+        *reinterpret_cast<uint2 *>(Hc + 2 * (k0 / Q)) = make_uint2(acc0[Q], acc0[Q + 1]);
+    }
+    if (nwin == 2) {
+        st_words<Q>(Ls, k1, acc1);
+        *reinterpret_cast<uint2 *>(Hc + 2 * (k1 / Q)) = make_uint2(acc1[Q], acc1[Q + 1]);
+    }
+    __syncthreads();
+
+    // q4: c = L + H in memory order, 2Q words (windows 2t, 2t+1) per thread.
+    constexpr int W2 = 2 * Q;
+    const uint32_t nw = p.nap + p.nbp;
+    const uint32_t base = 2 * Q * t;
+    const bool owns = base < nw;
+    uint32_t s[W2];
+    uint32_t g = 0, pr = 0;
+    if (owns) {
+        ld_words<W2>(Ls, base, s);
+        uint32_t h[W2];
+#pragma unroll
+        for (int q = 0; q < W2; ++q) h[q] = 0;
+        if (t > 0) {
+            const uint2 sp = *reinterpret_cast<const uint2 *>(Hc + 2 * (2 * t - 1));
+            h[0] = sp.x; h[1] = sp.y;
+        }
+        const uint2 sp = *reinterpret_cast<const uint2 *>(Hc + 2 * (2 * t));
+        h[Q] = sp.x; h[Q + 1] = sp.y;
+        uint32_t carry = 0, all = 0xffffffffu;
+#pragma unroll
+        for (int q = 0; q < W2; ++q) {
+            const uint64_t v = (uint64_t)s[q] + h[q] + carry;
+            s[q] = (uint32_t)v;
+            carry = (uint32_t)(v >> 32);
+            all &= s[q];
+        }
+        g = carry;
+        pr = all == 0xffffffffu;
+    }
+    const uint32_t cin = group_carry_in(g, pr, p.group, flags);
+    if (owns) {
+        uint32_t carry = cin;
+#pragma unroll
+        for (int q = 0; q < W2; ++q) {
+            const uint64_t v = (uint64_t)s[q] + carry;
+            s[q] = (uint32_t)v;
+            carry = (uint32_t)(v >> 32);
+        }
+        st_words<W2>(Ls, base, s);
+    }
+    __syncthreads();
+    if (!live) return;
+    uint32_t *crow = p.c + inst * p.nout;
+    if (p.vec_c) {
+        for (uint32_t x = 4 * t; x < p.nout; x += 4 * p.group)
+            st_stream_v4(crow + x, *reinterpret_cast<const uint4 *>(Ls + phys(x)));
+    } else {
+        for (uint32_t x = t; x < p.nout; x += p.group) st_stream(crow + x, Ls[phys(x)]);
+    }
+}
+
+uint32_t roundup(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
+
+struct Geometry {
+    uint32_t nap, nbp, units, group, ipb, inst_words, ab_words, hc_offset, block, smem;
+};
+
+Geometry geometry(uint32_t na, uint32_t nb, uint32_t Q, uint32_t cta_target) {
+    Geometry g{};
+    g.nbp = roundup(nb, 2 * Q);
+    g.nap = roundup(na, Q);
+    if (g.nap < g.nbp) g.nap = g.nbp;
+    g.units = g.nap / Q;
+    if (g.units <= 32) {
+        g.group = 1;
+        while (g.group < g.units) g.group <<= 1;
+    } else {
+        g.group = roundup(g.units, 32);
+    }
+    g.ipb = g.group < cta_target ? cta_target / g.group : 1;
+    // A at [0, phys_size(nap)), B (logical -Q .. nbp+Q) after it; L reuses
+    // both; H spill words follow.
+    const uint32_t a_words = roundup(phys_size(g.nap), 4);
+    const uint32_t b_words = roundup(phys_size(g.nbp + 2 * Q), 4);
+    const uint32_t l_words = roundup(phys_size(g.nap + g.nbp), 4);
+    g.ab_words = a_words;
+    const uint32_t region = a_words + b_words > l_words ? a_words + b_words : l_words;
+    g.hc_offset = region;
+    const uint32_t windows = (g.nap + g.nbp) / Q;
+    g.inst_words = roundup(region + 2 * windows, 4);
+    g.block = g.group * g.ipb;
+    g.smem = 4 * (g.inst_words * g.ipb + 32);
+    return g;
+}
+
+uint32_t default_q(uint32_t na, uint32_t nb) {
+    (void)nb;
+    return na <= 64 ? 4 : 8;
+}
+
+}  // namespace
+
+bn_status quad_configure(QuadConfig &cfg, uint32_t na, uint32_t nb, const bn_tuning *t) {
+    if (na == 0 || nb == 0) return BN_EINVAL;
+    if (na > BN_MUL_MAX_LIMBS || nb > BN_MUL_MAX_LIMBS) return BN_EUNSUPPORTED;
+    cfg = QuadConfig{};
+    cfg.na = na;
+    cfg.nb = nb;
+    cfg.nout = na + nb;
+    const uint32_t hi = na > nb ? na : nb, lo = na > nb ? nb : na;
+    cfg.q = default_q(hi, lo);
+    if (t) {
+        if (t->reserved[0] || t->reserved[1]) return BN_EINVAL;
+        if (t->limbs_per_thread) {
+            if (t->limbs_per_thread != 4 && t->limbs_per_thread != 8) return BN_EINVAL;
+            cfg.q = t->limbs_per_thread;
+        }
+        if (t->cta_threads && (t->cta_threads % 32 || t->cta_threads > 1024)) return BN_EINVAL;
+        cfg.cta_threads = t->cta_threads;
+    }
+    const Geometry g = geometry(hi, lo, cfg.q, cfg.cta_threads ? cfg.cta_threads : 256);
+    if (g.group > kQuadMaxThreads) return BN_EUNSUPPORTED;  // needs a larger window
+    if (g.smem > 227u * 1024u) return BN_EUNSUPPORTED;
+    cfg.threads = g.group;
+    return BN_OK;
+}
+
+cudaError_t quad_launch(const QuadConfig &cfg, const uint32_t *a, const uint32_t *b, uint32_t *c,
+                        uint64_t batch, cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    uint32_t na = cfg.na, nb = cfg.nb;
+    if (na < nb) {  // the product is symmetric; make a the longer operand
+        const uint32_t *tp = a; a = b; b = tp;
+        const uint32_t tn = na; na = nb; nb = tn;
+    }
+    const Geometry g = geometry(na, nb, cfg.q, cfg.cta_threads ? cfg.cta_threads : 256);
+    QuadArgs args{};
+    args.a = a; args.b = b; args.c = c;
+    args.na = na; args.nb = nb; args.nap = g.nap; args.nbp = g.nbp;
+    args.nout = na + nb;
+    args.units = g.units;
+    args.group = g.group;
+    args.ipb = g.ipb;
+    args.inst_words = g.inst_words;
+    args.ab_words = g.ab_words;
+    args.hc_offset = g.hc_offset;
+    args.vec_a = (na % 4 == 0) && ((uintptr_t)a % 16 == 0);
+    args.vec_b = (nb % 4 == 0) && ((uintptr_t)b % 16 == 0);
+    args.vec_c = (args.nout % 4 == 0) && ((uintptr_t)c % 16 == 0);
+    args.batch = batch;
+    const uint64_t grid = (batch + g.ipb - 1) / g.ipb;
+    if (grid > 0x7fffffffull) return cudaErrorInvalidConfiguration;
+    cudaError_t e;
+    if (cfg.q == 4) {
+        e = cudaFuncSetAttribute(k_mul_quad<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
+        if (e != cudaSuccess) return e;
+        k_mul_quad<4><<<(unsigned)grid, g.block, g.smem, st>>>(args);
+    } else {
+        e = cudaFuncSetAttribute(k_mul_quad<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
+        if (e != cudaSuccess) return e;
+        k_mul_quad<8><<<(unsigned)grid, g.block, g.smem, st>>>(args);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace bn
