@@ -1,0 +1,528 @@
+#!/usr/bin/env python3
+"""Benchmark of batched midsize integer addition and multiplication on GB300.
+
+One step = one pass of the whole hot path over the size-sweep workload:
+  * addition and schoolbook multiplication of 1K .. 256K-bit integers
+    (u32 limbs), each size a batch holding 64 MiB of operand limbs per side;
+  * transform multiplication (one 64-bit prime with 16-bit digits, and two
+    primes with 32-bit digits and CRT) at 16K .. 256K bits, same batches.
+Each operation is one kernel launch through the library's C ABI (plans).
+
+Printed: one JSON line (rank 0).  `value` is multiplications completed per
+second over the step (inputs resident in HBM); the addition throughput, the
+per-operation breakdown, the roofline of the dominant kernel, the clocks seen
+during the timed region, an end-to-end figure through the host-buffer entry
+point, and the CPU oracle timed on a bounded sample are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs the same per-rank workload (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+from dataclasses import dataclass, field
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+from paper_2405_14642_gb300 import workloads  # noqa: E402
+
+METRIC = "integer mults/s and add GB/s, 1K–256K bits; mixed-size batched vs plain"
+UNIT = "mults/s"
+NUM_SMS_NOMINAL = 152
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+@dataclass
+class Op:
+    name: str          # add | quad | ntt64 | crt
+    bits: int
+    na: int
+    nb: int
+    batch: int
+    seed: int
+    mults: int = 0     # multiplications per launch
+    bytes: int = 0     # algorithmic HBM bytes per launch
+    imad: int = 0      # algorithmic 32-bit multiply-adds per launch
+    times_ms: list = field(default_factory=list)
+
+    @property
+    def nout(self):
+        return self.na + 1 if self.name == "add" else self.na + self.nb
+
+    @property
+    def label(self):
+        return f"{self.name}@{self.bits // 1024}K"
+
+
+def ntt_lengths(n: int):
+    """Transform lengths and 64-bit modular products per pair (per prime)."""
+    n64 = 1 << math.ceil(math.log2(4 * n))      # 16-bit digits, 2n + 2n digits
+    ncrt = 1 << math.ceil(math.log2(2 * n))     # 32-bit digits, n + n digits
+    def modmuls(N):                              # 3 transforms + pointwise + scale
+        return 3 * (N // 2) * int(math.log2(N)) + 2 * N
+    return n64, ncrt, modmuls(n64), 2 * modmuls(ncrt)
+
+
+def build_ops(quick: bool = False):
+    pts = workloads.sweep_points()
+    if quick:
+        pts = [p for p in pts if p.bits in (1024, 32768, 262144)]
+    ops = []
+    for p in pts:
+        n = p.limbs
+        ops.append(Op("add", p.bits, n, n, p.batch, p.seed, mults=0,
+                      bytes=4 * (3 * n + 1) * p.batch))
+        ops.append(Op("quad", p.bits, n, n, p.batch, p.seed, mults=p.batch,
+                      bytes=4 * 4 * n * p.batch, imad=2 * n * n * p.batch))
+    for p in pts:
+        if p.bits not in workloads.NTT_BITS:
+            continue
+        n = p.limbs
+        _, _, mm64, mmcrt = ntt_lengths(n)
+        # A 64x64-bit modular product needs at least the 4 word products of
+        # its 128-bit product, 2 multiply-adds (lo, hi) each.
+        ops.append(Op("ntt64", p.bits, n, n, p.batch, p.seed, mults=p.batch,
+                      bytes=16 * n * p.batch, imad=8 * mm64 * p.batch))
+        ops.append(Op("crt", p.bits, n, n, p.batch, p.seed, mults=p.batch,
+                      bytes=16 * n * p.batch, imad=8 * mmcrt * p.batch))
+    return ops
+
+
+def workload_config(ops, world: int):
+    bits = sorted({o.bits for o in ops})
+    return {
+        "workload": "size sweep 1K-256K bits: add + schoolbook mul at 9 sizes, NTT mul "
+                    "(1x64-bit prime/16-bit digits and 2-prime CRT/32-bit digits) at 16K-256K; "
+                    "64 MiB of u32 operand limbs per side per size",
+        "sizes_bits": bits,
+        "batch_per_size": {str(b): next(o.batch for o in ops if o.bits == b) for b in bits},
+        "ops_per_step": [o.label for o in ops],
+        "cache": "inputs larger than L2 (>= 128 MiB of operands per launch)",
+        "per_rank": "each rank runs the full workload (weak scaling)",
+        "ranks": world,
+    }
+
+
+# ---- clocks ---------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in Path(self.path).read_text().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        power = [num(r[3]) for r in rows if num(r[3])]
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(num(r[2]) or 0 for r in rows),
+                "sm_mhz_min": min(sm) if sm else None,
+                "power_w_max": max(power) if power else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- GPU arm ---------------------------------------------------------------
+
+def imad_peak(torch, bn, dev):
+    """Time the register-only multiply-add probe; derive the per-clock rate."""
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    out = torch.zeros(sms * 8, dtype=torch.int32, device=dev)
+    res = {}
+    for name, kind in (("mad_lo", 0), ("mad_hi", 1), ("mad_wide", 2), ("mac_chain", 3)):
+        iters = 2048
+        bn.bn_probe_int_throughput(kind, sms * 8, 256, 64, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(dev.index or 0)
+        sampler.start()
+        best = None
+        for _ in range(3):
+            e0.record()
+            ops = bn.bn_probe_int_throughput(kind, sms * 8, 256, iters, out)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        clk = sampler.stop()
+        total = ops * sms * 8 * 256
+        rate = total / (best * 1e-3)
+        mhz = clk.get("sm_mhz") or SM_MAX_MHZ_NOMINAL
+        res[name] = {"ops_per_s": rate, "per_clk_per_sm": rate / (sms * mhz * 1e6), "sm_mhz": mhz}
+    # Unit count: the mad.lo rate per clock, snapped to the nearest power of two.
+    per_clk = res["mad_lo"]["per_clk_per_sm"]
+    units = 2 ** round(math.log2(per_clk)) if per_clk > 0 else 64
+    peak = units * sms * SM_MAX_MHZ_NOMINAL * 1e6
+    return {"units_per_clk_per_sm": units, "sms": sms, "peak_ops_per_s": peak, "probe": res}
+
+
+def read_measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        try:
+            d = json.loads(p.read_text())
+            return float(d["hbm_gbs"]), "measured"
+        except (ValueError, KeyError):
+            pass
+    return 6800.0, "fallback"
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import paper_2405_14642_gb300 as bn
+
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    bn.load()
+    ops = build_ops(args.quick)
+    if args.only:
+        keep = set(args.only.split(","))
+        ops = [o for o in ops if o.name in keep or o.label in keep]
+    stream = torch.cuda.current_stream(dev)
+
+    # Inputs: one seeded pair per size, shared by the ops at that size.
+    inputs, hosts = {}, {}
+    for o in ops:
+        if o.bits in inputs:
+            continue
+        a, b = workloads.pair_batch(o.batch, o.na, o.nb, seed=o.seed + 7919 * rank, edges=False)
+        ta = torch.from_numpy(a.view(np.int32)).to(dev)
+        tb = torch.from_numpy(b.view(np.int32)).to(dev)
+        inputs[o.bits] = (ta, tb)
+        hosts[o.bits] = (a, b)
+    outs = {}
+    plans = {}
+    skipped = []
+    for o in list(ops):
+        opcode = {"add": bn.BN_OP_ADD, "quad": bn.BN_OP_MUL_QUAD, "ntt64": bn.BN_OP_MUL_NTT64,
+                  "crt": bn.BN_OP_MUL_NTT_CRT}[o.name]
+        try:
+            plans[o.label] = bn.Plan(opcode, o.na, o.nb, o.batch)
+        except bn.BnError as e:
+            if e.status != 4:       # only "unsupported size" may be skipped, and is reported
+                raise
+            skipped.append(o.label)
+            ops.remove(o)
+            continue
+        key = (o.bits, o.nout)
+        if key not in outs:
+            outs[key] = torch.empty((o.batch, o.nout), dtype=torch.int32, device=dev)
+
+    def step(record=None):
+        for i, o in enumerate(ops):
+            ta, tb = inputs[o.bits]
+            if record is not None:
+                record[i][0].record(stream)
+            plans[o.label].execute(ta, tb, out=outs[(o.bits, o.nout)], stream=stream)
+            if record is not None:
+                record[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    peak_info = imad_peak(torch, bn, dev) if rank == 0 else None
+
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+            for _ in ops] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    t0.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    for i, o in enumerate(ops):
+        o.times_ms = [evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(args.steps)]
+    max_ms = allreduce_max(elapsed_ms, world, dev)
+    mults_per_step = sum(o.mults for o in ops)
+    value = world * mults_per_step * args.steps / (max_ms * 1e-3)
+    ms_per_step = max_ms / args.steps
+    gpu_launches = args.steps * len(ops)
+
+    # End to end: host arrays in pinned memory through the host-buffer entry point.
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = run_e2e(args, torch, bn, ops, hosts, dev)
+
+    if rank != 0:
+        return None
+    hbm_peak, hbm_kind = read_measured_peaks()
+    rows, rooflines = [], []
+    for o in ops:
+        ms = float(np.mean(o.times_ms))
+        row = {"op": o.label, "ms": round(ms, 4), "batch": o.batch}
+        if o.name == "add":
+            gbs = o.bytes / (ms * 1e-3) / 1e9
+            row.update(gbs=round(gbs, 1), adds_per_s=o.batch / (ms * 1e-3))
+            rooflines.append({"op": o.label, "bound": "hbm", "achieved": round(gbs, 1),
+                              "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
+                              "peak_kind": hbm_kind, "traffic": None})
+        else:
+            tops = o.imad / (ms * 1e-3) / 1e12
+            peak_t = peak_info["peak_ops_per_s"] / 1e12
+            row.update(mults_per_s=o.batch / (ms * 1e-3), imad_tops=round(tops, 3))
+            rooflines.append({"op": o.label, "bound": "alu", "achieved": round(tops, 3),
+                              "peak": round(peak_t, 3), "unit": "T mul-add/s",
+                              "frac": round(tops / peak_t, 4),
+                              "peak_kind": "derived: %d mul-add/clk/SM (probe) x %d SMs x %.0f MHz"
+                                           % (peak_info["units_per_clk_per_sm"], peak_info["sms"],
+                                              SM_MAX_MHZ_NOMINAL),
+                              "traffic": None})
+        rows.append(row)
+    total_ms = [sum(o.times_ms[k] for o in ops) for k in range(args.steps)]
+    dom = max(range(len(ops)), key=lambda i: np.mean(ops[i].times_ms))
+    roof = dict(rooflines[dom])
+    roof["kernel_share_of_step"] = round(float(np.mean(ops[dom].times_ms)) / float(np.mean(total_ms)), 4)
+    add_ops = [o for o in ops if o.name == "add"]
+    add_gbs = (sum(o.bytes for o in add_ops) / (sum(np.mean(o.times_ms) for o in add_ops) * 1e-3) / 1e9
+               if add_ops else None)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(ops, budget_s=args.cpu_budget)
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": workload_config(ops, world),
+        "add_gbs": round(add_gbs, 1) if add_gbs else None,
+        "roofline": roof, "rooflines": rooflines, "breakdown": rows,
+        "imad_probe": peak_info, "clocks": clocks, "gpu_launches": gpu_launches,
+        "e2e": e2e, "cpu_baseline": cpu, "impl": "ours", "skipped_ops": skipped,
+    }
+
+
+def run_e2e(args, torch, bn, ops, hosts, dev):
+    """Same metric through bn_plan_execute_host with pinned host buffers."""
+    pinned_in, pinned_out, plans = {}, {}, {}
+    for o in ops:
+        if o.bits not in pinned_in:
+            a, b = hosts[o.bits]
+            pa = torch.from_numpy(a.view(np.int32)).pin_memory()
+            pb = torch.from_numpy(b.view(np.int32)).pin_memory()
+            pinned_in[o.bits] = (pa, pb)
+        key = (o.bits, o.nout)
+        if key not in pinned_out:
+            pinned_out[key] = torch.empty((o.batch, o.nout), dtype=torch.int32).pin_memory()
+        opcode = {"add": bn.BN_OP_ADD, "quad": bn.BN_OP_MUL_QUAD, "ntt64": bn.BN_OP_MUL_NTT64,
+                  "crt": bn.BN_OP_MUL_NTT_CRT}[o.name]
+        plans[o.label] = bn.Plan(opcode, o.na, o.nb, o.batch)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for o in ops:
+            pa, pb = pinned_in[o.bits]
+            plans[o.label].execute_host(pa, pb, pinned_out[(o.bits, o.nout)], stream=stream)
+
+    step()  # allocates staging buffers
+    steps = max(1, min(args.steps, args.e2e_steps))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        step()
+    el = time.perf_counter() - t
+    for p in plans.values():
+        p.close()
+    mults = sum(o.mults for o in ops)
+    h2d = sum(4 * (o.na + o.nb) * o.batch for o in ops)
+    d2h = sum(4 * o.nout * o.batch for o in ops)
+    return {"value": mults * steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps, "ms_per_step": round(el / steps * 1e3, 3),
+            "api": "bn_plan_execute_host (pinned host buffers, copies inside the timed region)"}
+
+
+# ---- CPU oracle ------------------------------------------------------------
+
+_SAMPLES = {}
+
+
+def _sample_inputs(o: Op, count: int):
+    key = (o.label, count)
+    if key not in _SAMPLES:
+        _SAMPLES[key] = workloads.pair_batch(count, o.na, o.nb, seed=o.seed, edges=False)
+    return _SAMPLES[key]
+
+
+def oracle_time_op(o: Op, count: int, threads: int):
+    """Seconds the oracle takes on `count` pairs of this op (inputs made beforehand)."""
+    import oracle
+    a, b = _sample_inputs(o, count)
+    t = time.perf_counter()
+    if o.name == "add":
+        oracle.add(a, b, threads=threads)
+    else:
+        oracle.mul(a, b, threads=threads)
+    return time.perf_counter() - t
+
+
+def sample_counts(ops, budget_s: float, threads: int):
+    """Pairs per op so the whole sample takes about budget_s on `threads` cores.
+    Each op's per-pair cost is calibrated on a small run of that op."""
+    per_pair = {}
+    for o in ops:
+        words = (o.na * o.nb / 4) if o.name != "add" else o.na
+        c0 = int(min(o.batch, max(threads, 2e6 / max(words, 1))))
+        per_pair[o.label] = oracle_time_op(o, c0, threads) / c0
+    full_s = sum(per_pair[o.label] * o.batch for o in ops)
+    frac = min(1.0, budget_s / full_s) if full_s > 0 else 1.0
+    return {o.label: int(min(o.batch, max(threads, round(o.batch * frac)))) for o in ops}, frac
+
+
+def cpu_baseline(ops, budget_s=15.0, counts=None):
+    import oracle
+    threads = oracle.default_threads()
+    if counts is None:
+        counts, _ = sample_counts(ops, budget_s, threads)
+    total_s = 0.0
+    for o in ops:
+        c = counts[o.label]
+        total_s += oracle_time_op(o, c, threads) * (o.batch / c)
+    mults = sum(o.mults for o in ops)
+    sample = ", ".join(f"{o.label}:{counts[o.label]}/{o.batch}" for o in ops)
+    return {"value": mults / total_s, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "pairs timed per op, each scaled to its full batch: " + sample,
+            "extrapolated_step_s": round(total_s, 3)}
+
+
+def run_reference(args, rank, world):
+    """The oracle, as it stands, on the host cores: each step a bounded sample."""
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    ops = build_ops(args.quick)
+    threads = oracle.default_threads()
+    counts, _ = sample_counts(ops, args.ref_step_budget, threads)
+    for _ in range(args.warmup):
+        cpu_baseline(ops, counts=counts)
+    vals, step_s = [], []
+    wall = time.perf_counter()
+    for _ in range(args.steps):
+        r = cpu_baseline(ops, counts=counts)
+        vals.append(r["value"])
+        step_s.append(r["extrapolated_step_s"])
+    wall = time.perf_counter() - wall
+    value = float(np.mean(vals))
+    sample = r["sample"]
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(float(np.mean(step_s)) * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": workload_config(ops, world), "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": threads,
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": round(wall, 2),
+    }
+
+
+# ---- distributed plumbing --------------------------------------------------
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x: float, world: int, dev):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--quick", action="store_true", help="3 sizes only (smoke runs)")
+    ap.add_argument("--only", default="", help="comma list of op names/labels to keep")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-step-budget", type=float, default=4.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        res = run_gpu(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -71,6 +71,8 @@ def load(build_if_missing: bool = False):
         "bn_status_str": ([ctypes.c_int], ctypes.c_char_p),
         "bn_last_error": ([], ctypes.c_char_p),
         "bn_version": ([], ctypes.c_int),
+        "bn_probe_int_throughput": ([ctypes.c_int, u32, u32, u32, u32p,
+                                     ctypes.POINTER(ctypes.c_uint64), vp], st),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -159,6 +161,19 @@ def bn_mul_ntt(a, b, crt: bool = False, out=None, stream=None):
     _check(lib.bn_mul_ntt(_ptr(a), _ptr(b), _ptr(out), na, nb, batch, int(bool(crt)),
                           _stream_handle(stream, a.device)), "bn_mul_ntt")
     return out
+
+
+PROBE_MAD_LO, PROBE_MAD_HI, PROBE_MAD_WIDE, PROBE_MAC_CHAIN = range(4)
+
+
+def bn_probe_int_throughput(kind: int, blocks: int, threads: int, iters: int, out, stream=None) -> int:
+    """Enqueue the integer multiply-add probe; returns multiply-adds per thread."""
+    lib = load()
+    out = _operand(out, "out") if out.dim() == 2 else out
+    ops = ctypes.c_uint64()
+    _check(lib.bn_probe_int_throughput(kind, blocks, threads, iters, _ptr(out), ctypes.byref(ops),
+                                       _stream_handle(stream, out.device)), "bn_probe_int_throughput")
+    return ops.value
 
 
 class Plan:

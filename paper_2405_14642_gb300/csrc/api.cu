@@ -8,6 +8,7 @@
 #include <mutex>
 #include <new>
 #include <tuple>
+#include <utility>
 
 #include "bn_internal.h"
 
@@ -147,6 +148,26 @@ bn_status one_shot(bn_op op, const uint32_t *a, const uint32_t *b, uint32_t *c, 
 }
 
 }  // namespace
+
+namespace bn {
+
+cudaError_t allow_max_smem(const void *kernel) {
+    static std::mutex m;
+    static std::map<std::pair<const void *, int>, bool> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(m);
+    auto key = std::make_pair(kernel, dev);
+    if (done.count(key)) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) done[key] = true;
+    return e;
+}
+
+}  // namespace bn
 
 extern "C" {
 

@@ -9,6 +9,11 @@
 
 namespace bn {
 
+// Raises a kernel's dynamic shared-memory cap to the device's opt-in maximum,
+// once per (kernel, device).  The cap is a property of the function, so
+// lowering it for one plan would break larger plans of the same kernel.
+cudaError_t allow_max_smem(const void *kernel);
+
 // ---- addition (Section 2) -------------------------------------------------
 struct AddConfig {
     uint32_t na = 0, nb = 0, n = 0, nout = 0;

@@ -1,17 +1,622 @@
-// Placeholder until the transform kernels land.
+// Batched multiplication through a number-theoretic transform (Section 4).
+//
+// Fields (Section 4.1, with the digit sizes read so that every convolution
+// coefficient stays below the modulus):
+//   * BN_OP_MUL_NTT64: PrimeField64, p1 = 29*2^57 + 1 with root g = 21 of
+//     order 2^57, 16-bit digits (coefficients < 2^46 at 256K bits);
+//   * BN_OP_MUL_NTT_CRT: 32-bit digits over p1 and p2 = 2^64 - 2^32 + 1 (root
+//     7^(2^32-1) of order 2^32), recombined by Garner's form of the CRT
+//     (coefficients < 2^77 < p1 p2).
+// Transform length N = next power of two >= digits(a) + digits(b), so the
+// cyclic convolution does not wrap (inputs are zero-padded).
+//
+// Arithmetic.  Section 4.1's field multiplies with a full-width modulo; here
+// p1 uses Montgomery multiplication (R = 2^64), whose reduction is cheap for
+// this prime: -p1^-1 mod 2^64 = 29*2^57 - 1, so the quotient digit m needs only
+// the low 7 bits of t*29.  p2 uses its direct reduction 2^64 = 2^32 - 1 (mod p2).
+// Twiddles are stored in each field's "twiddle form" (Montgomery form for p1,
+// plain for p2) so that mul(x, w) = x*w; the pointwise product and the final
+// 1/N scale absorb Montgomery's extra 1/R.
+//
+// Work mapping.  One CTA transforms one integer pair at a time in shared
+// memory (a persistent grid walks the batch).  Forward transforms are
+// decimation-in-frequency (natural order in, bit-reversed out), the inverse
+// is decimation-in-time (bit-reversed in, natural out), so no permutation
+// pass is needed (Section 4.2's fft reorders first).  Stages are grouped into
+// radix-8 passes: a thread loads 8 elements, runs 3 butterfly stages in
+// registers and stores them back, one barrier per pass instead of one per
+// stage.
+//
+// Sizes beyond shared memory.  Both spectra of a sub-transform of length L
+// must fit (L <= 8192 u64 each).  A longer transform, N = S*L with S in
+// {2, 4}, is split into S independent length-L problems: the first radix-S
+// decimation-in-frequency stage is folded into the digit load (sub-problem s
+// transforms y_s[j] = w_N^{js} sum_r x[j + rL] w_S^{rs}), each sub-problem is
+// multiplied pointwise and inverted on its own, and the last radix-S inverse
+// stage is folded into the final combine, reading the S partial results back
+// from a per-CTA scratch slot (L2-resident, since the grid is persistent).
+//
+// Normalisation (Section 4.2's splitFftReg/baddRegMul2Fft, here with whole
+// 16/32-bit digits).  Each thread folds the coefficients of its window of
+// limbs into limbs plus a carried spill, the spill is added into the next
+// window, and the remaining one-bit carries are resolved with the Section 2
+// carry scan across threads.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bn_device.cuh"
 #include "bn_internal.h"
 
 namespace bn {
-struct NttPlan {};
-bn_status ntt_create(NttPlan **out, bool, uint32_t, uint32_t, const bn_tuning *) {
+
+namespace {
+
+typedef unsigned __int128 u128;
+
+constexpr uint32_t kMaxSubLength = 8192;  // both spectra in shared memory
+constexpr int kRadixLog = 3;              // radix-8 passes
+
+// ---- device fields ---------------------------------------------------------
+
+struct FieldP1 {  // 29 * 2^57 + 1, Montgomery form with R = 2^64
+    static constexpr uint64_t P = 4179340454199820289ull;
+    __device__ static __forceinline__ uint64_t add(uint64_t a, uint64_t b) {
+        const uint64_t r = a + b;
+        return r >= P ? r - P : r;
+    }
+    __device__ static __forceinline__ uint64_t sub(uint64_t a, uint64_t b) {
+        return a >= b ? a - b : a - b + P;
+    }
+    // a * b / 2^64 mod P for a, b < P.
+    __device__ static __forceinline__ uint64_t mul(uint64_t a, uint64_t b) {
+        const uint64_t lo = a * b, hi = __umul64hi(a, b);
+        const uint64_t m = ((uint64_t)(((uint32_t)lo * 29u) & 127u) << 57) - lo;
+        const uint64_t r = hi + __umul64hi(m, P) + (lo != 0);
+        return r >= P ? r - P : r;
+    }
+};
+
+struct FieldP2 {  // 2^64 - 2^32 + 1, plain form
+    static constexpr uint64_t P = 0xFFFFFFFF00000001ull;
+    static constexpr uint64_t EPS = 0xFFFFFFFFull;  // 2^64 mod P
+    __device__ static __forceinline__ uint64_t add(uint64_t a, uint64_t b) {
+        uint64_t r = a + b;
+        if (r < a) r += EPS;
+        else if (r >= P) r -= P;
+        return r;
+    }
+    __device__ static __forceinline__ uint64_t sub(uint64_t a, uint64_t b) {
+        const uint64_t r = a - b;
+        return a < b ? r - EPS : r;
+    }
+    __device__ static __forceinline__ uint64_t reduce(uint64_t hi, uint64_t lo) {
+        const uint64_t hh = hi >> 32, hl = hi & EPS;
+        uint64_t t0 = lo - hh;
+        if (lo < hh) t0 -= EPS;
+        const uint64_t t1 = hl * EPS;
+        uint64_t r = t0 + t1;
+        if (r < t1) r += EPS;
+        return r >= P ? r - P : r;
+    }
+    __device__ static __forceinline__ uint64_t mul(uint64_t a, uint64_t b) {
+        return reduce(__umul64hi(a, b), a * b);
+    }
+};
+
+// Shared-memory index with one u64 of padding per 16 (bank spread).
+__device__ __forceinline__ uint32_t phys(uint32_t i) { return i + (i >> 4); }
+__host__ __device__ constexpr uint32_t phys_words(uint32_t n) { return n + (n >> 4) + 1; }
+
+struct PrimeTab {
+    const uint64_t *twf;    // [L]: twf[h + j] = w_{2h}^j (h = 1 .. L/2, j < h)
+    const uint64_t *twi;    // [L]: w_{2h}^-j
+    const uint64_t *ffold;  // [S*L]: w_N^{js}            (S > 1)
+    const uint64_t *ifold;  // [S*L]: scale * w_N^{-js}   (S > 1)
+    uint64_t ws[4], iws[4]; // w_S^k, w_S^-k
+    uint64_t scale;         // N^-1 (times R for p1), S == 1
+};
+
+struct NttArgs {
+    const uint32_t *a, *b;
+    uint32_t *c;
+    uint32_t na, nb, nout;
+    uint32_t N, L, logL, S, digit_bits;
+    uint32_t vec_c;
+    uint64_t batch;
+    uint64_t *scratch;
+    uint64_t scratch_stride;  // u64 words per CTA
+    uint64_t garner_inv;      // p1^-1 mod p2
+    PrimeTab t1, t2;
+};
+
+__device__ __forceinline__ uint64_t digit(const uint32_t *row, uint32_t ndig, uint32_t m,
+                                          uint32_t bits) {
+    if (m >= ndig) return 0;
+    return bits == 16 ? (row[m >> 1] >> ((m & 1u) << 4)) & 0xFFFFu : row[m];
+}
+
+// Sub-problem s of the forward transform: y_s[j] = w_N^{js} sum_r x[j + rL] w_S^{rs}.
+template <class F>
+__device__ void load_fold(const NttArgs &p, const PrimeTab &tb, const uint32_t *row, uint32_t n,
+                          uint32_t s, uint64_t *buf) {
+    const uint32_t ndig = p.digit_bits == 16 ? 2 * n : n;
+    for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) {
+        uint64_t acc = digit(row, ndig, j, p.digit_bits);
+        if (p.S > 1) {
+            for (uint32_t r = 1; r < p.S; ++r) {
+                const uint32_t m = j + r * p.L;
+                if (m >= ndig) break;
+                const uint64_t d = digit(row, ndig, m, p.digit_bits);
+                const uint32_t k = (r * s) & (p.S - 1);
+                acc = F::add(acc, k == 0 ? d : F::mul(d, tb.ws[k]));
+            }
+            acc = F::mul(acc, tb.ffold[s * p.L + j]);
+        }
+        buf[phys(j)] = acc;
+    }
+}
+
+// KK decimation-in-frequency stages with half-sizes H, H/2, ..., H >> (KK-1).
+template <class F, int KK>
+__device__ __forceinline__ void dif_pass(uint64_t *buf, uint32_t L, uint32_t H, const uint64_t *tw) {
+    constexpr int E = 1 << KK;
+    const uint32_t step = H >> (KK - 1);
+    const uint32_t lstep = __ffs(step) - 1;
+    for (uint32_t g = threadIdx.x; g < (L >> KK); g += blockDim.x) {
+        const uint32_t base = ((g >> lstep) << (lstep + KK)) | (g & (step - 1));
+        uint64_t x[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) x[m] = buf[phys(base + m * step)];
+#pragma unroll
+        for (int st = 0; st < KK; ++st) {
+            const uint32_t hm = 1u << (KK - 1 - st), h = hm * step;
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                if (m & hm) continue;
+                const uint64_t u = x[m], v = x[m + hm];
+                x[m] = F::add(u, v);
+                const uint64_t d = F::sub(u, v);
+                x[m + hm] = h == 1 ? d : F::mul(d, __ldg(tw + h + ((base + m * step) & (h - 1))));
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < E; ++m) buf[phys(base + m * step)] = x[m];
+    }
+}
+
+// KK decimation-in-time stages with half-sizes h0, 2 h0, ..., h0 << (KK-1).
+template <class F, int KK>
+__device__ __forceinline__ void dit_pass(uint64_t *buf, uint32_t L, uint32_t h0, const uint64_t *tw) {
+    constexpr int E = 1 << KK;
+    const uint32_t step = h0;
+    const uint32_t lstep = __ffs(step) - 1;
+    for (uint32_t g = threadIdx.x; g < (L >> KK); g += blockDim.x) {
+        const uint32_t base = ((g >> lstep) << (lstep + KK)) | (g & (step - 1));
+        uint64_t x[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) x[m] = buf[phys(base + m * step)];
+#pragma unroll
+        for (int st = 0; st < KK; ++st) {
+            const uint32_t hm = 1u << st, h = hm * step;
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                if (m & hm) continue;
+                const uint64_t u = x[m];
+                const uint64_t v = h == 1 ? x[m + hm]
+                                          : F::mul(x[m + hm], __ldg(tw + h + ((base + m * step) & (h - 1))));
+                x[m] = F::add(u, v);
+                x[m + hm] = F::sub(u, v);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < E; ++m) buf[phys(base + m * step)] = x[m];
+    }
+}
+
+template <class F>
+__device__ void forward2(const NttArgs &p, const uint64_t *tw, uint64_t *A, uint64_t *B) {
+    uint32_t H = p.L >> 1, left = p.logL;
+    while (left >= (uint32_t)kRadixLog) {
+        dif_pass<F, kRadixLog>(A, p.L, H, tw);
+        dif_pass<F, kRadixLog>(B, p.L, H, tw);
+        __syncthreads();
+        H >>= kRadixLog;
+        left -= kRadixLog;
+    }
+    if (left == 2) {
+        dif_pass<F, 2>(A, p.L, H, tw);
+        dif_pass<F, 2>(B, p.L, H, tw);
+        __syncthreads();
+    } else if (left == 1) {
+        dif_pass<F, 1>(A, p.L, H, tw);
+        dif_pass<F, 1>(B, p.L, H, tw);
+        __syncthreads();
+    }
+}
+
+template <class F>
+__device__ void inverse(const NttArgs &p, const uint64_t *tw, uint64_t *B) {
+    uint32_t h0 = 1, left = p.logL;
+    while (left >= (uint32_t)kRadixLog) {
+        dit_pass<F, kRadixLog>(B, p.L, h0, tw);
+        __syncthreads();
+        h0 <<= kRadixLog;
+        left -= kRadixLog;
+    }
+    if (left == 2) {
+        dit_pass<F, 2>(B, p.L, h0, tw);
+        __syncthreads();
+    } else if (left == 1) {
+        dit_pass<F, 1>(B, p.L, h0, tw);
+        __syncthreads();
+    }
+}
+
+// Coefficients of a*b mod the field's prime, scaled by 1/N.  With keep and
+// S == 1 they stay in B (padded layout); otherwise they go to dest[0 .. N).
+template <class F>
+__device__ void prime_product(const NttArgs &p, const PrimeTab &tb, const uint32_t *arow,
+                              const uint32_t *brow, uint64_t *A, uint64_t *B, uint64_t *Z,
+                              uint64_t *dest, bool keep) {
+    for (uint32_t s = 0; s < p.S; ++s) {
+        load_fold<F>(p, tb, arow, p.na, s, A);   // n1: digits (and the folded first stage)
+        load_fold<F>(p, tb, brow, p.nb, s, B);
+        __syncthreads();
+        forward2<F>(p, tb.twf, A, B);            // n2: forward transforms
+        for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x)   // n3: pointwise
+            B[phys(j)] = F::mul(A[phys(j)], B[phys(j)]);
+        __syncthreads();
+        inverse<F>(p, tb.twi, B);                // n4: inverse transform (unscaled)
+        if (p.S > 1) {
+            for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) Z[s * p.L + j] = B[phys(j)];
+            __syncthreads();
+        }
+    }
+    if (p.S == 1) {
+        for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) {
+            const uint64_t v = F::mul(B[phys(j)], tb.scale);
+            if (keep) B[phys(j)] = v;
+            else dest[j] = v;
+        }
+    } else {
+        // Last radix-S inverse stage: c[j + rL] = sum_s w_S^{-rs} (scale w_N^{-js} z_s[j]).
+        for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) {
+            uint64_t u[4];
+            for (uint32_t s = 0; s < p.S; ++s) u[s] = F::mul(Z[s * p.L + j], tb.ifold[s * p.L + j]);
+            for (uint32_t r = 0; r < p.S; ++r) {
+                uint64_t acc = u[0];
+                for (uint32_t s = 1; s < p.S; ++s) {
+                    const uint32_t k = (r * s) & (p.S - 1);
+                    acc = F::add(acc, k == 0 ? u[s] : F::mul(u[s], tb.iws[k]));
+                }
+                dest[j + r * p.L] = acc;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Limb k's share of the product: the digit coefficients that start in limb k.
+template <bool CRT>
+__device__ __forceinline__ u128 limb_value(const NttArgs &p, uint32_t k, const uint64_t *B,
+                                           bool in_smem, const uint64_t *C1, const uint64_t *Cs) {
+    if constexpr (!CRT) {
+        const uint64_t c0 = in_smem ? B[phys(2 * k)] : Cs[2 * k];
+        const uint64_t c1 = in_smem ? B[phys(2 * k + 1)] : Cs[2 * k + 1];
+        return (u128)(c0 + (c1 << 16));  // < 2^46 + 2^62
+    } else {
+        const uint64_t r1 = C1[k];
+        const uint64_t r2 = in_smem ? B[phys(k)] : Cs[k];
+        // Garner: c = r1 + p1 * ((r2 - r1) p1^-1 mod p2), exact since c < p1 p2.
+        const uint64_t v = FieldP2::mul(FieldP2::sub(r2, r1), p.garner_inv);
+        return (u128)r1 + (u128)v * FieldP1::P;
+    }
+}
+
+template <bool CRT>
+__device__ void normalize(const NttArgs &p, uint64_t inst, uint32_t *out_s, const uint64_t *B,
+                          bool in_smem, const uint64_t *C1, const uint64_t *Cs, uint64_t *spill,
+                          uint32_t *flags) {
+    const uint32_t T = blockDim.x, t = threadIdx.x;
+    uint32_t QN = (p.nout + T - 1) / T;
+    if (QN < 2) QN = 2;  // a window must absorb a two-word spill
+    const uint32_t k0 = t * QN;
+    const uint32_t k1 = k0 + QN < p.nout ? k0 + QN : p.nout;
+    // (a) this window's limbs, carrying within the window
+    u128 carry = 0;
+    for (uint32_t k = k0; k < k1; ++k) {
+        const u128 v = limb_value<CRT>(p, k, B, in_smem, C1, Cs) + carry;
+        out_s[k] = (uint32_t)v;
+        carry = v >> 32;
+    }
+    spill[t] = (uint64_t)carry;  // < 2^46
+    __syncthreads();
+    // (b) add the previous window's spill; one carry bit may leave the window
+    uint64_t c = t > 0 ? spill[t - 1] : 0;
+    uint32_t all = 0xffffffffu;
+    for (uint32_t k = k0; k < k1; ++k) {
+        const uint64_t v = (uint64_t)out_s[k] + (c & 0xffffffffu);
+        out_s[k] = (uint32_t)v;
+        c = (c >> 32) + (v >> 32);
+        all &= out_s[k];
+    }
+    const bool owns = k0 < k1;
+    // (c) resolve the carries across windows (Section 2 carry scan)
+    const uint32_t cin = group_carry_in(owns && c != 0, owns && all == 0xffffffffu, T, flags);
+    if (cin)
+        for (uint32_t k = k0; k < k1; ++k)
+            if (++out_s[k] != 0) break;
+    __syncthreads();
+    // (d) coalesced copy-out
+    uint32_t *crow = p.c + inst * p.nout;
+    if (p.vec_c) {
+        for (uint32_t x = 4 * t; x < p.nout; x += 4 * T)
+            st_stream_v4(crow + x, *reinterpret_cast<const uint4 *>(out_s + x));
+    } else {
+        for (uint32_t x = t; x < p.nout; x += T) st_stream(crow + x, out_s[x]);
+    }
+    __syncthreads();
+}
+
+template <bool CRT>
+__global__ void __launch_bounds__(1024) k_mul_ntt(NttArgs p) {
+    extern __shared__ __align__(16) uint64_t sm64[];
+    const uint32_t Lp = phys_words(p.L);
+    uint64_t *A = sm64;
+    uint64_t *B = sm64 + ((Lp + 1) & ~1u);
+    uint64_t *spill = B + ((Lp + 1) & ~1u);
+    uint32_t *flags = reinterpret_cast<uint32_t *>(spill + blockDim.x);
+    uint64_t *scr = p.scratch + blockIdx.x * p.scratch_stride;
+    uint64_t *Z = scr;                                  // [N] partial results (S > 1)
+    uint64_t *C1 = scr + (p.S > 1 ? p.N : 0);           // [N] p1 coefficients (CRT)
+    uint64_t *Cs = C1 + (CRT ? p.N : 0);                // [N] final-prime coefficients (S > 1)
+    for (uint64_t inst = blockIdx.x; inst < p.batch; inst += gridDim.x) {
+        const uint32_t *arow = p.a + inst * p.na, *brow = p.b + inst * p.nb;
+        const bool keep = p.S == 1;
+        if constexpr (CRT) {
+            prime_product<FieldP1>(p, p.t1, arow, brow, A, B, Z, C1, false);
+            prime_product<FieldP2>(p, p.t2, arow, brow, A, B, Z, Cs, keep);
+        } else {
+            prime_product<FieldP1>(p, p.t1, arow, brow, A, B, Z, Cs, keep);
+        }
+        normalize<CRT>(p, inst, reinterpret_cast<uint32_t *>(A), B, keep, C1, Cs, spill, flags);
+    }
+}
+
+// ---- host side: fields, tables, plan ----------------------------------------
+
+struct HostField {
+    uint64_t p, g;  // g has order exactly 2^n
+    uint32_t n;
+    bool montgomery;
+};
+
+uint64_t hmul(uint64_t a, uint64_t b, uint64_t p) { return (uint64_t)((u128)a * b % p); }
+
+uint64_t hpow(uint64_t a, uint64_t e, uint64_t p) {
+    uint64_t r = 1 % p;
+    a %= p;
+    while (e) {
+        if (e & 1) r = hmul(r, a, p);
+        a = hmul(a, a, p);
+        e >>= 1;
+    }
+    return r;
+}
+
+uint64_t hinv(uint64_t a, uint64_t p) { return hpow(a, p - 2, p); }
+
+HostField field_p1() { return {4179340454199820289ull, 21, 57, true}; }
+
+HostField field_p2() {
+    const uint64_t p = 0xFFFFFFFF00000001ull;
+    return {p, hpow(7, (p - 1) >> 32, p), 32, false};
+}
+
+// The form in which the device keeps constants: mul(x, form(w)) = x*w.
+uint64_t to_form(const HostField &f, uint64_t x) {
+    return f.montgomery ? (uint64_t)((((u128)x) << 64) % f.p) : x;
+}
+
+uint64_t root_of_unity(const HostField &f, uint64_t m) { return hpow(f.g, (1ull << f.n) / m, f.p); }
+
+// Host copy of one prime's tables; offsets are in u64 words.
+struct HostTables {
+    std::vector<uint64_t> twf, twi, ffold, ifold;
+    uint64_t ws[4] = {0, 0, 0, 0}, iws[4] = {0, 0, 0, 0}, scale = 0;
+};
+
+HostTables make_tables(const HostField &f, uint32_t N, uint32_t S) {
+    const uint32_t L = N / S;
+    HostTables t;
+    const uint64_t wN = root_of_unity(f, N), wL = hpow(wN, S, f.p);
+    const uint64_t wLi = hinv(wL, f.p), wNi = hinv(wN, f.p);
+    t.twf.assign(L, 0);
+    t.twi.assign(L, 0);
+    for (uint32_t h = 1; h < L; h <<= 1) {
+        const uint64_t w = hpow(wL, L / (2 * h), f.p), wi = hpow(wLi, L / (2 * h), f.p);
+        uint64_t x = 1, xi = 1;
+        for (uint32_t j = 0; j < h; ++j) {
+            t.twf[h + j] = to_form(f, x);
+            t.twi[h + j] = to_form(f, xi);
+            x = hmul(x, w, f.p);
+            xi = hmul(xi, wi, f.p);
+        }
+    }
+    // 1/N, times R for Montgomery fields (the pointwise product divided by R).
+    const uint64_t R = f.montgomery ? (uint64_t)(((u128)1 << 64) % f.p) : 1;
+    const uint64_t scale = hmul(hinv(N % f.p, f.p), R, f.p);
+    t.scale = to_form(f, scale);
+    if (S > 1) {
+        t.ffold.assign((size_t)S * L, 0);
+        t.ifold.assign((size_t)S * L, 0);
+        for (uint32_t s = 0; s < S; ++s) {
+            const uint64_t ws = hpow(wN, s, f.p), wsi = hpow(wNi, s, f.p);
+            uint64_t x = 1, xi = scale;
+            for (uint32_t j = 0; j < L; ++j) {
+                t.ffold[(size_t)s * L + j] = to_form(f, x);
+                t.ifold[(size_t)s * L + j] = to_form(f, xi);
+                x = hmul(x, ws, f.p);
+                xi = hmul(xi, wsi, f.p);
+            }
+        }
+        const uint64_t wS = hpow(wN, N / S, f.p), wSi = hinv(wS, f.p);
+        for (uint32_t k = 0; k < S; ++k) {
+            t.ws[k] = to_form(f, hpow(wS, k, f.p));
+            t.iws[k] = to_form(f, hpow(wSi, k, f.p));
+        }
+    }
+    return t;
+}
+
+uint32_t next_pow2(uint32_t x) {
+    uint32_t t = 1;
+    while (t < x) t <<= 1;
+    return t;
+}
+
+}  // namespace
+
+struct NttPlan {
+    bool crt = false;
+    uint32_t na = 0, nb = 0, nout = 0, N = 0, L = 0, logL = 0, S = 1, threads = 0;
+    uint32_t smem = 0, max_grid = 0;
+    uint64_t scratch_stride = 0;
+    size_t scratch_bytes = 0;
+    uint64_t *dev = nullptr;      // tables followed by scratch
+    uint64_t *scratch = nullptr;  // max_grid slots of scratch_stride words
+    PrimeTab t1{}, t2{};
+    uint64_t garner_inv = 0;
+};
+
+bn_status ntt_create(NttPlan **out, bool crt, uint32_t na, uint32_t nb, const bn_tuning *tun) {
     *out = nullptr;
-    return BN_EUNSUPPORTED;
+    if (na == 0 || nb == 0) return BN_EINVAL;
+    if (na > BN_MUL_MAX_LIMBS || nb > BN_MUL_MAX_LIMBS) return BN_EUNSUPPORTED;
+    uint32_t cta = 0;
+    if (tun) {
+        if (tun->reserved[0] || tun->reserved[1] || tun->limbs_per_thread) return BN_EINVAL;
+        if (tun->cta_threads && (tun->cta_threads % 32 || tun->cta_threads > 1024)) return BN_EINVAL;
+        cta = tun->cta_threads;
+    }
+    NttPlan *p = new (std::nothrow) NttPlan();
+    if (!p) return BN_ENOMEM;
+    p->crt = crt;
+    p->na = na;
+    p->nb = nb;
+    p->nout = na + nb;
+    const uint32_t digits = crt ? na + nb : 2 * (na + nb);
+    p->N = next_pow2(digits < 2 ? 2 : digits);
+    p->S = p->N > kMaxSubLength ? p->N / kMaxSubLength : 1;
+    p->L = p->N / p->S;
+    while ((1u << p->logL) < p->L) ++p->logL;
+    uint32_t T = p->L / 8;
+    if (T < 32) T = 32;
+    if (T > 1024) T = 1024;
+    if (cta) T = cta;
+    p->threads = T;
+    const uint32_t Lp2 = (phys_words(p->L) + 1) & ~1u;
+    p->smem = 8u * (2u * Lp2 + T) + 4u * 32u;
+
+    cudaError_t e;
+    auto *kern = crt ? k_mul_ntt<true> : k_mul_ntt<false>;
+    e = allow_max_smem((const void *)kern);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)T, p->smem);
+    if (e != cudaSuccess || per_sm == 0) {
+        delete p;
+        return e == cudaSuccess ? BN_EUNSUPPORTED : BN_ECUDA;
+    }
+    p->max_grid = (uint32_t)(sms * per_sm);
+    p->scratch_stride = (p->S > 1 ? 2ull * p->N : 0ull) + (crt ? (uint64_t)p->N : 0ull);
+
+    // Tables for each prime, then scratch, in one allocation.
+    std::vector<HostTables> tabs;
+    tabs.push_back(make_tables(field_p1(), p->N, p->S));
+    if (crt) tabs.push_back(make_tables(field_p2(), p->N, p->S));
+    size_t words = 0;
+    for (auto &t : tabs) words += t.twf.size() + t.twi.size() + t.ffold.size() + t.ifold.size();
+    const size_t table_words = (words + 31) & ~size_t(31);
+    p->scratch_bytes = (size_t)p->max_grid * p->scratch_stride * 8u;
+    e = cudaMalloc(&p->dev, table_words * 8u + p->scratch_bytes);
+    if (e != cudaSuccess) {
+        delete p;
+        return e == cudaErrorMemoryAllocation ? BN_ENOMEM : BN_ECUDA;
+    }
+    std::vector<uint64_t> host(table_words, 0);
+    size_t off = 0;
+    for (size_t i = 0; i < tabs.size(); ++i) {
+        HostTables &t = tabs[i];
+        PrimeTab &pt = i == 0 ? p->t1 : p->t2;
+        auto put = [&](const std::vector<uint64_t> &v) -> const uint64_t * {
+            if (v.empty()) return nullptr;
+            std::memcpy(host.data() + off, v.data(), v.size() * 8u);
+            const uint64_t *d = p->dev + off;
+            off += v.size();
+            return d;
+        };
+        pt.twf = put(t.twf);
+        pt.twi = put(t.twi);
+        pt.ffold = put(t.ffold);
+        pt.ifold = put(t.ifold);
+        std::memcpy(pt.ws, t.ws, sizeof pt.ws);
+        std::memcpy(pt.iws, t.iws, sizeof pt.iws);
+        pt.scale = t.scale;
+    }
+    e = cudaMemcpy(p->dev, host.data(), table_words * 8u, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p->dev);
+        delete p;
+        return BN_ECUDA;
+    }
+    p->scratch = p->dev + table_words;
+    const HostField f1 = field_p1(), f2 = field_p2();
+    p->garner_inv = hinv(f1.p % f2.p, f2.p);
+    *out = p;
+    return BN_OK;
 }
-void ntt_destroy(NttPlan *) {}
-cudaError_t ntt_launch(NttPlan *, const uint32_t *, const uint32_t *, uint32_t *, uint64_t,
-                       cudaStream_t) {
-    return cudaErrorNotSupported;
+
+void ntt_destroy(NttPlan *p) {
+    if (!p) return;
+    cudaFree(p->dev);
+    delete p;
 }
-size_t ntt_scratch_bytes(const NttPlan *) { return 0; }
-uint32_t ntt_length(const NttPlan *) { return 0; }
+
+size_t ntt_scratch_bytes(const NttPlan *p) { return p ? p->scratch_bytes : 0; }
+
+uint32_t ntt_length(const NttPlan *p) { return p ? p->N : 0; }
+
+cudaError_t ntt_launch(NttPlan *p, const uint32_t *a, const uint32_t *b, uint32_t *c,
+                       uint64_t batch, cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    NttArgs args{};
+    args.a = a;
+    args.b = b;
+    args.c = c;
+    args.na = p->na;
+    args.nb = p->nb;
+    args.nout = p->nout;
+    args.N = p->N;
+    args.L = p->L;
+    args.logL = p->logL;
+    args.S = p->S;
+    args.digit_bits = p->crt ? 32 : 16;
+    args.vec_c = (p->nout % 4 == 0) && ((uintptr_t)c % 16 == 0);
+    args.batch = batch;
+    args.scratch = p->scratch;
+    args.scratch_stride = p->scratch_stride;
+    args.garner_inv = p->garner_inv;
+    args.t1 = p->t1;
+    args.t2 = p->t2;
+    const uint64_t grid = batch < p->max_grid ? batch : p->max_grid;
+    if (p->crt) k_mul_ntt<true><<<(unsigned)grid, p->threads, p->smem, st>>>(args);
+    else k_mul_ntt<false><<<(unsigned)grid, p->threads, p->smem, st>>>(args);
+    return cudaGetLastError();
+}
+
 }  // namespace bn

@@ -367,12 +367,10 @@ cudaError_t quad_launch(const QuadConfig &cfg, const uint32_t *a, const uint32_t
     if (grid > 0x7fffffffull) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (cfg.q == 4) {
-        e = cudaFuncSetAttribute(k_mul_quad<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
-        if (e != cudaSuccess) return e;
+        if ((e = allow_max_smem((const void *)k_mul_quad<4>)) != cudaSuccess) return e;
         k_mul_quad<4><<<(unsigned)grid, g.block, g.smem, st>>>(args);
     } else {
-        e = cudaFuncSetAttribute(k_mul_quad<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
-        if (e != cudaSuccess) return e;
+        if ((e = allow_max_smem((const void *)k_mul_quad<8>)) != cudaSuccess) return e;
         k_mul_quad<8><<<(unsigned)grid, g.block, g.smem, st>>>(args);
     }
     return cudaGetLastError();
