@@ -130,6 +130,36 @@ bn_status bn_mul_quad(const uint32_t *a, const uint32_t *b, uint32_t *c,
 bn_status bn_mul_ntt(const uint32_t *a, const uint32_t *b, uint32_t *c,
                      uint32_t na, uint32_t nb, uint64_t batch, int crt, void *stream);
 
+/* Transform multiplication that allocates nothing, for callers that cannot
+ * call cudaMalloc: code whose device memory is wholly owned by another
+ * allocator (a framework's memory pool, a fixed budget reserved at start-up)
+ * and latency-sensitive loops that must not take cudaMalloc/cudaFree's
+ * implicit device-wide synchronisation.  The paper has no counterpart.
+ *
+ * Same operation, arguments, layout and results as bn_mul_ntt (a, b, c are
+ * caller-owned device memory; crt selects the two-prime form).  Instead of
+ * plan-owned memory it uses two file-scope device arrays that every GPU which
+ * loads the library holds until the process exits:
+ *   scratch   BN_NOALLOC_SCRATCH_BYTES (32 MiB), which caps the number of
+ *             CTAs (at 256K bits: 64 CTAs, so large sizes run slower than
+ *             bn_mul_ntt), and
+ *   tables    768 KiB of twiddle tables, regenerated on the device (on
+ *             `stream`) whenever the transform length or field changes.
+ * Operand sizes above BN_NOALLOC_MAX_LIMBS return BN_EUNSUPPORTED with a
+ * bn_last_error() text saying so.  No call allocates host or device memory.
+ *
+ * The first call on a device sets that device up (looks up the arrays'
+ * device addresses, raises the kernel's shared-memory cap), so make that
+ * first call before any stream capture.  Every call shares the arrays and
+ * they keep the last call's contents (nothing in them has to start at zero:
+ * each call writes every scratch and table word before reading it), so
+ * calls that overlap on the GPU (different streams, other host threads)
+ * race and give wrong results: serialise them on one stream. */
+#define BN_NOALLOC_SCRATCH_BYTES (32ull << 20)
+#define BN_NOALLOC_MAX_LIMBS 8192u
+bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, uint32_t *c,
+                             uint32_t na, uint32_t nb, uint64_t batch, int crt, void *stream);
+
 /* Static description of a status code. */
 const char *bn_status_str(bn_status s);
 

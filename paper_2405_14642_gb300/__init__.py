@@ -15,8 +15,10 @@ The compute path is the CUDA library built from ``csrc/`` (C ABI in
 """
 from ._binding import (BN_ADD_MAX_LIMBS, BN_MUL_MAX_LIMBS, BN_OP_ADD, BN_OP_MUL_NTT64,
                        BN_OP_MUL_NTT_CRT, BN_OP_MUL_QUAD, BnError, Plan, bn_add, bn_mul_ntt,
-                       bn_mul_quad, bn_probe_int_throughput, library_path, load)
+                       bn_mul_ntt_noalloc, bn_mul_quad, bn_probe_int_throughput, library_path,
+                       load)
 
 __all__ = ["bn_add", "bn_mul_quad", "bn_mul_ntt", "Plan", "BnError", "load", "library_path",
            "BN_OP_ADD", "BN_OP_MUL_QUAD", "BN_OP_MUL_NTT64", "BN_OP_MUL_NTT_CRT",
-           "BN_ADD_MAX_LIMBS", "BN_MUL_MAX_LIMBS", "bn_probe_int_throughput"]
+           "BN_ADD_MAX_LIMBS", "BN_MUL_MAX_LIMBS", "bn_probe_int_throughput",
+           "bn_mul_ntt_noalloc"]

@@ -71,6 +71,7 @@ def load(build_if_missing: bool = False):
         "bn_status_str": ([ctypes.c_int], ctypes.c_char_p),
         "bn_last_error": ([], ctypes.c_char_p),
         "bn_version": ([], ctypes.c_int),
+        "bn_mul_ntt_noalloc": ([u32p, u32p, u32p, u32, u32, u64, ctypes.c_int, vp], st),
         "bn_probe_int_throughput": ([ctypes.c_int, u32, u32, u32, u32p,
                                      ctypes.POINTER(ctypes.c_uint64), vp], st),
     }
@@ -160,6 +161,20 @@ def bn_mul_ntt(a, b, crt: bool = False, out=None, stream=None):
     out = _out(out, batch, na + nb, a)
     _check(lib.bn_mul_ntt(_ptr(a), _ptr(b), _ptr(out), na, nb, batch, int(bool(crt)),
                           _stream_handle(stream, a.device)), "bn_mul_ntt")
+    return out
+
+
+def bn_mul_ntt_noalloc(a, b, crt: bool = False, out=None, stream=None):
+    """As bn_mul_ntt, but the library allocates nothing: scratch and tables
+    live in fixed device arrays shared by all calls (see include/bn.h), for
+    callers that cannot call cudaMalloc.  Pass `out` to allocate nothing here
+    either; calls that overlap on the GPU race."""
+    lib = load()
+    a, b = _pair(a, b)
+    batch, na, nb = a.shape[0], a.shape[1], b.shape[1]
+    out = _out(out, batch, na + nb, a)
+    _check(lib.bn_mul_ntt_noalloc(_ptr(a), _ptr(b), _ptr(out), na, nb, batch, int(bool(crt)),
+                                  _stream_handle(stream, a.device)), "bn_mul_ntt_noalloc")
     return out
 
 

@@ -151,6 +151,8 @@ bn_status one_shot(bn_op op, const uint32_t *a, const uint32_t *b, uint32_t *c, 
 
 namespace bn {
 
+void record_error(const char *what) { set_error_text(what); }
+
 cudaError_t allow_max_smem(const void *kernel) {
     static std::mutex m;
     static std::map<std::pair<const void *, int>, bool> done;

@@ -14,6 +14,9 @@ namespace bn {
 // lowering it for one plan would break larger plans of the same kernel.
 cudaError_t allow_max_smem(const void *kernel);
 
+// Records `what` as this host thread's bn_last_error() text.
+void record_error(const char *what);
+
 // ---- addition (Section 2) -------------------------------------------------
 struct AddConfig {
     uint32_t na = 0, nb = 0, n = 0, nout = 0;

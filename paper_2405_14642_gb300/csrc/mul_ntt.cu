@@ -44,6 +44,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -619,4 +620,240 @@ cudaError_t ntt_launch(NttPlan *p, const uint32_t *a, const uint32_t *b, uint32_
     return cudaGetLastError();
 }
 
+// ---- transform multiplication without allocation ------------------------
+//
+// bn_mul_ntt_noalloc (include/bn.h) runs the same kernel as the plans above,
+// but its scratch and twiddle tables live in two file-scope device arrays
+// instead of plan-owned memory, for callers that cannot call cudaMalloc.  The
+// tables are generated by a small kernel on the caller's stream, so neither
+// host nor device memory is allocated on any call.
+
+namespace {
+
+constexpr size_t kNoAllocScratchWords = BN_NOALLOC_SCRATCH_BYTES / 8;
+// Largest table set: two primes at N = 16384 split into two 8192-point
+// halves, each prime holding twf + twi (2 L) and both folds (2 N) words.
+constexpr size_t kNoAllocTableWords = 2 * (2 * 8192 + 2 * 16384);
+static_assert(kNoAllocTableWords >= 2 * 8192 + 2 * 32768, "one prime at N = 32768 fits");
+
+static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocScratchWords];
+static __device__ __align__(256) uint64_t g_noalloc_tables[kNoAllocTableWords];
+
+constexpr int kNoAllocMaxDevices = 64;
+struct NoAllocDevice {
+    bool ready = false;
+    uint64_t *scratch = nullptr, *tables = nullptr;  // device addresses of the arrays
+    int sms = 0;
+    bool have_tables = false;  // the table array holds (crt, N)
+    bool crt = false;
+    uint32_t N = 0;
+};
+NoAllocDevice g_noalloc_devices[kNoAllocMaxDevices];
+std::mutex g_noalloc_mutex;
+
+template <class F>
+__device__ uint64_t form_pow(uint64_t base, uint64_t e, uint64_t one) {
+    uint64_t r = one;
+    while (e) {
+        if (e & 1) r = F::mul(r, base);
+        base = F::mul(base, base);
+        e >>= 1;
+    }
+    return r;
+}
+
+// One prime's tables (layout twf[L] | twi[L] | ffold[S L] | ifold[S L]), the
+// same values the plans build on the host; all inputs are in twiddle form.
+template <class F>
+__global__ void k_noalloc_tables(uint64_t *tab, uint32_t L, uint32_t S, uint64_t one, uint64_t wL,
+                                 uint64_t wLi, uint64_t wN, uint64_t wNi, uint64_t scale) {
+    const uint32_t total = 2 * L + (S > 1 ? 2 * S * L : 0);
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += gridDim.x * blockDim.x) {
+        if (idx < 2 * L) {
+            const uint32_t inv = idx >= L, i = idx - inv * L;
+            uint64_t v = 0;
+            if (i > 0) {
+                const uint32_t h = 1u << (31 - __clz(i)), j = i - h;
+                v = form_pow<F>(form_pow<F>(inv ? wLi : wL, L / (2 * h), one), j, one);
+            }
+            tab[idx] = v;
+        } else {
+            const uint32_t k = idx - 2 * L, inv = k >= S * L, r = k - inv * S * L;
+            const uint32_t sidx = r / L, j = r - sidx * L;
+            const uint64_t w = form_pow<F>(inv ? wNi : wN, (uint64_t)j * sidx, one);
+            tab[idx] = inv ? F::mul(scale, w) : w;
+        }
+    }
+}
+
+// Host constants of one prime for (N, S), in twiddle form; no allocation.
+struct NoAllocPrime {
+    uint64_t one, wL, wLi, wN, wNi, scale;
+    PrimeTab tab;
+};
+
+NoAllocPrime noalloc_prime(const HostField &f, uint32_t N, uint32_t S, uint64_t *dtab) {
+    NoAllocPrime c{};
+    const uint32_t L = N / S;
+    const uint64_t wN = root_of_unity(f, N), wL = hpow(wN, S, f.p);
+    const uint64_t R = f.montgomery ? (uint64_t)(((u128)1 << 64) % f.p) : 1;
+    const uint64_t scale = hmul(hinv(N % f.p, f.p), R, f.p);
+    c.one = to_form(f, 1);
+    c.wL = to_form(f, wL);
+    c.wLi = to_form(f, hinv(wL, f.p));
+    c.wN = to_form(f, wN);
+    c.wNi = to_form(f, hinv(wN, f.p));
+    c.scale = to_form(f, scale);
+    c.tab.twf = dtab;
+    c.tab.twi = dtab + L;
+    c.tab.ffold = S > 1 ? dtab + 2 * L : nullptr;
+    c.tab.ifold = S > 1 ? dtab + 2 * L + (size_t)S * L : nullptr;
+    c.tab.scale = c.scale;
+    if (S > 1) {
+        const uint64_t wS = hpow(wN, N / S, f.p), wSi = hinv(wS, f.p);
+        for (uint32_t k = 0; k < S; ++k) {
+            c.tab.ws[k] = to_form(f, hpow(wS, k, f.p));
+            c.tab.iws[k] = to_form(f, hpow(wSi, k, f.p));
+        }
+    }
+    return c;
+}
+
+size_t noalloc_prime_words(uint32_t N, uint32_t S) {
+    return 2 * (N / S) + (S > 1 ? 2 * (size_t)N : 0);
+}
+
+}  // namespace
+
 }  // namespace bn
+
+extern "C" bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, uint32_t *c,
+                                        uint32_t na, uint32_t nb, uint64_t batch, int crt_flag,
+                                        void *stream) {
+    using namespace bn;
+    if (na == 0 || nb == 0) {
+        record_error("zero limb count");
+        return BN_EINVAL;
+    }
+    if (na > BN_NOALLOC_MAX_LIMBS || nb > BN_NOALLOC_MAX_LIMBS) {
+        record_error("operand above BN_NOALLOC_MAX_LIMBS (8192 limbs) for bn_mul_ntt_noalloc");
+        return BN_EUNSUPPORTED;
+    }
+    if (batch == 0) return BN_OK;
+    if (!a || !b || !c) {
+        record_error("null operand or result pointer");
+        return BN_EINVAL;
+    }
+    const uint32_t nout = na + nb;
+    {
+        const uintptr_t ca = (uintptr_t)c, ce = ca + batch * nout * 4ull;
+        const uintptr_t aa = (uintptr_t)a, ae = aa + batch * na * 4ull;
+        const uintptr_t ba = (uintptr_t)b, be = ba + batch * nb * 4ull;
+        if ((ca < ae && aa < ce) || (ca < be && ba < ce)) {
+            record_error("result overlaps an operand");
+            return BN_EINVAL;
+        }
+    }
+    const bool crt = crt_flag != 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto *kern = crt ? k_mul_ntt<true> : k_mul_ntt<false>;
+
+    // Geometry, as for a plan.
+    const uint32_t digits = crt ? nout : 2 * nout;
+    const uint32_t N = next_pow2(digits < 2 ? 2 : digits);
+    const uint32_t S = N > kMaxSubLength ? N / kMaxSubLength : 1;
+    const uint32_t L = N / S;
+    uint32_t logL = 0;
+    while ((1u << logL) < L) ++logL;
+    uint32_t T = L / 8;
+    if (T < 32) T = 32;
+    if (T > 1024) T = 1024;
+    const uint32_t Lp2 = (phys_words(L) + 1) & ~1u;
+    const uint32_t smem = 8u * (2u * Lp2 + T) + 4u * 32u;
+    const uint64_t stride = (S > 1 ? 2ull * N : 0ull) + (crt ? (uint64_t)N : 0ull);
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        record_error("no usable current device for bn_mul_ntt_noalloc");
+        return BN_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoAllocDevice &d = g_noalloc_devices[dev];
+    if (!d.ready) {  // once per device, with that device current
+        void *ps = nullptr, *pt = nullptr;
+        int optin = 0;
+        e = cudaGetSymbolAddress(&ps, g_noalloc_scratch);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&pt, g_noalloc_tables);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_mul_ntt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_mul_ntt<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (e != cudaSuccess) {
+            record_error("bn_mul_ntt_noalloc device set-up failed");
+            return BN_ECUDA;
+        }
+        d.scratch = static_cast<uint64_t *>(ps);
+        d.tables = static_cast<uint64_t *>(pt);
+        d.ready = true;
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)T, smem);
+    if (e != cudaSuccess || per_sm == 0) {
+        record_error("bn_mul_ntt_noalloc: kernel does not fit on this device");
+        return BN_ECUDA;
+    }
+    uint64_t max_grid = (uint64_t)d.sms * per_sm;
+    if (stride > 0 && kNoAllocScratchWords / stride < max_grid) max_grid = kNoAllocScratchWords / stride;
+
+    const NoAllocPrime c1 = noalloc_prime(field_p1(), N, S, d.tables);
+    const NoAllocPrime c2 = noalloc_prime(field_p2(), N, S, d.tables + noalloc_prime_words(N, S));
+    if (!d.have_tables || d.crt != crt || d.N != N) {
+        const uint32_t words = (uint32_t)noalloc_prime_words(N, S);
+        const unsigned blocks = (words + 255) / 256 < 1024 ? (words + 255) / 256 : 1024;
+        k_noalloc_tables<FieldP1><<<blocks, 256, 0, st>>>(d.tables, L, S, c1.one, c1.wL, c1.wLi,
+                                                           c1.wN, c1.wNi, c1.scale);
+        if (crt)
+            k_noalloc_tables<FieldP2><<<blocks, 256, 0, st>>>(d.tables + words, L, S, c2.one, c2.wL,
+                                                               c2.wLi, c2.wN, c2.wNi, c2.scale);
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            d.have_tables = false;
+            record_error("bn_mul_ntt_noalloc table kernel launch failed");
+            return BN_ECUDA;
+        }
+        d.have_tables = true;
+        d.crt = crt;
+        d.N = N;
+    }
+
+    NttArgs args{};
+    args.a = a;
+    args.b = b;
+    args.c = c;
+    args.na = na;
+    args.nb = nb;
+    args.nout = nout;
+    args.N = N;
+    args.L = L;
+    args.logL = logL;
+    args.S = S;
+    args.digit_bits = crt ? 32 : 16;
+    args.vec_c = (nout % 4 == 0) && ((uintptr_t)c % 16 == 0);
+    args.batch = batch;
+    args.scratch = d.scratch;
+    args.scratch_stride = stride;
+    args.garner_inv = hinv(field_p1().p % field_p2().p, field_p2().p);
+    args.t1 = c1.tab;
+    args.t2 = c2.tab;
+    const uint64_t grid = batch < max_grid ? batch : max_grid;
+    if (crt) k_mul_ntt<true><<<(unsigned)grid, T, smem, st>>>(args);
+    else k_mul_ntt<false><<<(unsigned)grid, T, smem, st>>>(args);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        record_error("bn_mul_ntt_noalloc kernel launch failed");
+        return BN_ECUDA;
+    }
+    return BN_OK;
+}
