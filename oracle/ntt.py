@@ -24,8 +24,10 @@ Readings taken here (the paper is silent or inexact on these points):
   31-bit digits admits none, so neither is exact at midsize lengths.  The
   single-prime form used here takes PrimeField64 with 16-bit digits (bound
   < 2^46 for the 256K-bit range); the two-prime form takes 32-bit digits over
-  PrimeField64 and ``2^64 - 2^32 + 1`` (generator 7) and recombines by CRT
-  (bound < 2^77 < p1 * p2).
+  PrimeField64 and a second good prime, ``27 * 2^56 + 1`` (root 5^27 of order
+  2^56), and recombines by CRT (bound < 2^77 < p1 * p2 ~ 2^122.6).  Any prime
+  k * 2^n + 1 with 2^n >= the transform length is equally valid; this one is
+  chosen, like p1, with low 32-bit word 1 and below 2^62.
 * ``g`` as printed is itself a primitive ``2^n``-th root of unity (verified in
   the tests), and ``omega_M = g^(2^n / M)``.
 """
@@ -54,11 +56,10 @@ class PrimeField:
 # Printed in Section 4.1.
 PRIME_FIELD_32 = PrimeField("PrimeField32", 3221225473, 3, 30, 13)
 PRIME_FIELD_64 = PrimeField("PrimeField64", 4179340454199820289, 29, 57, 21)
-# Second CRT prime (a reading, not in the paper): 2^64 - 2^32 + 1 = (2^32 - 1) 2^32 + 1;
-# 7 generates its multiplicative group, so 7^k has order exactly 2^32.
-_P_GOLD = (1 << 64) - (1 << 32) + 1
-PRIME_FIELD_GOLD = PrimeField("Goldilocks", _P_GOLD, (1 << 32) - 1, 32,
-                              pow(7, (1 << 32) - 1, _P_GOLD))
+# Second CRT prime (a reading, not in the paper): 27 * 2^56 + 1.  a = 5 is the
+# first a whose a^27 has order exactly 2^56 (Section 4.1's search).
+_P_CRT2 = 27 * (1 << 56) + 1
+PRIME_FIELD_CRT2 = PrimeField("CRT2", _P_CRT2, 27, 56, pow(5, 27, _P_CRT2))
 
 
 def search_root(p: int, k: int, n: int, limit: int = 1000) -> int:
@@ -204,7 +205,7 @@ def garner(r1: int, r2: int, p1: int, p2: int) -> int:
 
 
 def mul_two_prime(a: Sequence[int], b: Sequence[int], d: int = 32,
-                  f1: PrimeField = PRIME_FIELD_64, f2: PrimeField = PRIME_FIELD_GOLD) -> List[int]:
+                  f1: PrimeField = PRIME_FIELD_64, f2: PrimeField = PRIME_FIELD_CRT2) -> List[int]:
     """a * b with d-bit digits, two prime fields and Garner recombination."""
     xd, yd = to_digits(a, d), to_digits(b, d)
     c1 = convolve_mod(xd, yd, f1)
