@@ -53,7 +53,7 @@ class Op:
     seed: int
     mults: int = 0     # multiplications per launch
     bytes: int = 0     # algorithmic HBM bytes per launch
-    imad: int = 0      # algorithmic 32-bit multiply-adds per launch
+    prods: int = 0     # algorithmic 32x32->64-bit word products per launch
     times_ms: list = field(default_factory=list)
 
     @property
@@ -84,18 +84,18 @@ def build_ops(quick: bool = False):
         ops.append(Op("add", p.bits, n, n, p.batch, p.seed, mults=0,
                       bytes=4 * (3 * n + 1) * p.batch))
         ops.append(Op("quad", p.bits, n, n, p.batch, p.seed, mults=p.batch,
-                      bytes=4 * 4 * n * p.batch, imad=2 * n * n * p.batch))
+                      bytes=4 * 4 * n * p.batch, prods=n * n * p.batch))
     for p in pts:
         if p.bits not in workloads.NTT_BITS:
             continue
         n = p.limbs
         _, _, mm64, mmcrt = ntt_lengths(n)
         # A 64x64-bit modular product needs at least the 4 word products of
-        # its 128-bit product, 2 multiply-adds (lo, hi) each.
+        # its 128-bit product (the reduction's products are not counted).
         ops.append(Op("ntt64", p.bits, n, n, p.batch, p.seed, mults=p.batch,
-                      bytes=16 * n * p.batch, imad=8 * mm64 * p.batch))
+                      bytes=16 * n * p.batch, prods=4 * mm64 * p.batch))
         ops.append(Op("crt", p.bits, n, n, p.batch, p.seed, mults=p.batch,
-                      bytes=16 * n * p.batch, imad=8 * mmcrt * p.batch))
+                      bytes=16 * n * p.batch, prods=4 * mmcrt * p.batch))
     return ops
 
 
@@ -173,7 +173,10 @@ class ClockSampler:
 # ---- GPU arm ---------------------------------------------------------------
 
 def imad_peak(torch, bn, dev):
-    """Time the register-only multiply-add probe; derive the per-clock rate."""
+    """Time the register-only multiply-add probe and derive the word-product
+    ceiling: a 32x32->64 product needs one mad.lo and one mad.hi, so with
+    per-clock rates lo and hi (snapped to powers of two) the ceiling is
+    1 / (1/lo + 1/hi) products per clock per SM, times SMs and the max clock."""
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     out = torch.zeros(sms * 8, dtype=torch.int32, device=dev)
@@ -198,11 +201,31 @@ def imad_peak(torch, bn, dev):
         rate = total / (best * 1e-3)
         mhz = clk.get("sm_mhz") or SM_MAX_MHZ_NOMINAL
         res[name] = {"ops_per_s": rate, "per_clk_per_sm": rate / (sms * mhz * 1e6), "sm_mhz": mhz}
-    # Unit count: the mad.lo rate per clock, snapped to the nearest power of two.
-    per_clk = res["mad_lo"]["per_clk_per_sm"]
-    units = 2 ** round(math.log2(per_clk)) if per_clk > 0 else 64
-    peak = units * sms * SM_MAX_MHZ_NOMINAL * 1e6
-    return {"units_per_clk_per_sm": units, "sms": sms, "peak_ops_per_s": peak, "probe": res}
+
+    def snap(x):
+        return 2 ** round(math.log2(x)) if x > 0 else 0
+    lo, hi = snap(res["mad_lo"]["per_clk_per_sm"]), snap(res["mad_hi"]["per_clk_per_sm"])
+    per_clk = 1.0 / (1.0 / lo + 1.0 / hi) if lo and hi else 0.0
+    peak = per_clk * sms * SM_MAX_MHZ_NOMINAL * 1e6
+    return {"mad_lo_per_clk_per_sm": lo, "mad_hi_per_clk_per_sm": hi,
+            "word_products_per_clk_per_sm": per_clk, "sms": sms, "peak_word_products_per_s": peak,
+            "probe": res}
+
+
+def kernel_traffic(op_label: str):
+    """DRAM bytes per launch from the committed ncu capture of this op, if the
+    kernel source is unchanged since the capture (else None)."""
+    import hashlib
+    p = ROOT / "profiles" / "traffic.json"
+    if not p.exists():
+        return None
+    entry = json.loads(p.read_text()).get(op_label)
+    if not entry:
+        return None
+    src = ROOT / entry["source"]
+    if not src.exists() or hashlib.sha256(src.read_bytes()).hexdigest() != entry["sha256"]:
+        return None
+    return entry["dram_bytes"]
 
 
 def read_measured_peaks():
@@ -290,7 +313,7 @@ def run_gpu(args, rank, world, local_rank):
         o.times_ms = [evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(args.steps)]
     max_ms = allreduce_max(elapsed_ms, world, dev)
     mults_per_step = sum(o.mults for o in ops)
-    value = world * mults_per_step * args.steps / (max_ms * 1e-3)
+    value = aggregate_value(mults_per_step, args.steps, max_ms, world)
     ms_per_step = max_ms / args.steps
     gpu_launches = args.steps * len(ops)
 
@@ -313,20 +336,24 @@ def run_gpu(args, rank, world, local_rank):
                               "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
                               "peak_kind": hbm_kind, "traffic": None})
         else:
-            tops = o.imad / (ms * 1e-3) / 1e12
-            peak_t = peak_info["peak_ops_per_s"] / 1e12
-            row.update(mults_per_s=o.batch / (ms * 1e-3), imad_tops=round(tops, 3))
-            rooflines.append({"op": o.label, "bound": "alu", "achieved": round(tops, 3),
-                              "peak": round(peak_t, 3), "unit": "T mul-add/s",
-                              "frac": round(tops / peak_t, 4),
-                              "peak_kind": "derived: %d mul-add/clk/SM (probe) x %d SMs x %.0f MHz"
-                                           % (peak_info["units_per_clk_per_sm"], peak_info["sms"],
-                                              SM_MAX_MHZ_NOMINAL),
+            gp = o.prods / (ms * 1e-3) / 1e12
+            peak_t = peak_info["peak_word_products_per_s"] / 1e12
+            row.update(mults_per_s=o.batch / (ms * 1e-3), word_tprods=round(gp, 3))
+            rooflines.append({"op": o.label, "bound": "alu", "achieved": round(gp, 3),
+                              "peak": round(peak_t, 3), "unit": "T word-products/s",
+                              "frac": round(gp / peak_t, 4),
+                              "peak_kind": "derived: 1/(1/%d + 1/%d) = %.2f word products/clk/SM "
+                                           "(mad.lo, mad.hi rates from the probe) x %d SMs x %.0f MHz"
+                                           % (peak_info["mad_lo_per_clk_per_sm"],
+                                              peak_info["mad_hi_per_clk_per_sm"],
+                                              peak_info["word_products_per_clk_per_sm"],
+                                              peak_info["sms"], SM_MAX_MHZ_NOMINAL),
                               "traffic": None})
         rows.append(row)
     total_ms = [sum(o.times_ms[k] for o in ops) for k in range(args.steps)]
     dom = max(range(len(ops)), key=lambda i: np.mean(ops[i].times_ms))
     roof = dict(rooflines[dom])
+    roof["traffic"] = kernel_traffic(ops[dom].label)
     roof["kernel_share_of_step"] = round(float(np.mean(ops[dom].times_ms)) / float(np.mean(total_ms)), 4)
     add_ops = [o for o in ops if o.name == "add"]
     add_gbs = (sum(o.bytes for o in add_ops) / (sum(np.mean(o.times_ms) for o in add_ops) * 1e-3) / 1e9
@@ -491,6 +518,12 @@ def allreduce_max(x: float, world: int, dev):
     t = torch.tensor([x], dtype=torch.float64, device=dev if dist.get_backend() == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_value(units_per_rank_step: int, steps: int, max_ms: float, world: int) -> float:
+    """Whole-job throughput: every rank processes the same per-rank work
+    (weak scaling), timed by the slowest rank."""
+    return world * units_per_rank_step * steps / (max_ms * 1e-3)
 
 
 def main(argv=None):

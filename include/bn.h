@@ -80,9 +80,11 @@ typedef enum bn_op {
 /* Optional launch tuning; a zero field takes the built-in default. */
 typedef struct bn_tuning {
     uint32_t limbs_per_thread;  /* add: limbs per thread (multiple of the vector width);
-                                   quad: result limbs per window (2..16) */
+                                   quad: result limbs per window (4 or 8) */
     uint32_t cta_threads;       /* threads per CTA (multiple of 32, <= 1024) */
-    uint32_t reserved[2];       /* must be zero */
+    uint32_t variant;           /* quad: 1 = carry-chain accumulation, 2 = per-column
+                                   64-bit sums with carry counts; other ops: 0 */
+    uint32_t reserved;          /* must be zero */
 } bn_tuning;
 
 typedef struct bn_plan_s *bn_plan;

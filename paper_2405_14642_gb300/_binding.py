@@ -36,7 +36,7 @@ class BnError(RuntimeError):
 
 class bn_tuning(ctypes.Structure):
     _fields_ = [("limbs_per_thread", ctypes.c_uint32), ("cta_threads", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("variant", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 def library_path():
@@ -195,11 +195,11 @@ class Plan:
     """A bn_plan: fixed op, sizes and batch; reusable across calls."""
 
     def __init__(self, op: int, na: int, nb: int, batch: int,
-                 limbs_per_thread: int = 0, cta_threads: int = 0):
+                 limbs_per_thread: int = 0, cta_threads: int = 0, variant: int = 0):
         lib = load()
         self._lib = lib
         self._h = ctypes.c_void_p()
-        tun = bn_tuning(limbs_per_thread, cta_threads)
+        tun = bn_tuning(limbs_per_thread, cta_threads, variant, 0)
         _check(lib.bn_plan_create(ctypes.byref(self._h), op, na, nb, batch, ctypes.byref(tun)),
                "bn_plan_create")
         self.op, self.na, self.nb, self.batch = op, na, nb, batch

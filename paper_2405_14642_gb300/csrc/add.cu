@@ -195,7 +195,7 @@ bn_status add_configure(AddConfig &cfg, uint32_t na, uint32_t nb, const bn_tunin
     cfg.n = na > nb ? na : nb;
     cfg.nout = cfg.n + 1;
     if (t) {
-        if (t->reserved[0] || t->reserved[1]) return BN_EINVAL;
+        if (t->reserved || t->variant) return BN_EINVAL;
         if (t->cta_threads && (t->cta_threads % 32 || t->cta_threads > 1024)) return BN_EINVAL;
         uint32_t l = t->limbs_per_thread;
         if (l && (l & (l - 1) || l > 32)) return BN_EINVAL;  // power of two <= 32

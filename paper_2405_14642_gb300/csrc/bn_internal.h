@@ -34,6 +34,7 @@ inline int add_launch_count() { return 1; }
 struct QuadConfig {
     uint32_t na = 0, nb = 0, nout = 0;
     uint32_t q = 0;        // result limbs per window
+    bool cols = false;     // per-column 64-bit sums instead of carry chains
     uint32_t threads = 0;  // threads per instance group
     uint32_t cta_threads = 0;
 };

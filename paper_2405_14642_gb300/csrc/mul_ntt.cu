@@ -4,19 +4,18 @@
 // coefficient stays below the modulus):
 //   * BN_OP_MUL_NTT64: PrimeField64, p1 = 29*2^57 + 1 with root g = 21 of
 //     order 2^57, 16-bit digits (coefficients < 2^46 at 256K bits);
-//   * BN_OP_MUL_NTT_CRT: 32-bit digits over p1 and p2 = 2^64 - 2^32 + 1 (root
-//     7^(2^32-1) of order 2^32), recombined by Garner's form of the CRT
+//   * BN_OP_MUL_NTT_CRT: 32-bit digits over p1 and p2 = 27*2^56 + 1 (root
+//     5^27 of order 2^56), recombined by Garner's form of the CRT
 //     (coefficients < 2^77 < p1 p2).
 // Transform length N = next power of two >= digits(a) + digits(b), so the
 // cyclic convolution does not wrap (inputs are zero-padded).
 //
 // Arithmetic.  Section 4.1's field multiplies with a full-width modulo; here
-// p1 uses Montgomery multiplication (R = 2^64), whose reduction is cheap for
-// this prime: -p1^-1 mod 2^64 = 29*2^57 - 1, so the quotient digit m needs only
-// the low 7 bits of t*29.  p2 uses its direct reduction 2^64 = 2^32 - 1 (mod p2).
-// Twiddles are stored in each field's "twiddle form" (Montgomery form for p1,
-// plain for p2) so that mul(x, w) = x*w; the pointwise product and the final
-// 1/N scale absorb Montgomery's extra 1/R.
+// both primes use a lazy Montgomery multiplication (R = 2^64, values kept in
+// [0, 2p)) that is cheap because each prime's low 32-bit word is 1 (see
+// MontField).  Twiddles are stored in Montgomery form so that
+// mul(x, form(w)) = x*w; the pointwise product and the final 1/N scale absorb
+// Montgomery's extra 1/R.
 //
 // Work mapping.  One CTA transforms one integer pair at a time in shared
 // memory (a persistent grid walks the batch).  Forward transforms are
@@ -62,50 +61,49 @@ constexpr int kRadixLog = 3;              // radix-8 passes
 
 // ---- device fields ---------------------------------------------------------
 
-struct FieldP1 {  // 29 * 2^57 + 1, Montgomery form with R = 2^64
-    static constexpr uint64_t P = 4179340454199820289ull;
+// Z_P for a prime P = k 2^m + 1 with m >= 32 (so P's low 32-bit word is 1)
+// and P < 2^62, in Montgomery form with R = 2^64.  Elements are kept lazily
+// in [0, 2P); canon() maps to [0, P).
+//   * mul: for a, b < 2P the 128-bit product comes from four 32x32->64
+//     multiply-adds with no carry handling (a, b < 2^63 keep the cross sum
+//     below 2^64).  Reduction: -P^-1 = P - 2 (mod 2^64), so the quotient
+//     m = t_lo (P - 2) has words (-x0, x0*P_hi - x1 - borrow); m*P needs two
+//     more multiply-adds since P's low word is 1; the result is < 2P because
+//     4P < 2^64.
+template <uint64_t P>
+struct MontField {
+    static constexpr uint64_t P_VALUE = P;
+    static constexpr uint32_t PH = (uint32_t)(P >> 32);
+    static constexpr uint64_t TWO_P = 2 * P;
+    static_assert((P & 0xffffffffull) == 1 && P < (1ull << 62), "P = k 2^m + 1, m >= 32, P < 2^62");
     __device__ static __forceinline__ uint64_t add(uint64_t a, uint64_t b) {
         const uint64_t r = a + b;
-        return r >= P ? r - P : r;
+        return r >= TWO_P ? r - TWO_P : r;
     }
     __device__ static __forceinline__ uint64_t sub(uint64_t a, uint64_t b) {
-        return a >= b ? a - b : a - b + P;
+        const uint64_t r = a + TWO_P - b;
+        return r >= TWO_P ? r - TWO_P : r;
     }
-    // a * b / 2^64 mod P for a, b < P.
+    __device__ static __forceinline__ uint64_t canon(uint64_t a) { return a >= P ? a - P : a; }
+    // a * b / 2^64 mod P, inputs and output in [0, 2P).
     __device__ static __forceinline__ uint64_t mul(uint64_t a, uint64_t b) {
-        const uint64_t lo = a * b, hi = __umul64hi(a, b);
-        const uint64_t m = ((uint64_t)(((uint32_t)lo * 29u) & 127u) << 57) - lo;
-        const uint64_t r = hi + __umul64hi(m, P) + (lo != 0);
-        return r >= P ? r - P : r;
+        const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+        const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+        const uint64_t p00 = (uint64_t)a0 * b0;
+        uint64_t t = (uint64_t)a0 * b1 + (p00 >> 32);
+        t += (uint64_t)a1 * b0;
+        const uint64_t hi = (uint64_t)a1 * b1 + (t >> 32);
+        const uint32_t x0 = (uint32_t)p00, x1 = (uint32_t)t;
+        const uint32_t m0 = 0u - x0;
+        const uint32_t m1 = x0 * PH - x1 - (x0 != 0u);
+        const uint64_t sm = (uint64_t)m0 * PH + m1;
+        const uint64_t h = (uint64_t)m1 * PH + (sm >> 32);
+        return hi + h + ((x0 | x1) != 0u);
     }
 };
 
-struct FieldP2 {  // 2^64 - 2^32 + 1, plain form
-    static constexpr uint64_t P = 0xFFFFFFFF00000001ull;
-    static constexpr uint64_t EPS = 0xFFFFFFFFull;  // 2^64 mod P
-    __device__ static __forceinline__ uint64_t add(uint64_t a, uint64_t b) {
-        uint64_t r = a + b;
-        if (r < a) r += EPS;
-        else if (r >= P) r -= P;
-        return r;
-    }
-    __device__ static __forceinline__ uint64_t sub(uint64_t a, uint64_t b) {
-        const uint64_t r = a - b;
-        return a < b ? r - EPS : r;
-    }
-    __device__ static __forceinline__ uint64_t reduce(uint64_t hi, uint64_t lo) {
-        const uint64_t hh = hi >> 32, hl = hi & EPS;
-        uint64_t t0 = lo - hh;
-        if (lo < hh) t0 -= EPS;
-        const uint64_t t1 = hl * EPS;
-        uint64_t r = t0 + t1;
-        if (r < t1) r += EPS;
-        return r >= P ? r - P : r;
-    }
-    __device__ static __forceinline__ uint64_t mul(uint64_t a, uint64_t b) {
-        return reduce(__umul64hi(a, b), a * b);
-    }
-};
+using FieldP1 = MontField<4179340454199820289ull>;  // 29 * 2^57 + 1 (PrimeField64)
+using FieldP2 = MontField<1945555039024054273ull>;  // 27 * 2^56 + 1
 
 // Shared-memory index with one u64 of padding per 16 (bank spread).
 __device__ __forceinline__ uint32_t phys(uint32_t i) { return i + (i >> 4); }
@@ -160,6 +158,13 @@ __device__ void load_fold(const NttArgs &p, const PrimeTab &tb, const uint32_t *
     }
 }
 
+// Twiddle index of group element m in the stage of half-size h (h = hm*step):
+// the position of element m within its 2h block.  Within one group it depends
+// only on m's bits below hm, so a stage needs hm distinct twiddles.
+__device__ __forceinline__ uint32_t tw_index(uint32_t base, uint32_t m, uint32_t step, uint32_t h) {
+    return h + ((base + m * step) & (h - 1));
+}
+
 // KK decimation-in-frequency stages with half-sizes H, H/2, ..., H >> (KK-1).
 template <class F, int KK>
 __device__ __forceinline__ void dif_pass(uint64_t *buf, uint32_t L, uint32_t H, const uint64_t *tw) {
@@ -174,13 +179,16 @@ __device__ __forceinline__ void dif_pass(uint64_t *buf, uint32_t L, uint32_t H, 
 #pragma unroll
         for (int st = 0; st < KK; ++st) {
             const uint32_t hm = 1u << (KK - 1 - st), h = hm * step;
+            uint64_t w[E / 2];
+#pragma unroll
+            for (int m = 0; m < (int)hm; ++m) w[m] = h == 1 ? 0 : __ldg(tw + tw_index(base, m, step, h));
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 if (m & hm) continue;
                 const uint64_t u = x[m], v = x[m + hm];
                 x[m] = F::add(u, v);
                 const uint64_t d = F::sub(u, v);
-                x[m + hm] = h == 1 ? d : F::mul(d, __ldg(tw + h + ((base + m * step) & (h - 1))));
+                x[m + hm] = h == 1 ? d : F::mul(d, w[m & (hm - 1)]);
             }
         }
 #pragma unroll
@@ -202,12 +210,14 @@ __device__ __forceinline__ void dit_pass(uint64_t *buf, uint32_t L, uint32_t h0,
 #pragma unroll
         for (int st = 0; st < KK; ++st) {
             const uint32_t hm = 1u << st, h = hm * step;
+            uint64_t w[E / 2];
+#pragma unroll
+            for (int m = 0; m < (int)hm; ++m) w[m] = h == 1 ? 0 : __ldg(tw + tw_index(base, m, step, h));
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 if (m & hm) continue;
                 const uint64_t u = x[m];
-                const uint64_t v = h == 1 ? x[m + hm]
-                                          : F::mul(x[m + hm], __ldg(tw + h + ((base + m * step) & (h - 1))));
+                const uint64_t v = h == 1 ? x[m + hm] : F::mul(x[m + hm], w[m & (hm - 1)]);
                 x[m] = F::add(u, v);
                 x[m + hm] = F::sub(u, v);
             }
@@ -278,7 +288,7 @@ __device__ void prime_product(const NttArgs &p, const PrimeTab &tb, const uint32
     }
     if (p.S == 1) {
         for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) {
-            const uint64_t v = F::mul(B[phys(j)], tb.scale);
+            const uint64_t v = F::canon(F::mul(B[phys(j)], tb.scale));
             if (keep) B[phys(j)] = v;
             else dest[j] = v;
         }
@@ -293,7 +303,7 @@ __device__ void prime_product(const NttArgs &p, const PrimeTab &tb, const uint32
                     const uint32_t k = (r * s) & (p.S - 1);
                     acc = F::add(acc, k == 0 ? u[s] : F::mul(u[s], tb.iws[k]));
                 }
-                dest[j + r * p.L] = acc;
+                dest[j + r * p.L] = F::canon(acc);
             }
         }
     }
@@ -309,11 +319,15 @@ __device__ __forceinline__ u128 limb_value(const NttArgs &p, uint32_t k, const u
         const uint64_t c1 = in_smem ? B[phys(2 * k + 1)] : Cs[2 * k + 1];
         return (u128)(c0 + (c1 << 16));  // < 2^46 + 2^62
     } else {
-        const uint64_t r1 = C1[k];
-        const uint64_t r2 = in_smem ? B[phys(k)] : Cs[k];
+        const uint64_t r1 = C1[k];                     // canonical mod p1
+        const uint64_t r2 = in_smem ? B[phys(k)] : Cs[k];  // canonical mod p2
         // Garner: c = r1 + p1 * ((r2 - r1) p1^-1 mod p2), exact since c < p1 p2.
-        const uint64_t v = FieldP2::mul(FieldP2::sub(r2, r1), p.garner_inv);
-        return (u128)r1 + (u128)v * FieldP1::P;
+        uint64_t r1m = r1;                             // r1 mod p2 (p1 < 3 p2)
+        if (r1m >= FieldP2::P_VALUE) r1m -= FieldP2::P_VALUE;
+        if (r1m >= FieldP2::P_VALUE) r1m -= FieldP2::P_VALUE;
+        const uint64_t d = r2 >= r1m ? r2 - r1m : r2 + FieldP2::P_VALUE - r1m;
+        const uint64_t v = FieldP2::canon(FieldP2::mul(d, p.garner_inv));
+        return (u128)r1 + (u128)v * FieldP1::P_VALUE;
     }
 }
 
@@ -410,11 +424,11 @@ uint64_t hpow(uint64_t a, uint64_t e, uint64_t p) {
 
 uint64_t hinv(uint64_t a, uint64_t p) { return hpow(a, p - 2, p); }
 
-HostField field_p1() { return {4179340454199820289ull, 21, 57, true}; }
+HostField field_p1() { return {FieldP1::P_VALUE, 21, 57, true}; }  // Section 4.1
 
 HostField field_p2() {
-    const uint64_t p = 0xFFFFFFFF00000001ull;
-    return {p, hpow(7, (p - 1) >> 32, p), 32, false};
+    const uint64_t p = FieldP2::P_VALUE;  // 27 * 2^56 + 1; 5^27 has order 2^56
+    return {p, hpow(5, 27, p), 56, true};
 }
 
 // The form in which the device keeps constants: mul(x, form(w)) = x*w.
@@ -499,7 +513,7 @@ bn_status ntt_create(NttPlan **out, bool crt, uint32_t na, uint32_t nb, const bn
     if (na > BN_MUL_MAX_LIMBS || nb > BN_MUL_MAX_LIMBS) return BN_EUNSUPPORTED;
     uint32_t cta = 0;
     if (tun) {
-        if (tun->reserved[0] || tun->reserved[1] || tun->limbs_per_thread) return BN_EINVAL;
+        if (tun->reserved || tun->variant || tun->limbs_per_thread) return BN_EINVAL;
         if (tun->cta_threads && (tun->cta_threads % 32 || tun->cta_threads > 1024)) return BN_EINVAL;
         cta = tun->cta_threads;
     }
@@ -577,7 +591,7 @@ bn_status ntt_create(NttPlan **out, bool crt, uint32_t na, uint32_t nb, const bn
     }
     p->scratch = p->dev + table_words;
     const HostField f1 = field_p1(), f2 = field_p2();
-    p->garner_inv = hinv(f1.p % f2.p, f2.p);
+    p->garner_inv = to_form(f2, hinv(f1.p % f2.p, f2.p));
     *out = p;
     return BN_OK;
 }
@@ -845,7 +859,7 @@ extern "C" bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, ui
     args.batch = batch;
     args.scratch = d.scratch;
     args.scratch_stride = stride;
-    args.garner_inv = hinv(field_p1().p % field_p2().p, field_p2().p);
+    args.garner_inv = to_form(field_p2(), hinv(field_p1().p % field_p2().p, field_p2().p));
     args.t1 = c1.tab;
     args.t2 = c2.tab;
     const uint64_t grid = batch < max_grid ? batch : max_grid;

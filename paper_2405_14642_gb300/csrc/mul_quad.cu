@@ -51,6 +51,7 @@ struct QuadArgs {
     uint32_t ipb;           // instances per CTA
     uint32_t inst_words;    // shared words per instance
     uint32_t ab_words;      // A region (B region follows at ab_words)
+    uint32_t l_offset;      // L words (result low words before the L + H addition)
     uint32_t hc_offset;     // H spill words (2 per window)
     uint32_t vec_a, vec_b, vec_c;  // 16-byte aligned rows
     uint64_t batch;
@@ -104,6 +105,37 @@ __device__ __forceinline__ void mac<8>(uint32_t (&acc)[10], uint32_t a, const ui
           "r"(w[7]));
 }
 
+// Column form (Section 3.2's accumulate step): column q keeps a 64-bit sum
+// and a carry count.  One mad.wide adds the full 64-bit product; the sum
+// wrapped exactly when its high word decreased, since a product's high word
+// is at most 2^32 - 2.
+template <int Q>
+__device__ __forceinline__ void mac_cols(uint64_t (&acc)[Q], uint32_t (&car)[Q], uint32_t a,
+                                         const uint32_t (&w)[Q]) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const uint32_t old_hi = (uint32_t)(acc[q] >> 32);
+        asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(a), "r"(w[q]));
+        car[q] += (uint32_t)(acc[q] >> 32) < old_hi;
+    }
+}
+
+// Window value sum_q (acc[q] + car[q] 2^64) 2^{32q} as Q+2 words.
+template <int Q>
+__device__ __forceinline__ void cols_to_words(const uint64_t (&acc)[Q], const uint32_t (&car)[Q],
+                                              uint32_t (&out)[Q + 2]) {
+    uint64_t c = 0;
+#pragma unroll
+    for (int q = 0; q < Q + 2; ++q) {
+        uint64_t v = c;
+        if (q < Q) v += (uint32_t)acc[q];
+        if (q >= 1 && q <= Q) v += (uint32_t)(acc[q - 1] >> 32);
+        if (q >= 2) v += car[q - 2];
+        out[q] = (uint32_t)v;
+        c = v >> 32;
+    }
+}
+
 template <int Q>
 __device__ __forceinline__ void ld_words(const uint32_t *S, uint32_t x, uint32_t (&v)[Q]) {
 #pragma unroll
@@ -124,31 +156,40 @@ __device__ __forceinline__ void st_words(uint32_t *S, uint32_t x, const uint32_t
 // Window starting at column k: sum over i in [ilo, ilo + steps) of
 // A_i * B[k-i .. k-i+Q).  B's logical index x lives at phys(x + Q).
 // ilo, k and steps are multiples of Q.
-template <int Q>
+template <int Q, bool COLS>
 __device__ __forceinline__ void conv_window(const uint32_t *As, const uint32_t *Bs, uint32_t k,
                                             uint32_t ilo, uint32_t steps, uint32_t (&acc)[Q + 2]) {
+    uint64_t cacc[Q];
+    uint32_t ccar[Q];
 #pragma unroll
     for (int q = 0; q < Q + 2; ++q) acc[q] = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        cacc[q] = 0;
+        ccar[q] = 0;
+    }
     // x0 + Q = (k - i0) + Q: the offset-Q index of the upper B chunk of the block.
     uint32_t xb = k - ilo + Q;
-    uint32_t bhi[Q], blo[Q], av[Q];
+    uint32_t bhi[Q], blo[Q], av[4];
     ld_words<Q>(Bs, xb, bhi);
     for (uint32_t i0 = ilo; i0 < ilo + steps; i0 += Q, xb -= Q) {
-        ld_words<Q>(As, i0, av);
         ld_words<Q>(Bs, xb - Q, blo);
 #pragma unroll
         for (int s = 0; s < Q; ++s) {
+            if (s % 4 == 0) ld_words<4>(As, i0 + s, av);  // A four words at a time
             uint32_t w[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 const int idx = Q - s + q;  // into (blo, bhi): B[k - i0 - s + q]
                 w[q] = idx < Q ? blo[idx] : bhi[idx - Q];
             }
-            mac<Q>(acc, av[s], w);
+            if constexpr (COLS) mac_cols<Q>(cacc, ccar, av[s % 4], w);
+            else mac<Q>(acc, av[s % 4], w);
         }
 #pragma unroll
         for (int q = 0; q < Q; ++q) bhi[q] = blo[q];
     }
+    if constexpr (COLS) cols_to_words<Q>(cacc, ccar, acc);
 }
 
 // Copies n words of a global row into shared memory at logical offset `off`
@@ -168,7 +209,7 @@ __device__ __forceinline__ void stage_row(uint32_t *S, const uint32_t *row, uint
     }
 }
 
-template <int Q>
+template <int Q, bool COLS>
 __global__ void __launch_bounds__(kQuadMaxThreads) k_mul_quad(QuadArgs p) {
     extern __shared__ __align__(16) uint32_t smem[];
     const uint32_t slot = threadIdx.x / p.group, t = threadIdx.x - slot * p.group;
@@ -176,7 +217,7 @@ __global__ void __launch_bounds__(kQuadMaxThreads) k_mul_quad(QuadArgs p) {
     const bool live = inst < p.batch;
     uint32_t *As = smem + slot * p.inst_words;
     uint32_t *Bs = As + p.ab_words;
-    uint32_t *Ls = As;                  // L reuses the operand region after the products
+    uint32_t *Ls = As + p.l_offset;     // L, then the H spill words
     uint32_t *Hc = As + p.hc_offset;
     uint32_t *flags = smem + p.ipb * p.inst_words;
 
@@ -186,40 +227,36 @@ __global__ void __launch_bounds__(kQuadMaxThreads) k_mul_quad(QuadArgs p) {
     stage_row(Bs, p.b + inst * p.nb, p.nb, Q, p.nbp + Q, p.vec_b, live, t, p.group);
     __syncthreads();
 
-    // q2: the products of this thread's unit (one or two windows).
+    // q2/q3: the products of this thread's unit (one or two windows); each
+    // window publishes its low words to L and its two spill words to H
+    // (Fig. 5) as soon as it is done.  L has its own region, so no barrier
+    // is needed first and nothing stays live across windows.
     const uint32_t R = p.nbp / Q;               // windows in each sloped region
     const uint32_t plateau = (p.nap - p.nbp) / Q;
-    uint32_t k0 = 0, k1 = 0, nwin = 0;
-    uint32_t acc0[Q + 2], acc1[Q + 2];
     if (t < p.units) {
+        uint32_t acc[Q + 2];
+        auto publish = [&](uint32_t k) {
+            st_words<Q>(Ls, k, acc);
+            *reinterpret_cast<uint2 *>(Hc + 2 * (k / Q)) = make_uint2(acc[Q], acc[Q + 1]);
+        };
         if (t < R / 2) {                        // rising pair
-            k0 = t * Q;
-            k1 = (R - 1 - t) * Q;
-            nwin = 2;
-            conv_window<Q>(As, Bs, k0, 0, k0 + Q, acc0);
-            conv_window<Q>(As, Bs, k1, 0, k1 + Q, acc1);
+            const uint32_t k0 = t * Q, k1 = (R - 1 - t) * Q;
+            conv_window<Q, COLS>(As, Bs, k0, 0, k0 + Q, acc);
+            publish(k0);
+            conv_window<Q, COLS>(As, Bs, k1, 0, k1 + Q, acc);
+            publish(k1);
         } else if (t < R / 2 + plateau) {       // plateau window
-            k0 = p.nbp + (t - R / 2) * Q;
-            nwin = 1;
-            conv_window<Q>(As, Bs, k0, k0 - p.nbp, p.nbp + Q, acc0);
+            const uint32_t k0 = p.nbp + (t - R / 2) * Q;
+            conv_window<Q, COLS>(As, Bs, k0, k0 - p.nbp, p.nbp + Q, acc);
+            publish(k0);
         } else {                                // falling pair
             const uint32_t r = t - R / 2 - plateau;
-            k0 = p.nap + r * Q;
-            k1 = p.nap + (R - 1 - r) * Q;
-            nwin = 2;
-            conv_window<Q>(As, Bs, k0, k0 - p.nbp, p.nap - (k0 - p.nbp), acc0);
-            conv_window<Q>(As, Bs, k1, k1 - p.nbp, p.nap - (k1 - p.nbp), acc1);
+            const uint32_t k0 = p.nap + r * Q, k1 = p.nap + (R - 1 - r) * Q;
+            conv_window<Q, COLS>(As, Bs, k0, k0 - p.nbp, p.nap - (k0 - p.nbp), acc);
+            publish(k0);
+            conv_window<Q, COLS>(As, Bs, k1, k1 - p.nbp, p.nap - (k1 - p.nbp), acc);
+            publish(k1);
         }
-    }
-    __syncthreads();
-    // q3: publish low words to L and the two spill words to H (Fig. 5).
-    if (nwin >= 1) {
-        st_words<Q>(Ls, k0, acc0);
-        *reinterpret_cast<uint2 *>(Hc + 2 * (k0 / Q)) = make_uint2(acc0[Q], acc0[Q + 1]);
-    }
-    if (nwin == 2) {
-        st_words<Q>(Ls, k1, acc1);
-        *reinterpret_cast<uint2 *>(Hc + 2 * (k1 / Q)) = make_uint2(acc1[Q], acc1[Q + 1]);
     }
     __syncthreads();
 
@@ -277,7 +314,7 @@ __global__ void __launch_bounds__(kQuadMaxThreads) k_mul_quad(QuadArgs p) {
 uint32_t roundup(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
 
 struct Geometry {
-    uint32_t nap, nbp, units, group, ipb, inst_words, ab_words, hc_offset, block, smem;
+    uint32_t nap, nbp, units, group, ipb, inst_words, ab_words, l_offset, hc_offset, block, smem;
 };
 
 Geometry geometry(uint32_t na, uint32_t nb, uint32_t Q, uint32_t cta_target) {
@@ -293,24 +330,26 @@ Geometry geometry(uint32_t na, uint32_t nb, uint32_t Q, uint32_t cta_target) {
         g.group = roundup(g.units, 32);
     }
     g.ipb = g.group < cta_target ? cta_target / g.group : 1;
-    // A at [0, phys_size(nap)), B (logical -Q .. nbp+Q) after it; L reuses
-    // both; H spill words follow.
+    // A at [0, phys_size(nap)), B (logical -Q .. nbp+Q) after it, then L
+    // (nap + nbp words) and the H spill words (2 per window).
     const uint32_t a_words = roundup(phys_size(g.nap), 4);
     const uint32_t b_words = roundup(phys_size(g.nbp + 2 * Q), 4);
     const uint32_t l_words = roundup(phys_size(g.nap + g.nbp), 4);
     g.ab_words = a_words;
-    const uint32_t region = a_words + b_words > l_words ? a_words + b_words : l_words;
-    g.hc_offset = region;
+    g.l_offset = a_words + b_words;
+    g.hc_offset = g.l_offset + l_words;
     const uint32_t windows = (g.nap + g.nbp) / Q;
-    g.inst_words = roundup(region + 2 * windows, 4);
+    g.inst_words = roundup(g.hc_offset + 2 * windows, 4);
     g.block = g.group * g.ipb;
     g.smem = 4 * (g.inst_words * g.ipb + 32);
     return g;
 }
 
+// Window size by the longer operand, from timings on GB300 (4 vs 8 at each
+// size of the sweep): 4 wins only at 256 and 512 limbs.
 uint32_t default_q(uint32_t na, uint32_t nb) {
     (void)nb;
-    return na <= 64 ? 4 : 8;
+    return (na > 128 && na <= 512) ? 4 : 8;
 }
 
 }  // namespace
@@ -325,7 +364,8 @@ bn_status quad_configure(QuadConfig &cfg, uint32_t na, uint32_t nb, const bn_tun
     const uint32_t hi = na > nb ? na : nb, lo = na > nb ? nb : na;
     cfg.q = default_q(hi, lo);
     if (t) {
-        if (t->reserved[0] || t->reserved[1]) return BN_EINVAL;
+        if (t->reserved || t->variant > 2) return BN_EINVAL;
+        if (t->variant) cfg.cols = t->variant == 2;
         if (t->limbs_per_thread) {
             if (t->limbs_per_thread != 4 && t->limbs_per_thread != 8) return BN_EINVAL;
             cfg.q = t->limbs_per_thread;
@@ -358,6 +398,7 @@ cudaError_t quad_launch(const QuadConfig &cfg, const uint32_t *a, const uint32_t
     args.ipb = g.ipb;
     args.inst_words = g.inst_words;
     args.ab_words = g.ab_words;
+    args.l_offset = g.l_offset;
     args.hc_offset = g.hc_offset;
     args.vec_a = (na % 4 == 0) && ((uintptr_t)a % 16 == 0);
     args.vec_b = (nb % 4 == 0) && ((uintptr_t)b % 16 == 0);
@@ -366,12 +407,15 @@ cudaError_t quad_launch(const QuadConfig &cfg, const uint32_t *a, const uint32_t
     const uint64_t grid = (batch + g.ipb - 1) / g.ipb;
     if (grid > 0x7fffffffull) return cudaErrorInvalidConfiguration;
     cudaError_t e;
+    const void *kern = cfg.q == 4 ? (cfg.cols ? (const void *)k_mul_quad<4, true> : (const void *)k_mul_quad<4, false>)
+                                  : (cfg.cols ? (const void *)k_mul_quad<8, true> : (const void *)k_mul_quad<8, false>);
+    if ((e = allow_max_smem(kern)) != cudaSuccess) return e;
     if (cfg.q == 4) {
-        if ((e = allow_max_smem((const void *)k_mul_quad<4>)) != cudaSuccess) return e;
-        k_mul_quad<4><<<(unsigned)grid, g.block, g.smem, st>>>(args);
+        if (cfg.cols) k_mul_quad<4, true><<<(unsigned)grid, g.block, g.smem, st>>>(args);
+        else k_mul_quad<4, false><<<(unsigned)grid, g.block, g.smem, st>>>(args);
     } else {
-        if ((e = allow_max_smem((const void *)k_mul_quad<8>)) != cudaSuccess) return e;
-        k_mul_quad<8><<<(unsigned)grid, g.block, g.smem, st>>>(args);
+        if (cfg.cols) k_mul_quad<8, true><<<(unsigned)grid, g.block, g.smem, st>>>(args);
+        else k_mul_quad<8, false><<<(unsigned)grid, g.block, g.smem, st>>>(args);
     }
     return cudaGetLastError();
 }
