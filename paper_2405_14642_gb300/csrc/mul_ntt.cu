@@ -100,6 +100,23 @@ struct MontField {
         const uint64_t h = (uint64_t)m1 * PH + (sm >> 32);
         return hi + h + ((x0 | x1) != 0u);
     }
+    // a * b / 2^64 mod P for any 64-bit a and a canonical b < P (a twiddle):
+    // a*b < P 2^64 keeps the result in [0, 2P); the cross sum takes one more
+    // add because a's high word may use all 32 bits.
+    __device__ static __forceinline__ uint64_t mulw(uint64_t a, uint64_t b) {
+        const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+        const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+        const uint64_t p00 = (uint64_t)a0 * b0;
+        const uint64_t t1 = (uint64_t)a1 * b0 + (p00 >> 32);
+        const uint64_t t2 = (uint64_t)a0 * b1 + (uint32_t)t1;
+        const uint64_t hi = (uint64_t)a1 * b1 + (t1 >> 32) + (t2 >> 32);
+        const uint32_t x0 = (uint32_t)p00, x1 = (uint32_t)t2;
+        const uint32_t m0 = 0u - x0;
+        const uint32_t m1 = x0 * PH - x1 - (x0 != 0u);
+        const uint64_t sm = (uint64_t)m0 * PH + m1;
+        const uint64_t h = (uint64_t)m1 * PH + (sm >> 32);
+        return hi + h + ((x0 | x1) != 0u);
+    }
 };
 
 using FieldP1 = MontField<4179340454199820289ull>;  // 29 * 2^57 + 1 (PrimeField64)
@@ -166,11 +183,13 @@ __device__ __forceinline__ uint32_t tw_index(uint32_t base, uint32_t m, uint32_t
 }
 
 // KK decimation-in-frequency stages with half-sizes H, H/2, ..., H >> (KK-1).
-template <class F, int KK>
+// UNIT: the group step is 1, so the last stage's twiddle is 1.  The
+// difference u - v + 2P (< 4P) goes to the twiddle multiply unreduced.
+template <class F, int KK, bool UNIT>
 __device__ __forceinline__ void dif_pass(uint64_t *buf, uint32_t L, uint32_t H, const uint64_t *tw) {
     constexpr int E = 1 << KK;
-    const uint32_t step = H >> (KK - 1);
-    const uint32_t lstep = __ffs(step) - 1;
+    const uint32_t step = UNIT ? 1u : H >> (KK - 1);
+    const uint32_t lstep = UNIT ? 0u : __ffs(step) - 1;
     for (uint32_t g = threadIdx.x; g < (L >> KK); g += blockDim.x) {
         const uint32_t base = ((g >> lstep) << (lstep + KK)) | (g & (step - 1));
         uint64_t x[E];
@@ -179,16 +198,16 @@ __device__ __forceinline__ void dif_pass(uint64_t *buf, uint32_t L, uint32_t H, 
 #pragma unroll
         for (int st = 0; st < KK; ++st) {
             const uint32_t hm = 1u << (KK - 1 - st), h = hm * step;
+            const bool trivial = UNIT && hm == 1;
             uint64_t w[E / 2];
 #pragma unroll
-            for (int m = 0; m < (int)hm; ++m) w[m] = h == 1 ? 0 : __ldg(tw + tw_index(base, m, step, h));
+            for (int m = 0; m < (int)hm; ++m) w[m] = trivial ? 0 : __ldg(tw + tw_index(base, m, step, h));
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 if (m & hm) continue;
                 const uint64_t u = x[m], v = x[m + hm];
                 x[m] = F::add(u, v);
-                const uint64_t d = F::sub(u, v);
-                x[m + hm] = h == 1 ? d : F::mul(d, w[m & (hm - 1)]);
+                x[m + hm] = trivial ? F::sub(u, v) : F::mulw(u + F::TWO_P - v, w[m & (hm - 1)]);
             }
         }
 #pragma unroll
@@ -197,11 +216,12 @@ __device__ __forceinline__ void dif_pass(uint64_t *buf, uint32_t L, uint32_t H, 
 }
 
 // KK decimation-in-time stages with half-sizes h0, 2 h0, ..., h0 << (KK-1).
-template <class F, int KK>
+// UNIT: h0 = 1, so the first stage's twiddle is 1.
+template <class F, int KK, bool UNIT>
 __device__ __forceinline__ void dit_pass(uint64_t *buf, uint32_t L, uint32_t h0, const uint64_t *tw) {
     constexpr int E = 1 << KK;
-    const uint32_t step = h0;
-    const uint32_t lstep = __ffs(step) - 1;
+    const uint32_t step = UNIT ? 1u : h0;
+    const uint32_t lstep = UNIT ? 0u : __ffs(step) - 1;
     for (uint32_t g = threadIdx.x; g < (L >> KK); g += blockDim.x) {
         const uint32_t base = ((g >> lstep) << (lstep + KK)) | (g & (step - 1));
         uint64_t x[E];
@@ -210,14 +230,15 @@ __device__ __forceinline__ void dit_pass(uint64_t *buf, uint32_t L, uint32_t h0,
 #pragma unroll
         for (int st = 0; st < KK; ++st) {
             const uint32_t hm = 1u << st, h = hm * step;
+            const bool trivial = UNIT && hm == 1;
             uint64_t w[E / 2];
 #pragma unroll
-            for (int m = 0; m < (int)hm; ++m) w[m] = h == 1 ? 0 : __ldg(tw + tw_index(base, m, step, h));
+            for (int m = 0; m < (int)hm; ++m) w[m] = trivial ? 0 : __ldg(tw + tw_index(base, m, step, h));
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 if (m & hm) continue;
                 const uint64_t u = x[m];
-                const uint64_t v = h == 1 ? x[m + hm] : F::mul(x[m + hm], w[m & (hm - 1)]);
+                const uint64_t v = trivial ? x[m + hm] : F::mul(x[m + hm], w[m & (hm - 1)]);
                 x[m] = F::add(u, v);
                 x[m + hm] = F::sub(u, v);
             }
@@ -228,40 +249,49 @@ __device__ __forceinline__ void dit_pass(uint64_t *buf, uint32_t L, uint32_t h0,
 }
 
 template <class F>
-__device__ void forward2(const NttArgs &p, const uint64_t *tw, uint64_t *A, uint64_t *B) {
-    uint32_t H = p.L >> 1, left = p.logL;
-    while (left >= (uint32_t)kRadixLog) {
-        dif_pass<F, kRadixLog>(A, p.L, H, tw);
-        dif_pass<F, kRadixLog>(B, p.L, H, tw);
+__device__ void forward2(uint32_t L, uint32_t logL, const uint64_t *tw, uint64_t *A, uint64_t *B) {
+    uint32_t H = L >> 1, left = logL;
+    while (left > (uint32_t)kRadixLog) {  // these passes have step >= 2
+        dif_pass<F, kRadixLog, false>(A, L, H, tw);
+        dif_pass<F, kRadixLog, false>(B, L, H, tw);
         __syncthreads();
         H >>= kRadixLog;
         left -= kRadixLog;
     }
-    if (left == 2) {
-        dif_pass<F, 2>(A, p.L, H, tw);
-        dif_pass<F, 2>(B, p.L, H, tw);
-        __syncthreads();
-    } else if (left == 1) {
-        dif_pass<F, 1>(A, p.L, H, tw);
-        dif_pass<F, 1>(B, p.L, H, tw);
-        __syncthreads();
+    if (left == 3) {                       // the last pass has step 1
+        dif_pass<F, 3, true>(A, L, H, tw);
+        dif_pass<F, 3, true>(B, L, H, tw);
+    } else if (left == 2) {
+        dif_pass<F, 2, true>(A, L, H, tw);
+        dif_pass<F, 2, true>(B, L, H, tw);
+    } else {
+        dif_pass<F, 1, true>(A, L, H, tw);
+        dif_pass<F, 1, true>(B, L, H, tw);
     }
+    __syncthreads();
 }
 
 template <class F>
-__device__ void inverse(const NttArgs &p, const uint64_t *tw, uint64_t *B) {
-    uint32_t h0 = 1, left = p.logL;
+__device__ void inverse(uint32_t L, uint32_t logL, const uint64_t *tw, uint64_t *B) {
+    uint32_t left = logL;
+    const uint32_t first = left >= (uint32_t)kRadixLog ? (uint32_t)kRadixLog : left;
+    if (first == 3) dit_pass<F, 3, true>(B, L, 1, tw);   // the first pass has h0 = 1
+    else if (first == 2) dit_pass<F, 2, true>(B, L, 1, tw);
+    else dit_pass<F, 1, true>(B, L, 1, tw);
+    __syncthreads();
+    uint32_t h0 = 1u << first;
+    left -= first;
     while (left >= (uint32_t)kRadixLog) {
-        dit_pass<F, kRadixLog>(B, p.L, h0, tw);
+        dit_pass<F, kRadixLog, false>(B, L, h0, tw);
         __syncthreads();
         h0 <<= kRadixLog;
         left -= kRadixLog;
     }
     if (left == 2) {
-        dit_pass<F, 2>(B, p.L, h0, tw);
+        dit_pass<F, 2, false>(B, L, h0, tw);
         __syncthreads();
     } else if (left == 1) {
-        dit_pass<F, 1>(B, p.L, h0, tw);
+        dit_pass<F, 1, false>(B, L, h0, tw);
         __syncthreads();
     }
 }
@@ -276,11 +306,11 @@ __device__ void prime_product(const NttArgs &p, const PrimeTab &tb, const uint32
         load_fold<F>(p, tb, arow, p.na, s, A);   // n1: digits (and the folded first stage)
         load_fold<F>(p, tb, brow, p.nb, s, B);
         __syncthreads();
-        forward2<F>(p, tb.twf, A, B);            // n2: forward transforms
+        forward2<F>(p.L, p.logL, tb.twf, A, B);  // n2: forward transforms
         for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x)   // n3: pointwise
             B[phys(j)] = F::mul(A[phys(j)], B[phys(j)]);
         __syncthreads();
-        inverse<F>(p, tb.twi, B);                // n4: inverse transform (unscaled)
+        inverse<F>(p.L, p.logL, tb.twi, B);      // n4: inverse transform (unscaled)
         if (p.S > 1) {
             for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) Z[s * p.L + j] = B[phys(j)];
             __syncthreads();
@@ -691,12 +721,12 @@ __global__ void k_noalloc_tables(uint64_t *tab, uint32_t L, uint32_t S, uint64_t
                 const uint32_t h = 1u << (31 - __clz(i)), j = i - h;
                 v = form_pow<F>(form_pow<F>(inv ? wLi : wL, L / (2 * h), one), j, one);
             }
-            tab[idx] = v;
+            tab[idx] = F::canon(v);
         } else {
             const uint32_t k = idx - 2 * L, inv = k >= S * L, r = k - inv * S * L;
             const uint32_t sidx = r / L, j = r - sidx * L;
             const uint64_t w = form_pow<F>(inv ? wNi : wN, (uint64_t)j * sidx, one);
-            tab[idx] = inv ? F::mul(scale, w) : w;
+            tab[idx] = F::canon(inv ? F::mul(scale, w) : w);
         }
     }
 }

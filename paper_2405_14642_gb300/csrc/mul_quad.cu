@@ -153,9 +153,31 @@ __device__ __forceinline__ void st_words(uint32_t *S, uint32_t x, const uint32_t
             make_uint4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
 }
 
+// Q steps i = i0 .. i0+Q-1 of a window: the B window for step s is
+// B[k-i0-s .. k-i0-s+Q), taken from the chunk pair (lo, hi) = B[k-i0-Q .. k-i0+Q).
+template <int Q, bool COLS>
+__device__ __forceinline__ void window_block(const uint32_t *As, uint32_t i0, const uint32_t (&lo)[Q],
+                                             const uint32_t (&hi)[Q], uint32_t (&acc)[Q + 2],
+                                             uint64_t (&cacc)[Q], uint32_t (&ccar)[Q]) {
+    uint32_t av[4];
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+        if (s % 4 == 0) ld_words<4>(As, i0 + s, av);  // A four words at a time
+        uint32_t w[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int idx = Q - s + q;
+            w[q] = idx < Q ? lo[idx] : hi[idx - Q];
+        }
+        if constexpr (COLS) mac_cols<Q>(cacc, ccar, av[s % 4], w);
+        else mac<Q>(acc, av[s % 4], w);
+    }
+}
+
 // Window starting at column k: sum over i in [ilo, ilo + steps) of
 // A_i * B[k-i .. k-i+Q).  B's logical index x lives at phys(x + Q).
-// ilo, k and steps are multiples of Q.
+// ilo, k and steps are multiples of Q.  Blocks alternate between two chunk
+// buffers, so the chunk that moves from "lower" to "upper" is never copied.
 template <int Q, bool COLS>
 __device__ __forceinline__ void conv_window(const uint32_t *As, const uint32_t *Bs, uint32_t k,
                                             uint32_t ilo, uint32_t steps, uint32_t (&acc)[Q + 2]) {
@@ -168,26 +190,22 @@ __device__ __forceinline__ void conv_window(const uint32_t *As, const uint32_t *
         cacc[q] = 0;
         ccar[q] = 0;
     }
-    // x0 + Q = (k - i0) + Q: the offset-Q index of the upper B chunk of the block.
-    uint32_t xb = k - ilo + Q;
-    uint32_t bhi[Q], blo[Q], av[4];
-    ld_words<Q>(Bs, xb, bhi);
-    for (uint32_t i0 = ilo; i0 < ilo + steps; i0 += Q, xb -= Q) {
-        ld_words<Q>(Bs, xb - Q, blo);
-#pragma unroll
-        for (int s = 0; s < Q; ++s) {
-            if (s % 4 == 0) ld_words<4>(As, i0 + s, av);  // A four words at a time
-            uint32_t w[Q];
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const int idx = Q - s + q;  // into (blo, bhi): B[k - i0 - s + q]
-                w[q] = idx < Q ? blo[idx] : bhi[idx - Q];
-            }
-            if constexpr (COLS) mac_cols<Q>(cacc, ccar, av[s % 4], w);
-            else mac<Q>(acc, av[s % 4], w);
-        }
-#pragma unroll
-        for (int q = 0; q < Q; ++q) bhi[q] = blo[q];
+    // xb = (k - i0) + Q: the offset-Q index of the current block's upper chunk.
+    uint32_t xb = k - ilo + Q, i0 = ilo;
+    const uint32_t nblk = steps / Q;
+    uint32_t c0[Q], c1[Q];
+    ld_words<Q>(Bs, xb, c1);
+    for (uint32_t b = 0; b + 1 < nblk; b += 2) {
+        ld_words<Q>(Bs, xb - Q, c0);
+        window_block<Q, COLS>(As, i0, c0, c1, acc, cacc, ccar);
+        ld_words<Q>(Bs, xb - 2 * Q, c1);
+        window_block<Q, COLS>(As, i0 + Q, c1, c0, acc, cacc, ccar);
+        xb -= 2 * Q;
+        i0 += 2 * Q;
+    }
+    if (nblk & 1) {
+        ld_words<Q>(Bs, xb - Q, c0);
+        window_block<Q, COLS>(As, i0, c0, c1, acc, cacc, ccar);
     }
     if constexpr (COLS) cols_to_words<Q>(cacc, ccar, acc);
 }
