@@ -317,6 +317,10 @@ def run_gpu(args, rank, world, local_rank):
     ms_per_step = max_ms / args.steps
     gpu_launches = args.steps * len(ops)
 
+    mixed = None
+    if args.mixed_items > 0:
+        mixed = run_mixed(args, torch, bn, dev, rank)
+
     # End to end: host arrays in pinned memory through the host-buffer entry point.
     e2e = None
     if args.e2e_steps > 0:
@@ -370,7 +374,52 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": roof, "rooflines": rooflines, "breakdown": rows,
         "imad_probe": peak_info, "clocks": clocks, "gpu_launches": gpu_launches,
         "e2e": e2e, "cpu_baseline": cpu, "impl": "ours", "skipped_ops": skipped,
+        "mixed": mixed,
     }
+
+
+def run_mixed(args, torch, bn, dev, rank):
+    """Mixed-size batch (200k operations by default, 70% products / 30% sums,
+    limb counts log-uniform in 32..8192 for each operand, 5% edge cases):
+    the batched graph (autotuned) against plain per-item launches of the same
+    items, same kernels; results must be identical."""
+    items, a, b, c_limbs = workloads.mixed_workload(args.mixed_items,
+                                                    seed=workloads.seed_for(3, 0) + 7919 * rank)
+    ta = torch.from_numpy(a.view(np.int32)).to(dev)
+    tb = torch.from_numpy(b.view(np.int32)).to(dev)
+    tc = torch.empty(c_limbs, dtype=torch.int32, device=dev)
+    n_mul = int((items["op"] != 0).sum())
+    stream = torch.cuda.current_stream(dev)
+    out, results = {}, {}
+    for name, flags, steps in (("batched", bn.BN_BATCH_AUTOTUNE, args.mixed_steps),
+                               ("plain", bn.BN_BATCH_PLAIN, 1)):
+        t = time.perf_counter()
+        batch = bn.Batch(items, flags)
+        create_ms = (time.perf_counter() - t) * 1e3
+        tc.fill_(-1)
+        batch.execute(ta, tb, tc, stream=stream)
+        torch.cuda.synchronize()
+        results[name] = tc.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            batch.execute(ta, tb, tc, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        info = batch.info
+        batch.close()
+        out[name] = {"ms": round(ms, 3), "ops_per_s": len(items) / (ms * 1e-3),
+                     "mults_per_s": n_mul / (ms * 1e-3), "launches": info["launches"],
+                     "classes": info["classes"], "create_ms": round(create_ms, 1), "steps": steps,
+                     "items_by_kernel": {k: info[k] for k in ("items_add", "items_quad",
+                                                              "items_ntt64", "items_crt")}}
+    identical = bool(torch.equal(results["batched"], results["plain"]))
+    return {"workload": f"{len(items)} ops, 70% mul (auto quad/NTT) / 30% add, limbs log-uniform "
+                        "32..8192 per operand, 5% edge cases",
+            "batched": out["batched"], "plain": out["plain"],
+            "speedup": round(out["plain"]["ms"] / out["batched"]["ms"], 2),
+            "results_identical": identical}
 
 
 def run_e2e(args, torch, bn, ops, hosts, dev):
@@ -538,6 +587,9 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-step-budget", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mixed-items", type=int, default=200000,
+                    help="operations in the mixed-size batch comparison (0 = skip)")
+    ap.add_argument("--mixed-steps", type=int, default=5)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -69,7 +69,10 @@ typedef enum bn_op {
     BN_OP_MUL_NTT64 = 2,
     /* Section 4 with 32-bit digits over two primes (29*2^57 + 1 and
      * 2^64 - 2^32 + 1), recombined by the Chinese remainder theorem. */
-    BN_OP_MUL_NTT_CRT = 3
+    BN_OP_MUL_NTT_CRT = 3,
+    /* Batch items only: multiplication by whichever of the above a mixed-size
+     * batch's cost model finds fastest for the item's sizes. */
+    BN_OP_MUL_AUTO = 4
 } bn_op;
 
 /* Largest limb counts per operand (256K bits for the products, 512K bits for
@@ -161,6 +164,56 @@ bn_status bn_mul_ntt(const uint32_t *a, const uint32_t *b, uint32_t *c,
 #define BN_NOALLOC_MAX_LIMBS 8192u
 bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, uint32_t *c,
                              uint32_t na, uint32_t nb, uint64_t batch, int crt, void *stream);
+
+/* ---- mixed-size batches ------------------------------------------------
+ * Many independent operations of different sizes and kinds in one call.  The
+ * paper evaluates one size per kernel launch (Section 6); this form runs a
+ * whole mixed workload as one CUDA graph: items are grouped into size classes,
+ * each class is one persistent kernel whose CTAs take items from a device
+ * work queue (largest first), and the classes run concurrently.  A cost
+ * model, calibrated at creation when BN_BATCH_AUTOTUNE is set (otherwise
+ * built-in GB300 timings), picks the window size and CTA size of each
+ * schoolbook class and, for BN_OP_MUL_AUTO items, schoolbook or transform.
+ *
+ * Layout: all a operands live in one flat u32 array, likewise b and c; item
+ * i reads a[a_offset .. a_offset+na) and b[b_offset .. b_offset+nb) and
+ * writes c[c_offset .. c_offset + out) with out = max(na,nb)+1 (add) or
+ * na+nb (products).  Result ranges must not overlap each other or the
+ * operands (not checked).  Sizes: 1..BN_ADD_MAX_LIMBS for add,
+ * 1..BN_MUL_MAX_LIMBS for products.
+ * bn_batch_create copies the item list, allocates device memory for it,
+ * the work queues and the transform tables/scratch, and captures the graph
+ * (on internal streams); it must not be called during stream capture.
+ * bn_batch_execute binds the flat arrays and enqueues the graph on `stream`;
+ * it must not overlap another execution of the same batch.
+ * BN_BATCH_PLAIN executes the same item list as one ordinary launch per
+ * item (same kernel choices, no graph), the baseline the batched form is
+ * measured against. */
+typedef struct bn_batch_item {
+    uint32_t op;         /* bn_op */
+    uint32_t na, nb;     /* limb counts */
+    uint32_t reserved;   /* must be zero */
+    uint64_t a_offset, b_offset, c_offset;  /* limb offsets into the flat arrays */
+} bn_batch_item;
+
+typedef struct bn_batch_info {
+    uint32_t classes;        /* size classes (kernel launches in the graph) */
+    uint32_t launches;       /* kernel launches per execution (plain: one per item) */
+    uint64_t items_add, items_quad, items_ntt64, items_crt;  /* after BN_OP_MUL_AUTO */
+    double tune_ms;          /* time spent calibrating at creation */
+} bn_batch_info;
+
+typedef struct bn_batch_s *bn_batch;
+
+#define BN_BATCH_AUTOTUNE 1u
+#define BN_BATCH_PLAIN 2u
+
+bn_status bn_batch_create(bn_batch *out, const bn_batch_item *items, uint64_t count,
+                          uint32_t flags);
+bn_status bn_batch_execute(bn_batch batch, const uint32_t *a, const uint32_t *b, uint32_t *c,
+                           void *stream);
+bn_status bn_batch_get_info(bn_batch batch, bn_batch_info *info);
+bn_status bn_batch_destroy(bn_batch batch);
 
 /* Static description of a status code. */
 const char *bn_status_str(bn_status s);

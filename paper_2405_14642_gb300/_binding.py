@@ -16,7 +16,11 @@ import numpy as np
 from . import _build
 
 BN_OK, BN_EINVAL, BN_ENOMEM, BN_ECUDA, BN_EUNSUPPORTED, BN_ETIMEOUT = range(6)
-BN_OP_ADD, BN_OP_MUL_QUAD, BN_OP_MUL_NTT64, BN_OP_MUL_NTT_CRT = range(4)
+BN_OP_ADD, BN_OP_MUL_QUAD, BN_OP_MUL_NTT64, BN_OP_MUL_NTT_CRT, BN_OP_MUL_AUTO = range(5)
+BN_BATCH_AUTOTUNE, BN_BATCH_PLAIN = 1, 2
+# Layout of struct bn_batch_item (include/bn.h), 40 bytes.
+BATCH_ITEM_DTYPE = np.dtype([("op", "<u4"), ("na", "<u4"), ("nb", "<u4"), ("reserved", "<u4"),
+                             ("a_offset", "<u8"), ("b_offset", "<u8"), ("c_offset", "<u8")])
 BN_ADD_MAX_LIMBS = 16384
 BN_MUL_MAX_LIMBS = 8192
 
@@ -32,6 +36,13 @@ class BnError(RuntimeError):
         text = lib.bn_status_str(status).decode() if lib else str(status)
         detail = lib.bn_last_error().decode() if lib else ""
         super().__init__(f"{where}: {text}" + (f" ({detail})" if detail else ""))
+
+
+class bn_batch_info(ctypes.Structure):
+    _fields_ = [("classes", ctypes.c_uint32), ("launches", ctypes.c_uint32),
+                ("items_add", ctypes.c_uint64), ("items_quad", ctypes.c_uint64),
+                ("items_ntt64", ctypes.c_uint64), ("items_crt", ctypes.c_uint64),
+                ("tune_ms", ctypes.c_double)]
 
 
 class bn_tuning(ctypes.Structure):
@@ -72,6 +83,10 @@ def load(build_if_missing: bool = False):
         "bn_last_error": ([], ctypes.c_char_p),
         "bn_version": ([], ctypes.c_int),
         "bn_mul_ntt_noalloc": ([u32p, u32p, u32p, u32, u32, u64, ctypes.c_int, vp], st),
+        "bn_batch_create": ([ctypes.POINTER(ctypes.c_void_p), vp, u64, u32], st),
+        "bn_batch_execute": ([vp, u32p, u32p, u32p, vp], st),
+        "bn_batch_get_info": ([vp, ctypes.POINTER(bn_batch_info)], st),
+        "bn_batch_destroy": ([vp], st),
         "bn_probe_int_throughput": ([ctypes.c_int, u32, u32, u32, u32p,
                                      ctypes.POINTER(ctypes.c_uint64), vp], st),
     }
@@ -263,3 +278,53 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """A bn_batch: a fixed list of mixed-size operations over flat arrays.
+
+    ``items`` is a numpy array of BATCH_ITEM_DTYPE (op, na, nb, offsets in
+    limbs into the flat a, b, c arrays).  ``execute`` runs them as one CUDA
+    graph (or, with BN_BATCH_PLAIN, as one launch per item)."""
+
+    def __init__(self, items: np.ndarray, flags: int = 0):
+        lib = load()
+        self._lib = lib
+        items = np.ascontiguousarray(items, dtype=BATCH_ITEM_DTYPE)
+        self.items = items
+        self._h = ctypes.c_void_p()
+        _check(lib.bn_batch_create(ctypes.byref(self._h), ctypes.c_void_p(items.ctypes.data),
+                                   items.shape[0], flags), "bn_batch_create")
+
+    @property
+    def info(self) -> dict:
+        inf = bn_batch_info()
+        _check(self._lib.bn_batch_get_info(self._h, ctypes.byref(inf)), "bn_batch_get_info")
+        return {k: getattr(inf, k) for k, _ in bn_batch_info._fields_}
+
+    def execute(self, a, b, c, stream=None):
+        """Run on flat device tensors (1-D, 32-bit limbs)."""
+        for t, name in ((a, "a"), (b, "b"), (c, "c")):
+            if not t.is_cuda or t.element_size() != 4 or not t.is_contiguous():
+                raise TypeError(f"{name} must be a contiguous 32-bit CUDA tensor")
+        _check(self._lib.bn_batch_execute(self._h, _ptr(a), _ptr(b), _ptr(c),
+                                          _stream_handle(stream, a.device)), "bn_batch_execute")
+        return c
+
+    def close(self):
+        if self._h:
+            _check(self._lib.bn_batch_destroy(self._h), "bn_batch_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -87,14 +87,12 @@ __global__ void __launch_bounds__(256) k_add_subwarp(AddArgs p) {
 // Teams of W whole warps (W <= 16), R rows of 32 chunks per warp.
 constexpr uint32_t kTeamMaxThreads = 512;
 
+// One instance by one team (warp w of the team, team_in_cta within the CTA).
+// Every thread of the CTA calls this together (it contains a barrier).
 template <int VEC, int R>
-__global__ void __launch_bounds__(kTeamMaxThreads) k_add_team(AddArgs p) {
-    __shared__ uint32_t warp_flags[kTeamMaxThreads / 32];
+__device__ __forceinline__ void add_team_instance(const AddArgs &p, uint64_t inst, bool inst_live,
+                                                  uint32_t team_in_cta, uint32_t w, uint32_t *warp_flags) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t team_in_cta = warp / p.warps_per_team;
-    const uint32_t w = warp - team_in_cta * p.warps_per_team;
-    const uint64_t inst = (uint64_t)blockIdx.x * p.teams_per_cta + team_in_cta;
-    const bool inst_live = inst < p.batch;
     const uint32_t j0 = w * R * 32 + lane;
 
     uint32_t s[R][VEC];
@@ -144,6 +142,46 @@ __global__ void __launch_bounds__(kTeamMaxThreads) k_add_team(AddArgs p) {
             store_chunk<VEC>(row, j, s[r]);
         }
     }
+}
+
+template <int VEC, int R>
+__global__ void __launch_bounds__(kTeamMaxThreads) k_add_team(AddArgs p) {
+    __shared__ uint32_t warp_flags[kTeamMaxThreads / 32];
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t team_in_cta = warp / p.warps_per_team;
+    const uint32_t w = warp - team_in_cta * p.warps_per_team;
+    const uint64_t inst = (uint64_t)blockIdx.x * p.teams_per_cta + team_in_cta;
+    add_team_instance<VEC, R>(p, inst, inst < p.batch, team_in_cta, w, warp_flags);
+}
+
+// Mixed-size batch of additions of one size class: team i of the grid takes
+// item i (items are sorted largest first); 32-bit loads, any sizes <= the
+// class maximum.
+template <int R>
+__global__ void __launch_bounds__(kTeamMaxThreads)
+    k_add_team_batch(const BatchItem *items, uint32_t count, const BatchBinding *bind,
+                     uint32_t warps_per_team, uint32_t teams_per_cta) {
+    __shared__ uint32_t warp_flags[kTeamMaxThreads / 32];
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t team_in_cta = warp / warps_per_team;
+    const uint32_t w = warp - team_in_cta * warps_per_team;
+    const uint64_t idx = (uint64_t)blockIdx.x * teams_per_cta + team_in_cta;
+    const bool live = idx < count;
+    BatchItem it{0, 0, 0, 1, 1};
+    if (live) it = items[idx];
+    AddArgs p{};
+    p.a = bind->a + it.off_a;
+    p.b = bind->b + it.off_b;
+    p.c = bind->c + it.off_c;
+    p.na = it.na;
+    p.nb = it.nb;
+    p.n = it.na > it.nb ? it.na : it.nb;
+    p.nout = p.n + 1;
+    p.chunks = p.n;
+    p.warps_per_team = warps_per_team;
+    p.teams_per_cta = teams_per_cta;
+    p.batch = 1;
+    add_team_instance<1, R>(p, 0, live, team_in_cta, w, warp_flags);
 }
 
 uint32_t next_pow2(uint32_t x) {
@@ -260,6 +298,40 @@ cudaError_t add_launch(const AddConfig &cfg, const uint32_t *a, const uint32_t *
     if (grid > 0x7fffffffull) return cudaErrorInvalidConfiguration;
     return vec == 4 ? launch_team_r<4>(R, args, block, grid, st)
                     : launch_team_r<1>(R, args, block, grid, st);
+}
+
+bn_status add_batch_class(AddClass &ac, uint32_t n_max) {
+    if (n_max == 0 || n_max > BN_ADD_MAX_LIMBS) return BN_EINVAL;
+    ac = AddClass{};
+    ac.n_max = n_max;
+    uint32_t R = 1, W = (n_max + 31) / 32;
+    while (W > 8 && R < kMaxRows1) {
+        R *= 2;
+        W = (n_max + 32 * R - 1) / (32 * R);
+    }
+    if (W > kTeamMaxThreads / 32) return BN_EUNSUPPORTED;
+    ac.rows = R;
+    ac.warps_per_team = W;
+    ac.teams_per_cta = 256 > 32 * W ? 256 / (32 * W) : 1;
+    ac.block = 32 * W * ac.teams_per_cta;
+    return BN_OK;
+}
+
+cudaError_t add_batch_launch(const AddClass &ac, const BatchItem *items, uint32_t count,
+                             const BatchBinding *bind, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const uint32_t grid = (count + ac.teams_per_cta - 1) / ac.teams_per_cta;
+#define BN_ADD_BATCH(RR)                                                                         \
+    case RR:                                                                                     \
+        k_add_team_batch<RR><<<grid, ac.block, 0, st>>>(items, count, bind, ac.warps_per_team,   \
+                                                        ac.teams_per_cta);                       \
+        break;
+    switch (ac.rows) {
+        BN_ADD_BATCH(1) BN_ADD_BATCH(2) BN_ADD_BATCH(4) BN_ADD_BATCH(8) BN_ADD_BATCH(16) BN_ADD_BATCH(32)
+    default: return cudaErrorInvalidConfiguration;
+    }
+#undef BN_ADD_BATCH
+    return cudaGetLastError();
 }
 
 }  // namespace bn

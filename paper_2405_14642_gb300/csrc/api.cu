@@ -163,8 +163,13 @@ cudaError_t allow_max_smem(const void *kernel) {
     auto key = std::make_pair(kernel, dev);
     if (done.count(key)) return cudaSuccess;
     int optin = 0;
+    cudaFuncAttributes fa{};
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    // The cap covers dynamic memory only; static plus dynamic must fit the opt-in limit.
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
     if (e == cudaSuccess) done[key] = true;
     return e;
 }

@@ -17,6 +17,20 @@ cudaError_t allow_max_smem(const void *kernel);
 // Records `what` as this host thread's bn_last_error() text.
 void record_error(const char *what);
 
+// ---- mixed-size batches ----------------------------------------------------
+// One operation of a batch: operands at the given limb offsets of the flat
+// a and b buffers, result at off_c of the flat c buffer.
+struct BatchItem {
+    uint64_t off_a, off_b, off_c;
+    uint32_t na, nb;
+};
+// Base pointers of the flat buffers, read by the batched kernels from device
+// memory so a captured graph can run on new buffers.
+struct BatchBinding {
+    const uint32_t *a, *b;
+    uint32_t *c;
+};
+
 // ---- addition (Section 2) -------------------------------------------------
 struct AddConfig {
     uint32_t na = 0, nb = 0, n = 0, nout = 0;
@@ -30,6 +44,14 @@ cudaError_t add_launch(const AddConfig &cfg, const uint32_t *a, const uint32_t *
 // Number of kernel launches one add_launch issues (for launch accounting).
 inline int add_launch_count() { return 1; }
 
+// Batched additions of one size class (both operands <= n_max limbs).
+struct AddClass {
+    uint32_t n_max = 0, rows = 1, warps_per_team = 1, teams_per_cta = 1, block = 32;
+};
+bn_status add_batch_class(AddClass &ac, uint32_t n_max);
+cudaError_t add_batch_launch(const AddClass &ac, const BatchItem *items, uint32_t count,
+                             const BatchBinding *bind, cudaStream_t stream);
+
 // ---- quadratic multiplication (Section 3) ---------------------------------
 struct QuadConfig {
     uint32_t na = 0, nb = 0, nout = 0;
@@ -42,6 +64,16 @@ bn_status quad_configure(QuadConfig &cfg, uint32_t na, uint32_t nb, const bn_tun
 cudaError_t quad_launch(const QuadConfig &cfg, const uint32_t *a, const uint32_t *b, uint32_t *c,
                         uint64_t batch, cudaStream_t stream);
 
+// Batched schoolbook products of one size class (longer operand <= n_max):
+// a persistent kernel whose CTAs take `ipb` items at a time from a work queue.
+struct QuadClass {
+    uint32_t q = 8, n_max = 0;
+    uint32_t group = 0, ipb = 0, block = 0, inst_words = 0, smem = 0, grid = 0;
+};
+bn_status quad_batch_class(QuadClass &qc, uint32_t q, uint32_t n_max, uint32_t cta_target);
+cudaError_t quad_batch_launch(const QuadClass &qc, const BatchItem *items, uint32_t count,
+                              uint32_t *queue, const BatchBinding *bind, cudaStream_t stream);
+
 // ---- NTT multiplication (Section 4) ---------------------------------------
 struct NttPlan;  // opaque; defined in mul_ntt.cu
 bn_status ntt_create(NttPlan **out, bool crt, uint32_t na, uint32_t nb, const bn_tuning *t);
@@ -49,6 +81,15 @@ void ntt_destroy(NttPlan *p);
 cudaError_t ntt_launch(NttPlan *p, const uint32_t *a, const uint32_t *b, uint32_t *c,
                        uint64_t batch, cudaStream_t stream);
 size_t ntt_scratch_bytes(const NttPlan *p);
+// Plan for a mixed-size batch class: transform length exactly N; the batched
+// kernel takes each item's sizes from its descriptor (digits(a)+digits(b) must
+// lie in (N/2, N]).
+bn_status ntt_batch_plan(NttPlan **out, bool crt, uint32_t N);
+cudaError_t ntt_batch_launch(NttPlan *p, const BatchItem *items, uint32_t count, uint32_t *queue,
+                             const BatchBinding *bind, cudaStream_t stream);
+// One product of na x nb limbs with the tables of plan p (same transform length).
+cudaError_t ntt_launch_sized(NttPlan *p, uint32_t na, uint32_t nb, const uint32_t *a,
+                             const uint32_t *b, uint32_t *c, cudaStream_t stream);
 uint32_t ntt_length(const NttPlan *p);
 
 }  // namespace bn

@@ -431,6 +431,51 @@ __global__ void __launch_bounds__(1024) k_mul_ntt(NttArgs p) {
     }
 }
 
+// Mixed-size batch of products that share the transform length N (and so
+// the tables and geometry in p): the CTA takes the next item from the work
+// queue, largest items first, and uses that item's sizes and rows.
+template <bool CRT>
+__global__ void __launch_bounds__(1024)
+    k_mul_ntt_batch(NttArgs p, const BatchItem *items, uint32_t count, uint32_t *queue,
+                    const BatchBinding *bind) {
+    extern __shared__ __align__(16) uint64_t sm64[];
+    __shared__ uint32_t next;
+    const uint32_t Lp = phys_words(p.L);
+    uint64_t *A = sm64;
+    uint64_t *B = sm64 + ((Lp + 1) & ~1u);
+    uint64_t *spill = B + ((Lp + 1) & ~1u);
+    uint32_t *flags = reinterpret_cast<uint32_t *>(spill + blockDim.x);
+    uint64_t *scr = p.scratch + blockIdx.x * p.scratch_stride;
+    uint64_t *Z = scr;
+    uint64_t *C1 = scr + (p.S > 1 ? p.N : 0);
+    uint64_t *Cs = C1 + (CRT ? p.N : 0);
+    for (;;) {
+        __syncthreads();  // the previous item is stored before `next` moves on
+        if (threadIdx.x == 0) next = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t i = next;
+        if (i >= count) break;
+        const BatchItem it = items[i];
+        NttArgs q = p;
+        q.a = bind->a + it.off_a;
+        q.b = bind->b + it.off_b;
+        q.c = bind->c + it.off_c;
+        q.na = it.na;
+        q.nb = it.nb;
+        q.nout = it.na + it.nb;
+        q.vec_c = (q.nout % 4 == 0) && ((uintptr_t)q.c % 16 == 0);
+        q.batch = 1;
+        const bool keep = q.S == 1;
+        if constexpr (CRT) {
+            prime_product<FieldP1>(q, q.t1, q.a, q.b, A, B, Z, C1, false);
+            prime_product<FieldP2>(q, q.t2, q.a, q.b, A, B, Z, Cs, keep);
+        } else {
+            prime_product<FieldP1>(q, q.t1, q.a, q.b, A, B, Z, Cs, keep);
+        }
+        normalize<CRT>(q, 0, reinterpret_cast<uint32_t *>(A), B, keep, C1, Cs, spill, flags);
+    }
+}
+
 // ---- host side: fields, tables, plan ----------------------------------------
 
 struct HostField {
@@ -636,13 +681,10 @@ size_t ntt_scratch_bytes(const NttPlan *p) { return p ? p->scratch_bytes : 0; }
 
 uint32_t ntt_length(const NttPlan *p) { return p ? p->N : 0; }
 
-cudaError_t ntt_launch(NttPlan *p, const uint32_t *a, const uint32_t *b, uint32_t *c,
-                       uint64_t batch, cudaStream_t st) {
-    if (batch == 0) return cudaSuccess;
+namespace {
+
+NttArgs plan_args(const NttPlan *p) {
     NttArgs args{};
-    args.a = a;
-    args.b = b;
-    args.c = c;
     args.na = p->na;
     args.nb = p->nb;
     args.nout = p->nout;
@@ -651,16 +693,70 @@ cudaError_t ntt_launch(NttPlan *p, const uint32_t *a, const uint32_t *b, uint32_
     args.logL = p->logL;
     args.S = p->S;
     args.digit_bits = p->crt ? 32 : 16;
-    args.vec_c = (p->nout % 4 == 0) && ((uintptr_t)c % 16 == 0);
-    args.batch = batch;
     args.scratch = p->scratch;
     args.scratch_stride = p->scratch_stride;
     args.garner_inv = p->garner_inv;
     args.t1 = p->t1;
     args.t2 = p->t2;
+    return args;
+}
+
+}  // namespace
+
+cudaError_t ntt_launch(NttPlan *p, const uint32_t *a, const uint32_t *b, uint32_t *c,
+                       uint64_t batch, cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    NttArgs args = plan_args(p);
+    args.a = a;
+    args.b = b;
+    args.c = c;
+    args.vec_c = (p->nout % 4 == 0) && ((uintptr_t)c % 16 == 0);
+    args.batch = batch;
     const uint64_t grid = batch < p->max_grid ? batch : p->max_grid;
     if (p->crt) k_mul_ntt<true><<<(unsigned)grid, p->threads, p->smem, st>>>(args);
     else k_mul_ntt<false><<<(unsigned)grid, p->threads, p->smem, st>>>(args);
+    return cudaGetLastError();
+}
+
+cudaError_t ntt_launch_sized(NttPlan *p, uint32_t na, uint32_t nb, const uint32_t *a,
+                             const uint32_t *b, uint32_t *c, cudaStream_t st) {
+    NttArgs args = plan_args(p);
+    args.a = a;
+    args.b = b;
+    args.c = c;
+    args.na = na;
+    args.nb = nb;
+    args.nout = na + nb;
+    args.vec_c = (args.nout % 4 == 0) && ((uintptr_t)c % 16 == 0);
+    args.batch = 1;
+    if (p->crt) k_mul_ntt<true><<<1, p->threads, p->smem, st>>>(args);
+    else k_mul_ntt<false><<<1, p->threads, p->smem, st>>>(args);
+    return cudaGetLastError();
+}
+
+bn_status ntt_batch_plan(NttPlan **out, bool crt, uint32_t N) {
+    // A plan whose transform length is exactly N: digits(a) + digits(b) = N.
+    if (N < 4 || (N & (N - 1))) return BN_EINVAL;
+    const uint32_t per_side = crt ? N / 2 : N / 4;
+    if (per_side > BN_MUL_MAX_LIMBS) return BN_EUNSUPPORTED;
+    cudaError_t e = allow_max_smem((const void *)k_mul_ntt_batch<true>);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_ntt_batch<false>);
+    if (e != cudaSuccess) return BN_ECUDA;
+    return ntt_create(out, crt, per_side, per_side, nullptr);
+}
+
+cudaError_t ntt_batch_launch(NttPlan *p, const BatchItem *items, uint32_t count, uint32_t *queue,
+                             const BatchBinding *bind, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const NttArgs args = plan_args(p);
+    const uint32_t grid = count < p->max_grid ? count : p->max_grid;
+    if (p->crt) {
+        if (cudaError_t e = allow_max_smem((const void *)k_mul_ntt_batch<true>)) return e;
+        k_mul_ntt_batch<true><<<grid, p->threads, p->smem, st>>>(args, items, count, queue, bind);
+    } else {
+        if (cudaError_t e = allow_max_smem((const void *)k_mul_ntt_batch<false>)) return e;
+        k_mul_ntt_batch<false><<<grid, p->threads, p->smem, st>>>(args, items, count, queue, bind);
+    }
     return cudaGetLastError();
 }
 

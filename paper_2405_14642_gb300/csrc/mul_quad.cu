@@ -40,6 +40,40 @@ constexpr uint32_t kQuadMaxThreads = 1024;
 __device__ __forceinline__ uint32_t phys(uint32_t x) { return x + 4u * (x >> 5); }
 __host__ __device__ constexpr uint32_t phys_size(uint32_t x) { return x + 4u * ((x + 31) >> 5); }
 
+__host__ __device__ inline uint32_t roundup(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
+
+struct Geometry {
+    uint32_t nap, nbp, units, group, ipb, inst_words, ab_words, l_offset, hc_offset, block, smem;
+};
+
+__host__ __device__ inline Geometry geometry(uint32_t na, uint32_t nb, uint32_t Q, uint32_t cta_target) {
+    Geometry g{};
+    g.nbp = roundup(nb, 2 * Q);
+    g.nap = roundup(na, Q);
+    if (g.nap < g.nbp) g.nap = g.nbp;
+    g.units = g.nap / Q;
+    if (g.units <= 32) {
+        g.group = 1;
+        while (g.group < g.units) g.group <<= 1;
+    } else {
+        g.group = roundup(g.units, 32);
+    }
+    g.ipb = g.group < cta_target ? cta_target / g.group : 1;
+    // A at [0, phys_size(nap)), B (logical -Q .. nbp+Q) after it, then L
+    // (nap + nbp words) and the H spill words (2 per window).
+    const uint32_t a_words = roundup(phys_size(g.nap), 4);
+    const uint32_t b_words = roundup(phys_size(g.nbp + 2 * Q), 4);
+    const uint32_t l_words = roundup(phys_size(g.nap + g.nbp), 4);
+    g.ab_words = a_words;
+    g.l_offset = a_words + b_words;
+    g.hc_offset = g.l_offset + l_words;
+    const uint32_t windows = (g.nap + g.nbp) / Q;
+    g.inst_words = roundup(g.hc_offset + 2 * windows, 4);
+    g.block = g.group * g.ipb;
+    g.smem = 4 * (g.inst_words * g.ipb + 32);
+    return g;
+}
+
 struct QuadArgs {
     const uint32_t *a, *b;  // a is the longer operand (na >= nb)
     uint32_t *c;
@@ -227,17 +261,15 @@ __device__ __forceinline__ void stage_row(uint32_t *S, const uint32_t *row, uint
     }
 }
 
+// One product a*b (instance `inst` of p's rows) by the `group` threads of one
+// slot; t is this thread's index in the slot and As the slot's shared words.
+// Every thread of the CTA calls this together (it contains barriers).
 template <int Q, bool COLS>
-__global__ void __launch_bounds__(kQuadMaxThreads) k_mul_quad(QuadArgs p) {
-    extern __shared__ __align__(16) uint32_t smem[];
-    const uint32_t slot = threadIdx.x / p.group, t = threadIdx.x - slot * p.group;
-    const uint64_t inst = (uint64_t)blockIdx.x * p.ipb + slot;
-    const bool live = inst < p.batch;
-    uint32_t *As = smem + slot * p.inst_words;
+__device__ __forceinline__ void quad_instance(const QuadArgs &p, uint64_t inst, bool live,
+                                              uint32_t *As, uint32_t *flags, uint32_t t) {
     uint32_t *Bs = As + p.ab_words;
     uint32_t *Ls = As + p.l_offset;     // L, then the H spill words
     uint32_t *Hc = As + p.hc_offset;
-    uint32_t *flags = smem + p.ipb * p.inst_words;
 
     // q1: stage the operands, zero-padded (B also below 0: logical [-Q, nbp + Q)).
     stage_row(As, p.a + inst * p.na, p.na, 0, p.nap, p.vec_a, live, t, p.group);
@@ -329,38 +361,62 @@ __global__ void __launch_bounds__(kQuadMaxThreads) k_mul_quad(QuadArgs p) {
     }
 }
 
-uint32_t roundup(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
+template <int Q, bool COLS>
+__global__ void __launch_bounds__(kQuadMaxThreads) k_mul_quad(QuadArgs p) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    const uint32_t slot = threadIdx.x / p.group, t = threadIdx.x - slot * p.group;
+    const uint64_t inst = (uint64_t)blockIdx.x * p.ipb + slot;
+    quad_instance<Q, COLS>(p, inst, inst < p.batch, smem + slot * p.inst_words,
+                           smem + p.ipb * p.inst_words, t);
+}
 
-struct Geometry {
-    uint32_t nap, nbp, units, group, ipb, inst_words, ab_words, l_offset, hc_offset, block, smem;
-};
-
-Geometry geometry(uint32_t na, uint32_t nb, uint32_t Q, uint32_t cta_target) {
-    Geometry g{};
-    g.nbp = roundup(nb, 2 * Q);
-    g.nap = roundup(na, Q);
-    if (g.nap < g.nbp) g.nap = g.nbp;
-    g.units = g.nap / Q;
-    if (g.units <= 32) {
-        g.group = 1;
-        while (g.group < g.units) g.group <<= 1;
-    } else {
-        g.group = roundup(g.units, 32);
+// Mixed-size batch: each slot of `group` threads takes one item from the work
+// queue (a counter the CTA's first thread advances by ipb); items are sorted
+// largest first, so slots of one CTA get similar sizes and the CTA-wide
+// barriers cost little.  Geometry is computed per item on the device.
+template <int Q>
+__global__ void __launch_bounds__(kQuadMaxThreads)
+    k_mul_quad_batch(const BatchItem *items, uint32_t count, uint32_t *queue,
+                     const BatchBinding *bind, uint32_t group, uint32_t ipb, uint32_t inst_words) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ uint32_t first;
+    const uint32_t slot = threadIdx.x / group, t = threadIdx.x - slot * group;
+    uint32_t *As = smem + slot * inst_words, *flags = smem + ipb * inst_words;
+    const uint32_t *A0 = bind->a, *B0 = bind->b;
+    uint32_t *C0 = bind->c;
+    for (;;) {
+        __syncthreads();  // the previous items are stored before `first` moves on
+        if (threadIdx.x == 0) first = atomicAdd(queue, ipb);
+        __syncthreads();
+        const uint32_t base = first;
+        if (base >= count) break;
+        const uint32_t idx = base + slot;
+        const bool live = idx < count;
+        BatchItem it{0, 0, 0, 1, 1};
+        if (live) it = items[idx];
+        const uint32_t *a = A0 + it.off_a, *b = B0 + it.off_b;
+        uint32_t na = it.na, nb = it.nb;
+        if (na < nb) {
+            const uint32_t *tp = a; a = b; b = tp;
+            const uint32_t tn = na; na = nb; nb = tn;
+        }
+        const Geometry g = geometry(na, nb, Q, 0);
+        QuadArgs p{};
+        p.a = a; p.b = b; p.c = C0 + it.off_c;
+        p.na = na; p.nb = nb; p.nap = g.nap; p.nbp = g.nbp; p.nout = na + nb;
+        p.units = g.units;
+        p.group = group;
+        p.ipb = ipb;
+        p.inst_words = inst_words;
+        p.ab_words = g.ab_words;
+        p.l_offset = g.l_offset;
+        p.hc_offset = g.hc_offset;
+        p.vec_a = (na % 4 == 0) && ((uintptr_t)a % 16 == 0);
+        p.vec_b = (nb % 4 == 0) && ((uintptr_t)b % 16 == 0);
+        p.vec_c = (p.nout % 4 == 0) && ((uintptr_t)p.c % 16 == 0);
+        p.batch = 1;
+        quad_instance<Q, false>(p, 0, live, As, flags, t);
     }
-    g.ipb = g.group < cta_target ? cta_target / g.group : 1;
-    // A at [0, phys_size(nap)), B (logical -Q .. nbp+Q) after it, then L
-    // (nap + nbp words) and the H spill words (2 per window).
-    const uint32_t a_words = roundup(phys_size(g.nap), 4);
-    const uint32_t b_words = roundup(phys_size(g.nbp + 2 * Q), 4);
-    const uint32_t l_words = roundup(phys_size(g.nap + g.nbp), 4);
-    g.ab_words = a_words;
-    g.l_offset = a_words + b_words;
-    g.hc_offset = g.l_offset + l_words;
-    const uint32_t windows = (g.nap + g.nbp) / Q;
-    g.inst_words = roundup(g.hc_offset + 2 * windows, 4);
-    g.block = g.group * g.ipb;
-    g.smem = 4 * (g.inst_words * g.ipb + 32);
-    return g;
 }
 
 // Window size by the longer operand, from timings on GB300 (4 vs 8 at each
@@ -435,6 +491,46 @@ cudaError_t quad_launch(const QuadConfig &cfg, const uint32_t *a, const uint32_t
         if (cfg.cols) k_mul_quad<8, true><<<(unsigned)grid, g.block, g.smem, st>>>(args);
         else k_mul_quad<8, false><<<(unsigned)grid, g.block, g.smem, st>>>(args);
     }
+    return cudaGetLastError();
+}
+
+bn_status quad_batch_class(QuadClass &qc, uint32_t q, uint32_t n_max, uint32_t cta_target) {
+    if (n_max == 0 || n_max > BN_MUL_MAX_LIMBS || (q != 4 && q != 8)) return BN_EINVAL;
+    if (cta_target == 0 || cta_target > 1024) return BN_EINVAL;
+    const Geometry g = geometry(n_max, n_max, q, cta_target);
+    if (g.group > kQuadMaxThreads) return BN_EUNSUPPORTED;
+    qc = QuadClass{};
+    qc.q = q;
+    qc.n_max = n_max;
+    qc.group = g.group;
+    qc.ipb = g.ipb;
+    qc.block = g.block;
+    qc.inst_words = g.inst_words;
+    qc.smem = g.smem;
+    const void *kern = q == 4 ? (const void *)k_mul_quad_batch<4> : (const void *)k_mul_quad_batch<8>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = allow_max_smem(kern);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)qc.block, qc.smem);
+    if (e != cudaSuccess) return BN_ECUDA;
+    if (per_sm == 0) return BN_EUNSUPPORTED;
+    qc.grid = (uint32_t)(sms * per_sm);
+    return BN_OK;
+}
+
+cudaError_t quad_batch_launch(const QuadClass &qc, const BatchItem *items, uint32_t count,
+                              uint32_t *queue, const BatchBinding *bind, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const uint32_t need = (count + qc.ipb - 1) / qc.ipb;
+    const uint32_t grid = need < qc.grid ? need : qc.grid;
+    if (qc.q == 4)
+        k_mul_quad_batch<4><<<grid, qc.block, qc.smem, st>>>(items, count, queue, bind, qc.group,
+                                                             qc.ipb, qc.inst_words);
+    else
+        k_mul_quad_batch<8><<<grid, qc.block, qc.smem, st>>>(items, count, queue, bind, qc.group,
+                                                             qc.ipb, qc.inst_words);
     return cudaGetLastError();
 }
 

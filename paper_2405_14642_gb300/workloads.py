@@ -102,3 +102,62 @@ def sweep_points(bits_list=SWEEP_BITS, side_bytes: int = SWEEP_SIDE_BYTES,
 def tiny_workload() -> Tuple[np.ndarray, np.ndarray]:
     """4096 pairs of 4096-bit integers (128 limbs) with 5% edge cases."""
     return pair_batch(4096, 128, seed=seed_for(0), edges=True)
+
+
+# Op codes of include/bn.h used by mixed workloads.
+OP_ADD, OP_MUL_AUTO = 0, 4
+MIXED_ITEM_DTYPE = np.dtype([("op", "<u4"), ("na", "<u4"), ("nb", "<u4"), ("reserved", "<u4"),
+                             ("a_offset", "<u8"), ("b_offset", "<u8"), ("c_offset", "<u8")])
+
+
+def log_uniform_sizes(rng: np.random.Generator, count: int, lo: int, hi: int) -> np.ndarray:
+    """Integer limb counts with log-uniform distribution on [lo, hi]."""
+    x = np.exp(rng.uniform(np.log(lo), np.log(hi), size=count))
+    return np.clip(np.rint(x), lo, hi).astype(np.uint32)
+
+
+def mixed_workload(count: int, seed: int, lo: int = 32, hi: int = 8192, mul_frac: float = 0.7,
+                   edges: bool = True, mul_op: int = OP_MUL_AUTO):
+    """Mixed batch: `count` operations, a fraction `mul_frac` products (op
+    `mul_op`) and the rest additions, operand limb counts log-uniform in
+    [lo, hi] independently for a and b, limbs uniform; with `edges`, every
+    20th item (i % 20 == 19) gets one of the five edge cases of the sweep.
+
+    Returns (items, a_flat, b_flat, c_limbs): items of MIXED_ITEM_DTYPE with
+    offsets into the flat operand arrays and a flat result array of c_limbs."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    items = np.zeros(count, MIXED_ITEM_DTYPE)
+    is_mul = rng.random(count) < mul_frac
+    items["op"] = np.where(is_mul, mul_op, OP_ADD)
+    items["na"] = log_uniform_sizes(rng, count, lo, hi)
+    items["nb"] = log_uniform_sizes(rng, count, lo, hi)
+    na = items["na"].astype(np.uint64)
+    nb = items["nb"].astype(np.uint64)
+    nout = np.where(is_mul, na + nb, np.maximum(na, nb) + 1).astype(np.uint64)
+    items["a_offset"] = np.concatenate(([0], np.cumsum(na)[:-1])) if count else []
+    items["b_offset"] = np.concatenate(([0], np.cumsum(nb)[:-1])) if count else []
+    items["c_offset"] = np.concatenate(([0], np.cumsum(nout)[:-1])) if count else []
+    a = uniform_limbs(1, int(na.sum()), rng)[0] if count else np.zeros(0, np.uint32)
+    b = uniform_limbs(1, int(nb.sum()), rng)[0] if count else np.zeros(0, np.uint32)
+    if edges:
+        for i in range(19, count, 20):
+            ao, bo = int(items["a_offset"][i]), int(items["b_offset"][i])
+            ra = a[ao:ao + int(na[i])]
+            rb = b[bo:bo + int(nb[i])]
+            kind = (i // 20) % 5
+            if kind == 0:
+                ra[:] = ALL_ONES
+                rb[:] = ALL_ONES
+            elif kind == 1:
+                ra[:] = ALL_ONES
+                rb[:] = 0
+                rb[0] = 1
+            elif kind == 2:
+                ra[:] = 0
+            elif kind == 3:
+                ra[1:] = 0
+                rb[1:] = 0
+            else:
+                ra[:] = ALL_ONES
+    return items, a, b, int(nout.sum())
+
