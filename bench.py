@@ -320,6 +320,9 @@ def run_gpu(args, rank, world, local_rank):
     mixed = None
     if args.mixed_items > 0:
         mixed = run_mixed(args, torch, bn, dev, rank)
+    serving = None
+    if args.serve_requests > 0:
+        serving = run_serving(args, torch, bn, dev, rank)
 
     # End to end: host arrays in pinned memory through the host-buffer entry point.
     e2e = None
@@ -374,7 +377,7 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": roof, "rooflines": rooflines, "breakdown": rows,
         "imad_probe": peak_info, "clocks": clocks, "gpu_launches": gpu_launches,
         "e2e": e2e, "cpu_baseline": cpu, "impl": "ours", "skipped_ops": skipped,
-        "mixed": mixed,
+        "mixed": mixed, "serving": serving,
     }
 
 
@@ -420,6 +423,77 @@ def run_mixed(args, torch, bn, dev, rank):
             "batched": out["batched"], "plain": out["plain"],
             "speedup": round(out["plain"]["ms"] / out["batched"]["ms"], 2),
             "results_identical": identical}
+
+
+def serve_trace(srv, bn, reqs, arrivals, poll_max=8192):
+    """Replay requests at their arrival times (server clock, microseconds);
+    returns per-request (arrival, done) in microseconds.  Arrival times are the
+    scheduled ones, so any lateness of this driver loop counts as latency."""
+    n = reqs.shape[0]
+    done = np.zeros(n, np.float64)
+    index = {}
+    i, got = 0, 0
+    t0 = srv.now_us()
+    reqs = reqs.copy()
+    reqs["arrival_us"] = arrivals + t0
+    while got < n:
+        now = srv.now_us()
+        j = int(np.searchsorted(reqs["arrival_us"], now, side="right"))
+        if j > i:
+            for k, t in enumerate(srv.submit(reqs[i:j])):
+                index[int(t)] = i + k
+            i = j
+        comps = srv.poll(poll_max)
+        if comps.shape[0]:
+            for c in comps:
+                done[index.pop(int(c["ticket"]))] = c["done_us"]
+            srv.release(comps["ticket"])
+            got += comps.shape[0]
+    return reqs["arrival_us"], done
+
+
+def run_serving(args, torch, bn, dev, rank):
+    """Poisson arrivals of products with limb counts log-uniform in 32..8192
+    (each operand independently), operands resident in device memory, an
+    8 GiB result pool; continuous batching vs one request at a time."""
+    rng = np.random.Generator(np.random.PCG64(workloads.seed_for(5, 0) + 7919 * rank))
+    pool_limbs = 32 << 20
+    ops_buf = torch.from_numpy(workloads.uniform_limbs(1, pool_limbs, rng)[0].view(np.int32)).to(dev)
+    base = ops_buf.data_ptr()
+
+    def make(count):
+        reqs = np.zeros(count, bn.REQUEST_DTYPE)
+        reqs["op"] = bn.BN_OP_MUL_AUTO
+        reqs["na"] = workloads.log_uniform_sizes(rng, count, 32, 8192)
+        reqs["nb"] = workloads.log_uniform_sizes(rng, count, 32, 8192)
+        for f, n in (("a", reqs["na"]), ("b", reqs["nb"])):
+            off = rng.integers(0, (pool_limbs - n.astype(np.int64)) // 4) * 4
+            reqs[f] = base + 4 * off.astype(np.uint64)
+        return reqs
+
+    out = {"workload": "products, limbs log-uniform 32..8192 per operand (1K-256K bits), "
+                       "Poisson arrivals, operands device-resident, 8 GiB result pool",
+           "runs": []}
+    plan = [("batched", rate, args.serve_requests if rate >= 100000 else args.serve_requests // 5)
+            for rate in (50000, 500000)]
+    plan.append(("sequential", 50000, max(200, args.serve_requests // 100)))
+    for mode, rate, count in plan:
+        reqs = make(count)
+        arrivals = np.cumsum(rng.exponential(1e6 / rate, size=count)) + 2000.0
+        with bn.Server(pool_bytes=8 << 30, sequential=(mode == "sequential")) as srv:
+            warm = make(64)
+            serve_trace(srv, bn, warm, np.zeros(64))            # first launches, plan warm-up
+            arr, done = serve_trace(srv, bn, reqs, arrivals)
+            st = srv.stats
+        lat = done - arr
+        span_s = (done.max() - arr.min()) * 1e-6
+        out["runs"].append({"mode": mode, "offered_per_s": rate, "requests": count,
+                            "throughput_per_s": round(count / span_s, 1),
+                            "p50_us": round(float(np.percentile(lat, 50)), 1),
+                            "p99_us": round(float(np.percentile(lat, 99)), 1),
+                            "batches": st["batches"] - (0 if mode == "sequential" else 0),
+                            "max_inflight": st["max_inflight_seen"]})
+    return out
 
 
 def run_e2e(args, torch, bn, ops, hosts, dev):
@@ -590,6 +664,8 @@ def main(argv=None):
     ap.add_argument("--mixed-items", type=int, default=200000,
                     help="operations in the mixed-size batch comparison (0 = skip)")
     ap.add_argument("--mixed-steps", type=int, default=5)
+    ap.add_argument("--serve-requests", type=int, default=50000,
+                    help="requests per serving run at 500k/s (0 = skip the serving runs)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -215,6 +215,77 @@ bn_status bn_batch_execute(bn_batch batch, const uint32_t *a, const uint32_t *b,
 bn_status bn_batch_get_info(bn_batch batch, bn_batch_info *info);
 bn_status bn_batch_destroy(bn_batch batch);
 
+/* ---- serving loop ---------------------------------------------------------
+ * A request server for products (and sums) of mixed sizes whose operands are
+ * already in device memory.  A scheduler thread owned by the server batches
+ * requests continuously: whenever one of `max_inflight` slots is free it
+ * admits pending requests in arrival order while their results fit in the
+ * device result pool (first-fit, at most BN_SERVER_MAX_POOL bytes), groups
+ * them into size classes (cost model as for batches) and launches the class
+ * kernels on that slot's stream; requests that arrive meanwhile wait for the
+ * next free slot, so their work overlaps the work already on the GPU.
+ * BN_SERVER_SEQUENTIAL instead runs one request at a time with an ordinary
+ * launch (the per-request baseline).  Results are bit-identical either way.
+ *
+ * Time: the server clock counts microseconds from creation
+ * (bn_server_now_us); a request's arrival time is given at submission (or
+ * taken from the clock if negative) and its completion time is when the
+ * scheduler sees its micro-batch finish.
+ * Memory: operands a, b stay caller-owned and must remain valid until the
+ * request completes; results live in the pool until bn_server_release.
+ * Transform tables and scratch (per slot) are allocated at creation, outside
+ * the pool.  Threads: the submit/poll/release calls may come from any host
+ * thread; the scheduler runs on its own thread. */
+#define BN_SERVER_MAX_POOL (8ull << 30)
+#define BN_SERVER_SEQUENTIAL 1u
+
+typedef struct bn_server_config {
+    uint64_t pool_bytes;      /* device result pool; 0 = 1 GiB; <= BN_SERVER_MAX_POOL */
+    uint32_t max_inflight;    /* micro-batches on the GPU at once; 0 = 4 */
+    uint32_t max_batch;       /* requests per micro-batch; 0 = 4096 */
+    uint32_t flags;           /* BN_SERVER_SEQUENTIAL or 0 */
+    uint32_t reserved;        /* must be zero */
+} bn_server_config;
+
+typedef struct bn_request {
+    uint32_t op;              /* BN_OP_ADD or a multiplication op (BN_OP_MUL_AUTO recommended) */
+    uint32_t na, nb;          /* limb counts (as for batch items) */
+    uint32_t reserved;        /* must be zero */
+    const uint32_t *a, *b;    /* device operands */
+    double arrival_us;        /* server-clock arrival time; < 0 = now */
+} bn_request;
+
+typedef struct bn_completion {
+    uint64_t ticket;
+    uint32_t *c;              /* device result (pool memory) */
+    uint32_t limbs;           /* result limbs */
+    uint32_t reserved;
+    double arrival_us, done_us;
+} bn_completion;
+
+typedef struct bn_server_stats {
+    uint64_t submitted, completed, batches, pool_high_water;
+    uint32_t max_inflight_seen, reserved;
+} bn_server_stats;
+
+typedef struct bn_server_s *bn_server;
+
+bn_status bn_server_create(bn_server *out, const bn_server_config *cfg);
+/* Enqueue `count` requests; tickets[i] receives request i's ticket.  Returns
+ * immediately (BN_EINVAL for a bad request, none of the batch enqueued). */
+bn_status bn_server_submit(bn_server s, const bn_request *reqs, uint32_t count, uint64_t *tickets);
+/* Move up to `max` completions into out; *n receives how many. */
+bn_status bn_server_poll(bn_server s, bn_completion *out, uint32_t max, uint32_t *n);
+/* Free the result memory of `count` completed requests (unknown tickets are
+ * skipped and reported as BN_EINVAL). */
+bn_status bn_server_release(bn_server s, const uint64_t *tickets, uint32_t count);
+/* Wait until nothing is pending or in flight (BN_ETIMEOUT after timeout_s). */
+bn_status bn_server_drain(bn_server s, double timeout_s);
+double bn_server_now_us(bn_server s);
+bn_status bn_server_get_stats(bn_server s, bn_server_stats *out);
+/* Stop the scheduler (after draining) and free everything. */
+bn_status bn_server_destroy(bn_server s);
+
 /* Static description of a status code. */
 const char *bn_status_str(bn_status s);
 

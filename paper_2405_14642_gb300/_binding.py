@@ -45,6 +45,26 @@ class bn_batch_info(ctypes.Structure):
                 ("tune_ms", ctypes.c_double)]
 
 
+class bn_server_config(ctypes.Structure):
+    _fields_ = [("pool_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
+                ("max_batch", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class bn_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("pool_high_water", ctypes.c_uint64),
+                ("max_inflight_seen", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+# Layouts of struct bn_request and struct bn_completion (include/bn.h), 40 bytes each.
+REQUEST_DTYPE = np.dtype([("op", "<u4"), ("na", "<u4"), ("nb", "<u4"), ("reserved", "<u4"),
+                          ("a", "<u8"), ("b", "<u8"), ("arrival_us", "<f8")])
+COMPLETION_DTYPE = np.dtype([("ticket", "<u8"), ("c", "<u8"), ("limbs", "<u4"), ("reserved", "<u4"),
+                             ("arrival_us", "<f8"), ("done_us", "<f8")])
+BN_SERVER_SEQUENTIAL = 1
+
+
 class bn_tuning(ctypes.Structure):
     _fields_ = [("limbs_per_thread", ctypes.c_uint32), ("cta_threads", ctypes.c_uint32),
                 ("variant", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
@@ -83,6 +103,14 @@ def load(build_if_missing: bool = False):
         "bn_last_error": ([], ctypes.c_char_p),
         "bn_version": ([], ctypes.c_int),
         "bn_mul_ntt_noalloc": ([u32p, u32p, u32p, u32, u32, u64, ctypes.c_int, vp], st),
+        "bn_server_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(bn_server_config)], st),
+        "bn_server_submit": ([vp, vp, u32, vp], st),
+        "bn_server_poll": ([vp, vp, u32, ctypes.POINTER(ctypes.c_uint32)], st),
+        "bn_server_release": ([vp, vp, u32], st),
+        "bn_server_drain": ([vp, ctypes.c_double], st),
+        "bn_server_now_us": ([vp], ctypes.c_double),
+        "bn_server_get_stats": ([vp, ctypes.POINTER(bn_server_stats)], st),
+        "bn_server_destroy": ([vp], st),
         "bn_batch_create": ([ctypes.POINTER(ctypes.c_void_p), vp, u64, u32], st),
         "bn_batch_execute": ([vp, u32p, u32p, u32p, vp], st),
         "bn_batch_get_info": ([vp, ctypes.POINTER(bn_batch_info)], st),
@@ -327,4 +355,84 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """A bn_server: continuous batching of device-resident requests."""
+
+    def __init__(self, pool_bytes: int = 0, max_inflight: int = 0, max_batch: int = 0,
+                 sequential: bool = False):
+        lib = load()
+        self._lib = lib
+        self._h = ctypes.c_void_p()
+        cfg = bn_server_config(pool_bytes, max_inflight, max_batch,
+                               BN_SERVER_SEQUENTIAL if sequential else 0, 0)
+        _check(lib.bn_server_create(ctypes.byref(self._h), ctypes.byref(cfg)), "bn_server_create")
+
+    def now_us(self) -> float:
+        return self._lib.bn_server_now_us(self._h)
+
+    def submit(self, reqs: np.ndarray) -> np.ndarray:
+        """Enqueue requests (REQUEST_DTYPE); returns their tickets."""
+        reqs = np.ascontiguousarray(reqs, dtype=REQUEST_DTYPE)
+        tickets = np.empty(reqs.shape[0], np.uint64)
+        _check(self._lib.bn_server_submit(self._h, ctypes.c_void_p(reqs.ctypes.data), reqs.shape[0],
+                                          ctypes.c_void_p(tickets.ctypes.data)), "bn_server_submit")
+        return tickets
+
+    def poll(self, max_items: int = 1 << 16) -> np.ndarray:
+        out = np.empty(max_items, COMPLETION_DTYPE)
+        n = ctypes.c_uint32()
+        _check(self._lib.bn_server_poll(self._h, ctypes.c_void_p(out.ctypes.data), max_items,
+                                        ctypes.byref(n)), "bn_server_poll")
+        return out[: n.value]
+
+    def release(self, tickets) -> None:
+        t = np.ascontiguousarray(tickets, dtype=np.uint64)
+        _check(self._lib.bn_server_release(self._h, ctypes.c_void_p(t.ctypes.data), t.shape[0]),
+               "bn_server_release")
+
+    def drain(self, timeout_s: float = 60.0) -> None:
+        _check(self._lib.bn_server_drain(self._h, timeout_s), "bn_server_drain")
+
+    @property
+    def stats(self) -> dict:
+        st = bn_server_stats()
+        _check(self._lib.bn_server_get_stats(self._h, ctypes.byref(st)), "bn_server_get_stats")
+        return {k: getattr(st, k) for k, _ in bn_server_stats._fields_ if k != "reserved"}
+
+    def close(self):
+        if self._h:
+            _check(self._lib.bn_server_destroy(self._h), "bn_server_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def device_to_host(ptr: int, limbs: int) -> np.ndarray:
+    """Copy `limbs` u32 words at a raw device address (e.g. a completion's
+    result) into a new numpy array, through the CUDA runtime the library uses."""
+    global _cudart
+    if _cudart is None:
+        _cudart = ctypes.CDLL("libcudart.so.13")
+        _cudart.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+        _cudart.cudaMemcpy.restype = ctypes.c_int
+    out = np.empty(limbs, np.uint32)
+    rc = _cudart.cudaMemcpy(ctypes.c_void_p(out.ctypes.data), ctypes.c_void_p(ptr), 4 * limbs, 2)
+    if rc != 0:
+        raise RuntimeError(f"cudaMemcpy failed ({rc})")
+    return out
+
+
+_cudart = None
 

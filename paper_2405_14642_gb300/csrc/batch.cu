@@ -42,21 +42,8 @@ uint32_t transform_length(bool crt, uint32_t na, uint32_t nb) {
     return 1u << ceil_log2(d < 2 ? 2 : d);
 }
 
-// Built-in cost figures (GB300, size-sweep batches, CUDA events).
-// Schoolbook word products per microsecond by ceil(log2(longer operand)).
-double default_quad_rate(uint32_t key) {
-    static const double r[14] = {0.5e6, 0.5e6, 0.5e6, 0.5e6, 0.5e6, 1.56e6, 1.69e6, 1.77e6, 3.15e6,
-                                 3.88e6, 4.37e6, 4.90e6, 5.20e6, 5.24e6};
-    return r[key < 14 ? key : 13];
-}
-// Transform microseconds per item by log2(N); below 2^11 the transform is not
-// considered (one small transform per CTA underuses the GPU).
-double default_ntt_us(bool crt, uint32_t logN) {
-    static const double t64[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0.0727, 0.159, 0.348, 0.882, 2.08};
-    static const double tcrt[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0.076, 0.148, 0.323, 0.70, 1.79, 0};
-    const double v = logN < 16 ? (crt ? tcrt[logN] : t64[logN]) : 0;
-    return v > 0 ? v : 1e30;
-}
+using bn::default_ntt_us;
+using bn::default_quad_rate;
 
 struct Class {
     Kind kind;

@@ -31,6 +31,16 @@ struct BatchBinding {
     uint32_t *c;
 };
 
+// ---- cost model (cost_model.cu) -------------------------------------------
+double default_quad_rate(uint32_t key);              // word products / us
+double default_ntt_us(bool crt, uint32_t log_n);     // us per product
+struct MulChoice {
+    uint32_t kind = 1;  // 1 schoolbook, 2 one-prime transform, 3 two-prime transform
+    uint32_t quad_key = 0, log_n64 = 0, log_ncrt = 0;
+    double est_us = 0;
+};
+MulChoice choose_mul(uint32_t na, uint32_t nb);
+
 // ---- addition (Section 2) -------------------------------------------------
 struct AddConfig {
     uint32_t na = 0, nb = 0, n = 0, nout = 0;
