@@ -317,6 +317,9 @@ def run_gpu(args, rank, world, local_rank):
     ms_per_step = max_ms / args.steps
     gpu_launches = args.steps * len(ops)
 
+    fused = None
+    if args.fused_reps > 0:
+        fused = run_fused(args, torch, bn, dev, inputs, peak_info)
     mixed = None
     if args.mixed_items > 0:
         mixed = run_mixed(args, torch, bn, dev, rank)
@@ -377,8 +380,56 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": roof, "rooflines": rooflines, "breakdown": rows,
         "imad_probe": peak_info, "clocks": clocks, "gpu_launches": gpu_launches,
         "e2e": e2e, "cpu_baseline": cpu, "impl": "ours", "skipped_ops": skipped,
-        "mixed": mixed, "serving": serving,
+        "mixed": mixed, "serving": serving, "fused": fused,
     }
+
+
+def run_fused(args, torch, bn, dev, inputs, peak_info):
+    """Section 6's programs at each sweep size on the same operands, results
+    kept at the operands' length n (mod 2^(32n)): 1-Add against 6-Add
+    (bn_add6, six dependent additions in one kernel) in GB/s by the paper's
+    count 3 * NumInsts * NumBits / 8, and 1-Mul (bn_mul_low, the low half of
+    the product) against Poly (bn_poly, four products and three additions in
+    one kernel) in word products per second (n(n+1)/2 per low product).  The
+    paper's scalability measures are the time ratios 6-Add / 1-Add and
+    Poly / 1-Mul."""
+    stream = torch.cuda.current_stream(dev)
+    peak_t = peak_info["peak_word_products_per_s"] / 1e12 if peak_info else None
+    rows = []
+    for bits in sorted(inputs):
+        ta, tb = inputs[bits]
+        batch, n = ta.shape
+        o1 = torch.empty((batch, n + 1), dtype=torch.int32, device=dev)
+        on = torch.empty((batch, n), dtype=torch.int32, device=dev)
+        calls = {"add": lambda: bn.bn_add(ta, tb, out=o1, stream=stream),
+                 "add6": lambda: bn.bn_add6(ta, tb, out=on, stream=stream),
+                 "mul_low": lambda: bn.bn_mul_low(ta, tb, out=on, stream=stream),
+                 "poly": lambda: bn.bn_poly(ta, tb, out=on, stream=stream)}
+        ms = {}
+        for name, fn in calls.items():
+            fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.fused_reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms[name] = e0.elapsed_time(e1) / args.fused_reps
+        paper_bytes = 3 * batch * bits / 8
+        prods = n * (n + 1) / 2 * batch
+        row = {"bits": bits, "batch": batch, **{f"{k}_ms": round(v, 4) for k, v in ms.items()},
+               "add6_gbs": round(paper_bytes / (ms["add6"] * 1e-3) / 1e9, 1),
+               "add6_over_add": round(ms["add6"] / ms["add"], 3),
+               "mul_low_tprods": round(prods / (ms["mul_low"] * 1e-3) / 1e12, 3),
+               "poly_tprods": round(4 * prods / (ms["poly"] * 1e-3) / 1e12, 3),
+               "poly_over_mul_low": round(ms["poly"] / ms["mul_low"], 3)}
+        if peak_t:
+            row["poly_frac_of_word_product_peak"] = round(row["poly_tprods"] / peak_t, 4)
+        rows.append(row)
+    return {"programs": "1-Add, 6-Add (x_{k+1} = x_k + x_{k-1}, result 8a + 13b), 1-Mul "
+                        "(low half), Poly (a*a + b)*(b*b + b) + a*b, all mod 2^(32n)",
+            "reps": args.fused_reps, "sizes": rows}
 
 
 def run_mixed(args, torch, bn, dev, rank):
@@ -664,6 +715,8 @@ def main(argv=None):
     ap.add_argument("--mixed-items", type=int, default=200000,
                     help="operations in the mixed-size batch comparison (0 = skip)")
     ap.add_argument("--mixed-steps", type=int, default=5)
+    ap.add_argument("--fused-reps", type=int, default=3,
+                    help="timed repetitions of each fused program per size (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=50000,
                     help="requests per serving run at 500k/s (0 = skip the serving runs)")
     args = ap.parse_args(argv)

@@ -165,6 +165,35 @@ bn_status bn_mul_ntt(const uint32_t *a, const uint32_t *b, uint32_t *c,
 bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, uint32_t *c,
                              uint32_t na, uint32_t nb, uint64_t batch, int crt, void *stream);
 
+/* ---- same-length arithmetic and fused programs (Sections 2 and 6) ------
+ * The paper's own benchmarks keep every result at the operands' length n,
+ * i.e. compute modulo 2^(32 n) (Section 2), and Section 6 measures two
+ * programs fused into one kernel each.  All three entry points take a, b, c
+ * as row-major device arrays of batch x n u32 limbs (little-endian limb
+ * order, instance i at offset i*n), write c only, and return once the kernel
+ * is enqueued on `stream`.  c must not overlap a or b; a == b is allowed.
+ * Errors: BN_EINVAL (n == 0, null pointer with batch > 0, overlap),
+ * BN_EUNSUPPORTED (n > BN_MUL_MAX_LIMBS), BN_ECUDA (launch failure,
+ * bn_last_error() has the CUDA text).  batch == 0 is a no-op.
+ *
+ * bn_mul_low  c = a*b mod 2^(32n): the schoolbook product restricted to its
+ *             low n columns (Section 3, Fig. 3: the rising triangle, each
+ *             thread taking a window and its mirror so all do equal work);
+ *             half the word products of bn_mul_quad.
+ * bn_poly     c = (a*a + b)*(b*b + b) + a*b mod 2^(32n) (Section 6's
+ *             polynomial program): four low products and three additions in
+ *             one kernel, every intermediate kept in shared memory.
+ * bn_add6     six dependent additions x_{k+1} = x_k + x_{k-1} from x_0 = a,
+ *             x_1 = b, c = x_7 = 8a + 13b mod 2^(32n) (Section 6's repeated
+ *             addition program; the paper does not spell out the chain, this
+ *             is the library's reading), intermediates in registers. */
+bn_status bn_mul_low(const uint32_t *a, const uint32_t *b, uint32_t *c,
+                     uint32_t n, uint64_t batch, void *stream);
+bn_status bn_poly(const uint32_t *a, const uint32_t *b, uint32_t *c,
+                  uint32_t n, uint64_t batch, void *stream);
+bn_status bn_add6(const uint32_t *a, const uint32_t *b, uint32_t *c,
+                  uint32_t n, uint64_t batch, void *stream);
+
 /* ---- mixed-size batches ------------------------------------------------
  * Many independent operations of different sizes and kinds in one call.  The
  * paper evaluates one size per kernel launch (Section 6); this form runs a

@@ -103,6 +103,9 @@ def load(build_if_missing: bool = False):
         "bn_last_error": ([], ctypes.c_char_p),
         "bn_version": ([], ctypes.c_int),
         "bn_mul_ntt_noalloc": ([u32p, u32p, u32p, u32, u32, u64, ctypes.c_int, vp], st),
+        "bn_mul_low": ([u32p, u32p, u32p, u32, u64, vp], st),
+        "bn_poly": ([u32p, u32p, u32p, u32, u64, vp], st),
+        "bn_add6": ([u32p, u32p, u32p, u32, u64, vp], st),
         "bn_server_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(bn_server_config)], st),
         "bn_server_submit": ([vp, vp, u32, vp], st),
         "bn_server_poll": ([vp, vp, u32, ctypes.POINTER(ctypes.c_uint32)], st),
@@ -205,6 +208,36 @@ def bn_mul_ntt(a, b, crt: bool = False, out=None, stream=None):
     _check(lib.bn_mul_ntt(_ptr(a), _ptr(b), _ptr(out), na, nb, batch, int(bool(crt)),
                           _stream_handle(stream, a.device)), "bn_mul_ntt")
     return out
+
+
+def _same_length(name, a, b, out, stream):
+    lib = load()
+    a, b = _pair(a, b)
+    if a.shape[1] != b.shape[1]:
+        raise ValueError(f"{name}: a and b need the same limb count")
+    batch, n = a.shape[0], a.shape[1]
+    out = _out(out, batch, n, a)
+    _check(getattr(lib, name)(_ptr(a), _ptr(b), _ptr(out), n, batch,
+                              _stream_handle(stream, a.device)), name)
+    return out
+
+
+def bn_mul_low(a, b, out=None, stream=None):
+    """c = a * b mod 2^(32 n) per row: the low half of the classical product,
+    n limbs like the operands (Section 3, Fig. 3)."""
+    return _same_length("bn_mul_low", a, b, out, stream)
+
+
+def bn_poly(a, b, out=None, stream=None):
+    """c = (a*a + b)*(b*b + b) + a*b mod 2^(32 n) per row, one fused kernel
+    (Section 6's polynomial program)."""
+    return _same_length("bn_poly", a, b, out, stream)
+
+
+def bn_add6(a, b, out=None, stream=None):
+    """Six dependent additions x_{k+1} = x_k + x_{k-1} from x_0 = a, x_1 = b,
+    i.e. c = 8a + 13b mod 2^(32 n) per row, one fused kernel (Section 6)."""
+    return _same_length("bn_add6", a, b, out, stream)
 
 
 def bn_mul_ntt_noalloc(a, b, crt: bool = False, out=None, stream=None):

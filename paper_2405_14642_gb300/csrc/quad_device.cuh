@@ -1,0 +1,226 @@
+// Device building blocks of the schoolbook product (Section 3), shared by the
+// plain, batched and fused kernels: the shared-memory layout, the per-window
+// multiply-accumulate chains and the window loop.  See mul_quad.cu for the
+// partition they implement.
+#pragma once
+#include "bn_device.cuh"
+
+namespace bn {
+namespace quad {
+
+constexpr uint32_t kQuadMaxThreads = 1024;
+
+// Shared-memory word index for logical index x: a 16-byte pad after every 32
+// words, which keeps 16-byte vector accesses at a stride of Q words free of
+// bank conflicts.  x must be a multiple of 4 for vector accesses.
+__device__ __forceinline__ uint32_t phys(uint32_t x) { return x + 4u * (x >> 5); }
+__host__ __device__ constexpr uint32_t phys_size(uint32_t x) { return x + 4u * ((x + 31) >> 5); }
+
+__host__ __device__ inline uint32_t roundup(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
+
+struct Geometry {
+    uint32_t nap, nbp, units, group, ipb, inst_words, ab_words, l_offset, hc_offset, block, smem;
+};
+
+__host__ __device__ inline Geometry geometry(uint32_t na, uint32_t nb, uint32_t Q, uint32_t cta_target) {
+    Geometry g{};
+    g.nbp = roundup(nb, 2 * Q);
+    g.nap = roundup(na, Q);
+    if (g.nap < g.nbp) g.nap = g.nbp;
+    g.units = g.nap / Q;
+    if (g.units <= 32) {
+        g.group = 1;
+        while (g.group < g.units) g.group <<= 1;
+    } else {
+        g.group = roundup(g.units, 32);
+    }
+    g.ipb = g.group < cta_target ? cta_target / g.group : 1;
+    // A at [0, phys_size(nap)), B (logical -Q .. nbp+Q) after it, then L
+    // (nap + nbp words) and the H spill words (2 per window).
+    const uint32_t a_words = roundup(phys_size(g.nap), 4);
+    const uint32_t b_words = roundup(phys_size(g.nbp + 2 * Q), 4);
+    const uint32_t l_words = roundup(phys_size(g.nap + g.nbp), 4);
+    g.ab_words = a_words;
+    g.l_offset = a_words + b_words;
+    g.hc_offset = g.l_offset + l_words;
+    const uint32_t windows = (g.nap + g.nbp) / Q;
+    g.inst_words = roundup(g.hc_offset + 2 * windows, 4);
+    g.block = g.group * g.ipb;
+    g.smem = 4 * (g.inst_words * g.ipb + 32);
+    return g;
+}
+
+
+// acc += a * (w[0] + w[1] 2^32 + ... + w[Q-1] 2^{32(Q-1)}), acc has Q+2 words.
+template <int Q>
+__device__ __forceinline__ void mac(uint32_t (&acc)[Q + 2], uint32_t a, const uint32_t (&w)[Q]);
+
+template <>
+__device__ __forceinline__ void mac<4>(uint32_t (&acc)[6], uint32_t a, const uint32_t (&w)[4]) {
+    asm("mad.lo.cc.u32  %0, %6, %7,  %0;\n\t"
+        "madc.lo.cc.u32 %1, %6, %8,  %1;\n\t"
+        "madc.lo.cc.u32 %2, %6, %9,  %2;\n\t"
+        "madc.lo.cc.u32 %3, %6, %10, %3;\n\t"
+        "addc.cc.u32    %4, %4, 0;\n\t"
+        "addc.u32       %5, %5, 0;\n\t"
+        "mad.hi.cc.u32  %1, %6, %7,  %1;\n\t"
+        "madc.hi.cc.u32 %2, %6, %8,  %2;\n\t"
+        "madc.hi.cc.u32 %3, %6, %9,  %3;\n\t"
+        "madc.hi.cc.u32 %4, %6, %10, %4;\n\t"
+        "addc.u32       %5, %5, 0;"
+        : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3]), "+r"(acc[4]), "+r"(acc[5])
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]));
+}
+
+template <>
+__device__ __forceinline__ void mac<8>(uint32_t (&acc)[10], uint32_t a, const uint32_t (&w)[8]) {
+    asm("mad.lo.cc.u32  %0, %10, %11, %0;\n\t"
+        "madc.lo.cc.u32 %1, %10, %12, %1;\n\t"
+        "madc.lo.cc.u32 %2, %10, %13, %2;\n\t"
+        "madc.lo.cc.u32 %3, %10, %14, %3;\n\t"
+        "madc.lo.cc.u32 %4, %10, %15, %4;\n\t"
+        "madc.lo.cc.u32 %5, %10, %16, %5;\n\t"
+        "madc.lo.cc.u32 %6, %10, %17, %6;\n\t"
+        "madc.lo.cc.u32 %7, %10, %18, %7;\n\t"
+        "addc.cc.u32    %8, %8, 0;\n\t"
+        "addc.u32       %9, %9, 0;\n\t"
+        "mad.hi.cc.u32  %1, %10, %11, %1;\n\t"
+        "madc.hi.cc.u32 %2, %10, %12, %2;\n\t"
+        "madc.hi.cc.u32 %3, %10, %13, %3;\n\t"
+        "madc.hi.cc.u32 %4, %10, %14, %4;\n\t"
+        "madc.hi.cc.u32 %5, %10, %15, %5;\n\t"
+        "madc.hi.cc.u32 %6, %10, %16, %6;\n\t"
+        "madc.hi.cc.u32 %7, %10, %17, %7;\n\t"
+        "madc.hi.cc.u32 %8, %10, %18, %8;\n\t"
+        "addc.u32       %9, %9, 0;"
+        : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3]), "+r"(acc[4]), "+r"(acc[5]),
+          "+r"(acc[6]), "+r"(acc[7]), "+r"(acc[8]), "+r"(acc[9])
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]),
+          "r"(w[7]));
+}
+
+// Column form (Section 3.2's accumulate step): column q keeps a 64-bit sum
+// and a carry count.  One mad.wide adds the full 64-bit product; the sum
+// wrapped exactly when its high word decreased, since a product's high word
+// is at most 2^32 - 2.
+template <int Q>
+__device__ __forceinline__ void mac_cols(uint64_t (&acc)[Q], uint32_t (&car)[Q], uint32_t a,
+                                         const uint32_t (&w)[Q]) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const uint32_t old_hi = (uint32_t)(acc[q] >> 32);
+        asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(a), "r"(w[q]));
+        car[q] += (uint32_t)(acc[q] >> 32) < old_hi;
+    }
+}
+
+// Window value sum_q (acc[q] + car[q] 2^64) 2^{32q} as Q+2 words.
+template <int Q>
+__device__ __forceinline__ void cols_to_words(const uint64_t (&acc)[Q], const uint32_t (&car)[Q],
+                                              uint32_t (&out)[Q + 2]) {
+    uint64_t c = 0;
+#pragma unroll
+    for (int q = 0; q < Q + 2; ++q) {
+        uint64_t v = c;
+        if (q < Q) v += (uint32_t)acc[q];
+        if (q >= 1 && q <= Q) v += (uint32_t)(acc[q - 1] >> 32);
+        if (q >= 2) v += car[q - 2];
+        out[q] = (uint32_t)v;
+        c = v >> 32;
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void ld_words(const uint32_t *S, uint32_t x, uint32_t (&v)[Q]) {
+#pragma unroll
+    for (int j = 0; j < Q / 4; ++j) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(S + phys(x + 4 * j));
+        v[4 * j] = t.x; v[4 * j + 1] = t.y; v[4 * j + 2] = t.z; v[4 * j + 3] = t.w;
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void st_words(uint32_t *S, uint32_t x, const uint32_t *v) {
+#pragma unroll
+    for (int j = 0; j < Q / 4; ++j)
+        *reinterpret_cast<uint4 *>(S + phys(x + 4 * j)) =
+            make_uint4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+}
+
+// Q steps i = i0 .. i0+Q-1 of a window: the B window for step s is
+// B[k-i0-s .. k-i0-s+Q), taken from the chunk pair (lo, hi) = B[k-i0-Q .. k-i0+Q).
+template <int Q, bool COLS>
+__device__ __forceinline__ void window_block(const uint32_t *As, uint32_t i0, const uint32_t (&lo)[Q],
+                                             const uint32_t (&hi)[Q], uint32_t (&acc)[Q + 2],
+                                             uint64_t (&cacc)[Q], uint32_t (&ccar)[Q]) {
+    uint32_t av[4];
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+        if (s % 4 == 0) ld_words<4>(As, i0 + s, av);  // A four words at a time
+        uint32_t w[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int idx = Q - s + q;
+            w[q] = idx < Q ? lo[idx] : hi[idx - Q];
+        }
+        if constexpr (COLS) mac_cols<Q>(cacc, ccar, av[s % 4], w);
+        else mac<Q>(acc, av[s % 4], w);
+    }
+}
+
+// Window starting at column k: sum over i in [ilo, ilo + steps) of
+// A_i * B[k-i .. k-i+Q).  B's logical index x lives at phys(x + Q).
+// ilo, k and steps are multiples of Q.  Blocks alternate between two chunk
+// buffers, so the chunk that moves from "lower" to "upper" is never copied.
+template <int Q, bool COLS>
+__device__ __forceinline__ void conv_window(const uint32_t *As, const uint32_t *Bs, uint32_t k,
+                                            uint32_t ilo, uint32_t steps, uint32_t (&acc)[Q + 2]) {
+    uint64_t cacc[Q];
+    uint32_t ccar[Q];
+#pragma unroll
+    for (int q = 0; q < Q + 2; ++q) acc[q] = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        cacc[q] = 0;
+        ccar[q] = 0;
+    }
+    // xb = (k - i0) + Q: the offset-Q index of the current block's upper chunk.
+    uint32_t xb = k - ilo + Q, i0 = ilo;
+    const uint32_t nblk = steps / Q;
+    uint32_t c0[Q], c1[Q];
+    ld_words<Q>(Bs, xb, c1);
+    for (uint32_t b = 0; b + 1 < nblk; b += 2) {
+        ld_words<Q>(Bs, xb - Q, c0);
+        window_block<Q, COLS>(As, i0, c0, c1, acc, cacc, ccar);
+        ld_words<Q>(Bs, xb - 2 * Q, c1);
+        window_block<Q, COLS>(As, i0 + Q, c1, c0, acc, cacc, ccar);
+        xb -= 2 * Q;
+        i0 += 2 * Q;
+    }
+    if (nblk & 1) {
+        ld_words<Q>(Bs, xb - Q, c0);
+        window_block<Q, COLS>(As, i0, c0, c1, acc, cacc, ccar);
+    }
+    if constexpr (COLS) cols_to_words<Q>(cacc, ccar, acc);
+}
+
+// Copies n words of a global row into shared memory at logical offset `off`
+// (layout phys), zero-filling logical [off + n, off + n_pad).
+__device__ __forceinline__ void stage_row(uint32_t *S, const uint32_t *row, uint32_t n,
+                                          uint32_t off, uint32_t n_pad, bool vec, bool live,
+                                          uint32_t t, uint32_t group) {
+    if (vec && live) {
+        for (uint32_t x = 4 * t; x < n; x += 4 * group) {
+            const uint4 v = ld_stream_v4(row + x);
+            *reinterpret_cast<uint4 *>(S + phys(off + x)) = v;
+        }
+        for (uint32_t x = n + t; x < n_pad; x += group) S[phys(off + x)] = 0;
+    } else {
+        for (uint32_t x = t; x < n_pad; x += group)
+            S[phys(off + x)] = (live && x < n) ? ld_stream(row + x) : 0u;
+    }
+}
+
+
+}  // namespace quad
+}  // namespace bn
