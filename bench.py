@@ -213,8 +213,8 @@ def imad_peak(torch, bn, dev):
 
 
 def kernel_traffic(op_label: str):
-    """DRAM bytes per launch from the committed ncu capture of this op, if the
-    kernel source is unchanged since the capture (else None)."""
+    """DRAM bytes per launch from the committed ncu capture of this op, if none
+    of the kernel's source files changed since the capture (else None)."""
     import hashlib
     p = ROOT / "profiles" / "traffic.json"
     if not p.exists():
@@ -222,9 +222,12 @@ def kernel_traffic(op_label: str):
     entry = json.loads(p.read_text()).get(op_label)
     if not entry:
         return None
-    src = ROOT / entry["source"]
-    if not src.exists() or hashlib.sha256(src.read_bytes()).hexdigest() != entry["sha256"]:
+    if not entry.get("sources"):
         return None
+    for rel, digest in entry["sources"].items():
+        src = ROOT / rel
+        if not src.exists() or hashlib.sha256(src.read_bytes()).hexdigest() != digest:
+            return None
     return entry["dram_bytes"]
 
 

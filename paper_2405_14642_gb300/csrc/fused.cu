@@ -199,119 +199,136 @@ __global__ void __launch_bounds__(1024) k_poly(LowArgs p) {
 }
 
 // ---- 6-Add ------------------------------------------------------------------
+//
+// Each thread owns one contiguous run of L limbs of an instance, so an
+// addition costs L add-with-carry steps, an all-ones test and ONE carry scan
+// per thread (the scan, not the limb arithmetic, dominated with 4-limb chunks).
 
-template <int VEC>
-__device__ __forceinline__ void load_chunk(const uint32_t *row, uint32_t j, bool in, uint32_t (&v)[VEC]) {
-    if constexpr (VEC == 4) {
-        const uint4 t = in ? ld_stream_v4(row + 4 * j) : make_uint4(0, 0, 0, 0);
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+// s = a + b over 8 limbs, returns the carry out; s may alias a.
+__device__ __forceinline__ uint32_t add8(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t cin) {
+    uint32_t c = cin;
+    asm("add.cc.u32 %8, %8, 0xffffffff;\n\t"   // CF = (cin != 0)
+        "addc.cc.u32 %0, %9, %17;\n\t"
+        "addc.cc.u32 %1, %10, %18;\n\t"
+        "addc.cc.u32 %2, %11, %19;\n\t"
+        "addc.cc.u32 %3, %12, %20;\n\t"
+        "addc.cc.u32 %4, %13, %21;\n\t"
+        "addc.cc.u32 %5, %14, %22;\n\t"
+        "addc.cc.u32 %6, %15, %23;\n\t"
+        "addc.cc.u32 %7, %16, %24;\n\t"
+        "addc.u32 %8, 0, 0;"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]),
+          "=r"(s[7]), "+r"(c)
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),
+          "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
+    return c;
+}
+
+// s += cin (cin in {0, 1}) over 8 limbs, returns the carry out.
+__device__ __forceinline__ uint32_t inc8(uint32_t *s, uint32_t cin) {
+    uint32_t c;
+    asm("add.cc.u32 %0, %0, %9;\n\t"
+        "addc.cc.u32 %1, %1, 0;\n\t"
+        "addc.cc.u32 %2, %2, 0;\n\t"
+        "addc.cc.u32 %3, %3, 0;\n\t"
+        "addc.cc.u32 %4, %4, 0;\n\t"
+        "addc.cc.u32 %5, %5, 0;\n\t"
+        "addc.cc.u32 %6, %6, 0;\n\t"
+        "addc.cc.u32 %7, %7, 0;\n\t"
+        "addc.u32 %8, 0, 0;"
+        : "+r"(s[0]), "+r"(s[1]), "+r"(s[2]), "+r"(s[3]), "+r"(s[4]), "+r"(s[5]), "+r"(s[6]),
+          "+r"(s[7]), "=r"(c)
+        : "r"(cin));
+    return c;
+}
+
+template <int L>
+__device__ __forceinline__ uint32_t add_run(const uint32_t (&a)[L], const uint32_t (&b)[L], uint32_t (&s)[L]) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < L; k += 8) c = add8(a + k, b + k, s + k, c);
+    return c;
+}
+
+template <int L>
+__device__ __forceinline__ void inc_run(uint32_t (&s)[L], uint32_t cin) {
+#pragma unroll
+    for (int k = 0; k < L; k += 8) cin = inc8(s + k, cin);
+}
+
+template <int L>
+__device__ __forceinline__ uint32_t all_ones_run(const uint32_t (&s)[L]) {
+    uint32_t x = s[0];
+#pragma unroll
+    for (int k = 1; k < L; ++k) x &= s[k];
+    return x == 0xffffffffu;
+}
+
+// Run j (limbs L*j .. L*j+L-1) of a row of n limbs, zero beyond n.  With VEC
+// the row start is 16-byte aligned and n a multiple of 4, so each group of 4
+// limbs is wholly inside or outside the row.
+template <int L, bool VEC>
+__device__ __forceinline__ void load_run(const uint32_t *row, uint32_t j, uint32_t n, bool live,
+                                         uint32_t (&v)[L]) {
+    const uint32_t x0 = L * j;
+    if constexpr (VEC) {
+#pragma unroll
+        for (int k = 0; k < L; k += 4) {
+            const bool in = live && x0 + k < n;
+            const uint4 t = in ? ld_stream_v4(row + x0 + k) : make_uint4(0, 0, 0, 0);
+            v[k] = t.x; v[k + 1] = t.y; v[k + 2] = t.z; v[k + 3] = t.w;
+        }
     } else {
-        v[0] = in ? ld_stream(row + j) : 0u;
+#pragma unroll
+        for (int k = 0; k < L; ++k) v[k] = (live && x0 + k < n) ? ld_stream(row + x0 + k) : 0u;
     }
 }
 
-template <int VEC>
-__device__ __forceinline__ void store_chunk(uint32_t *row, uint32_t j, const uint32_t (&v)[VEC]) {
-    if constexpr (VEC == 4) st_stream_v4(row + 4 * j, make_uint4(v[0], v[1], v[2], v[3]));
-    else st_stream(row + j, v[0]);
+template <int L, bool VEC>
+__device__ __forceinline__ void store_run(uint32_t *row, uint32_t j, uint32_t n, const uint32_t (&v)[L]) {
+    const uint32_t x0 = L * j;
+    if constexpr (VEC) {
+#pragma unroll
+        for (int k = 0; k < L; k += 4)
+            if (x0 + k < n) st_stream_v4(row + x0 + k, make_uint4(v[k], v[k + 1], v[k + 2], v[k + 3]));
+    } else {
+#pragma unroll
+        for (int k = 0; k < L; ++k)
+            if (x0 + k < n) st_stream(row + x0 + k, v[k]);
+    }
 }
 
 struct Add6Args {
     const uint32_t *a, *b;
     uint32_t *c;
-    uint32_t n, chunks, group, log2_group, warps_per_team, teams_per_cta;
+    uint32_t n, group, ipb;
     uint64_t batch;
 };
 
-// Instances of at most 32 chunks: `group` lanes (a power of two) per instance,
-// one chunk per lane, each addition one segmented warp scan.
-template <int VEC>
-__global__ void __launch_bounds__(256) k_add6_sub(Add6Args p) {
-    const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t inst = gt >> p.log2_group;
-    const uint32_t j = (uint32_t)gt & (p.group - 1);
-    const bool live = inst < p.batch && j < p.chunks;
-    uint32_t x[2][VEC];
-    load_chunk<VEC>(p.a + inst * p.n, j, live, x[0]);
-    load_chunk<VEC>(p.b + inst * p.n, j, live, x[1]);
-    // Step k overwrites x_{k-1} (set k % 2) with x_{k+1} = x_k + x_{k-1}.
+// `group` threads per instance (a power of two <= 32, or whole warps), `ipb`
+// instances per CTA.  Step k overwrites x_{k-1} (register set k % 2) with
+// x_{k+1} = x_k + x_{k-1}; after six steps set 1 holds x_7.  For whole-warp
+// groups the warp summaries alternate between two buffers, so one barrier
+// per addition suffices: a warp writes buffer k % 2 only after passing
+// addition k-1's barrier, which every reader of addition k-2 reached after
+// its read.
+template <int L, bool VEC>
+__global__ void __launch_bounds__(512) k_add6(Add6Args p) {
+    __shared__ uint32_t flags[2][16];
+    const uint32_t slot = threadIdx.x / p.group, t = threadIdx.x - slot * p.group;
+    const uint64_t inst = (uint64_t)blockIdx.x * p.ipb + slot;
+    const bool live = inst < p.batch;
+    uint32_t x[2][L];
+    load_run<L, VEC>(p.a + inst * p.n, t, p.n, live, x[0]);
+    load_run<L, VEC>(p.b + inst * p.n, t, p.n, live, x[1]);
 #pragma unroll
     for (int step = 0; step < 6; ++step) {
-        uint32_t(&z)[VEC] = x[step % 2];
-        const uint32_t g = chunk_add<VEC>(z, x[(step + 1) % 2], z);
-        const uint32_t cin = group_carry_in(g, chunk_all_ones<VEC>(z), p.group, nullptr);
-        chunk_inc<VEC>(z, cin);
+        uint32_t(&z)[L] = x[step % 2];
+        const uint32_t g = add_run<L>(z, x[(step + 1) % 2], z);
+        const uint32_t cin = group_carry_in(g, all_ones_run<L>(z), p.group, flags[step % 2]);
+        inc_run<L>(z, cin);
     }
-    if (live) store_chunk<VEC>(p.c + inst * p.n, j, x[1]);
-}
-
-// z = z + y over the team's chunks (R rows of 32 chunks of VEC limbs per
-// warp), carries resolved across the team as in k_add_team; no carry out.
-// The warp summaries alternate between two buffers, so one barrier per
-// addition suffices: a warp writes buffer k % 2 only after passing addition
-// k-1's barrier, which every reader of addition k-2 reached after its read.
-template <int VEC, int R>
-__device__ __forceinline__ void team_add(uint32_t (&z)[R][VEC], const uint32_t (&y)[R][VEC],
-                                         uint32_t w, uint32_t team_in_cta, uint32_t warps_per_team,
-                                         uint32_t *warp_flags) {
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t gbits = 0, pbits = 0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        gbits |= chunk_add<VEC>(z[r], y[r], z[r]) << r;
-        pbits |= chunk_all_ones<VEC>(z[r]) << r;
-    }
-    uint32_t wg = 0, wp = 1;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const RowFlags f{__ballot_sync(FULL_MASK, (gbits >> r) & 1u), __ballot_sync(FULL_MASK, (pbits >> r) & 1u)};
-        uint32_t rg;
-        row_carries(f, 0, rg);
-        carry_compose(wg, wp, rg, f.P == FULL_MASK);
-    }
-    if (lane == 0) warp_flags[warp] = wg | (wp << 1);
-    __syncthreads();
-    const uint32_t sw = lane < warps_per_team ? warp_flags[team_in_cta * warps_per_team + lane] : 0u;
-    const RowFlags fw{__ballot_sync(FULL_MASK, sw & 1u), __ballot_sync(FULL_MASK, (sw >> 1) & 1u)};
-    uint32_t unused;
-    uint32_t cin = (row_carries(fw, 0, unused) >> w) & 1u;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const RowFlags f{__ballot_sync(FULL_MASK, (gbits >> r) & 1u), __ballot_sync(FULL_MASK, (pbits >> r) & 1u)};
-        uint32_t cout;
-        const uint32_t ci = (row_carries(f, cin, cout) >> lane) & 1u;
-        cin = cout;
-        chunk_inc<VEC>(z[r], ci);
-    }
-}
-
-// Instances of more than 32 chunks: a team of whole warps per instance.
-template <int VEC, int R>
-__global__ void __launch_bounds__(512) k_add6_team(Add6Args p) {
-    __shared__ uint32_t warp_flags[2][16];
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t team_in_cta = warp / p.warps_per_team, w = warp - team_in_cta * p.warps_per_team;
-    const uint64_t inst = (uint64_t)blockIdx.x * p.teams_per_cta + team_in_cta;
-    const bool live = inst < p.batch;
-    const uint32_t j0 = w * R * 32 + lane;
-    uint32_t x[2][R][VEC];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t j = j0 + r * 32;
-        const bool in = live && j < p.chunks;
-        load_chunk<VEC>(p.a + inst * p.n, j, in, x[0][r]);
-        load_chunk<VEC>(p.b + inst * p.n, j, in, x[1][r]);
-    }
-#pragma unroll
-    for (int step = 0; step < 6; ++step)
-        team_add<VEC, R>(x[step % 2], x[(step + 1) % 2], w, team_in_cta, p.warps_per_team,
-                         warp_flags[step % 2]);
-    if (!live) return;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t j = j0 + r * 32;
-        if (j < p.chunks) store_chunk<VEC>(p.c + inst * p.n, j, x[1][r]);
-    }
+    if (live) store_run<L, VEC>(p.c + inst * p.n, t, p.n, x[1]);
 }
 
 // ---- host side ---------------------------------------------------------------
@@ -378,9 +395,9 @@ bn_status launch_low(bool poly, const uint32_t *a, const uint32_t *b, uint32_t *
     return BN_OK;
 }
 
-template <int VEC, int R>
+template <int L, bool VEC>
 void launch_add6_t(const Add6Args &p, uint32_t block, uint64_t grid, cudaStream_t st) {
-    k_add6_team<VEC, R><<<(unsigned)grid, block, 0, st>>>(p);
+    k_add6<L, VEC><<<(unsigned)grid, block, 0, st>>>(p);
 }
 
 bn_status launch_add6(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_t n, uint64_t batch,
@@ -388,45 +405,26 @@ bn_status launch_add6(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_
     const bool vec = (n % 4 == 0) && ((uintptr_t)a % 16 == 0) && ((uintptr_t)b % 16 == 0);
     Add6Args p{};
     p.a = a; p.b = b; p.c = c; p.n = n; p.batch = batch;
-    const uint32_t V = vec ? 4 : 1;
-    p.chunks = (n + V - 1) / V;
-    if (p.chunks <= 32) {
+    // 8 limbs a thread while an instance fits in 8 warps, else 16 (<= 16 warps).
+    const uint32_t L = n <= 8 * 256 ? 8 : 16;
+    const uint32_t runs = (n + L - 1) / L;
+    if (runs <= 32) {
         p.group = 1;
-        p.log2_group = 0;
-        while (p.group < p.chunks) {
-            p.group <<= 1;
-            ++p.log2_group;
-        }
-        const uint32_t block = 256;
-        const uint64_t grid = ((batch << p.log2_group) + block - 1) / block;
-        if (grid > 0x7fffffffull) return BN_EUNSUPPORTED;
-        if (vec) k_add6_sub<4><<<(unsigned)grid, block, 0, st>>>(p);
-        else k_add6_sub<1><<<(unsigned)grid, block, 0, st>>>(p);
+        while (p.group < runs) p.group <<= 1;
     } else {
-        // Up to 16 limbs a thread in each of the two register sets.
-        const uint32_t r_max = vec ? 4 : 16;
-        uint32_t R = 1, W = (p.chunks + 31) / 32;
-        while (W > 8 && R < r_max) {
-            R *= 2;
-            W = (p.chunks + 32 * R - 1) / (32 * R);
-        }
-        if (W > 16) return BN_EUNSUPPORTED;
-        p.warps_per_team = W;
-        p.teams_per_cta = 256 > 32 * W ? 256 / (32 * W) : 1;
-        const uint32_t block = 32 * W * p.teams_per_cta;
-        const uint64_t grid = (batch + p.teams_per_cta - 1) / p.teams_per_cta;
-        if (grid > 0x7fffffffull) return BN_EUNSUPPORTED;
-        if (vec) {
-            if (R == 1) launch_add6_t<4, 1>(p, block, grid, st);
-            else if (R == 2) launch_add6_t<4, 2>(p, block, grid, st);
-            else launch_add6_t<4, 4>(p, block, grid, st);
-        } else {
-            if (R == 1) launch_add6_t<1, 1>(p, block, grid, st);
-            else if (R == 2) launch_add6_t<1, 2>(p, block, grid, st);
-            else if (R == 4) launch_add6_t<1, 4>(p, block, grid, st);
-            else if (R == 8) launch_add6_t<1, 8>(p, block, grid, st);
-            else launch_add6_t<1, 16>(p, block, grid, st);
-        }
+        p.group = roundup(runs, 32);
+    }
+    if (p.group > 512) return BN_EUNSUPPORTED;
+    p.ipb = p.group < 256 ? 256 / p.group : 1;
+    const uint32_t block = p.group * p.ipb;
+    const uint64_t grid = (batch + p.ipb - 1) / p.ipb;
+    if (grid > 0x7fffffffull) return BN_EUNSUPPORTED;
+    if (L == 8) {
+        if (vec) launch_add6_t<8, true>(p, block, grid, st);
+        else launch_add6_t<8, false>(p, block, grid, st);
+    } else {
+        if (vec) launch_add6_t<16, true>(p, block, grid, st);
+        else launch_add6_t<16, false>(p, block, grid, st);
     }
     if (cudaError_t e = cudaGetLastError()) {
         record_error(cudaGetErrorString(e));
