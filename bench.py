@@ -320,6 +320,7 @@ def run_gpu(args, rank, world, local_rank):
     ms_per_step = max_ms / args.steps
     gpu_launches = args.steps * len(ops)
 
+    isolated = run_isolated(args, torch, ops, plans, inputs, outs, stream, dev) if args.isolated_reps else None
     fused = None
     if args.fused_reps > 0:
         fused = run_fused(args, torch, bn, dev, inputs, peak_info)
@@ -383,8 +384,44 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": roof, "rooflines": rooflines, "breakdown": rows,
         "imad_probe": peak_info, "clocks": clocks, "gpu_launches": gpu_launches,
         "e2e": e2e, "cpu_baseline": cpu, "impl": "ours", "skipped_ops": skipped,
-        "mixed": mixed, "serving": serving, "fused": fused,
+        "mixed": mixed, "serving": serving, "fused": fused, "isolated": isolated,
     }
+
+
+def run_isolated(args, torch, ops, plans, inputs, outs, stream, dev):
+    """Each op of the step timed alone, outside the timed region: before every
+    launch a read-only pass over 256 MiB evicts whatever the previous kernel
+    left dirty in L2 (inside the step, an op pays for writing back the
+    previous op's result, up to 128 MiB).  Results still in L2 when the timed
+    launch ends are written back after it, so these are per-kernel figures,
+    not a substitute for the step time."""
+    clean_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    rows = []
+    for o in ops:
+        ta, tb = inputs[o.bits]
+        out = outs[(o.bits, o.nout)]
+        ts = []
+        for _ in range(args.isolated_reps):
+            clean_buf.sum(dtype=torch.int64)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plans[o.label].execute(ta, tb, out=out, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        row = {"op": o.label, "ms": round(ms, 4)}
+        if o.name == "add":
+            row["gbs"] = round(o.bytes / (ms * 1e-3) / 1e9, 1)
+        else:
+            row["word_tprods"] = round(o.prods / (ms * 1e-3) / 1e12, 3)
+        rows.append(row)
+    add_rows = [(o, r) for o, r in zip(ops, rows) if o.name == "add"]
+    add_gbs = (sum(o.bytes for o, _ in add_rows) / (sum(r["ms"] for _, r in add_rows) * 1e-3) / 1e9
+               if add_rows else None)
+    return {"how": "median of %d launches, each after a read-only pass over 256 MiB (L2 holds "
+                   "no dirty lines from other kernels)" % args.isolated_reps,
+            "add_gbs": round(add_gbs, 1) if add_gbs else None, "ops": rows}
 
 
 def run_fused(args, torch, bn, dev, inputs, peak_info):
@@ -718,6 +755,8 @@ def main(argv=None):
     ap.add_argument("--mixed-items", type=int, default=200000,
                     help="operations in the mixed-size batch comparison (0 = skip)")
     ap.add_argument("--mixed-steps", type=int, default=5)
+    ap.add_argument("--isolated-reps", type=int, default=3,
+                    help="launches per op in the isolated per-kernel pass (0 = skip)")
     ap.add_argument("--fused-reps", type=int, default=3,
                     help="timed repetitions of each fused program per size (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=50000,

@@ -27,14 +27,11 @@ __device__ void low_product(const uint32_t *As, const uint32_t *Bs, uint32_t np,
                             uint32_t *Hc, uint32_t *out, uint32_t *flags, uint32_t t, uint32_t group) {
     const uint32_t R = np / Q;
     if (t < R / 2) {
-        uint32_t acc[Q + 2];
-        const uint32_t k0 = t * Q, k1 = (R - 1 - t) * Q;
-        conv_window<Q, false>(As, Bs, k0, 0, k0 + Q, acc);
-        st_words<Q>(Ls, k0, acc);
-        *reinterpret_cast<uint2 *>(Hc + 2 * (k0 / Q)) = make_uint2(acc[Q], acc[Q + 1]);
-        conv_window<Q, false>(As, Bs, k1, 0, k1 + Q, acc);
-        st_words<Q>(Ls, k1, acc);
-        *reinterpret_cast<uint2 *>(Hc + 2 * (k1 / Q)) = make_uint2(acc[Q], acc[Q + 1]);
+        const Unit u{t * Q, 0, t + 1, (R - 1 - t) * Q, 0, R - t};
+        conv_unit<Q>(As, Bs, u, [&](uint32_t k, const uint32_t (&acc)[Q + 2]) {
+            st_words<Q>(Ls, k, acc);
+            *reinterpret_cast<uint2 *>(Hc + 2 * (k / Q)) = make_uint2(acc[Q], acc[Q + 1]);
+        });
     }
     __syncthreads();
     constexpr int W2 = 2 * Q;
@@ -200,7 +197,7 @@ __global__ void __launch_bounds__(1024) k_poly(LowArgs p) {
 
 // ---- 6-Add ------------------------------------------------------------------
 //
-// Each thread owns one contiguous run of L limbs of an instance, so an
+// Each thread owns one contiguous run of L = 16 limbs of an instance, so an
 // addition costs L add-with-carry steps, an all-ones test and ONE carry scan
 // per thread (the scan, not the limb arithmetic, dominated with 4-limb chunks).
 
@@ -405,8 +402,10 @@ bn_status launch_add6(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_
     const bool vec = (n % 4 == 0) && ((uintptr_t)a % 16 == 0) && ((uintptr_t)b % 16 == 0);
     Add6Args p{};
     p.a = a; p.b = b; p.c = c; p.n = n; p.batch = batch;
-    // 8 limbs a thread while an instance fits in 8 warps, else 16 (<= 16 warps).
-    const uint32_t L = n <= 8 * 256 ? 8 : 16;
+    // 16 limbs a thread: timed against 8 (the scan's cost is per thread, so
+    // 16 wins up to 16K bits and ties above) and 32 (register-bound, slower
+    // from 32K bits on).
+    constexpr uint32_t L = 16;
     const uint32_t runs = (n + L - 1) / L;
     if (runs <= 32) {
         p.group = 1;
@@ -419,13 +418,8 @@ bn_status launch_add6(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_
     const uint32_t block = p.group * p.ipb;
     const uint64_t grid = (batch + p.ipb - 1) / p.ipb;
     if (grid > 0x7fffffffull) return BN_EUNSUPPORTED;
-    if (L == 8) {
-        if (vec) launch_add6_t<8, true>(p, block, grid, st);
-        else launch_add6_t<8, false>(p, block, grid, st);
-    } else {
-        if (vec) launch_add6_t<16, true>(p, block, grid, st);
-        else launch_add6_t<16, false>(p, block, grid, st);
-    }
+    if (vec) launch_add6_t<L, true>(p, block, grid, st);
+    else launch_add6_t<L, false>(p, block, grid, st);
     if (cudaError_t e = cudaGetLastError()) {
         record_error(cudaGetErrorString(e));
         return BN_ECUDA;

@@ -73,7 +73,23 @@ __device__ __forceinline__ void quad_instance(const QuadArgs &p, uint64_t inst, 
     // is needed first and nothing stays live across windows.
     const uint32_t R = p.nbp / Q;               // windows in each sloped region
     const uint32_t plateau = (p.nap - p.nbp) / Q;
-    if (t < p.units) {
+    if (!COLS && t < p.units) {
+        Unit u{};
+        if (t < R / 2) {                        // rising pair: t+1 and R-t blocks
+            u = Unit{t * Q, 0, t + 1, (R - 1 - t) * Q, 0, R - t};
+        } else if (t < R / 2 + plateau) {       // plateau window: R+1 blocks
+            const uint32_t k0 = p.nbp + (t - R / 2) * Q;
+            u = Unit{k0, k0 - p.nbp, R + 1, 0, 0, 0};
+        } else {                                // falling pair: R-r and r+1 blocks
+            const uint32_t r = t - R / 2 - plateau;
+            const uint32_t k0 = p.nap + r * Q, k1 = p.nap + (R - 1 - r) * Q;
+            u = Unit{k0, k0 - p.nbp, R - r, k1, k1 - p.nbp, r + 1};
+        }
+        conv_unit<Q>(As, Bs, u, [&](uint32_t k, const uint32_t (&acc)[Q + 2]) {
+            st_words<Q>(Ls, k, acc);
+            *reinterpret_cast<uint2 *>(Hc + 2 * (k / Q)) = make_uint2(acc[Q], acc[Q + 1]);
+        });
+    } else if (t < p.units) {
         uint32_t acc[Q + 2];
         auto publish = [&](uint32_t k) {
             st_words<Q>(Ls, k, acc);

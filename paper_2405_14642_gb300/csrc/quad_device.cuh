@@ -204,6 +204,55 @@ __device__ __forceinline__ void conv_window(const uint32_t *As, const uint32_t *
     if constexpr (COLS) cols_to_words<Q>(cacc, ccar, acc);
 }
 
+// A unit of work: up to two windows run back to back as ONE loop of n0 + n1
+// blocks.  Window w starts at column k_w with first step ilo_w and takes n_w
+// blocks (n1 = 0: one window).  Every unit of the partition has the same
+// total (R + 1 blocks), so the lanes of a warp share one trip count whatever
+// their windows; only the hand-over between the windows diverges.  Each
+// finished window goes to publish(k, acc).
+struct Unit {
+    uint32_t k0, ilo0, n0, k1, ilo1, n1;
+};
+
+template <int Q, class Publish>
+__device__ __forceinline__ void conv_unit(const uint32_t *As, const uint32_t *Bs, const Unit &u,
+                                          Publish &&publish) {
+    uint32_t acc[Q + 2];
+    uint64_t cacc[Q];  // unused by the chain form
+    uint32_t ccar[Q];
+#pragma unroll
+    for (int q = 0; q < Q + 2; ++q) acc[q] = 0;
+    uint32_t k = u.k0, i0 = u.ilo0, left = u.n0, second = u.n1;
+    const uint32_t total = u.n0 + u.n1;
+    uint32_t c0[Q], c1[Q];
+    ld_words<Q>(Bs, k - i0 + Q, c1);  // upper chunk of the first block
+    // After a window's last block: publish it and start the next one, whose
+    // upper chunk goes to the buffer the next block reads as "upper".
+    auto finish = [&](uint32_t (&next_hi)[Q]) {
+        publish(k, acc);
+#pragma unroll
+        for (int q = 0; q < Q + 2; ++q) acc[q] = 0;
+        if (second) {
+            k = u.k1;
+            i0 = u.ilo1;
+            left = second;
+            second = 0;
+            ld_words<Q>(Bs, k - i0 + Q, next_hi);
+        }
+    };
+    for (uint32_t b = 0; b < total; b += 2) {
+        ld_words<Q>(Bs, k - i0, c0);
+        window_block<Q, false>(As, i0, c0, c1, acc, cacc, ccar);
+        i0 += Q;
+        if (--left == 0) finish(c0);
+        if (b + 1 == total) break;
+        ld_words<Q>(Bs, k - i0, c1);
+        window_block<Q, false>(As, i0, c1, c0, acc, cacc, ccar);
+        i0 += Q;
+        if (--left == 0) finish(c1);
+    }
+}
+
 // Copies n words of a global row into shared memory at logical offset `off`
 // (layout phys), zero-filling logical [off + n, off + n_pad).
 __device__ __forceinline__ void stage_row(uint32_t *S, const uint32_t *row, uint32_t n,
