@@ -30,6 +30,13 @@ Readings taken here (the paper is silent or inexact on these points):
   chosen, like p1, with low 32-bit word 1 and below 2^62.
 * ``g`` as printed is itself a primitive ``2^n``-th root of unity (verified in
   the tests), and ``omega_M = g^(2^n / M)``.
+* Three-prime form (not in the paper; Section 4 uses one field per product).
+  32-bit digits over three good primes below 2^30 -- 7 * 2^26 + 1,
+  45 * 2^24 + 1 and 119 * 2^23 + 1 -- recombined by Garner's mixed-radix CRT.
+  Their product (~2^88.2) exceeds the coefficient bound N (2^32 - 1)^2 for
+  every transform length up to 2^23, and primes below 2^30 are what lets a
+  GPU keep field elements in 32-bit words with lazy reductions.  Each root is
+  the first hit of Section 4.1's search.
 """
 from __future__ import annotations
 
@@ -60,6 +67,11 @@ PRIME_FIELD_64 = PrimeField("PrimeField64", 4179340454199820289, 29, 57, 21)
 # first a whose a^27 has order exactly 2^56 (Section 4.1's search).
 _P_CRT2 = 27 * (1 << 56) + 1
 PRIME_FIELD_CRT2 = PrimeField("CRT2", _P_CRT2, 27, 56, pow(5, 27, _P_CRT2))
+
+
+def _search_root_field(name: str, k: int, n: int) -> PrimeField:
+    p = k * (1 << n) + 1
+    return PrimeField(name, p, k, n, search_root(p, k, n))
 
 
 def search_root(p: int, k: int, n: int, limit: int = 1000) -> int:
@@ -211,5 +223,34 @@ def mul_two_prime(a: Sequence[int], b: Sequence[int], d: int = 32,
     c1 = convolve_mod(xd, yd, f1)
     c2 = convolve_mod(xd, yd, f2)
     coeffs = [garner(u, v, f1.p, f2.p) for u, v in zip(c1, c2)]
+    value = sum(c << (d * k) for k, c in enumerate(coeffs))
+    return int_to_limbs(value % (1 << (32 * (len(a) + len(b)))), len(a) + len(b))
+
+
+# ---- three 32-bit primes ---------------------------------------------------
+
+PRIME_FIELDS_3X32 = (
+    _search_root_field("P32a", 7, 26),     # 469762049
+    _search_root_field("P32b", 45, 24),    # 754974721
+    _search_root_field("P32c", 119, 23),   # 998244353
+)
+
+
+def garner3(r: Sequence[int], p: Sequence[int]) -> int:
+    """The unique c < p0 p1 p2 with c = r_i (mod p_i), by mixed radix:
+    c = v0 + v1 p0 + v2 p0 p1 with v0 = r0, v1 = (r1 - v0) / p0 mod p1,
+    v2 = ((r2 - v0) / p0 - v1) / p1 mod p2."""
+    v0 = r[0]
+    v1 = (r[1] - v0) * pow(p[0], -1, p[1]) % p[1]
+    v2 = ((r[2] - v0) * pow(p[0], -1, p[2]) - v1) * pow(p[1], -1, p[2]) % p[2]
+    return v0 + v1 * p[0] + v2 * p[0] * p[1]
+
+
+def mul_three_prime(a: Sequence[int], b: Sequence[int], d: int = 32,
+                    fields: Sequence[PrimeField] = PRIME_FIELDS_3X32) -> List[int]:
+    """a * b with d-bit digits, three prime fields and Garner recombination."""
+    xd, yd = to_digits(a, d), to_digits(b, d)
+    residues = [convolve_mod(xd, yd, f) for f in fields]
+    coeffs = [garner3(rs, [f.p for f in fields]) for rs in zip(*residues)]
     value = sum(c << (d * k) for k, c in enumerate(coeffs))
     return int_to_limbs(value % (1 << (32 * (len(a) + len(b)))), len(a) + len(b))

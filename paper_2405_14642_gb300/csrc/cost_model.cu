@@ -7,8 +7,8 @@ namespace bn {
 
 double default_quad_rate(uint32_t key) {
     // Schoolbook word products per microsecond by ceil(log2(longer operand)).
-    static const double r[14] = {0.5e6, 0.5e6, 0.5e6, 0.5e6, 0.5e6, 1.56e6, 1.69e6, 1.77e6, 3.15e6,
-                                 3.88e6, 4.37e6, 4.90e6, 5.20e6, 5.24e6};
+    static const double r[14] = {1.0e6, 1.0e6, 1.0e6, 1.0e6, 1.0e6, 3.12e6, 3.88e6, 4.41e6, 4.72e6,
+                                 5.12e6, 5.34e6, 5.45e6, 5.51e6, 5.33e6};
     return r[key < 14 ? key : 13];
 }
 

@@ -338,10 +338,10 @@ LowGeometry low_geometry(uint32_t n, bool poly) {
     LowGeometry g{};
     // Window size from GB300 timings over the 1K..256K-bit sweep: Q = 4 puts
     // twice the threads on an instance for the same shared memory, which wins
-    // where shared memory bounds the resident CTAs (small instances packed
-    // many to a CTA, and Poly's six buffers); Q = 8 halves the shared-memory
-    // loads per word product, which wins elsewhere.
-    const bool q4 = poly ? (n <= 192 || (n > 384 && n <= 1536)) : (n <= 48 || (n > 384 && n <= 768));
+    // only for the smallest instances (packed many to a CTA, where shared
+    // memory bounds the resident CTAs); Q = 8 halves the shared-memory loads
+    // per word product and wins from 2K bits (1-Mul) or 4K bits (Poly) up.
+    const bool q4 = poly ? n <= 96 : n <= 48;
     g.q = q4 ? 4 : 8;
     g.np = roundup(n, 2 * g.q);
     const uint32_t units = g.np / (2 * g.q);

