@@ -68,11 +68,19 @@ typedef enum bn_op {
      * digits, transform length the next power of two >= 2(na + nb). */
     BN_OP_MUL_NTT64 = 2,
     /* Section 4 with 32-bit digits over two primes (29*2^57 + 1 and
-     * 2^64 - 2^32 + 1), recombined by the Chinese remainder theorem. */
+     * 27*2^56 + 1), recombined by the Chinese remainder theorem. */
     BN_OP_MUL_NTT_CRT = 3,
     /* Batch items only: multiplication by whichever of the above a mixed-size
      * batch's cost model finds fastest for the item's sizes. */
-    BN_OP_MUL_AUTO = 4
+    BN_OP_MUL_AUTO = 4,
+    /* Section 4's transform product over three 32-bit good primes
+     * (7*2^26 + 1, 45*2^24 + 1, 119*2^23 + 1; roots by the Section 4.1
+     * search) with 32-bit digits, recombined by Garner's mixed-radix CRT
+     * (coefficients < 2^78 < the primes' product).  Transform length the next
+     * power of two >= na + nb, at most 16384 (na + nb <= 16384).  Field
+     * elements are single 32-bit words.  Plans and one-shot calls only (not a
+     * batch item op). */
+    BN_OP_MUL_NTT3 = 5
 } bn_op;
 
 /* Largest limb counts per operand (256K bits for the products, 512K bits for
@@ -134,6 +142,10 @@ bn_status bn_mul_quad(const uint32_t *a, const uint32_t *b, uint32_t *c,
                       uint32_t na, uint32_t nb, uint64_t batch, void *stream);
 bn_status bn_mul_ntt(const uint32_t *a, const uint32_t *b, uint32_t *c,
                      uint32_t na, uint32_t nb, uint64_t batch, int crt, void *stream);
+/* One-shot BN_OP_MUL_NTT3 (three 32-bit primes): same arguments, layout,
+ * result (na + nb limbs) and errors as bn_mul_ntt. */
+bn_status bn_mul_ntt3(const uint32_t *a, const uint32_t *b, uint32_t *c,
+                      uint32_t na, uint32_t nb, uint64_t batch, void *stream);
 
 /* Transform multiplication that allocates nothing, for callers that cannot
  * call cudaMalloc: code whose device memory is wholly owned by another

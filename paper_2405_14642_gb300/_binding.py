@@ -16,7 +16,7 @@ import numpy as np
 from . import _build
 
 BN_OK, BN_EINVAL, BN_ENOMEM, BN_ECUDA, BN_EUNSUPPORTED, BN_ETIMEOUT = range(6)
-BN_OP_ADD, BN_OP_MUL_QUAD, BN_OP_MUL_NTT64, BN_OP_MUL_NTT_CRT, BN_OP_MUL_AUTO = range(5)
+BN_OP_ADD, BN_OP_MUL_QUAD, BN_OP_MUL_NTT64, BN_OP_MUL_NTT_CRT, BN_OP_MUL_AUTO, BN_OP_MUL_NTT3 = range(6)
 BN_BATCH_AUTOTUNE, BN_BATCH_PLAIN = 1, 2
 # Layout of struct bn_batch_item (include/bn.h), 40 bytes.
 BATCH_ITEM_DTYPE = np.dtype([("op", "<u4"), ("na", "<u4"), ("nb", "<u4"), ("reserved", "<u4"),
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = False):
         "bn_add": ([u32p, u32p, u32p, u32, u32, u64, vp], st),
         "bn_mul_quad": ([u32p, u32p, u32p, u32, u32, u64, vp], st),
         "bn_mul_ntt": ([u32p, u32p, u32p, u32, u32, u64, ctypes.c_int, vp], st),
+        "bn_mul_ntt3": ([u32p, u32p, u32p, u32, u32, u64, vp], st),
         "bn_status_str": ([ctypes.c_int], ctypes.c_char_p),
         "bn_last_error": ([], ctypes.c_char_p),
         "bn_version": ([], ctypes.c_int),
@@ -207,6 +208,18 @@ def bn_mul_ntt(a, b, crt: bool = False, out=None, stream=None):
     out = _out(out, batch, na + nb, a)
     _check(lib.bn_mul_ntt(_ptr(a), _ptr(b), _ptr(out), na, nb, batch, int(bool(crt)),
                           _stream_handle(stream, a.device)), "bn_mul_ntt")
+    return out
+
+
+def bn_mul_ntt3(a, b, out=None, stream=None):
+    """c = a * b per row through transforms over three 32-bit primes with
+    32-bit digits and Garner recombination (Section 4's method); na + nb limbs."""
+    lib = load()
+    a, b = _pair(a, b)
+    batch, na, nb = a.shape[0], a.shape[1], b.shape[1]
+    out = _out(out, batch, na + nb, a)
+    _check(lib.bn_mul_ntt3(_ptr(a), _ptr(b), _ptr(out), na, nb, batch,
+                           _stream_handle(stream, a.device)), "bn_mul_ntt3")
     return out
 
 

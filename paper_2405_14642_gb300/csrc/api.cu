@@ -20,6 +20,7 @@ struct bn_plan_s {
     bn::AddConfig add;
     bn::QuadConfig quad;
     bn::NttPlan *ntt = nullptr;
+    bn::Ntt3Plan *ntt3 = nullptr;
     // Device staging for bn_plan_execute_host (allocated on first use).
     uint32_t *d_a = nullptr, *d_b = nullptr, *d_c = nullptr;
     uint64_t staged_batch = 0;
@@ -59,6 +60,8 @@ bn_status configure(bn_plan_s *p, const bn_tuning *t) {
     case BN_OP_MUL_NTT64:
     case BN_OP_MUL_NTT_CRT:
         return bn::ntt_create(&p->ntt, p->op == BN_OP_MUL_NTT_CRT, p->na, p->nb, t);
+    case BN_OP_MUL_NTT3: return bn::ntt3_create(&p->ntt3, p->na, p->nb, t);
+    default: break;
     }
     return BN_EINVAL;
 }
@@ -85,6 +88,8 @@ bn_status launch(bn_plan_s *p, const uint32_t *a, const uint32_t *b, uint32_t *c
     case BN_OP_MUL_QUAD: e = bn::quad_launch(p->quad, a, b, c, batch, st); break;
     case BN_OP_MUL_NTT64:
     case BN_OP_MUL_NTT_CRT: e = bn::ntt_launch(p->ntt, a, b, c, batch, st); break;
+    case BN_OP_MUL_NTT3: e = bn::ntt3_launch(p->ntt3, a, b, c, batch, st); break;
+    default: e = cudaErrorInvalidValue; break;
     }
     return cuda_status("kernel launch", e);
 }
@@ -185,7 +190,8 @@ bn_status bn_plan_create(bn_plan *out, bn_op op, uint32_t na, uint32_t nb, uint6
         return BN_EINVAL;
     }
     *out = nullptr;
-    if (op != BN_OP_ADD && op != BN_OP_MUL_QUAD && op != BN_OP_MUL_NTT64 && op != BN_OP_MUL_NTT_CRT) {
+    if (op != BN_OP_ADD && op != BN_OP_MUL_QUAD && op != BN_OP_MUL_NTT64 && op != BN_OP_MUL_NTT_CRT &&
+        op != BN_OP_MUL_NTT3) {
         set_error_text("unknown op");
         return BN_EINVAL;
     }
@@ -278,6 +284,7 @@ bn_status bn_plan_destroy(bn_plan plan) {
     cudaFree(plan->d_b);
     cudaFree(plan->d_c);
     if (plan->ntt) bn::ntt_destroy(plan->ntt);
+    if (plan->ntt3) bn::ntt3_destroy(plan->ntt3);
     delete plan;
     return cuda_status("cudaDeviceSynchronize", e);
 }
@@ -285,10 +292,12 @@ bn_status bn_plan_destroy(bn_plan plan) {
 uint32_t bn_plan_out_limbs(bn_plan plan) { return plan ? plan->nout : 0; }
 
 size_t bn_plan_scratch_bytes(bn_plan plan) {
+    if (plan && plan->ntt3) return bn::ntt3_scratch_bytes(plan->ntt3);
     return (plan && plan->ntt) ? bn::ntt_scratch_bytes(plan->ntt) : 0;
 }
 
 uint32_t bn_plan_transform_length(bn_plan plan) {
+    if (plan && plan->ntt3) return bn::ntt3_length(plan->ntt3);
     return (plan && plan->ntt) ? bn::ntt_length(plan->ntt) : 0;
 }
 
@@ -305,6 +314,11 @@ bn_status bn_mul_quad(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_
 bn_status bn_mul_ntt(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_t na, uint32_t nb,
                      uint64_t batch, int crt, void *stream) {
     return one_shot(crt ? BN_OP_MUL_NTT_CRT : BN_OP_MUL_NTT64, a, b, c, na, nb, batch, stream);
+}
+
+bn_status bn_mul_ntt3(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_t na, uint32_t nb,
+                      uint64_t batch, void *stream) {
+    return one_shot(BN_OP_MUL_NTT3, a, b, c, na, nb, batch, stream);
 }
 
 const char *bn_status_str(bn_status s) {

@@ -102,4 +102,13 @@ cudaError_t ntt_launch_sized(NttPlan *p, uint32_t na, uint32_t nb, const uint32_
                              const uint32_t *b, uint32_t *c, cudaStream_t stream);
 uint32_t ntt_length(const NttPlan *p);
 
+// Three 32-bit primes (mul_ntt32.cu).
+struct Ntt3Plan;  // opaque
+bn_status ntt3_create(Ntt3Plan **out, uint32_t na, uint32_t nb, const bn_tuning *t);
+void ntt3_destroy(Ntt3Plan *p);
+cudaError_t ntt3_launch(Ntt3Plan *p, const uint32_t *a, const uint32_t *b, uint32_t *c, uint64_t batch,
+                        cudaStream_t st);
+size_t ntt3_scratch_bytes(const Ntt3Plan *p);
+uint32_t ntt3_length(const Ntt3Plan *p);
+
 }  // namespace bn

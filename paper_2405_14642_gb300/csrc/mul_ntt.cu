@@ -47,17 +47,16 @@
 #include <new>
 #include <vector>
 
-#include "bn_device.cuh"
 #include "bn_internal.h"
+#include "ntt_device.cuh"
 
 namespace bn {
 
 namespace {
 
-typedef unsigned __int128 u128;
+using namespace ntt;
 
 constexpr uint32_t kMaxSubLength = 8192;  // both spectra in shared memory
-constexpr int kRadixLog = 3;              // radix-8 passes
 
 // ---- device fields ---------------------------------------------------------
 
@@ -72,6 +71,7 @@ constexpr int kRadixLog = 3;              // radix-8 passes
 //     4P < 2^64.
 template <uint64_t P>
 struct MontField {
+    using Elem = uint64_t;
     static constexpr uint64_t P_VALUE = P;
     static constexpr uint32_t PH = (uint32_t)(P >> 32);
     static constexpr uint64_t TWO_P = 2 * P;
@@ -122,10 +122,6 @@ struct MontField {
 using FieldP1 = MontField<4179340454199820289ull>;  // 29 * 2^57 + 1 (PrimeField64)
 using FieldP2 = MontField<1945555039024054273ull>;  // 27 * 2^56 + 1
 
-// Shared-memory index with one u64 of padding per 16 (bank spread).
-__device__ __forceinline__ uint32_t phys(uint32_t i) { return i + (i >> 4); }
-__host__ __device__ constexpr uint32_t phys_words(uint32_t n) { return n + (n >> 4) + 1; }
-
 struct PrimeTab {
     const uint64_t *twf;    // [L]: twf[h + j] = w_{2h}^j (h = 1 .. L/2, j < h)
     const uint64_t *twi;    // [L]: w_{2h}^-j
@@ -172,127 +168,6 @@ __device__ void load_fold(const NttArgs &p, const PrimeTab &tb, const uint32_t *
             acc = F::mul(acc, tb.ffold[s * p.L + j]);
         }
         buf[phys(j)] = acc;
-    }
-}
-
-// Twiddle index of group element m in the stage of half-size h (h = hm*step):
-// the position of element m within its 2h block.  Within one group it depends
-// only on m's bits below hm, so a stage needs hm distinct twiddles.
-__device__ __forceinline__ uint32_t tw_index(uint32_t base, uint32_t m, uint32_t step, uint32_t h) {
-    return h + ((base + m * step) & (h - 1));
-}
-
-// KK decimation-in-frequency stages with half-sizes H, H/2, ..., H >> (KK-1).
-// UNIT: the group step is 1, so the last stage's twiddle is 1.  The
-// difference u - v + 2P (< 4P) goes to the twiddle multiply unreduced.
-template <class F, int KK, bool UNIT>
-__device__ __forceinline__ void dif_pass(uint64_t *buf, uint32_t L, uint32_t H, const uint64_t *tw) {
-    constexpr int E = 1 << KK;
-    const uint32_t step = UNIT ? 1u : H >> (KK - 1);
-    const uint32_t lstep = UNIT ? 0u : __ffs(step) - 1;
-    for (uint32_t g = threadIdx.x; g < (L >> KK); g += blockDim.x) {
-        const uint32_t base = ((g >> lstep) << (lstep + KK)) | (g & (step - 1));
-        uint64_t x[E];
-#pragma unroll
-        for (int m = 0; m < E; ++m) x[m] = buf[phys(base + m * step)];
-#pragma unroll
-        for (int st = 0; st < KK; ++st) {
-            const uint32_t hm = 1u << (KK - 1 - st), h = hm * step;
-            const bool trivial = UNIT && hm == 1;
-            uint64_t w[E / 2];
-#pragma unroll
-            for (int m = 0; m < (int)hm; ++m) w[m] = trivial ? 0 : __ldg(tw + tw_index(base, m, step, h));
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                if (m & hm) continue;
-                const uint64_t u = x[m], v = x[m + hm];
-                x[m] = F::add(u, v);
-                x[m + hm] = trivial ? F::sub(u, v) : F::mulw(u + F::TWO_P - v, w[m & (hm - 1)]);
-            }
-        }
-#pragma unroll
-        for (int m = 0; m < E; ++m) buf[phys(base + m * step)] = x[m];
-    }
-}
-
-// KK decimation-in-time stages with half-sizes h0, 2 h0, ..., h0 << (KK-1).
-// UNIT: h0 = 1, so the first stage's twiddle is 1.
-template <class F, int KK, bool UNIT>
-__device__ __forceinline__ void dit_pass(uint64_t *buf, uint32_t L, uint32_t h0, const uint64_t *tw) {
-    constexpr int E = 1 << KK;
-    const uint32_t step = UNIT ? 1u : h0;
-    const uint32_t lstep = UNIT ? 0u : __ffs(step) - 1;
-    for (uint32_t g = threadIdx.x; g < (L >> KK); g += blockDim.x) {
-        const uint32_t base = ((g >> lstep) << (lstep + KK)) | (g & (step - 1));
-        uint64_t x[E];
-#pragma unroll
-        for (int m = 0; m < E; ++m) x[m] = buf[phys(base + m * step)];
-#pragma unroll
-        for (int st = 0; st < KK; ++st) {
-            const uint32_t hm = 1u << st, h = hm * step;
-            const bool trivial = UNIT && hm == 1;
-            uint64_t w[E / 2];
-#pragma unroll
-            for (int m = 0; m < (int)hm; ++m) w[m] = trivial ? 0 : __ldg(tw + tw_index(base, m, step, h));
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                if (m & hm) continue;
-                const uint64_t u = x[m];
-                const uint64_t v = trivial ? x[m + hm] : F::mul(x[m + hm], w[m & (hm - 1)]);
-                x[m] = F::add(u, v);
-                x[m + hm] = F::sub(u, v);
-            }
-        }
-#pragma unroll
-        for (int m = 0; m < E; ++m) buf[phys(base + m * step)] = x[m];
-    }
-}
-
-template <class F>
-__device__ void forward2(uint32_t L, uint32_t logL, const uint64_t *tw, uint64_t *A, uint64_t *B) {
-    uint32_t H = L >> 1, left = logL;
-    while (left > (uint32_t)kRadixLog) {  // these passes have step >= 2
-        dif_pass<F, kRadixLog, false>(A, L, H, tw);
-        dif_pass<F, kRadixLog, false>(B, L, H, tw);
-        __syncthreads();
-        H >>= kRadixLog;
-        left -= kRadixLog;
-    }
-    if (left == 3) {                       // the last pass has step 1
-        dif_pass<F, 3, true>(A, L, H, tw);
-        dif_pass<F, 3, true>(B, L, H, tw);
-    } else if (left == 2) {
-        dif_pass<F, 2, true>(A, L, H, tw);
-        dif_pass<F, 2, true>(B, L, H, tw);
-    } else {
-        dif_pass<F, 1, true>(A, L, H, tw);
-        dif_pass<F, 1, true>(B, L, H, tw);
-    }
-    __syncthreads();
-}
-
-template <class F>
-__device__ void inverse(uint32_t L, uint32_t logL, const uint64_t *tw, uint64_t *B) {
-    uint32_t left = logL;
-    const uint32_t first = left >= (uint32_t)kRadixLog ? (uint32_t)kRadixLog : left;
-    if (first == 3) dit_pass<F, 3, true>(B, L, 1, tw);   // the first pass has h0 = 1
-    else if (first == 2) dit_pass<F, 2, true>(B, L, 1, tw);
-    else dit_pass<F, 1, true>(B, L, 1, tw);
-    __syncthreads();
-    uint32_t h0 = 1u << first;
-    left -= first;
-    while (left >= (uint32_t)kRadixLog) {
-        dit_pass<F, kRadixLog, false>(B, L, h0, tw);
-        __syncthreads();
-        h0 <<= kRadixLog;
-        left -= kRadixLog;
-    }
-    if (left == 2) {
-        dit_pass<F, 2, false>(B, L, h0, tw);
-        __syncthreads();
-    } else if (left == 1) {
-        dit_pass<F, 1, false>(B, L, h0, tw);
-        __syncthreads();
     }
 }
 
@@ -365,45 +240,8 @@ template <bool CRT>
 __device__ void normalize(const NttArgs &p, uint64_t inst, uint32_t *out_s, const uint64_t *B,
                           bool in_smem, const uint64_t *C1, const uint64_t *Cs, uint64_t *spill,
                           uint32_t *flags) {
-    const uint32_t T = blockDim.x, t = threadIdx.x;
-    uint32_t QN = (p.nout + T - 1) / T;
-    if (QN < 2) QN = 2;  // a window must absorb a two-word spill
-    const uint32_t k0 = t * QN;
-    const uint32_t k1 = k0 + QN < p.nout ? k0 + QN : p.nout;
-    // (a) this window's limbs, carrying within the window
-    u128 carry = 0;
-    for (uint32_t k = k0; k < k1; ++k) {
-        const u128 v = limb_value<CRT>(p, k, B, in_smem, C1, Cs) + carry;
-        out_s[k] = (uint32_t)v;
-        carry = v >> 32;
-    }
-    spill[t] = (uint64_t)carry;  // < 2^46
-    __syncthreads();
-    // (b) add the previous window's spill; one carry bit may leave the window
-    uint64_t c = t > 0 ? spill[t - 1] : 0;
-    uint32_t all = 0xffffffffu;
-    for (uint32_t k = k0; k < k1; ++k) {
-        const uint64_t v = (uint64_t)out_s[k] + (c & 0xffffffffu);
-        out_s[k] = (uint32_t)v;
-        c = (c >> 32) + (v >> 32);
-        all &= out_s[k];
-    }
-    const bool owns = k0 < k1;
-    // (c) resolve the carries across windows (Section 2 carry scan)
-    const uint32_t cin = group_carry_in(owns && c != 0, owns && all == 0xffffffffu, T, flags);
-    if (cin)
-        for (uint32_t k = k0; k < k1; ++k)
-            if (++out_s[k] != 0) break;
-    __syncthreads();
-    // (d) coalesced copy-out
-    uint32_t *crow = p.c + inst * p.nout;
-    if (p.vec_c) {
-        for (uint32_t x = 4 * t; x < p.nout; x += 4 * T)
-            st_stream_v4(crow + x, *reinterpret_cast<const uint4 *>(out_s + x));
-    } else {
-        for (uint32_t x = t; x < p.nout; x += T) st_stream(crow + x, out_s[x]);
-    }
-    __syncthreads();
+    normalize_limbs(p.nout, p.c + inst * p.nout, p.vec_c, out_s, spill, flags,
+                    [&](uint32_t k) { return limb_value<CRT>(p, k, B, in_smem, C1, Cs); });
 }
 
 template <bool CRT>

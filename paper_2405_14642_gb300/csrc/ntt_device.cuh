@@ -1,0 +1,208 @@
+// Device building blocks of the transform products (Section 4), shared by the
+// 64-bit (one and two primes) and 32-bit (three primes) kernels: the radix-8
+// butterfly passes over a shared-memory buffer, whole forward / inverse
+// transforms, and the normalisation of convolution coefficients into limbs.
+//
+// A field type F provides Elem (the word type of its elements), TWO_P, and
+// add / sub / mul / mulw / canon on lazily reduced elements in [0, 2P):
+//   mul(a, b)  for a, b < 2P,
+//   mulw(a, w) for any a < 4P and a canonical twiddle w < P,
+// both returning a value in [0, 2P).  Twiddles are kept in the field's
+// multiplication form, so that mul(x, form(w)) = x*w.
+#pragma once
+#include "bn_device.cuh"
+
+namespace bn {
+namespace ntt {
+
+typedef unsigned __int128 u128;
+
+constexpr int kRadixLog = 3;  // radix-8 passes
+
+// Shared-memory index with one element of padding per 16 (bank spread).
+__device__ __forceinline__ uint32_t phys(uint32_t i) { return i + (i >> 4); }
+__host__ __device__ constexpr uint32_t phys_words(uint32_t n) { return n + (n >> 4) + 1; }
+
+// Twiddle index of group element m in the stage of half-size h (h = hm*step):
+// the position of element m within its 2h block.  Within one group it depends
+// only on m's bits below hm, so a stage needs hm distinct twiddles.
+__device__ __forceinline__ uint32_t tw_index(uint32_t base, uint32_t m, uint32_t step, uint32_t h) {
+    return h + ((base + m * step) & (h - 1));
+}
+
+// KK decimation-in-frequency stages with half-sizes H, H/2, ..., H >> (KK-1).
+// UNIT: the group step is 1, so the last stage's twiddle is 1.  The
+// difference u - v + 2P (< 4P) goes to the twiddle multiply unreduced.
+template <class F, int KK, bool UNIT>
+__device__ __forceinline__ void dif_pass(typename F::Elem *buf, uint32_t L, uint32_t H,
+                                         const typename F::Elem *tw) {
+    using T = typename F::Elem;
+    constexpr int E = 1 << KK;
+    const uint32_t step = UNIT ? 1u : H >> (KK - 1);
+    const uint32_t lstep = UNIT ? 0u : __ffs(step) - 1;
+    for (uint32_t g = threadIdx.x; g < (L >> KK); g += blockDim.x) {
+        const uint32_t base = ((g >> lstep) << (lstep + KK)) | (g & (step - 1));
+        T x[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) x[m] = buf[phys(base + m * step)];
+#pragma unroll
+        for (int st = 0; st < KK; ++st) {
+            const uint32_t hm = 1u << (KK - 1 - st), h = hm * step;
+            const bool trivial = UNIT && hm == 1;
+            T w[E / 2];
+#pragma unroll
+            for (int m = 0; m < (int)hm; ++m) w[m] = trivial ? 0 : __ldg(tw + tw_index(base, m, step, h));
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                if (m & hm) continue;
+                const T u = x[m], v = x[m + hm];
+                x[m] = F::add(u, v);
+                x[m + hm] = trivial ? F::sub(u, v) : F::mulw(u + F::TWO_P - v, w[m & (hm - 1)]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < E; ++m) buf[phys(base + m * step)] = x[m];
+    }
+}
+
+// KK decimation-in-time stages with half-sizes h0, 2 h0, ..., h0 << (KK-1).
+// UNIT: h0 = 1, so the first stage's twiddle is 1.
+template <class F, int KK, bool UNIT>
+__device__ __forceinline__ void dit_pass(typename F::Elem *buf, uint32_t L, uint32_t h0,
+                                         const typename F::Elem *tw) {
+    using T = typename F::Elem;
+    constexpr int E = 1 << KK;
+    const uint32_t step = UNIT ? 1u : h0;
+    const uint32_t lstep = UNIT ? 0u : __ffs(step) - 1;
+    for (uint32_t g = threadIdx.x; g < (L >> KK); g += blockDim.x) {
+        const uint32_t base = ((g >> lstep) << (lstep + KK)) | (g & (step - 1));
+        T x[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) x[m] = buf[phys(base + m * step)];
+#pragma unroll
+        for (int st = 0; st < KK; ++st) {
+            const uint32_t hm = 1u << st, h = hm * step;
+            const bool trivial = UNIT && hm == 1;
+            T w[E / 2];
+#pragma unroll
+            for (int m = 0; m < (int)hm; ++m) w[m] = trivial ? 0 : __ldg(tw + tw_index(base, m, step, h));
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                if (m & hm) continue;
+                const T u = x[m];
+                const T v = trivial ? x[m + hm] : F::mul(x[m + hm], w[m & (hm - 1)]);
+                x[m] = F::add(u, v);
+                x[m + hm] = F::sub(u, v);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < E; ++m) buf[phys(base + m * step)] = x[m];
+    }
+}
+
+// Forward transforms of A and B (natural order in, bit-reversed out); ends
+// with a barrier.
+template <class F>
+__device__ void forward2(uint32_t L, uint32_t logL, const typename F::Elem *tw, typename F::Elem *A,
+                         typename F::Elem *B) {
+    uint32_t H = L >> 1, left = logL;
+    while (left > (uint32_t)kRadixLog) {  // these passes have step >= 2
+        dif_pass<F, kRadixLog, false>(A, L, H, tw);
+        dif_pass<F, kRadixLog, false>(B, L, H, tw);
+        __syncthreads();
+        H >>= kRadixLog;
+        left -= kRadixLog;
+    }
+    if (left == 3) {                       // the last pass has step 1
+        dif_pass<F, 3, true>(A, L, H, tw);
+        dif_pass<F, 3, true>(B, L, H, tw);
+    } else if (left == 2) {
+        dif_pass<F, 2, true>(A, L, H, tw);
+        dif_pass<F, 2, true>(B, L, H, tw);
+    } else {
+        dif_pass<F, 1, true>(A, L, H, tw);
+        dif_pass<F, 1, true>(B, L, H, tw);
+    }
+    __syncthreads();
+}
+
+// Unscaled inverse transform of B (bit-reversed in, natural out); ends with a
+// barrier.
+template <class F>
+__device__ void inverse(uint32_t L, uint32_t logL, const typename F::Elem *tw, typename F::Elem *B) {
+    uint32_t left = logL;
+    const uint32_t first = left >= (uint32_t)kRadixLog ? (uint32_t)kRadixLog : left;
+    if (first == 3) dit_pass<F, 3, true>(B, L, 1, tw);   // the first pass has h0 = 1
+    else if (first == 2) dit_pass<F, 2, true>(B, L, 1, tw);
+    else dit_pass<F, 1, true>(B, L, 1, tw);
+    __syncthreads();
+    uint32_t h0 = 1u << first;
+    left -= first;
+    while (left >= (uint32_t)kRadixLog) {
+        dit_pass<F, kRadixLog, false>(B, L, h0, tw);
+        __syncthreads();
+        h0 <<= kRadixLog;
+        left -= kRadixLog;
+    }
+    if (left == 2) {
+        dit_pass<F, 2, false>(B, L, h0, tw);
+        __syncthreads();
+    } else if (left == 1) {
+        dit_pass<F, 1, false>(B, L, h0, tw);
+        __syncthreads();
+    }
+}
+
+// Normalisation (Section 4.2's splitFftReg/baddRegMul2Fft, with whole
+// digits): limb(k) gives the part of the product that starts in limb k (the
+// digit coefficients aligned there, < 2^96 in total).  Each thread folds the
+// limbs of its window, carrying inside the window, the window's carry spills
+// into the next window, and the remaining one-bit carries are resolved with
+// the Section 2 carry scan across the CTA.  The nout limbs are assembled in
+// out_s (shared) and then copied to crow.  Every thread of the CTA calls it;
+// spill has one word per thread, flags one per warp.
+template <class LimbFn>
+__device__ void normalize_limbs(uint32_t nout, uint32_t *crow, bool vec_c, uint32_t *out_s,
+                                uint64_t *spill, uint32_t *flags, LimbFn &&limb) {
+    const uint32_t T = blockDim.x, t = threadIdx.x;
+    uint32_t QN = (nout + T - 1) / T;
+    if (QN < 2) QN = 2;  // a window must absorb a two-word spill
+    const uint32_t k0 = t * QN;
+    const uint32_t k1 = k0 + QN < nout ? k0 + QN : nout;
+    // (a) this window's limbs, carrying within the window
+    u128 carry = 0;
+    for (uint32_t k = k0; k < k1; ++k) {
+        const u128 v = limb(k) + carry;
+        out_s[k] = (uint32_t)v;
+        carry = v >> 32;
+    }
+    spill[t] = (uint64_t)carry;  // < 2^64: the coefficients are below 2^96
+    __syncthreads();
+    // (b) add the previous window's spill; one carry bit may leave the window
+    uint64_t c = t > 0 ? spill[t - 1] : 0;
+    uint32_t all = 0xffffffffu;
+    for (uint32_t k = k0; k < k1; ++k) {
+        const uint64_t v = (uint64_t)out_s[k] + (c & 0xffffffffu);
+        out_s[k] = (uint32_t)v;
+        c = (c >> 32) + (v >> 32);
+        all &= out_s[k];
+    }
+    const bool owns = k0 < k1;
+    // (c) resolve the carries across windows (Section 2 carry scan)
+    const uint32_t cin = group_carry_in(owns && c != 0, owns && all == 0xffffffffu, T, flags);
+    if (cin)
+        for (uint32_t k = k0; k < k1; ++k)
+            if (++out_s[k] != 0) break;
+    __syncthreads();
+    // (d) coalesced copy-out
+    if (vec_c) {
+        for (uint32_t x = 4 * t; x < nout; x += 4 * T)
+            st_stream_v4(crow + x, *reinterpret_cast<const uint4 *>(out_s + x));
+    } else {
+        for (uint32_t x = t; x < nout; x += T) st_stream(crow + x, out_s[x]);
+    }
+    __syncthreads();
+}
+
+}  // namespace ntt
+}  // namespace bn
