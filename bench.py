@@ -45,7 +45,7 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 
 @dataclass
 class Op:
-    name: str          # add | quad | ntt64 | crt
+    name: str          # add | quad | ntt64 | crt | ntt3
     bits: int
     na: int
     nb: int
@@ -63,6 +63,11 @@ class Op:
     @property
     def label(self):
         return f"{self.name}@{self.bits // 1024}K"
+
+
+OPCODES = {"add": lambda bn: bn.BN_OP_ADD, "quad": lambda bn: bn.BN_OP_MUL_QUAD,
+           "ntt64": lambda bn: bn.BN_OP_MUL_NTT64, "crt": lambda bn: bn.BN_OP_MUL_NTT_CRT,
+           "ntt3": lambda bn: bn.BN_OP_MUL_NTT3}
 
 
 def ntt_lengths(n: int):
@@ -96,6 +101,10 @@ def build_ops(quick: bool = False):
                       bytes=16 * n * p.batch, prods=4 * mm64 * p.batch))
         ops.append(Op("crt", p.bits, n, n, p.batch, p.seed, mults=p.batch,
                       bytes=16 * n * p.batch, prods=4 * mmcrt * p.batch))
+        # Three 32-bit primes at the CRT form's length: one word product per
+        # modular product.
+        ops.append(Op("ntt3", p.bits, n, n, p.batch, p.seed, mults=p.batch,
+                      bytes=16 * n * p.batch, prods=3 * (mmcrt // 2) * p.batch))
     return ops
 
 
@@ -103,8 +112,9 @@ def workload_config(ops, world: int):
     bits = sorted({o.bits for o in ops})
     return {
         "workload": "size sweep 1K-256K bits: add + schoolbook mul at 9 sizes, NTT mul "
-                    "(1x64-bit prime/16-bit digits and 2-prime CRT/32-bit digits) at 16K-256K; "
-                    "64 MiB of u32 operand limbs per side per size",
+                    "(1x64-bit prime/16-bit digits, 2-prime CRT/32-bit digits and 3x32-bit "
+                    "primes/32-bit digits) at 16K-256K; 64 MiB of u32 operand limbs per side "
+                    "per size",
         "sizes_bits": bits,
         "batch_per_size": {str(b): next(o.batch for o in ops if o.bits == b) for b in bits},
         "ops_per_step": [o.label for o in ops],
@@ -269,8 +279,7 @@ def run_gpu(args, rank, world, local_rank):
     plans = {}
     skipped = []
     for o in list(ops):
-        opcode = {"add": bn.BN_OP_ADD, "quad": bn.BN_OP_MUL_QUAD, "ntt64": bn.BN_OP_MUL_NTT64,
-                  "crt": bn.BN_OP_MUL_NTT_CRT}[o.name]
+        opcode = OPCODES[o.name](bn)
         try:
             plans[o.label] = bn.Plan(opcode, o.na, o.nb, o.batch)
         except bn.BnError as e:
@@ -507,7 +516,8 @@ def run_mixed(args, torch, bn, dev, rank):
                      "mults_per_s": n_mul / (ms * 1e-3), "launches": info["launches"],
                      "classes": info["classes"], "create_ms": round(create_ms, 1), "steps": steps,
                      "items_by_kernel": {k: info[k] for k in ("items_add", "items_quad",
-                                                              "items_ntt64", "items_crt")}}
+                                                              "items_ntt64", "items_crt",
+                                                              "items_ntt3")}}
     identical = bool(torch.equal(results["batched"], results["plain"]))
     return {"workload": f"{len(items)} ops, 70% mul (auto quad/NTT) / 30% add, limbs log-uniform "
                         "32..8192 per operand, 5% edge cases",
@@ -599,8 +609,7 @@ def run_e2e(args, torch, bn, ops, hosts, dev):
         key = (o.bits, o.nout)
         if key not in pinned_out:
             pinned_out[key] = torch.empty((o.batch, o.nout), dtype=torch.int32).pin_memory()
-        opcode = {"add": bn.BN_OP_ADD, "quad": bn.BN_OP_MUL_QUAD, "ntt64": bn.BN_OP_MUL_NTT64,
-                  "crt": bn.BN_OP_MUL_NTT_CRT}[o.name]
+        opcode = OPCODES[o.name](bn)
         plans[o.label] = bn.Plan(opcode, o.na, o.nb, o.batch)
     stream = torch.cuda.current_stream(dev)
 

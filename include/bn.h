@@ -70,8 +70,9 @@ typedef enum bn_op {
     /* Section 4 with 32-bit digits over two primes (29*2^57 + 1 and
      * 27*2^56 + 1), recombined by the Chinese remainder theorem. */
     BN_OP_MUL_NTT_CRT = 3,
-    /* Batch items only: multiplication by whichever of the above a mixed-size
-     * batch's cost model finds fastest for the item's sizes. */
+    /* Batch items only: multiplication by whichever of the schoolbook and
+     * transform products (BN_OP_MUL_NTT3 included) a mixed-size batch's cost
+     * model finds fastest for the item's sizes. */
     BN_OP_MUL_AUTO = 4,
     /* Section 4's transform product over three 32-bit good primes
      * (7*2^26 + 1, 45*2^24 + 1, 119*2^23 + 1; roots by the Section 4.1
@@ -242,6 +243,7 @@ typedef struct bn_batch_info {
     uint32_t launches;       /* kernel launches per execution (plain: one per item) */
     uint64_t items_add, items_quad, items_ntt64, items_crt;  /* after BN_OP_MUL_AUTO */
     double tune_ms;          /* time spent calibrating at creation */
+    uint64_t items_ntt3;     /* BN_OP_MUL_AUTO items on the three-prime transform */
 } bn_batch_info;
 
 typedef struct bn_batch_s *bn_batch;

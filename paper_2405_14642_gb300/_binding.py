@@ -42,7 +42,7 @@ class bn_batch_info(ctypes.Structure):
     _fields_ = [("classes", ctypes.c_uint32), ("launches", ctypes.c_uint32),
                 ("items_add", ctypes.c_uint64), ("items_quad", ctypes.c_uint64),
                 ("items_ntt64", ctypes.c_uint64), ("items_crt", ctypes.c_uint64),
-                ("tune_ms", ctypes.c_double)]
+                ("tune_ms", ctypes.c_double), ("items_ntt3", ctypes.c_uint64)]
 
 
 class bn_server_config(ctypes.Structure):

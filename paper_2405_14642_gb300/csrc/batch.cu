@@ -29,7 +29,7 @@
 
 namespace {
 
-enum Kind { K_ADD = 0, K_QUAD = 1, K_NTT64 = 2, K_CRT = 3 };
+enum Kind { K_ADD = 0, K_QUAD = 1, K_NTT64 = 2, K_CRT = 3, K_NTT3 = 4 };
 
 uint32_t ceil_log2(uint32_t x) {
     uint32_t l = 0;
@@ -53,6 +53,7 @@ struct Class {
     bn::AddClass ac;
     bn::QuadClass qc;
     bn::NttPlan *ntt = nullptr;
+    bn::Ntt3Plan *ntt3 = nullptr;
 };
 
 }  // namespace
@@ -82,8 +83,10 @@ void release(bn_batch_s *b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto e : b->events) cudaEventDestroy(e);
     for (auto s : b->streams) cudaStreamDestroy(s);
-    for (auto &c : b->classes)
+    for (auto &c : b->classes) {
         if (c.ntt) bn::ntt_destroy(c.ntt);
+        if (c.ntt3) bn::ntt3_destroy(c.ntt3);
+    }
     cudaFree(b->d_items);
     cudaFree(b->d_queues);
     cudaFree(b->d_bind);
@@ -102,6 +105,7 @@ cudaError_t launch_class(const Class &c, const bn::BatchItem *items, uint32_t *q
     switch (c.kind) {
     case K_ADD: return bn::add_batch_launch(c.ac, items + c.first, c.count, bind, st);
     case K_QUAD: return bn::quad_batch_launch(c.qc, items + c.first, c.count, queue, bind, st);
+    case K_NTT3: return bn::ntt3_batch_launch(c.ntt3, items + c.first, c.count, queue, bind, st);
     default: return bn::ntt_batch_launch(c.ntt, items + c.first, c.count, queue, bind, st);
     }
 }
@@ -197,14 +201,14 @@ bn_status bn_batch_create(bn_batch *out, const bn_batch_item *items, uint64_t co
     // Schoolbook rates and transform times: built-in, or measured.
     std::map<uint32_t, double> quad_rate;          // key -> word products per us
     std::map<uint32_t, std::pair<uint32_t, uint32_t>> quad_cfg;  // key -> (Q, CTA target)
-    std::map<uint32_t, double> t64, tcrt;          // logN -> us per item
+    std::map<uint32_t, double> t64, tcrt, t3;      // logN -> us per item
     auto quad_key = [](uint32_t na, uint32_t nb) { return ceil_log2(std::max(na, nb)); };
     for (uint64_t i = 0; i < count; ++i) {
         const bn_batch_item &it = items[i];
         if (it.op == BN_OP_ADD) continue;
         const uint32_t k = quad_key(it.na, it.nb);
         quad_rate[k] = default_quad_rate(k);
-        quad_cfg[k] = {(std::max(it.na, it.nb) > 128 && std::max(it.na, it.nb) <= 512) ? 4u : 8u, 256u};
+        quad_cfg[k] = {8u, 256u};
         if (it.op == BN_OP_MUL_AUTO || it.op == BN_OP_MUL_NTT64) {
             const uint32_t l = ceil_log2(transform_length(false, it.na, it.nb));
             t64[l] = default_ntt_us(false, l);
@@ -212,6 +216,10 @@ bn_status bn_batch_create(bn_batch *out, const bn_batch_item *items, uint64_t co
         if (it.op == BN_OP_MUL_AUTO || it.op == BN_OP_MUL_NTT_CRT) {
             const uint32_t l = ceil_log2(transform_length(true, it.na, it.nb));
             tcrt[l] = default_ntt_us(true, l);
+        }
+        if (it.op == BN_OP_MUL_AUTO) {
+            const uint32_t l = ceil_log2(transform_length(true, it.na, it.nb));
+            t3[l] = default_ntt3_us(l);
         }
     }
     std::map<std::pair<int, uint32_t>, NttPlan *> ntt_plans;  // (crt, logN) -> plan
@@ -224,10 +232,22 @@ bn_status bn_batch_create(bn_batch *out, const bn_batch_item *items, uint64_t co
         ntt_plans[key] = p;
         return p;
     };
+    std::map<uint32_t, Ntt3Plan *> ntt3_plans;  // logN -> plan
+    auto get_plan3 = [&](uint32_t logN) -> Ntt3Plan * {
+        auto it = ntt3_plans.find(logN);
+        if (it != ntt3_plans.end()) return it->second;
+        Ntt3Plan *p = nullptr;
+        if (ntt3_batch_plan(&p, 1u << logN) != BN_OK) p = nullptr;
+        ntt3_plans[logN] = p;
+        return p;
+    };
     auto free_unused_plans = [&]() {
         for (auto &kv : ntt_plans)
             if (kv.second) ntt_destroy(kv.second);
         ntt_plans.clear();
+        for (auto &kv : ntt3_plans)
+            if (kv.second) ntt3_destroy(kv.second);
+        ntt3_plans.clear();
     };
 
     if (flags & BN_BATCH_AUTOTUNE) {
@@ -263,6 +283,14 @@ bn_status bn_batch_create(bn_batch *out, const bn_batch_item *items, uint64_t co
                 c.ntt = p;
                 kv.second = tu.time_class(c, side, side, 2 * 152, 2 * side);
             }
+        for (auto &kv : t3) {
+            Ntt3Plan *p = get_plan3(kv.first);
+            const uint32_t side = (1u << kv.first) / 2;
+            if (!p || side > BN_MUL_MAX_LIMBS) continue;
+            Class c{K_NTT3, kv.first};
+            c.ntt3 = p;
+            kv.second = tu.time_class(c, side, side, 4 * 152, 2 * side);
+        }
         if (cudaGetLastError() != cudaSuccess) {
             free_unused_plans();
             return fail(b, BN_ECUDA, "autotuning failed");
@@ -296,12 +324,14 @@ bn_status bn_batch_create(bn_batch *out, const bn_batch_item *items, uint64_t co
         else if (it.op == BN_OP_MUL_NTT_CRT) k = K_CRT;
         else if (it.op == BN_OP_MUL_AUTO) {
             const double c64 = t64.count(l64) ? t64[l64] : 1e30, cc = tcrt.count(lcrt) ? tcrt[lcrt] : 1e30;
+            const double c3 = t3.count(lcrt) ? t3[lcrt] : 1e30;
             if (c64 < cost) { k = K_NTT64; cost = c64; }
             if (cc < cost) { k = K_CRT; cost = cc; }
+            if (c3 < cost) { k = K_NTT3; cost = c3; }
         }
         if (k == K_NTT64) cost = t64.count(l64) ? t64[l64] : default_ntt_us(false, l64);
         if (k == K_CRT) cost = tcrt.count(lcrt) ? tcrt[lcrt] : default_ntt_us(true, lcrt);
-        const uint32_t key = k == K_QUAD ? qk : (k == K_NTT64 ? l64 : lcrt);
+        const uint32_t key = k == K_QUAD ? qk : (k == K_NTT64 ? l64 : lcrt);  // K_NTT3: lcrt
         tmp.push_back({k, key, k == K_QUAD ? (double)it.na * it.nb : cost * 1e6 + it.na + it.nb, bi});
     }
     std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp &x, const Tmp &y) {
@@ -328,6 +358,11 @@ bn_status bn_batch_create(bn_batch *out, const bn_batch_item *items, uint64_t co
             st = quad_batch_class(c.qc, cfg.first, std::min(1u << c.key, BN_MUL_MAX_LIMBS), cfg.second);
             for (size_t k = i; k < j; ++k)
                 c.est_us += (double)tmp[k].item.na * tmp[k].item.nb / quad_rate[c.key];
+        } else if (c.kind == K_NTT3) {
+            c.ntt3 = get_plan3(c.key);
+            if (!c.ntt3) st = BN_ENOMEM;
+            ntt3_plans.erase(c.key);  // owned by the class now
+            c.est_us = (t3.count(c.key) ? t3[c.key] : 1.0) * c.count;
         } else {
             c.ntt = get_plan(c.kind == K_CRT, c.key);
             if (!c.ntt) st = BN_ENOMEM;
@@ -350,6 +385,7 @@ bn_status bn_batch_create(bn_batch *out, const bn_batch_item *items, uint64_t co
             case K_QUAD: ++b->info.items_quad; break;
             case K_NTT64: ++b->info.items_ntt64; break;
             case K_CRT: ++b->info.items_crt; break;
+            case K_NTT3: ++b->info.items_ntt3; break;
             }
         }
         i = j;
@@ -454,7 +490,8 @@ bn_status bn_batch_execute(bn_batch b, const uint32_t *a, const uint32_t *bb, ui
                 const Class *cls = nullptr;
                 for (const auto &cl : b->classes)
                     if (i >= cl.first && i < cl.first + cl.count) cls = &cl;
-                e = ntt_launch_sized(cls->ntt, it.na, it.nb, pa, pb, pc, st);
+                e = cls->ntt3 ? ntt3_launch_sized(cls->ntt3, it.na, it.nb, pa, pb, pc, st)
+                              : ntt_launch_sized(cls->ntt, it.na, it.nb, pa, pb, pc, st);
             }
             if (e != cudaSuccess) {
                 record_error("plain batch launch failed");

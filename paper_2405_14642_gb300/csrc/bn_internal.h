@@ -35,10 +35,11 @@ struct BatchBinding {
 double default_quad_rate(uint32_t key);              // word products / us
 double default_ntt_us(bool crt, uint32_t log_n);     // us per product
 struct MulChoice {
-    uint32_t kind = 1;  // 1 schoolbook, 2 one-prime transform, 3 two-prime transform
-    uint32_t quad_key = 0, log_n64 = 0, log_ncrt = 0;
+    uint32_t kind = 1;  // 1 schoolbook, 2 one-prime, 3 two-prime, 4 three-prime transform
+    uint32_t quad_key = 0, log_n64 = 0, log_ncrt = 0;  // log_ncrt is also the three-prime length
     double est_us = 0;
 };
+double default_ntt3_us(uint32_t log_n);               // us per product, three 32-bit primes
 MulChoice choose_mul(uint32_t na, uint32_t nb);
 
 // ---- addition (Section 2) -------------------------------------------------
@@ -110,5 +111,11 @@ cudaError_t ntt3_launch(Ntt3Plan *p, const uint32_t *a, const uint32_t *b, uint3
                         cudaStream_t st);
 size_t ntt3_scratch_bytes(const Ntt3Plan *p);
 uint32_t ntt3_length(const Ntt3Plan *p);
+// Batch form: a plan of transform length exactly N (items with na + nb <= N).
+bn_status ntt3_batch_plan(Ntt3Plan **out, uint32_t N);
+cudaError_t ntt3_batch_launch(Ntt3Plan *p, const BatchItem *items, uint32_t count, uint32_t *queue,
+                              const BatchBinding *bind, cudaStream_t st);
+cudaError_t ntt3_launch_sized(Ntt3Plan *p, uint32_t na, uint32_t nb, const uint32_t *a, const uint32_t *b,
+                              uint32_t *c, cudaStream_t st);
 
 }  // namespace bn

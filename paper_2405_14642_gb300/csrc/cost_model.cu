@@ -21,6 +21,15 @@ double default_ntt_us(bool crt, uint32_t logN) {
     return v > 0 ? v : 1e30;
 }
 
+double default_ntt3_us(uint32_t logN) {
+    // Three 32-bit primes, microseconds per item by log2(N) (N = next power
+    // of two >= na + nb), from 2^6 (1K-bit operands) to 2^14 (256K bits).
+    static const double t3[15] = {0, 0, 0, 0, 0, 0, 0.00597, 0.00819, 0.01146, 0.02355, 0.0483,
+                                  0.1006, 0.2132, 0.4853, 1.0235};
+    const double v = logN < 15 ? t3[logN] : 0;
+    return v > 0 ? v : 1e30;
+}
+
 namespace {
 uint32_t clog2(uint32_t x) {
     uint32_t l = 0;
@@ -42,6 +51,8 @@ MulChoice choose_mul(uint32_t na, uint32_t nb) {
     c.est_us = q;
     if (t64 < c.est_us) { c.kind = 2; c.est_us = t64; }
     if (tc < c.est_us) { c.kind = 3; c.est_us = tc; }
+    const double t3 = default_ntt3_us(c.log_ncrt);
+    if (t3 < c.est_us) { c.kind = 4; c.est_us = t3; }
     return c;
 }
 

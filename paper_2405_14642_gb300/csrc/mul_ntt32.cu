@@ -154,6 +154,42 @@ __global__ void __launch_bounds__(1024) k_mul_ntt3(Ntt3Args p) {
     }
 }
 
+// Mixed-size batch of products sharing the transform length N (the plan's):
+// the CTA takes the next item from the work queue (largest first) and uses
+// that item's sizes and rows.
+__global__ void __launch_bounds__(1024)
+    k_mul_ntt3_batch(Ntt3Args p, const BatchItem *items, uint32_t count, uint32_t *queue,
+                     const BatchBinding *bind) {
+    extern __shared__ __align__(16) uint32_t sm32[];
+    __shared__ uint32_t next;
+    const uint32_t Np = (phys_words(p.N) + 3) & ~3u;
+    uint32_t *A = sm32;
+    uint32_t *B = sm32 + Np;
+    uint64_t *spill = reinterpret_cast<uint64_t *>(B + Np);
+    uint32_t *flags = reinterpret_cast<uint32_t *>(spill + blockDim.x);
+    uint32_t *R0 = p.scratch + blockIdx.x * p.scratch_stride;
+    uint32_t *R1 = R0 + p.N;
+    for (;;) {
+        __syncthreads();  // the previous item is stored before `next` moves on
+        if (threadIdx.x == 0) next = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t i = next;
+        if (i >= count) break;
+        const BatchItem it = items[i];
+        p.na = it.na;
+        p.nb = it.nb;
+        p.nout = it.na + it.nb;
+        const uint32_t *arow = bind->a + it.off_a, *brow = bind->b + it.off_b;
+        uint32_t *crow = bind->c + it.off_c;
+        prime_product3<F0>(p, p.t[0], arow, brow, A, B, R0);
+        prime_product3<F1>(p, p.t[1], arow, brow, A, B, R1);
+        prime_product3<F2>(p, p.t[2], arow, brow, A, B, nullptr);
+        const bool vec_c = (p.nout % 4 == 0) && ((uintptr_t)crow % 16 == 0);
+        normalize_limbs(p.nout, crow, vec_c, A, spill, flags,
+                        [&](uint32_t k) { return garner3(p, R0[k], R1[k], B[phys(k)]); });
+    }
+}
+
 // ---- host side ---------------------------------------------------------------
 
 uint32_t mulmod(uint32_t a, uint32_t b, uint32_t p) { return (uint32_t)((uint64_t)a * b % p); }
@@ -306,6 +342,58 @@ void ntt3_destroy(Ntt3Plan *p) {
 size_t ntt3_scratch_bytes(const Ntt3Plan *p) { return p ? p->scratch_bytes : 0; }
 
 uint32_t ntt3_length(const Ntt3Plan *p) { return p ? p->N : 0; }
+
+namespace {
+
+Ntt3Args plan_args3(const Ntt3Plan *p) {
+    Ntt3Args args{};
+    args.na = p->na;
+    args.nb = p->nb;
+    args.nout = p->nout;
+    args.N = p->N;
+    args.logN = p->logN;
+    args.scratch = p->scratch;
+    args.scratch_stride = p->scratch_stride;
+    for (int i = 0; i < 3; ++i) args.t[i] = p->t[i];
+    args.g01 = p->g01;
+    args.g02 = p->g02;
+    args.g12 = p->g12;
+    return args;
+}
+
+}  // namespace
+
+bn_status ntt3_batch_plan(Ntt3Plan **out, uint32_t N) {
+    // A plan whose transform length is exactly N: na + nb = N.
+    if (N < 2 || (N & (N - 1))) return BN_EINVAL;
+    if (N / 2 > BN_MUL_MAX_LIMBS) return BN_EUNSUPPORTED;
+    if (allow_max_smem((const void *)k_mul_ntt3_batch) != cudaSuccess) return BN_ECUDA;
+    return ntt3_create(out, N / 2, N / 2, nullptr);
+}
+
+cudaError_t ntt3_batch_launch(Ntt3Plan *p, const BatchItem *items, uint32_t count, uint32_t *queue,
+                              const BatchBinding *bind, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    if (cudaError_t e = allow_max_smem((const void *)k_mul_ntt3_batch)) return e;
+    const uint32_t grid = count < p->max_grid ? count : p->max_grid;
+    k_mul_ntt3_batch<<<grid, p->threads, p->smem, st>>>(plan_args3(p), items, count, queue, bind);
+    return cudaGetLastError();
+}
+
+cudaError_t ntt3_launch_sized(Ntt3Plan *p, uint32_t na, uint32_t nb, const uint32_t *a, const uint32_t *b,
+                              uint32_t *c, cudaStream_t st) {
+    Ntt3Args args = plan_args3(p);
+    args.a = a;
+    args.b = b;
+    args.c = c;
+    args.na = na;
+    args.nb = nb;
+    args.nout = na + nb;
+    args.vec_c = (args.nout % 4 == 0) && ((uintptr_t)c % 16 == 0);
+    args.batch = 1;
+    k_mul_ntt3<<<1, p->threads, p->smem, st>>>(args);
+    return cudaGetLastError();
+}
 
 cudaError_t ntt3_launch(Ntt3Plan *p, const uint32_t *a, const uint32_t *b, uint32_t *c, uint64_t batch,
                         cudaStream_t st) {

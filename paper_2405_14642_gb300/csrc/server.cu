@@ -97,6 +97,7 @@ struct Slot {
     uint32_t *d_queues = nullptr;
     bn::BatchBinding *d_bind = nullptr;
     std::map<std::pair<int, uint32_t>, bn::NttPlan *> plans;  // (crt, log2 N)
+    std::map<uint32_t, bn::Ntt3Plan *> plans3;                 // three primes, log2 N
 };
 
 constexpr uint32_t kMaxClasses = 64;
@@ -142,8 +143,17 @@ bn::NttPlan *slot_plan(Slot &s, bool crt, uint32_t logn) {
     return p;
 }
 
+bn::Ntt3Plan *slot_plan3(Slot &s, uint32_t logn) {
+    auto it = s.plans3.find(logn);
+    if (it != s.plans3.end()) return it->second;
+    bn::Ntt3Plan *p = nullptr;
+    if (bn::ntt3_batch_plan(&p, 1u << logn) != BN_OK) p = nullptr;
+    s.plans3[logn] = p;
+    return p;
+}
+
 struct Choice {
-    uint32_t kind, key;  // 0 add, 1 schoolbook, 2 ntt64, 3 crt; class key
+    uint32_t kind, key;  // 0 add, 1 schoolbook, 2 ntt64, 3 crt, 4 three primes; class key
     double cost;
 };
 
@@ -176,6 +186,9 @@ cudaError_t launch_slot(bn_server_s *sv, Slot &s) {
                 bn::QuadConfig cfg;
                 bn::quad_configure(cfg, r.na, r.nb, nullptr);
                 e = bn::quad_launch(cfg, r.a, r.b, c, 1, s.stream);
+            } else if (ch.kind == 4) {
+                bn::Ntt3Plan *p = slot_plan3(s, ch.key);
+                e = p ? bn::ntt3_launch_sized(p, r.na, r.nb, r.a, r.b, c, s.stream) : cudaErrorMemoryAllocation;
             } else {
                 bn::NttPlan *p = slot_plan(s, ch.kind == 3, ch.key);
                 e = p ? bn::ntt_launch_sized(p, r.na, r.nb, r.a, r.b, c, s.stream) : cudaErrorMemoryAllocation;
@@ -209,6 +222,10 @@ cudaError_t launch_slot(bn_server_s *sv, Slot &s) {
             e = bn::add_batch_launch(sv->add_classes.at(key), s.d_items + i, cnt, s.d_bind, s.stream);
         } else if (kind == 1) {
             e = bn::quad_batch_launch(sv->quad_classes.at(key), s.d_items + i, cnt, queue, s.d_bind, s.stream);
+        } else if (kind == 4) {
+            bn::Ntt3Plan *p = slot_plan3(s, key);
+            e = p ? bn::ntt3_batch_launch(p, s.d_items + i, cnt, queue, s.d_bind, s.stream)
+                  : cudaErrorMemoryAllocation;
         } else {
             bn::NttPlan *p = slot_plan(s, kind == 3, key);
             e = p ? bn::ntt_batch_launch(p, s.d_items + i, cnt, queue, s.d_bind, s.stream)
@@ -293,6 +310,8 @@ void destroy_server(bn_server_s *sv) {
     for (Slot &s : sv->slots) {
         for (auto &kv : s.plans)
             if (kv.second) bn::ntt_destroy(kv.second);
+        for (auto &kv : s.plans3)
+            if (kv.second) bn::ntt3_destroy(kv.second);
         if (s.h_items) cudaFreeHost(s.h_items);
         cudaFree(s.d_items);
         cudaFree(s.d_queues);
@@ -351,8 +370,7 @@ bn_status bn_server_create(bn_server *out, const bn_server_config *cfg_in) {
         if (add_batch_class(ac, n) == BN_OK) sv->add_classes[key] = ac;
         if ((1u << key) <= BN_MUL_MAX_LIMBS) {
             QuadClass qc;
-            const uint32_t q = (n > 128 && n <= 512) ? 4 : 8;
-            if (quad_batch_class(qc, q, n, 256) == BN_OK) sv->quad_classes[key] = qc;
+            if (quad_batch_class(qc, 8, n, 256) == BN_OK) sv->quad_classes[key] = qc;
         }
     }
     sv->slots.resize(cfg.max_inflight);
@@ -372,6 +390,7 @@ bn_status bn_server_create(bn_server *out, const bn_server_config *cfg_in) {
         }
         for (uint32_t l = 11; l <= 15; ++l) slot_plan(s, false, l);  // transforms the
         for (uint32_t l = 10; l <= 14; ++l) slot_plan(s, true, l);   // cost model can pick
+        for (uint32_t l = 9; l <= 14; ++l) slot_plan3(s, l);
     }
     sv->worker = std::thread(worker_main, sv);
     *out = sv;

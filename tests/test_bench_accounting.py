@@ -24,13 +24,16 @@ def test_transform_lengths_and_counts():
 def test_ops_and_algorithmic_work():
     ops = bench.build_ops()
     labels = [o.label for o in ops]
-    assert len(ops) == 9 * 2 + 5 * 2
-    assert labels[:2] == ["add@1K", "quad@1K"] and labels[-1] == "crt@256K"
+    assert len(ops) == 9 * 2 + 5 * 3
+    assert labels[:2] == ["add@1K", "quad@1K"] and labels[-2:] == ["crt@256K", "ntt3@256K"]
     add = next(o for o in ops if o.label == "add@256K")
     assert add.bytes == 4 * (3 * 8192 + 1) * 2048 and add.mults == 0
     quad = next(o for o in ops if o.label == "quad@256K")
     assert quad.prods == 8192 * 8192 * 2048 and quad.nout == 16384
     ntt = next(o for o in ops if o.label == "ntt64@256K")
     assert ntt.prods == 4 * bench.ntt_lengths(8192)[2] * 2048
+    # three primes of 32 bits at N = 16384: 3 * (3 * 8192 * 14 + 2 * 16384) word products
+    ntt3 = next(o for o in ops if o.label == "ntt3@256K")
+    assert ntt3.prods == 3 * (3 * 8192 * 14 + 2 * 16384) * 2048 and ntt3.nout == 16384
     cfg = bench.workload_config(ops, 1)
     assert cfg["sizes_bits"][-1] == 262144 and cfg["batch_per_size"]["1024"] == 524288

@@ -41,7 +41,8 @@ def test_mixed_small_sizes_all_items(flags):
     torch_cuda()
     items, a, b, c_limbs = workloads.mixed_workload(700, seed=workloads.seed_for(3, 1), lo=1, hi=700)
     c, info = run(items, a, b, c_limbs, flags)
-    assert info["items_add"] + info["items_quad"] + info["items_ntt64"] + info["items_crt"] == 700
+    assert (info["items_add"] + info["items_quad"] + info["items_ntt64"] + info["items_crt"]
+            + info["items_ntt3"]) == 700
     check_items(items, a, b, c)
 
 
@@ -69,6 +70,19 @@ def test_full_range_sampled_and_plain_equals_graph():
     rng = np.random.default_rng(5)
     sample = np.union1d(rng.choice(1500, 60, replace=False), np.arange(19, 1500, 20)[:40])
     check_items(items, a, b, c_graph, sample)
+
+
+@pytest.mark.parametrize("flags", [0, 2, 1], ids=["graph", "plain", "autotune"])
+def test_auto_large_products_take_three_primes(flags):
+    """Products of 1024..8192 limbs: the cost model sends them to the
+    three-prime transform (the fastest form there), with exact results."""
+    torch_cuda()
+    items, a, b, c_limbs = workloads.mixed_workload(120, seed=workloads.seed_for(3, 30), lo=1024,
+                                                    hi=8192, mul_frac=1.0)
+    c, info = run(items, a, b, c_limbs, flags)
+    assert info["items_ntt3"] > 60, info
+    assert info["items_ntt3"] + info["items_quad"] + info["items_ntt64"] + info["items_crt"] == 120
+    check_items(items, a, b, c)
 
 
 def test_rebinding_buffers():
