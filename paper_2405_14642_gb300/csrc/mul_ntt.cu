@@ -72,6 +72,7 @@ constexpr uint32_t kMaxSubLength = 8192;  // both spectra in shared memory
 template <uint64_t P>
 struct MontField {
     using Elem = uint64_t;
+    using Tw = uint64_t;  // twiddles in Montgomery form
     static constexpr uint64_t P_VALUE = P;
     static constexpr uint32_t PH = (uint32_t)(P >> 32);
     static constexpr uint64_t TWO_P = 2 * P;
@@ -117,6 +118,8 @@ struct MontField {
         const uint64_t h = (uint64_t)m1 * PH + (sm >> 32);
         return hi + h + ((x0 | x1) != 0u);
     }
+    __device__ static __forceinline__ uint64_t twiddle(uint64_t a, uint64_t w) { return mulw(a, w); }
+    __device__ static __forceinline__ uint64_t twiddle_lazy(uint64_t a, uint64_t w) { return mul(a, w); }
 };
 
 using FieldP1 = MontField<4179340454199820289ull>;  // 29 * 2^57 + 1 (PrimeField64)

@@ -45,7 +45,7 @@ constexpr uint32_t kMaxLength3 = 16384;  // both u32 spectra in shared memory
 
 // Z_P for a prime P < 2^30 in Montgomery form with R = 2^32; NINV = -P^-1
 // mod 2^32.  Elements are kept lazily in [0, 2P); canon() maps to [0, P).
-//   mul(a, b): t = a b < 4P^2 (a, b < 2P, or a < 4P and b < P); the quotient
+//   mul(a, b): t = a b < 4P^2 (a, b < 2P); the quotient
 //   m = t_lo NINV makes t + m P divisible by 2^32, and (t + m P) / 2^32 =
 //   t_hi + hi(m P) + (t_lo != 0) < 4P^2 / 2^32 + P < 2P.
 template <uint32_t P, uint32_t NINV>
@@ -70,9 +70,18 @@ struct MontField32 {
         const uint32_t m = lo * NINV;
         return hi + __umulhi(m, P) + (lo != 0u);
     }
-    __device__ static __forceinline__ uint32_t mulw(uint32_t a, uint32_t b) { return mul(a, b); }
     // Any 32-bit digit d into the field: d (R mod P) / R = d (mod P), < 2P.
     __device__ static __forceinline__ uint32_t from_digit(uint32_t d) { return mul(d, R_MOD_P); }
+    // Twiddles by Shoup's method: an entry is (w, w' = floor(w 2^32 / P)) with
+    // w < P, and for any a < 2^32, q = hi(a w') gives a w - q P in [0, 2P),
+    // exact in 32-bit arithmetic.  One high and two low multiplies, against
+    // Montgomery's two high, two low and a correction.
+    using Tw = uint2;
+    __device__ static __forceinline__ uint32_t twiddle(uint32_t a, uint2 w) {
+        const uint32_t q = __umulhi(a, w.y);
+        return a * w.x - q * P;
+    }
+    __device__ static __forceinline__ uint32_t twiddle_lazy(uint32_t a, uint2 w) { return twiddle(a, w); }
 };
 
 using F0 = MontField32<469762049u, 0x1bffffffu>;  // 7 * 2^26 + 1
@@ -81,8 +90,8 @@ using F2 = MontField32<998244353u, 0x3b7fffffu>;  // 119 * 2^23 + 1
 static_assert(F0::P_VALUE < F1::P_VALUE && F1::P_VALUE < F2::P_VALUE, "Garner order");
 
 struct Tab3 {
-    const uint32_t *twf;  // [N]: twf[h + j] = form(w_{2h}^j)
-    const uint32_t *twi;  // [N]: form(w_{2h}^-j)
+    const uint2 *twf;     // [N]: twf[h + j] = Shoup pair of w_{2h}^j
+    const uint2 *twi;     // [N]: Shoup pair of w_{2h}^-j
     uint32_t scale;       // N^-1 R^2 mod p: mul(x, scale) undoes the 1/R of the pointwise product
 };
 
@@ -103,19 +112,19 @@ template <class F>
 __device__ void prime_product3(const Ntt3Args &p, const Tab3 &tb, const uint32_t *arow,
                                const uint32_t *brow, uint32_t *A, uint32_t *B, uint32_t *dest) {
     for (uint32_t j = threadIdx.x; j < p.N; j += blockDim.x) {  // n1: digits
-        A[phys(j)] = j < p.na ? F::from_digit(__ldg(arow + j)) : 0u;
-        B[phys(j)] = j < p.nb ? F::from_digit(__ldg(brow + j)) : 0u;
+        A[phys4(j)] = j < p.na ? F::from_digit(__ldg(arow + j)) : 0u;
+        B[phys4(j)] = j < p.nb ? F::from_digit(__ldg(brow + j)) : 0u;
     }
     __syncthreads();
     forward2<F>(p.N, p.logN, tb.twf, A, B);                       // n2: forward transforms
     for (uint32_t j = threadIdx.x; j < p.N; j += blockDim.x)      // n3: pointwise
-        B[phys(j)] = F::mul(A[phys(j)], B[phys(j)]);
+        B[phys4(j)] = F::mul(A[phys4(j)], B[phys4(j)]);
     __syncthreads();
     inverse<F>(p.N, p.logN, tb.twi, B);                           // n4: inverse (unscaled)
     for (uint32_t j = threadIdx.x; j < p.nout; j += blockDim.x) {
-        const uint32_t v = F::canon(F::mul(B[phys(j)], tb.scale));
+        const uint32_t v = F::canon(F::mul(B[phys4(j)], tb.scale));
         if (dest) dest[j] = v;
-        else B[phys(j)] = v;
+        else B[phys4(j)] = v;
     }
     __syncthreads();
 }
@@ -136,7 +145,7 @@ __device__ __forceinline__ u128 garner3(const Ntt3Args &p, uint32_t r0, uint32_t
 
 __global__ void __launch_bounds__(1024) k_mul_ntt3(Ntt3Args p) {
     extern __shared__ __align__(16) uint32_t sm32[];
-    const uint32_t Np = (phys_words(p.N) + 3) & ~3u;
+    const uint32_t Np = (phys4_words(p.N) + 3) & ~3u;  // B stays 16-byte aligned
     uint32_t *A = sm32;
     uint32_t *B = sm32 + Np;
     uint64_t *spill = reinterpret_cast<uint64_t *>(B + Np);
@@ -150,7 +159,7 @@ __global__ void __launch_bounds__(1024) k_mul_ntt3(Ntt3Args p) {
         prime_product3<F2>(p, p.t[2], arow, brow, A, B, nullptr);
         // n6: recombine and carry into limbs (A's words serve as the staging row)
         normalize_limbs(p.nout, p.c + inst * p.nout, p.vec_c, A, spill, flags,
-                        [&](uint32_t k) { return garner3(p, R0[k], R1[k], B[phys(k)]); });
+                        [&](uint32_t k) { return garner3(p, R0[k], R1[k], B[phys4(k)]); });
     }
 }
 
@@ -162,7 +171,7 @@ __global__ void __launch_bounds__(1024)
                      const BatchBinding *bind) {
     extern __shared__ __align__(16) uint32_t sm32[];
     __shared__ uint32_t next;
-    const uint32_t Np = (phys_words(p.N) + 3) & ~3u;
+    const uint32_t Np = (phys4_words(p.N) + 3) & ~3u;  // B stays 16-byte aligned
     uint32_t *A = sm32;
     uint32_t *B = sm32 + Np;
     uint64_t *spill = reinterpret_cast<uint64_t *>(B + Np);
@@ -186,7 +195,7 @@ __global__ void __launch_bounds__(1024)
         prime_product3<F2>(p, p.t[2], arow, brow, A, B, nullptr);
         const bool vec_c = (p.nout % 4 == 0) && ((uintptr_t)crow % 16 == 0);
         normalize_limbs(p.nout, crow, vec_c, A, spill, flags,
-                        [&](uint32_t k) { return garner3(p, R0[k], R1[k], B[phys(k)]); });
+                        [&](uint32_t k) { return garner3(p, R0[k], R1[k], B[phys4(k)]); });
     }
 }
 
@@ -224,15 +233,18 @@ HostField32 make_field(uint32_t k, uint32_t n) {
     return f;
 }
 
-void make_tables3(const HostField32 &f, uint32_t N, uint32_t *twf, uint32_t *twi, uint32_t &scale) {
+// Shoup pair (w, floor(w 2^32 / p)) of a canonical w.
+uint2 shoup(uint32_t w, uint32_t p) { return make_uint2(w, (uint32_t)(((uint64_t)w << 32) / p)); }
+
+void make_tables3(const HostField32 &f, uint32_t N, uint2 *twf, uint2 *twi, uint32_t &scale) {
     const uint32_t w = powmod(f.g, (1ull << f.n) / N, f.p), wi = invmod(w, f.p);
-    twf[0] = twi[0] = 0;
+    twf[0] = twi[0] = make_uint2(0, 0);
     for (uint32_t h = 1; h < N; h <<= 1) {
         const uint32_t s = powmod(w, N / (2 * h), f.p), si = powmod(wi, N / (2 * h), f.p);
         uint32_t x = 1, xi = 1;
         for (uint32_t j = 0; j < h; ++j) {
-            twf[h + j] = form(x, f.p);
-            twi[h + j] = form(xi, f.p);
+            twf[h + j] = shoup(x, f.p);
+            twi[h + j] = shoup(xi, f.p);
             x = mulmod(x, s, f.p);
             xi = mulmod(xi, si, f.p);
         }
@@ -289,7 +301,7 @@ bn_status ntt3_create(Ntt3Plan **out, uint32_t na, uint32_t nb, const bn_tuning 
     if (T > 1024) T = 1024;
     if (cta) T = cta;
     p->threads = T;
-    const uint32_t Np = (phys_words(p->N) + 3) & ~3u;
+    const uint32_t Np = (phys4_words(p->N) + 3) & ~3u;
     p->smem = 4u * 2u * Np + 8u * T + 4u * 32u;
 
     cudaError_t e = allow_max_smem((const void *)k_mul_ntt3);
@@ -305,7 +317,7 @@ bn_status ntt3_create(Ntt3Plan **out, uint32_t na, uint32_t nb, const bn_tuning 
     p->max_grid = (uint32_t)(sms * per_sm);
     p->scratch_stride = 2ull * p->N;
 
-    const size_t table_words = ((size_t)6 * p->N + 63) & ~size_t(63);
+    const size_t table_words = ((size_t)12 * p->N + 63) & ~size_t(63);  // 3 primes x 2 tables x N pairs
     p->scratch_bytes = (size_t)p->max_grid * p->scratch_stride * 4u;
     e = cudaMalloc(&p->dev, table_words * 4u + p->scratch_bytes);
     if (e != cudaSuccess) {
@@ -314,9 +326,9 @@ bn_status ntt3_create(Ntt3Plan **out, uint32_t na, uint32_t nb, const bn_tuning 
     }
     std::vector<uint32_t> host(table_words, 0);
     for (int i = 0; i < 3; ++i) {
-        uint32_t *twf = host.data() + (size_t)2 * i * p->N, *twi = twf + p->N;
+        uint2 *twf = reinterpret_cast<uint2 *>(host.data()) + (size_t)2 * i * p->N, *twi = twf + p->N;
         make_tables3(fs[i], p->N, twf, twi, p->t[i].scale);
-        p->t[i].twf = p->dev + (size_t)2 * i * p->N;
+        p->t[i].twf = reinterpret_cast<const uint2 *>(p->dev) + (size_t)2 * i * p->N;
         p->t[i].twi = p->t[i].twf + p->N;
     }
     e = cudaMemcpy(p->dev, host.data(), table_words * 4u, cudaMemcpyHostToDevice);

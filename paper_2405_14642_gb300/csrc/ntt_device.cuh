@@ -3,12 +3,12 @@
 // butterfly passes over a shared-memory buffer, whole forward / inverse
 // transforms, and the normalisation of convolution coefficients into limbs.
 //
-// A field type F provides Elem (the word type of its elements), TWO_P, and
-// add / sub / mul / mulw / canon on lazily reduced elements in [0, 2P):
-//   mul(a, b)  for a, b < 2P,
-//   mulw(a, w) for any a < 4P and a canonical twiddle w < P,
-// both returning a value in [0, 2P).  Twiddles are kept in the field's
-// multiplication form, so that mul(x, form(w)) = x*w.
+// A field type F provides Elem (the word type of its elements), Tw (the type
+// of a twiddle table entry), TWO_P, and on lazily reduced elements in [0, 2P):
+//   add, sub, canon, mul(a, b) for a, b < 2P,
+//   twiddle(a, w)      = a * (the twiddle w) for any a < 4P,
+//   twiddle_lazy(a, w) = the same for a < 2P (may be cheaper),
+// all returning a value in [0, 2P).
 #pragma once
 #include "bn_device.cuh"
 
@@ -19,9 +19,63 @@ typedef unsigned __int128 u128;
 
 constexpr int kRadixLog = 3;  // radix-8 passes
 
-// Shared-memory index with one element of padding per 16 (bank spread).
+// Shared-memory index with one element of padding per 16 (bank spread) for
+// 64-bit elements.
 __device__ __forceinline__ uint32_t phys(uint32_t i) { return i + (i >> 4); }
 __host__ __device__ constexpr uint32_t phys_words(uint32_t n) { return n + (n >> 4) + 1; }
+
+// Shared-memory index for 32-bit elements: four words of padding per 32, so
+// groups of 4 consecutive elements stay 16-byte aligned (vector accesses) and
+// every pass below meets 32 distinct banks: strides 4, 8 and 16 through the
+// padding, unit-stride groups through 16-byte vector accesses.
+__device__ __forceinline__ uint32_t phys4(uint32_t i) { return i + 4u * (i >> 5); }
+__host__ __device__ constexpr uint32_t phys4_words(uint32_t n) { return n + 4u * ((n + 31) >> 5); }
+
+template <class T>
+__device__ __forceinline__ uint32_t pidx(uint32_t i) {
+    if constexpr (sizeof(T) == 4) return phys4(i);
+    else return phys(i);
+}
+
+// E consecutive elements starting at logical index `base` (a multiple of E).
+// 32-bit elements move as 8- or 16-byte vectors: a run of E <= 8 from a
+// multiple of E never crosses a 32-element padding boundary.
+template <class T, int E>
+__device__ __forceinline__ void load_run(const T *buf, uint32_t base, T (&x)[E]) {
+    if constexpr (sizeof(T) == 4 && E >= 2) {
+        const T *p = buf + phys4(base);
+        if constexpr (E == 2) {
+            const uint2 v = *reinterpret_cast<const uint2 *>(p);
+            x[0] = v.x; x[1] = v.y;
+        } else {
+#pragma unroll
+            for (int k = 0; k < E; k += 4) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(p + k);
+                x[k] = v.x; x[k + 1] = v.y; x[k + 2] = v.z; x[k + 3] = v.w;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) x[m] = buf[pidx<T>(base + m)];
+    }
+}
+
+template <class T, int E>
+__device__ __forceinline__ void store_run(T *buf, uint32_t base, const T (&x)[E]) {
+    if constexpr (sizeof(T) == 4 && E >= 2) {
+        T *p = buf + phys4(base);
+        if constexpr (E == 2) {
+            *reinterpret_cast<uint2 *>(p) = make_uint2(x[0], x[1]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < E; k += 4)
+                *reinterpret_cast<uint4 *>(p + k) = make_uint4(x[k], x[k + 1], x[k + 2], x[k + 3]);
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) buf[pidx<T>(base + m)] = x[m];
+    }
+}
 
 // Twiddle index of group element m in the stage of half-size h (h = hm*step):
 // the position of element m within its 2h block.  Within one group it depends
@@ -35,33 +89,40 @@ __device__ __forceinline__ uint32_t tw_index(uint32_t base, uint32_t m, uint32_t
 // difference u - v + 2P (< 4P) goes to the twiddle multiply unreduced.
 template <class F, int KK, bool UNIT>
 __device__ __forceinline__ void dif_pass(typename F::Elem *buf, uint32_t L, uint32_t H,
-                                         const typename F::Elem *tw) {
+                                         const typename F::Tw *tw) {
     using T = typename F::Elem;
+    using W = typename F::Tw;
     constexpr int E = 1 << KK;
     const uint32_t step = UNIT ? 1u : H >> (KK - 1);
     const uint32_t lstep = UNIT ? 0u : __ffs(step) - 1;
     for (uint32_t g = threadIdx.x; g < (L >> KK); g += blockDim.x) {
         const uint32_t base = ((g >> lstep) << (lstep + KK)) | (g & (step - 1));
         T x[E];
+        if constexpr (UNIT) load_run<T, E>(buf, base, x);
+        else {
 #pragma unroll
-        for (int m = 0; m < E; ++m) x[m] = buf[phys(base + m * step)];
+            for (int m = 0; m < E; ++m) x[m] = buf[pidx<T>(base + m * step)];
+        }
 #pragma unroll
         for (int st = 0; st < KK; ++st) {
             const uint32_t hm = 1u << (KK - 1 - st), h = hm * step;
             const bool trivial = UNIT && hm == 1;
-            T w[E / 2];
+            W w[E / 2];
 #pragma unroll
-            for (int m = 0; m < (int)hm; ++m) w[m] = trivial ? 0 : __ldg(tw + tw_index(base, m, step, h));
+            for (int m = 0; m < (int)hm; ++m) w[m] = trivial ? W{} : __ldg(tw + tw_index(base, m, step, h));
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 if (m & hm) continue;
                 const T u = x[m], v = x[m + hm];
                 x[m] = F::add(u, v);
-                x[m + hm] = trivial ? F::sub(u, v) : F::mulw(u + F::TWO_P - v, w[m & (hm - 1)]);
+                x[m + hm] = trivial ? F::sub(u, v) : F::twiddle(u + F::TWO_P - v, w[m & (hm - 1)]);
             }
         }
+        if constexpr (UNIT) store_run<T, E>(buf, base, x);
+        else {
 #pragma unroll
-        for (int m = 0; m < E; ++m) buf[phys(base + m * step)] = x[m];
+            for (int m = 0; m < E; ++m) buf[pidx<T>(base + m * step)] = x[m];
+        }
     }
 }
 
@@ -69,43 +130,68 @@ __device__ __forceinline__ void dif_pass(typename F::Elem *buf, uint32_t L, uint
 // UNIT: h0 = 1, so the first stage's twiddle is 1.
 template <class F, int KK, bool UNIT>
 __device__ __forceinline__ void dit_pass(typename F::Elem *buf, uint32_t L, uint32_t h0,
-                                         const typename F::Elem *tw) {
+                                         const typename F::Tw *tw) {
     using T = typename F::Elem;
+    using W = typename F::Tw;
     constexpr int E = 1 << KK;
     const uint32_t step = UNIT ? 1u : h0;
     const uint32_t lstep = UNIT ? 0u : __ffs(step) - 1;
     for (uint32_t g = threadIdx.x; g < (L >> KK); g += blockDim.x) {
         const uint32_t base = ((g >> lstep) << (lstep + KK)) | (g & (step - 1));
         T x[E];
+        if constexpr (UNIT) load_run<T, E>(buf, base, x);
+        else {
 #pragma unroll
-        for (int m = 0; m < E; ++m) x[m] = buf[phys(base + m * step)];
+            for (int m = 0; m < E; ++m) x[m] = buf[pidx<T>(base + m * step)];
+        }
 #pragma unroll
         for (int st = 0; st < KK; ++st) {
             const uint32_t hm = 1u << st, h = hm * step;
             const bool trivial = UNIT && hm == 1;
-            T w[E / 2];
+            W w[E / 2];
 #pragma unroll
-            for (int m = 0; m < (int)hm; ++m) w[m] = trivial ? 0 : __ldg(tw + tw_index(base, m, step, h));
+            for (int m = 0; m < (int)hm; ++m) w[m] = trivial ? W{} : __ldg(tw + tw_index(base, m, step, h));
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 if (m & hm) continue;
                 const T u = x[m];
-                const T v = trivial ? x[m + hm] : F::mul(x[m + hm], w[m & (hm - 1)]);
+                const T v = trivial ? x[m + hm] : F::twiddle_lazy(x[m + hm], w[m & (hm - 1)]);
                 x[m] = F::add(u, v);
                 x[m + hm] = F::sub(u, v);
             }
         }
+        if constexpr (UNIT) store_run<T, E>(buf, base, x);
+        else {
 #pragma unroll
-        for (int m = 0; m < E; ++m) buf[phys(base + m * step)] = x[m];
+            for (int m = 0; m < E; ++m) buf[pidx<T>(base + m * step)] = x[m];
+        }
     }
 }
 
 // Forward transforms of A and B (natural order in, bit-reversed out); ends
-// with a barrier.
+// with a barrier.  For 32-bit elements the passes that are not radix 8 come
+// first (large strides), so no pass runs at stride 2, the one pattern the
+// 32-bit padding leaves with bank conflicts.
 template <class F>
-__device__ void forward2(uint32_t L, uint32_t logL, const typename F::Elem *tw, typename F::Elem *A,
+__device__ void forward2(uint32_t L, uint32_t logL, const typename F::Tw *tw, typename F::Elem *A,
                          typename F::Elem *B) {
     uint32_t H = L >> 1, left = logL;
+    if constexpr (sizeof(typename F::Elem) == 4) {
+        const uint32_t rem = left % kRadixLog;
+        if (rem == 2 && left > 2) {
+            dif_pass<F, 2, false>(A, L, H, tw);
+            dif_pass<F, 2, false>(B, L, H, tw);
+            __syncthreads();
+            H >>= 2;
+            left -= 2;
+        } else if (rem == 1 && left > 1) {
+            dif_pass<F, 1, false>(A, L, H, tw);
+            dif_pass<F, 1, false>(B, L, H, tw);
+            __syncthreads();
+            H >>= 1;
+            left -= 1;
+        }
+    }
     while (left > (uint32_t)kRadixLog) {  // these passes have step >= 2
         dif_pass<F, kRadixLog, false>(A, L, H, tw);
         dif_pass<F, kRadixLog, false>(B, L, H, tw);
@@ -129,7 +215,7 @@ __device__ void forward2(uint32_t L, uint32_t logL, const typename F::Elem *tw, 
 // Unscaled inverse transform of B (bit-reversed in, natural out); ends with a
 // barrier.
 template <class F>
-__device__ void inverse(uint32_t L, uint32_t logL, const typename F::Elem *tw, typename F::Elem *B) {
+__device__ void inverse(uint32_t L, uint32_t logL, const typename F::Tw *tw, typename F::Elem *B) {
     uint32_t left = logL;
     const uint32_t first = left >= (uint32_t)kRadixLog ? (uint32_t)kRadixLog : left;
     if (first == 3) dit_pass<F, 3, true>(B, L, 1, tw);   // the first pass has h0 = 1
