@@ -139,7 +139,6 @@ struct NttArgs {
     uint32_t *c;
     uint32_t na, nb, nout;
     uint32_t N, L, logL, S, digit_bits;
-    uint32_t vec_c;
     uint64_t batch;
     uint64_t *scratch;
     uint64_t scratch_stride;  // u64 words per CTA
@@ -243,7 +242,7 @@ template <bool CRT>
 __device__ void normalize(const NttArgs &p, uint64_t inst, uint32_t *out_s, const uint64_t *B,
                           bool in_smem, const uint64_t *C1, const uint64_t *Cs, uint64_t *spill,
                           uint32_t *flags) {
-    normalize_limbs(p.nout, p.c + inst * p.nout, p.vec_c, out_s, spill, flags,
+    normalize_limbs(p.nout, p.c + inst * p.nout, out_s, spill, flags,
                     [&](uint32_t k) { return limb_value<CRT>(p, k, B, in_smem, C1, Cs); });
 }
 
@@ -304,7 +303,6 @@ __global__ void __launch_bounds__(1024)
         q.na = it.na;
         q.nb = it.nb;
         q.nout = it.na + it.nb;
-        q.vec_c = (q.nout % 4 == 0) && ((uintptr_t)q.c % 16 == 0);
         q.batch = 1;
         const bool keep = q.S == 1;
         if constexpr (CRT) {
@@ -551,7 +549,6 @@ cudaError_t ntt_launch(NttPlan *p, const uint32_t *a, const uint32_t *b, uint32_
     args.a = a;
     args.b = b;
     args.c = c;
-    args.vec_c = (p->nout % 4 == 0) && ((uintptr_t)c % 16 == 0);
     args.batch = batch;
     const uint64_t grid = batch < p->max_grid ? batch : p->max_grid;
     if (p->crt) k_mul_ntt<true><<<(unsigned)grid, p->threads, p->smem, st>>>(args);
@@ -568,7 +565,6 @@ cudaError_t ntt_launch_sized(NttPlan *p, uint32_t na, uint32_t nb, const uint32_
     args.na = na;
     args.nb = nb;
     args.nout = na + nb;
-    args.vec_c = (args.nout % 4 == 0) && ((uintptr_t)c % 16 == 0);
     args.batch = 1;
     if (p->crt) k_mul_ntt<true><<<1, p->threads, p->smem, st>>>(args);
     else k_mul_ntt<false><<<1, p->threads, p->smem, st>>>(args);
@@ -822,7 +818,6 @@ extern "C" bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, ui
     args.logL = logL;
     args.S = S;
     args.digit_bits = crt ? 32 : 16;
-    args.vec_c = (nout % 4 == 0) && ((uintptr_t)c % 16 == 0);
     args.batch = batch;
     args.scratch = d.scratch;
     args.scratch_stride = stride;

@@ -98,7 +98,7 @@ struct Tab3 {
 struct Ntt3Args {
     const uint32_t *a, *b;
     uint32_t *c;
-    uint32_t na, nb, nout, N, logN, vec_c;
+    uint32_t na, nb, nout, N, logN;
     uint64_t batch;
     uint32_t *scratch;        // per CTA: residues mod p0 [N], mod p1 [N]
     uint64_t scratch_stride;  // u32 words per CTA
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(1024) k_mul_ntt3(Ntt3Args p) {
         prime_product3<F1>(p, p.t[1], arow, brow, A, B, R1);
         prime_product3<F2>(p, p.t[2], arow, brow, A, B, nullptr);
         // n6: recombine and carry into limbs (A's words serve as the staging row)
-        normalize_limbs(p.nout, p.c + inst * p.nout, p.vec_c, A, spill, flags,
+        normalize_limbs(p.nout, p.c + inst * p.nout, A, spill, flags,
                         [&](uint32_t k) { return garner3(p, R0[k], R1[k], B[phys4(k)]); });
     }
 }
@@ -193,8 +193,7 @@ __global__ void __launch_bounds__(1024)
         prime_product3<F0>(p, p.t[0], arow, brow, A, B, R0);
         prime_product3<F1>(p, p.t[1], arow, brow, A, B, R1);
         prime_product3<F2>(p, p.t[2], arow, brow, A, B, nullptr);
-        const bool vec_c = (p.nout % 4 == 0) && ((uintptr_t)crow % 16 == 0);
-        normalize_limbs(p.nout, crow, vec_c, A, spill, flags,
+        normalize_limbs(p.nout, crow, A, spill, flags,
                         [&](uint32_t k) { return garner3(p, R0[k], R1[k], B[phys4(k)]); });
     }
 }
@@ -401,7 +400,6 @@ cudaError_t ntt3_launch_sized(Ntt3Plan *p, uint32_t na, uint32_t nb, const uint3
     args.na = na;
     args.nb = nb;
     args.nout = na + nb;
-    args.vec_c = (args.nout % 4 == 0) && ((uintptr_t)c % 16 == 0);
     args.batch = 1;
     k_mul_ntt3<<<1, p->threads, p->smem, st>>>(args);
     return cudaGetLastError();
@@ -419,7 +417,6 @@ cudaError_t ntt3_launch(Ntt3Plan *p, const uint32_t *a, const uint32_t *b, uint3
     args.nout = p->nout;
     args.N = p->N;
     args.logN = p->logN;
-    args.vec_c = (p->nout % 4 == 0) && ((uintptr_t)c % 16 == 0);
     args.batch = batch;
     args.scratch = p->scratch;
     args.scratch_stride = p->scratch_stride;

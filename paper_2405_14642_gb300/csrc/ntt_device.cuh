@@ -245,11 +245,15 @@ __device__ void inverse(uint32_t L, uint32_t logL, const typename F::Tw *tw, typ
 // limbs of its window, carrying inside the window, the window's carry spills
 // into the next window, and the remaining one-bit carries are resolved with
 // the Section 2 carry scan across the CTA.  The nout limbs are assembled in
-// out_s (shared) and then copied to crow.  Every thread of the CTA calls it;
-// spill has one word per thread, flags one per warp.
+// the shared staging row out_s (limb k at k + k/16: the threads' windows are
+// 16 limbs apart, and the padding puts them in distinct banks; out_s holds
+// nout + nout/16 + 1 words) and then copied to crow.  Every thread of the CTA
+// calls it; spill has one word per thread, flags one per warp.
+__device__ __forceinline__ uint32_t stage_index(uint32_t k) { return k + (k >> 4); }
+
 template <class LimbFn>
-__device__ void normalize_limbs(uint32_t nout, uint32_t *crow, bool vec_c, uint32_t *out_s,
-                                uint64_t *spill, uint32_t *flags, LimbFn &&limb) {
+__device__ void normalize_limbs(uint32_t nout, uint32_t *crow, uint32_t *out_s, uint64_t *spill,
+                                uint32_t *flags, LimbFn &&limb) {
     const uint32_t T = blockDim.x, t = threadIdx.x;
     uint32_t QN = (nout + T - 1) / T;
     if (QN < 2) QN = 2;  // a window must absorb a two-word spill
@@ -259,7 +263,7 @@ __device__ void normalize_limbs(uint32_t nout, uint32_t *crow, bool vec_c, uint3
     u128 carry = 0;
     for (uint32_t k = k0; k < k1; ++k) {
         const u128 v = limb(k) + carry;
-        out_s[k] = (uint32_t)v;
+        out_s[stage_index(k)] = (uint32_t)v;
         carry = v >> 32;
     }
     spill[t] = (uint64_t)carry;  // < 2^64: the coefficients are below 2^96
@@ -268,25 +272,20 @@ __device__ void normalize_limbs(uint32_t nout, uint32_t *crow, bool vec_c, uint3
     uint64_t c = t > 0 ? spill[t - 1] : 0;
     uint32_t all = 0xffffffffu;
     for (uint32_t k = k0; k < k1; ++k) {
-        const uint64_t v = (uint64_t)out_s[k] + (c & 0xffffffffu);
-        out_s[k] = (uint32_t)v;
+        const uint64_t v = (uint64_t)out_s[stage_index(k)] + (c & 0xffffffffu);
+        out_s[stage_index(k)] = (uint32_t)v;
         c = (c >> 32) + (v >> 32);
-        all &= out_s[k];
+        all &= (uint32_t)v;
     }
     const bool owns = k0 < k1;
     // (c) resolve the carries across windows (Section 2 carry scan)
     const uint32_t cin = group_carry_in(owns && c != 0, owns && all == 0xffffffffu, T, flags);
     if (cin)
         for (uint32_t k = k0; k < k1; ++k)
-            if (++out_s[k] != 0) break;
+            if (++out_s[stage_index(k)] != 0) break;
     __syncthreads();
     // (d) coalesced copy-out
-    if (vec_c) {
-        for (uint32_t x = 4 * t; x < nout; x += 4 * T)
-            st_stream_v4(crow + x, *reinterpret_cast<const uint4 *>(out_s + x));
-    } else {
-        for (uint32_t x = t; x < nout; x += T) st_stream(crow + x, out_s[x]);
-    }
+    for (uint32_t x = t; x < nout; x += T) st_stream(crow + x, out_s[stage_index(x)]);
     __syncthreads();
 }
 
