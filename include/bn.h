@@ -122,6 +122,18 @@ bn_status bn_plan_execute(bn_plan plan, const uint32_t *a, const uint32_t *b,
 bn_status bn_plan_execute_host(bn_plan plan, const uint32_t *a, const uint32_t *b,
                                uint32_t *c, void *stream);
 
+/* Same copies and kernel, enqueued on `stream` without the final
+ * synchronisation, so that the copies and kernels of several plans on
+ * several streams overlap (the copy engines run beside the kernels).  a and b
+ * must stay unchanged and c untouched until `stream` reaches the end of the
+ * call; with pinned host memory the copies are asynchronous (pageable memory
+ * makes them partly synchronous).  The plan's staging buffers are reused by
+ * every call on the plan, so calls on one plan must be on one stream (or
+ * otherwise ordered).  Errors as bn_plan_execute_host; errors of the queued
+ * work surface on stream synchronisation. */
+bn_status bn_plan_execute_host_async(bn_plan plan, const uint32_t *a, const uint32_t *b,
+                                     uint32_t *c, void *stream);
+
 /* Free the plan's device resources (synchronises the device first). */
 bn_status bn_plan_destroy(bn_plan plan);
 

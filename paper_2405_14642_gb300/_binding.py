@@ -92,6 +92,7 @@ def load(build_if_missing: bool = False):
                             ctypes.POINTER(bn_tuning)], st),
         "bn_plan_execute": ([vp, u32p, u32p, u32p, vp], st),
         "bn_plan_execute_host": ([vp, u32p, u32p, u32p, vp], st),
+        "bn_plan_execute_host_async": ([vp, u32p, u32p, u32p, vp], st),
         "bn_plan_destroy": ([vp], st),
         "bn_plan_out_limbs": ([vp], u32),
         "bn_plan_scratch_bytes": ([vp], ctypes.c_size_t),
@@ -335,6 +336,25 @@ class Plan:
         _check(self._lib.bn_plan_execute_host(self._h, pa, pb, pc, ctypes.c_void_p(s.cuda_stream)),
                "bn_plan_execute_host")
         return kc
+
+    def execute_host_async(self, a, b, out, stream=None):
+        """Enqueue copy-in, kernel and copy-out on `stream` without waiting
+        (bn_plan_execute_host_async).  a, b and out must be contiguous pinned
+        torch CPU tensors of 32-bit limbs that the caller keeps alive, a and b
+        unchanged, until the stream has passed this call."""
+        ptrs = []
+        for x, shape, name in ((a, (self.batch, self.na), "a"), (b, (self.batch, self.nb), "b"),
+                               (out, (self.batch, self.out_limbs), "out")):
+            if not hasattr(x, "data_ptr") or x.is_cuda or not x.is_pinned():
+                raise TypeError(f"{name} must be a pinned torch CPU tensor")
+            if tuple(x.shape) != shape or not x.is_contiguous() or x.element_size() != 4:
+                raise ValueError(f"{name} must be a contiguous 32-bit {shape} tensor")
+            ptrs.append(ctypes.c_void_p(x.data_ptr()))
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(self._lib.bn_plan_execute_host_async(self._h, *ptrs, ctypes.c_void_p(s.cuda_stream)),
+               "bn_plan_execute_host_async")
+        return out
 
     def close(self):
         if self._h:

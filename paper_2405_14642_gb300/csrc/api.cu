@@ -231,8 +231,10 @@ bn_status bn_plan_execute(bn_plan plan, const uint32_t *a, const uint32_t *b, ui
     return execute(plan, a, b, c, plan->batch, stream);
 }
 
-bn_status bn_plan_execute_host(bn_plan plan, const uint32_t *a, const uint32_t *b, uint32_t *c,
-                               void *stream) {
+namespace {
+
+bn_status execute_host(bn_plan plan, const uint32_t *a, const uint32_t *b, uint32_t *c, void *stream,
+                       bool sync) {
     if (!plan) {
         set_error_text("null plan");
         return BN_EINVAL;
@@ -265,7 +267,19 @@ bn_status bn_plan_execute_host(bn_plan plan, const uint32_t *a, const uint32_t *
     if (s != BN_OK) return s;
     e = cudaMemcpyAsync(c, plan->d_c, cb, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_status("device to host copy", e);
-    return cuda_status("stream synchronize", cudaStreamSynchronize(st));
+    return sync ? cuda_status("stream synchronize", cudaStreamSynchronize(st)) : BN_OK;
+}
+
+}  // namespace
+
+bn_status bn_plan_execute_host(bn_plan plan, const uint32_t *a, const uint32_t *b, uint32_t *c,
+                               void *stream) {
+    return execute_host(plan, a, b, c, stream, true);
+}
+
+bn_status bn_plan_execute_host_async(bn_plan plan, const uint32_t *a, const uint32_t *b, uint32_t *c,
+                                     void *stream) {
+    return execute_host(plan, a, b, c, stream, false);
 }
 
 bn_status bn_plan_destroy(bn_plan plan) {

@@ -87,3 +87,35 @@ def test_ntt3_rejects_batch_items_and_oversize():
     empty = torch.zeros((0, 4), dtype=torch.int32, device="cuda")
     assert bn.bn_mul_ntt3(empty, empty).shape == (0, 8)
     assert to_host(bn.bn_mul_ntt3(x, x)).sum() == 0
+
+
+def test_host_async_plans_on_streams():
+    """bn_plan_execute_host_async: three plans of different ops on three
+    streams with pinned host buffers, enqueued back to back, each result equal
+    to the oracle once the streams are synchronised."""
+    torch = torch_cuda()
+    import paper_2405_14642_gb300 as bn
+    cases = [(bn.BN_OP_MUL_NTT3, 600, 500), (bn.BN_OP_MUL_QUAD, 300, 77), (bn.BN_OP_ADD, 1000, 999)]
+    streams = [torch.cuda.Stream() for _ in cases]
+    runs = []
+    for k, (op, na, nb) in enumerate(cases):
+        a, b = workloads.pair_batch(33, na, nb, seed=workloads.seed_for(8, 500 + k))
+        plan = bn.Plan(op, na, nb, 33)
+        pa = torch.from_numpy(a.view(np.int32)).pin_memory()
+        pb = torch.from_numpy(b.view(np.int32)).pin_memory()
+        pc = torch.empty((33, plan.out_limbs), dtype=torch.int32).pin_memory()
+        runs.append((op, a, b, plan, pa, pb, pc))
+    for rep in range(2):
+        for (op, a, b, plan, pa, pb, pc), st in zip(runs, streams):
+            pc.fill_(-1)
+            plan.execute_host_async(pa, pb, pc, stream=st)
+        torch.cuda.synchronize()
+        for op, a, b, plan, pa, pb, pc in runs:
+            want = oracle.add(a, b) if op == bn.BN_OP_ADD else oracle.mul(a, b)
+            assert_limbs_equal(pc.numpy().view(np.uint32), want, f"async op {op} rep {rep}")
+    for run in runs:
+        run[3].close()
+    with bn.Plan(bn.BN_OP_ADD, 4, 4, 2) as plan:
+        with pytest.raises(TypeError):
+            plan.execute_host_async(np.zeros((2, 4), np.uint32), np.zeros((2, 4), np.uint32),
+                                    np.zeros((2, 5), np.uint32))
