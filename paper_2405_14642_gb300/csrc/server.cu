@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "bn_internal.h"
+#include "pool_alloc.h"
 
 namespace {
 
@@ -36,48 +37,7 @@ uint32_t clog2(uint32_t x) {
     return l;
 }
 
-// First-fit allocator over [0, size) with coalescing frees.
-class PoolAllocator {
-  public:
-    explicit PoolAllocator(uint64_t size) : size_(size) { free_[0] = size; }
-    bool alloc(uint64_t bytes, uint64_t *off) {
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second < bytes) continue;
-            *off = it->first;
-            const uint64_t rest = it->second - bytes;
-            const uint64_t start = it->first + bytes;
-            free_.erase(it);
-            if (rest) free_[start] = rest;
-            used_ += bytes;
-            high_ = std::max(high_, used_);
-            return true;
-        }
-        return false;
-    }
-    void release(uint64_t off, uint64_t bytes) {
-        auto next = free_.lower_bound(off);
-        uint64_t start = off, len = bytes;
-        if (next != free_.end() && next->first == off + bytes) {
-            len += next->second;
-            next = free_.erase(next);
-        }
-        if (next != free_.begin()) {
-            auto prev = std::prev(next);
-            if (prev->first + prev->second == off) {
-                start = prev->first;
-                len += prev->second;
-                free_.erase(prev);
-            }
-        }
-        free_[start] = len;
-        used_ -= bytes;
-    }
-    uint64_t high_water() const { return high_; }
-
-  private:
-    uint64_t size_, used_ = 0, high_ = 0;
-    std::map<uint64_t, uint64_t> free_;
-};
+using bn::PoolAllocator;
 
 struct Req {
     uint64_t ticket;
