@@ -329,6 +329,14 @@ def run_gpu(args, rank, world, local_rank):
     ms_per_step = max_ms / args.steps
     gpu_launches = args.steps * len(ops)
 
+    # End to end: host arrays in pinned memory through the host-buffer entry
+    # point, on every rank (whole-job figure, like the step).
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = run_e2e(args, torch, bn, ops, hosts, dev, world)
+    if rank != 0:
+        return None
+    # Per-GPU sections, on rank 0 only.
     isolated = run_isolated(args, torch, ops, plans, inputs, outs, stream, dev) if args.isolated_reps else None
     fused = None
     if args.fused_reps > 0:
@@ -339,14 +347,6 @@ def run_gpu(args, rank, world, local_rank):
     serving = None
     if args.serve_requests > 0:
         serving = run_serving(args, torch, bn, dev, rank)
-
-    # End to end: host arrays in pinned memory through the host-buffer entry point.
-    e2e = None
-    if args.e2e_steps > 0:
-        e2e = run_e2e(args, torch, bn, ops, hosts, dev)
-
-    if rank != 0:
-        return None
     hbm_peak, hbm_kind = read_measured_peaks()
     rows, rooflines = [], []
     for o in ops:
@@ -597,7 +597,7 @@ def run_serving(args, torch, bn, dev, rank):
     return out
 
 
-def run_e2e(args, torch, bn, ops, hosts, dev):
+def run_e2e(args, torch, bn, ops, hosts, dev, world=1):
     """Same metric through the host-buffer entry point with pinned host
     buffers: every op copies its operands in and its result out inside the
     timed region (bn_plan_execute_host_async), the ops spread round-robin over
@@ -626,18 +626,22 @@ def run_e2e(args, torch, bn, ops, hosts, dev):
     step()  # allocates staging buffers
     torch.cuda.synchronize()
     steps = max(1, min(args.steps, args.e2e_steps))
+    barrier(world)
     t = time.perf_counter()
     for _ in range(steps):
         step()
     torch.cuda.synchronize()
     el = time.perf_counter() - t
+    barrier(world)
+    el = allreduce_max(el, world, dev)
     for p in plans.values():
         p.close()
     mults = sum(o.mults for o in ops)
     h2d = sum(4 * (o.na + o.nb) * o.batch for o in ops)
     d2h = sum(4 * o.nout * o.batch for o in ops)
-    return {"value": mults * steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "steps": steps, "ms_per_step": round(el / steps * 1e3, 3),
+    return {"value": world * mults * steps / el, "unit": UNIT, "h2d_bytes_per_step": world * h2d,
+            "d2h_bytes_per_step": world * d2h, "steps": steps, "ms_per_step": round(el / steps * 1e3, 3),
+            "ranks": world,
             "api": "bn_plan_execute_host_async on 3 streams (pinned host buffers, copies "
                    "inside the timed region)"}
 

@@ -70,9 +70,11 @@ typedef enum bn_op {
     /* Section 4 with 32-bit digits over two primes (29*2^57 + 1 and
      * 27*2^56 + 1), recombined by the Chinese remainder theorem. */
     BN_OP_MUL_NTT_CRT = 3,
-    /* Batch items only: multiplication by whichever of the schoolbook and
-     * transform products (BN_OP_MUL_NTT3 included) a mixed-size batch's cost
-     * model finds fastest for the item's sizes. */
+    /* Multiplication by whichever of the schoolbook and transform products
+     * (BN_OP_MUL_NTT3 included) the cost model finds fastest for the sizes:
+     * per item in a mixed-size batch; for a plan (and bn_mul) once, at
+     * creation (bn_plan_op reports the choice; tuning applies only when the
+     * choice is the schoolbook product). */
     BN_OP_MUL_AUTO = 4,
     /* Section 4's transform product over three 32-bit good primes
      * (7*2^26 + 1, 45*2^24 + 1, 119*2^23 + 1; roots by the Section 4.1
@@ -140,6 +142,10 @@ bn_status bn_plan_destroy(bn_plan plan);
 /* Result limbs per instance: max(na,nb)+1 for add, na+nb for products. */
 uint32_t bn_plan_out_limbs(bn_plan plan);
 
+/* The plan's concrete op (a BN_OP_MUL_AUTO plan reports the product it
+ * chose); -1 for a null plan. */
+int bn_plan_op(bn_plan plan);
+
 /* Device scratch the plan holds (bytes; 0 for add and quad). */
 size_t bn_plan_scratch_bytes(bn_plan plan);
 
@@ -159,6 +165,11 @@ bn_status bn_mul_ntt(const uint32_t *a, const uint32_t *b, uint32_t *c,
  * result (na + nb limbs) and errors as bn_mul_ntt. */
 bn_status bn_mul_ntt3(const uint32_t *a, const uint32_t *b, uint32_t *c,
                       uint32_t na, uint32_t nb, uint64_t batch, void *stream);
+/* One-shot BN_OP_MUL_AUTO: c = a * b by the fastest product for the sizes
+ * (schoolbook for small operands, the three-prime transform from about 16K
+ * bits on GB300); arguments, layout, result and errors as bn_mul_quad. */
+bn_status bn_mul(const uint32_t *a, const uint32_t *b, uint32_t *c,
+                 uint32_t na, uint32_t nb, uint64_t batch, void *stream);
 
 /* Transform multiplication that allocates nothing, for callers that cannot
  * call cudaMalloc: code whose device memory is wholly owned by another

@@ -6,6 +6,7 @@ The compute path is the CUDA library built from ``csrc/`` (C ABI in
 ``include/bn.h``); this package is its thin ctypes binding.  Operations:
 
 * :func:`bn_add` - addition by a carry-propagation scan (Section 2);
+* :func:`bn_mul` - multiplication by the fastest method for the sizes;
 * :func:`bn_mul_quad` - classical multiplication with a load-balanced
   per-thread partition of the result (Section 3);
 * :func:`bn_mul_ntt` - multiplication through a number-theoretic transform
@@ -23,7 +24,7 @@ from ._binding import (COMPLETION_DTYPE, REQUEST_DTYPE, Server, device_to_host,
                        BATCH_ITEM_DTYPE, BN_BATCH_AUTOTUNE, BN_BATCH_PLAIN, BN_OP_MUL_AUTO, Batch,
                        BN_ADD_MAX_LIMBS, BN_MUL_MAX_LIMBS, BN_OP_ADD, BN_OP_MUL_NTT64,
                        BN_OP_MUL_NTT_CRT, BN_OP_MUL_NTT3, BN_OP_MUL_QUAD, BnError, Plan, bn_add,
-                       bn_mul_ntt, bn_mul_ntt3,
+                       bn_mul, bn_mul_ntt, bn_mul_ntt3,
                        bn_add6, bn_mul_low, bn_mul_ntt_noalloc, bn_mul_quad, bn_poly,
                        bn_probe_int_throughput, library_path, load)
 
@@ -32,4 +33,4 @@ __all__ = ["bn_add", "bn_mul_quad", "bn_mul_ntt", "Plan", "BnError", "load", "li
            "BN_ADD_MAX_LIMBS", "BN_MUL_MAX_LIMBS", "bn_probe_int_throughput",
            "bn_mul_ntt_noalloc", "Batch", "BATCH_ITEM_DTYPE", "BN_BATCH_AUTOTUNE", "BN_BATCH_PLAIN",
            "BN_OP_MUL_AUTO", "Server", "REQUEST_DTYPE", "COMPLETION_DTYPE", "device_to_host",
-           "bn_mul_low", "bn_poly", "bn_add6", "bn_mul_ntt3", "BN_OP_MUL_NTT3"]
+           "bn_mul_low", "bn_poly", "bn_add6", "bn_mul_ntt3", "BN_OP_MUL_NTT3", "bn_mul"]

@@ -101,6 +101,8 @@ def load(build_if_missing: bool = False):
         "bn_mul_quad": ([u32p, u32p, u32p, u32, u32, u64, vp], st),
         "bn_mul_ntt": ([u32p, u32p, u32p, u32, u32, u64, ctypes.c_int, vp], st),
         "bn_mul_ntt3": ([u32p, u32p, u32p, u32, u32, u64, vp], st),
+        "bn_mul": ([u32p, u32p, u32p, u32, u32, u64, vp], st),
+        "bn_plan_op": ([vp], ctypes.c_int),
         "bn_status_str": ([ctypes.c_int], ctypes.c_char_p),
         "bn_last_error": ([], ctypes.c_char_p),
         "bn_version": ([], ctypes.c_int),
@@ -212,6 +214,18 @@ def bn_mul_ntt(a, b, crt: bool = False, out=None, stream=None):
     return out
 
 
+def bn_mul(a, b, out=None, stream=None):
+    """c = a * b per row by the product the cost model finds fastest for the
+    sizes (schoolbook or a transform); na + nb limbs."""
+    lib = load()
+    a, b = _pair(a, b)
+    batch, na, nb = a.shape[0], a.shape[1], b.shape[1]
+    out = _out(out, batch, na + nb, a)
+    _check(lib.bn_mul(_ptr(a), _ptr(b), _ptr(out), na, nb, batch, _stream_handle(stream, a.device)),
+           "bn_mul")
+    return out
+
+
 def bn_mul_ntt3(a, b, out=None, stream=None):
     """c = a * b per row through transforms over three 32-bit primes with
     32-bit digits and Garner recombination (Section 4's method); na + nb limbs."""
@@ -292,7 +306,8 @@ class Plan:
         tun = bn_tuning(limbs_per_thread, cta_threads, variant, 0)
         _check(lib.bn_plan_create(ctypes.byref(self._h), op, na, nb, batch, ctypes.byref(tun)),
                "bn_plan_create")
-        self.op, self.na, self.nb, self.batch = op, na, nb, batch
+        self.na, self.nb, self.batch = na, nb, batch
+        self.op = lib.bn_plan_op(self._h)  # the concrete op (an AUTO plan's choice)
         self.out_limbs = lib.bn_plan_out_limbs(self._h)
 
     @property

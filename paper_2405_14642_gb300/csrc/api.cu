@@ -191,13 +191,26 @@ bn_status bn_plan_create(bn_plan *out, bn_op op, uint32_t na, uint32_t nb, uint6
     }
     *out = nullptr;
     if (op != BN_OP_ADD && op != BN_OP_MUL_QUAD && op != BN_OP_MUL_NTT64 && op != BN_OP_MUL_NTT_CRT &&
-        op != BN_OP_MUL_NTT3) {
+        op != BN_OP_MUL_NTT3 && op != BN_OP_MUL_AUTO) {
         set_error_text("unknown op");
         return BN_EINVAL;
     }
     if (na == 0 || nb == 0) {
         set_error_text("zero limb count");
         return BN_EINVAL;
+    }
+    if (op == BN_OP_MUL_AUTO) {
+        // The cost model's fastest product for the sizes (same choice as a
+        // batch item without autotuning).
+        if (na > BN_MUL_MAX_LIMBS || nb > BN_MUL_MAX_LIMBS) {
+            set_error_text("size not supported by this op");
+            return BN_EUNSUPPORTED;
+        }
+        static const bn_op kinds[5] = {BN_OP_MUL_QUAD, BN_OP_MUL_QUAD, BN_OP_MUL_NTT64, BN_OP_MUL_NTT_CRT,
+                                       BN_OP_MUL_NTT3};
+        const uint32_t k = bn::choose_mul(na, nb).kind;
+        op = kinds[k < 5 ? k : 1];
+        if (tuning && op != BN_OP_MUL_QUAD) tuning = nullptr;  // schoolbook tuning only
     }
     bn_plan_s *p = new (std::nothrow) bn_plan_s();
     if (!p) return BN_ENOMEM;
@@ -305,6 +318,8 @@ bn_status bn_plan_destroy(bn_plan plan) {
 
 uint32_t bn_plan_out_limbs(bn_plan plan) { return plan ? plan->nout : 0; }
 
+int bn_plan_op(bn_plan plan) { return plan ? (int)plan->op : -1; }
+
 size_t bn_plan_scratch_bytes(bn_plan plan) {
     if (plan && plan->ntt3) return bn::ntt3_scratch_bytes(plan->ntt3);
     return (plan && plan->ntt) ? bn::ntt_scratch_bytes(plan->ntt) : 0;
@@ -333,6 +348,11 @@ bn_status bn_mul_ntt(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_t
 bn_status bn_mul_ntt3(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_t na, uint32_t nb,
                       uint64_t batch, void *stream) {
     return one_shot(BN_OP_MUL_NTT3, a, b, c, na, nb, batch, stream);
+}
+
+bn_status bn_mul(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_t na, uint32_t nb,
+                 uint64_t batch, void *stream) {
+    return one_shot(BN_OP_MUL_AUTO, a, b, c, na, nb, batch, stream);
 }
 
 const char *bn_status_str(bn_status s) {

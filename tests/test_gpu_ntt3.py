@@ -119,3 +119,22 @@ def test_host_async_plans_on_streams():
         with pytest.raises(TypeError):
             plan.execute_host_async(np.zeros((2, 4), np.uint32), np.zeros((2, 4), np.uint32),
                                     np.zeros((2, 5), np.uint32))
+
+
+@pytest.mark.parametrize("na,nb,kind", [(64, 64, "quad"), (256, 200, "quad"), (8192, 1, "quad"),
+                                        (1024, 1024, "ntt3"), (4096, 3000, "ntt3"), (8192, 8192, "ntt3")])
+def test_auto_plans_and_bn_mul(na, nb, kind):
+    """BN_OP_MUL_AUTO plans resolve to the cost model's product (schoolbook for
+    small operands, three primes from 16K bits) and bn_mul equals the oracle."""
+    torch_cuda()
+    import paper_2405_14642_gb300 as bn
+    batch = 9 if max(na, nb) > 2048 else 31
+    a, b = workloads.pair_batch(batch, na, nb, seed=workloads.seed_for(8, 700 + na + nb))
+    with bn.Plan(bn.BN_OP_MUL_AUTO, na, nb, batch) as plan:
+        want_op = bn.BN_OP_MUL_QUAD if kind == "quad" else bn.BN_OP_MUL_NTT3
+        assert plan.op == want_op and plan.out_limbs == na + nb
+        got_plan = to_host(plan.execute(to_dev(a), to_dev(b)))
+    got = to_host(bn.bn_mul(to_dev(a), to_dev(b)))
+    want = oracle.mul(a, b)
+    assert_limbs_equal(got, want, f"bn_mul {na}x{nb}")
+    assert_limbs_equal(got_plan, want, f"auto plan {na}x{nb}")
