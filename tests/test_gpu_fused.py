@@ -102,3 +102,16 @@ def test_fused_errors():
             getattr(bn, "bn_" + name)(x, x[:, :8].contiguous())
         empty = torch.zeros((0, 16), dtype=torch.int32, device="cuda")
         assert getattr(bn, "bn_" + name)(empty, empty).shape == (0, 16)
+
+
+@pytest.mark.parametrize("name", OPS)
+@pytest.mark.parametrize("bits", [65536, 262144])
+def test_fused_full_size_sampled(name, bits):
+    """The size-sweep batch (64 MiB of operands per side), launched as the
+    benchmark launches it, checked against the oracle on sampled rows."""
+    torch_cuda()
+    p = [q for q in workloads.sweep_points() if q.bits == bits][0]
+    a, b = workloads.pair_batch(p.batch, p.limbs, seed=p.seed, edges=True)
+    got = _run(name, to_dev(a), to_dev(b))
+    rows = np.union1d(np.random.default_rng(bits).choice(p.batch, 4, replace=False), [19, 39, 59])
+    assert_limbs_equal(got[rows], getattr(programs, name)(a[rows], b[rows]), f"{name} {bits} sampled")
