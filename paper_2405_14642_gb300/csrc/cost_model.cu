@@ -24,8 +24,8 @@ double default_ntt_us(bool crt, uint32_t logN) {
 double default_ntt3_us(uint32_t logN) {
     // Three 32-bit primes, microseconds per item by log2(N) (N = next power
     // of two >= na + nb), from 2^6 (1K-bit operands) to 2^14 (256K bits).
-    static const double t3[15] = {0, 0, 0, 0, 0, 0, 0.00498, 0.00666, 0.01003, 0.01997, 0.04344,
-                                  0.09025, 0.1901, 0.4347, 0.9115};
+    static const double t3[15] = {0, 0, 0, 0, 0, 0, 0.00451, 0.00616, 0.00938, 0.01856, 0.04031,
+                                  0.08362, 0.1766, 0.4060, 0.7945};
     const double v = logN < 15 ? t3[logN] : 0;
     return v > 0 ? v : 1e30;
 }

@@ -56,15 +56,18 @@ struct MontField32 {
     static constexpr uint32_t R_MOD_P = (uint32_t)((1ull << 32) % P);
     static_assert(P < (1u << 30), "4P < 2^32");
     static_assert((uint32_t)(P * NINV) == 0xffffffffu, "NINV = -P^-1 mod 2^32");
+    // Reductions as unsigned minima: for r < 4P, r - 2P wraps above r exactly
+    // when r < 2P, so min(r, r - 2P) is r mod-reduced into [0, 2P) (one
+    // min and one subtract instead of a compare, a select and a subtract).
     __device__ static __forceinline__ uint32_t add(uint32_t a, uint32_t b) {
         const uint32_t r = a + b;
-        return r >= TWO_P ? r - TWO_P : r;
+        return min(r, r - TWO_P);
     }
     __device__ static __forceinline__ uint32_t sub(uint32_t a, uint32_t b) {
         const uint32_t r = a + TWO_P - b;
-        return r >= TWO_P ? r - TWO_P : r;
+        return min(r, r - TWO_P);
     }
-    __device__ static __forceinline__ uint32_t canon(uint32_t a) { return a >= P ? a - P : a; }
+    __device__ static __forceinline__ uint32_t canon(uint32_t a) { return min(a, a - P); }
     __device__ static __forceinline__ uint32_t mul(uint32_t a, uint32_t b) {
         const uint32_t lo = a * b, hi = __umulhi(a, b);
         const uint32_t m = lo * NINV;
