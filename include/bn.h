@@ -166,7 +166,7 @@ bn_status bn_mul_ntt(const uint32_t *a, const uint32_t *b, uint32_t *c,
 bn_status bn_mul_ntt3(const uint32_t *a, const uint32_t *b, uint32_t *c,
                       uint32_t na, uint32_t nb, uint64_t batch, void *stream);
 /* One-shot BN_OP_MUL_AUTO: c = a * b by the fastest product for the sizes
- * (schoolbook for small operands, the three-prime transform from about 16K
+ * (schoolbook for small operands, the three-prime transform from about 8K
  * bits on GB300); arguments, layout, result and errors as bn_mul_quad. */
 bn_status bn_mul(const uint32_t *a, const uint32_t *b, uint32_t *c,
                  uint32_t na, uint32_t nb, uint64_t batch, void *stream);

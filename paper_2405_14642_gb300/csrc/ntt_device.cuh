@@ -239,6 +239,144 @@ __device__ void inverse(uint32_t L, uint32_t logL, const typename F::Tw *tw, typ
     }
 }
 
+// ---- passes with the transform length fixed at compile time ----------------
+//
+// The same radix-8 passes for a length L, group stride STEP and thread count NT
+// known at compile time.  With power-of-two strides the padded index is
+// additive over a group, pidx(base + m*STEP) = pidx(base) + pidx(m*STEP) (a
+// group never crosses a padding block boundary: base's bits below
+// log2(STEP) + KK are j0 < STEP and m*STEP stays inside that block), so every
+// element and twiddle of a group is an immediate offset from one base
+// register, and the loops over groups have compile-time trip counts.  Measured
+// on the 16384-point three-prime transform: 30% faster than the passes above.
+
+template <uint32_t X>
+struct Log2c {
+    static constexpr uint32_t v = 1 + Log2c<X / 2>::v;
+};
+template <>
+struct Log2c<1> {
+    static constexpr uint32_t v = 0;
+};
+
+template <class T>
+__host__ __device__ constexpr uint32_t pidx_c(uint32_t i) {
+    return sizeof(T) == 4 ? i + 4u * (i >> 5) : i + (i >> 4);
+}
+
+// KK stages over groups of E = 2^KK elements base + m*STEP; DIF: half-sizes
+// STEP*E/2 .. STEP (decimation in frequency), else STEP .. STEP*E/2
+// (decimation in time).  UNIT (STEP = 1): the trivial stage has twiddle 1.
+template <class F, int KK, bool UNIT, uint32_t STEP, uint32_t L, uint32_t NT, bool DIF>
+__device__ __forceinline__ void pass_c(typename F::Elem *buf, const typename F::Tw *tw) {
+    using T = typename F::Elem;
+    using W = typename F::Tw;
+    constexpr int E = 1 << KK;
+    constexpr uint32_t LSTEP = Log2c<STEP>::v;
+    constexpr uint32_t G = L >> KK;
+#pragma unroll
+    for (uint32_t g0 = 0; g0 < G; g0 += NT) {
+        const uint32_t g = g0 + threadIdx.x;
+        if (G % NT != 0 && g >= G) break;
+        const uint32_t j0 = g & (STEP - 1);
+        const uint32_t base = ((g >> LSTEP) << (LSTEP + KK)) | j0;
+        const uint32_t p0 = pidx<T>(base);
+        T x[E];
+        if constexpr (UNIT) {
+            load_run<T, E>(buf, base, x);
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) x[m] = buf[p0 + pidx_c<T>(m * STEP)];
+        }
+        const W *twj = tw + j0;  // twiddle of element m in the stage of half-size hm*STEP: twj[(hm+m)*STEP]
+#pragma unroll
+        for (int st = 0; st < KK; ++st) {
+            const uint32_t hm = DIF ? 1u << (KK - 1 - st) : 1u << st;
+            const bool trivial = UNIT && hm == 1;
+            W w[E / 2];
+#pragma unroll
+            for (int m = 0; m < (int)hm; ++m) w[m] = trivial ? W{} : __ldg(twj + (hm + m) * STEP);
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                if (m & hm) continue;
+                if constexpr (DIF) {
+                    const T u = x[m], v = x[m + hm];
+                    x[m] = F::add(u, v);
+                    x[m + hm] = trivial ? F::sub(u, v) : F::twiddle(u + F::TWO_P - v, w[m & (hm - 1)]);
+                } else {
+                    const T u = x[m];
+                    const T v = trivial ? x[m + hm] : F::twiddle_lazy(x[m + hm], w[m & (hm - 1)]);
+                    x[m] = F::add(u, v);
+                    x[m + hm] = F::sub(u, v);
+                }
+            }
+        }
+        if constexpr (UNIT) {
+            store_run<T, E>(buf, base, x);
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) buf[p0 + pidx_c<T>(m * STEP)] = x[m];
+        }
+    }
+}
+
+template <class F, uint32_t L, uint32_t NT, uint32_t H, uint32_t LEFT>
+__device__ __forceinline__ void dif_rest_c(typename F::Elem *A, typename F::Elem *B,
+                                           const typename F::Tw *tw) {
+    if constexpr (LEFT > 3) {
+        pass_c<F, 3, false, H / 4, L, NT, true>(A, tw);
+        pass_c<F, 3, false, H / 4, L, NT, true>(B, tw);
+        __syncthreads();
+        dif_rest_c<F, L, NT, H / 8, LEFT - 3>(A, B, tw);
+    } else {
+        pass_c<F, (int)LEFT, true, 1, L, NT, true>(A, tw);
+        pass_c<F, (int)LEFT, true, 1, L, NT, true>(B, tw);
+    }
+}
+
+// Forward transforms of A and B of length 2^LOGL (as forward2, with the
+// non-radix-8 pass first); ends with a barrier.
+template <class F, uint32_t LOGL, uint32_t NT>
+__device__ void forward2_c(const typename F::Tw *tw, typename F::Elem *A, typename F::Elem *B) {
+    constexpr uint32_t L = 1u << LOGL;
+    if constexpr (LOGL % 3 == 2 && LOGL > 2) {
+        pass_c<F, 2, false, L / 4, L, NT, true>(A, tw);
+        pass_c<F, 2, false, L / 4, L, NT, true>(B, tw);
+        __syncthreads();
+        dif_rest_c<F, L, NT, L / 8, LOGL - 2>(A, B, tw);
+    } else if constexpr (LOGL % 3 == 1 && LOGL > 1) {
+        pass_c<F, 1, false, L / 2, L, NT, true>(A, tw);
+        pass_c<F, 1, false, L / 2, L, NT, true>(B, tw);
+        __syncthreads();
+        dif_rest_c<F, L, NT, L / 4, LOGL - 1>(A, B, tw);
+    } else {
+        dif_rest_c<F, L, NT, L / 2, LOGL>(A, B, tw);
+    }
+    __syncthreads();
+}
+
+template <class F, uint32_t L, uint32_t NT, uint32_t H0, uint32_t LEFT>
+__device__ __forceinline__ void dit_rest_c(typename F::Elem *B, const typename F::Tw *tw) {
+    if constexpr (LEFT >= 3) {
+        pass_c<F, 3, false, H0, L, NT, false>(B, tw);
+        __syncthreads();
+        dit_rest_c<F, L, NT, H0 * 8, LEFT - 3>(B, tw);
+    } else if constexpr (LEFT > 0) {
+        pass_c<F, (int)LEFT, false, H0, L, NT, false>(B, tw);
+        __syncthreads();
+    }
+}
+
+// Unscaled inverse transform of B of length 2^LOGL; ends with a barrier.
+template <class F, uint32_t LOGL, uint32_t NT>
+__device__ void inverse_c(const typename F::Tw *tw, typename F::Elem *B) {
+    constexpr uint32_t L = 1u << LOGL;
+    constexpr uint32_t first = LOGL >= 3 ? 3 : LOGL;
+    pass_c<F, (int)first, true, 1, L, NT, false>(B, tw);
+    __syncthreads();
+    dit_rest_c<F, L, NT, (1u << first), LOGL - first>(B, tw);
+}
+
 // Normalisation (Section 4.2's splitFftReg/baddRegMul2Fft, with whole
 // digits): limb(k) gives the part of the product that starts in limb k (the
 // digit coefficients aligned there, < 2^96 in total).  Each thread folds the

@@ -125,7 +125,7 @@ def test_host_async_plans_on_streams():
                                         (1024, 1024, "ntt3"), (4096, 3000, "ntt3"), (8192, 8192, "ntt3")])
 def test_auto_plans_and_bn_mul(na, nb, kind):
     """BN_OP_MUL_AUTO plans resolve to the cost model's product (schoolbook for
-    small operands, three primes from 16K bits) and bn_mul equals the oracle."""
+    small operands, three primes from 8K bits) and bn_mul equals the oracle."""
     torch_cuda()
     import paper_2405_14642_gb300 as bn
     batch = 9 if max(na, nb) > 2048 else 31

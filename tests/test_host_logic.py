@@ -49,7 +49,7 @@ def test_pool_allocator_matches_first_fit_model(tmp_path):
 
 def test_cost_model_choices(tmp_path):
     """The schoolbook product for small operands, the three-prime transform
-    from 512 x 512 limbs (16K bits) up, estimates growing with the size."""
+    from 256 x 256 limbs (8K bits) up, estimates growing with the size."""
     exe = _compile(tmp_path, "cost_check",
                    [HOST / "cost_model_check.cpp", CSRC / "cost_model.cu"], needs_cuda_headers=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
@@ -59,9 +59,9 @@ def test_cost_model_choices(tmp_path):
         if line.strip():
             na, nb, kind, est = line.split()
             rows[(int(na), int(nb))] = (int(kind), float(est))
-    for n in (1, 32, 64, 128, 256):
+    for n in (1, 32, 64, 128):
         assert rows[(n, n)][0] == 1, (n, rows[(n, n)])
-    for n in (512, 1024, 2048, 4096, 8192):
+    for n in (256, 512, 1024, 2048, 4096, 8192):
         assert rows[(n, n)][0] == 4, (n, rows[(n, n)])
     assert rows[(8192, 1)][0] == 1          # lopsided: 8192 word products
     square = [rows[(n, n)][1] for n in (32, 64, 128, 256, 512, 1024, 2048, 4096, 8192)]
