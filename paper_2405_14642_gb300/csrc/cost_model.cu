@@ -24,8 +24,8 @@ double default_ntt_us(bool crt, uint32_t logN) {
 double default_ntt3_us(uint32_t logN) {
     // Three 32-bit primes, microseconds per item by log2(N) (N = next power
     // of two >= na + nb), from 2^6 (1K-bit operands) to 2^14 (256K bits).
-    static const double t3[15] = {0, 0, 0, 0, 0, 0, 0.00297, 0.00412, 0.00627, 0.01288, 0.02762,
-                                  0.05712, 0.1252, 0.2670, 0.5530};
+    static const double t3[15] = {0, 0, 0, 0, 0, 0, 0.00286, 0.00390, 0.00583, 0.01191, 0.02588,
+                                  0.05375, 0.1188, 0.2545, 0.5270};
     const double v = logN < 15 ? t3[logN] : 0;
     return v > 0 ? v : 1e30;
 }

@@ -88,7 +88,7 @@ HostField32 make_field(uint32_t k, uint32_t n) {
 // Shoup pair (w, floor(w 2^32 / p)) of a canonical w.
 uint2 shoup(uint32_t w, uint32_t p) { return make_uint2(w, (uint32_t)(((uint64_t)w << 32) / p)); }
 
-void make_tables3(const HostField32 &f, uint32_t N, uint2 *twf, uint2 *twi, uint32_t &scale) {
+void make_tables3(const HostField32 &f, uint32_t N, uint2 *twf, uint2 *twi, uint2 &scale) {
     const uint32_t w = powmod(f.g, (1ull << f.n) / N, f.p), wi = invmod(w, f.p);
     twf[0] = twi[0] = make_uint2(0, 0);
     for (uint32_t h = 1; h < N; h <<= 1) {
@@ -102,7 +102,7 @@ void make_tables3(const HostField32 &f, uint32_t N, uint2 *twf, uint2 *twi, uint
         }
     }
     const uint32_t r = (uint32_t)((1ull << 32) % f.p);
-    scale = mulmod(invmod(N % f.p, f.p), mulmod(r, r, f.p), f.p);
+    scale = shoup(mulmod(invmod(N % f.p, f.p), r, f.p), f.p);
 }
 
 uint32_t next_pow2_u32(uint32_t x) {

@@ -24,7 +24,7 @@ struct MontField32 {
     using Elem = uint32_t;
     static constexpr uint32_t P_VALUE = P;
     static constexpr uint32_t TWO_P = 2 * P;
-    static constexpr uint32_t R_MOD_P = (uint32_t)((1ull << 32) % P);
+    static constexpr uint32_t RECIP = (uint32_t)((1ull << 32) / P);  // floor(2^32 / P)
     static_assert(P < (1u << 30), "4P < 2^32");
     static_assert((uint32_t)(P * NINV) == 0xffffffffu, "NINV = -P^-1 mod 2^32");
     // Reductions as unsigned minima: for r < 4P, r - 2P wraps above r exactly
@@ -44,8 +44,9 @@ struct MontField32 {
         const uint32_t m = lo * NINV;
         return hi + __umulhi(m, P) + (lo != 0u);
     }
-    // Any 32-bit digit d into the field: d (R mod P) / R = d (mod P), < 2P.
-    __device__ static __forceinline__ uint32_t from_digit(uint32_t d) { return mul(d, R_MOD_P); }
+    // Any 32-bit digit d into [0, 2P): Shoup's product with the pair (1, RECIP),
+    // d - hi(d RECIP) P (two multiplies).
+    __device__ static __forceinline__ uint32_t from_digit(uint32_t d) { return d - __umulhi(d, RECIP) * P; }
     // Twiddles by Shoup's method: an entry is (w, w' = floor(w 2^32 / P)) with
     // w < P, and for any a < 2^32, q = hi(a w') gives a w - q P in [0, 2P),
     // exact in 32-bit arithmetic.  One high and two low multiplies, against
@@ -66,7 +67,7 @@ static_assert(F0::P_VALUE < F1::P_VALUE && F1::P_VALUE < F2::P_VALUE, "Garner or
 struct Tab3 {
     const uint2 *twf;     // [N]: twf[h + j] = Shoup pair of w_{2h}^j
     const uint2 *twi;     // [N]: Shoup pair of w_{2h}^-j
-    uint32_t scale;       // N^-1 R^2 mod p: mul(x, scale) undoes the 1/R of the pointwise product
+    uint2 scale;          // Shoup pair of N^-1 R mod p: also undoes the 1/R of the pointwise product
 };
 
 struct Ntt3Args {
@@ -104,7 +105,7 @@ __device__ void prime_product3(const Ntt3Args &p, const Tab3 &tb, const uint32_t
     __syncthreads();
     inverse_c<F, LOGN, NT>(tb.twi, B);                                  // n4: inverse (unscaled)
     for (uint32_t j = threadIdx.x; j < p.nout; j += NT) {
-        const uint32_t v = F::canon(F::mul(B[phys4(j)], tb.scale));
+        const uint32_t v = F::canon(F::twiddle(B[phys4(j)], tb.scale));
         if (dest) dest[j] = v;
         else B[phys4(j)] = v;
     }
