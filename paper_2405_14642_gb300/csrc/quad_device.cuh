@@ -51,52 +51,61 @@ __host__ __device__ inline Geometry geometry(uint32_t na, uint32_t nb, uint32_t 
 }
 
 
-// acc += a * (w[0] + w[1] 2^32 + ... + w[Q-1] 2^{32(Q-1)}), acc has Q+2 words.
+// acc + cnt 2^{32Q} += a * (w[0] + w[1] 2^32 + ... + w[Q-1] 2^{32(Q-1)}): acc has Q+2
+// words; the carry out of the low-half chain, which belongs at word Q, is
+// counted in cnt instead of being carried through words Q and Q+1 (one
+// instruction instead of two per chain); fold_count adds it in once per
+// window.
 template <int Q>
-__device__ __forceinline__ void mac(uint32_t (&acc)[Q + 2], uint32_t a, const uint32_t (&w)[Q]);
+__device__ __forceinline__ void mac(uint32_t (&acc)[Q + 2], uint32_t &cnt, uint32_t a, const uint32_t (&w)[Q]);
 
 template <>
-__device__ __forceinline__ void mac<4>(uint32_t (&acc)[6], uint32_t a, const uint32_t (&w)[4]) {
-    asm("mad.lo.cc.u32  %0, %6, %7,  %0;\n\t"
-        "madc.lo.cc.u32 %1, %6, %8,  %1;\n\t"
-        "madc.lo.cc.u32 %2, %6, %9,  %2;\n\t"
-        "madc.lo.cc.u32 %3, %6, %10, %3;\n\t"
-        "addc.cc.u32    %4, %4, 0;\n\t"
-        "addc.u32       %5, %5, 0;\n\t"
-        "mad.hi.cc.u32  %1, %6, %7,  %1;\n\t"
-        "madc.hi.cc.u32 %2, %6, %8,  %2;\n\t"
-        "madc.hi.cc.u32 %3, %6, %9,  %3;\n\t"
-        "madc.hi.cc.u32 %4, %6, %10, %4;\n\t"
+__device__ __forceinline__ void mac<4>(uint32_t (&acc)[6], uint32_t &cnt, uint32_t a, const uint32_t (&w)[4]) {
+    asm("mad.lo.cc.u32  %0, %7, %8,  %0;\n\t"
+        "madc.lo.cc.u32 %1, %7, %9,  %1;\n\t"
+        "madc.lo.cc.u32 %2, %7, %10, %2;\n\t"
+        "madc.lo.cc.u32 %3, %7, %11, %3;\n\t"
+        "addc.u32       %6, %6, 0;\n\t"
+        "mad.hi.cc.u32  %1, %7, %8,  %1;\n\t"
+        "madc.hi.cc.u32 %2, %7, %9,  %2;\n\t"
+        "madc.hi.cc.u32 %3, %7, %10, %3;\n\t"
+        "madc.hi.cc.u32 %4, %7, %11, %4;\n\t"
         "addc.u32       %5, %5, 0;"
-        : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3]), "+r"(acc[4]), "+r"(acc[5])
+        : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3]), "+r"(acc[4]), "+r"(acc[5]), "+r"(cnt)
         : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]));
 }
 
 template <>
-__device__ __forceinline__ void mac<8>(uint32_t (&acc)[10], uint32_t a, const uint32_t (&w)[8]) {
-    asm("mad.lo.cc.u32  %0, %10, %11, %0;\n\t"
-        "madc.lo.cc.u32 %1, %10, %12, %1;\n\t"
-        "madc.lo.cc.u32 %2, %10, %13, %2;\n\t"
-        "madc.lo.cc.u32 %3, %10, %14, %3;\n\t"
-        "madc.lo.cc.u32 %4, %10, %15, %4;\n\t"
-        "madc.lo.cc.u32 %5, %10, %16, %5;\n\t"
-        "madc.lo.cc.u32 %6, %10, %17, %6;\n\t"
-        "madc.lo.cc.u32 %7, %10, %18, %7;\n\t"
-        "addc.cc.u32    %8, %8, 0;\n\t"
-        "addc.u32       %9, %9, 0;\n\t"
-        "mad.hi.cc.u32  %1, %10, %11, %1;\n\t"
-        "madc.hi.cc.u32 %2, %10, %12, %2;\n\t"
-        "madc.hi.cc.u32 %3, %10, %13, %3;\n\t"
-        "madc.hi.cc.u32 %4, %10, %14, %4;\n\t"
-        "madc.hi.cc.u32 %5, %10, %15, %5;\n\t"
-        "madc.hi.cc.u32 %6, %10, %16, %6;\n\t"
-        "madc.hi.cc.u32 %7, %10, %17, %7;\n\t"
-        "madc.hi.cc.u32 %8, %10, %18, %8;\n\t"
+__device__ __forceinline__ void mac<8>(uint32_t (&acc)[10], uint32_t &cnt, uint32_t a, const uint32_t (&w)[8]) {
+    asm("mad.lo.cc.u32  %0, %11, %12, %0;\n\t"
+        "madc.lo.cc.u32 %1, %11, %13, %1;\n\t"
+        "madc.lo.cc.u32 %2, %11, %14, %2;\n\t"
+        "madc.lo.cc.u32 %3, %11, %15, %3;\n\t"
+        "madc.lo.cc.u32 %4, %11, %16, %4;\n\t"
+        "madc.lo.cc.u32 %5, %11, %17, %5;\n\t"
+        "madc.lo.cc.u32 %6, %11, %18, %6;\n\t"
+        "madc.lo.cc.u32 %7, %11, %19, %7;\n\t"
+        "addc.u32       %10, %10, 0;\n\t"
+        "mad.hi.cc.u32  %1, %11, %12, %1;\n\t"
+        "madc.hi.cc.u32 %2, %11, %13, %2;\n\t"
+        "madc.hi.cc.u32 %3, %11, %14, %3;\n\t"
+        "madc.hi.cc.u32 %4, %11, %15, %4;\n\t"
+        "madc.hi.cc.u32 %5, %11, %16, %5;\n\t"
+        "madc.hi.cc.u32 %6, %11, %17, %6;\n\t"
+        "madc.hi.cc.u32 %7, %11, %18, %7;\n\t"
+        "madc.hi.cc.u32 %8, %11, %19, %8;\n\t"
         "addc.u32       %9, %9, 0;"
         : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3]), "+r"(acc[4]), "+r"(acc[5]),
-          "+r"(acc[6]), "+r"(acc[7]), "+r"(acc[8]), "+r"(acc[9])
+          "+r"(acc[6]), "+r"(acc[7]), "+r"(acc[8]), "+r"(acc[9]), "+r"(cnt)
         : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]),
           "r"(w[7]));
+}
+
+// acc += cnt 2^{32Q} (the low-chain carries counted by mac), then cnt = 0.
+template <int Q>
+__device__ __forceinline__ void fold_count(uint32_t (&acc)[Q + 2], uint32_t &cnt) {
+    asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+r"(acc[Q]), "+r"(acc[Q + 1]) : "r"(cnt));
+    cnt = 0;
 }
 
 // Column form (Section 3.2's accumulate step): column q keeps a 64-bit sum
@@ -151,7 +160,7 @@ __device__ __forceinline__ void st_words(uint32_t *S, uint32_t x, const uint32_t
 // B[k-i0-s .. k-i0-s+Q), taken from the chunk pair (lo, hi) = B[k-i0-Q .. k-i0+Q).
 template <int Q, bool COLS>
 __device__ __forceinline__ void window_block(const uint32_t *As, uint32_t i0, const uint32_t (&lo)[Q],
-                                             const uint32_t (&hi)[Q], uint32_t (&acc)[Q + 2],
+                                             const uint32_t (&hi)[Q], uint32_t (&acc)[Q + 2], uint32_t &cnt,
                                              uint64_t (&cacc)[Q], uint32_t (&ccar)[Q]) {
     uint32_t av[4];
 #pragma unroll
@@ -164,7 +173,7 @@ __device__ __forceinline__ void window_block(const uint32_t *As, uint32_t i0, co
             w[q] = idx < Q ? lo[idx] : hi[idx - Q];
         }
         if constexpr (COLS) mac_cols<Q>(cacc, ccar, av[s % 4], w);
-        else mac<Q>(acc, av[s % 4], w);
+        else mac<Q>(acc, cnt, av[s % 4], w);
     }
 }
 
@@ -177,6 +186,7 @@ __device__ __forceinline__ void conv_window(const uint32_t *As, const uint32_t *
                                             uint32_t ilo, uint32_t steps, uint32_t (&acc)[Q + 2]) {
     uint64_t cacc[Q];
     uint32_t ccar[Q];
+    uint32_t cnt = 0;
 #pragma unroll
     for (int q = 0; q < Q + 2; ++q) acc[q] = 0;
 #pragma unroll
@@ -191,17 +201,18 @@ __device__ __forceinline__ void conv_window(const uint32_t *As, const uint32_t *
     ld_words<Q>(Bs, xb, c1);
     for (uint32_t b = 0; b + 1 < nblk; b += 2) {
         ld_words<Q>(Bs, xb - Q, c0);
-        window_block<Q, COLS>(As, i0, c0, c1, acc, cacc, ccar);
+        window_block<Q, COLS>(As, i0, c0, c1, acc, cnt, cacc, ccar);
         ld_words<Q>(Bs, xb - 2 * Q, c1);
-        window_block<Q, COLS>(As, i0 + Q, c1, c0, acc, cacc, ccar);
+        window_block<Q, COLS>(As, i0 + Q, c1, c0, acc, cnt, cacc, ccar);
         xb -= 2 * Q;
         i0 += 2 * Q;
     }
     if (nblk & 1) {
         ld_words<Q>(Bs, xb - Q, c0);
-        window_block<Q, COLS>(As, i0, c0, c1, acc, cacc, ccar);
+        window_block<Q, COLS>(As, i0, c0, c1, acc, cnt, cacc, ccar);
     }
     if constexpr (COLS) cols_to_words<Q>(cacc, ccar, acc);
+    else fold_count<Q>(acc, cnt);
 }
 
 // A unit of work: up to two windows run back to back as ONE loop of n0 + n1
@@ -218,6 +229,7 @@ template <int Q, class Publish>
 __device__ __forceinline__ void conv_unit(const uint32_t *As, const uint32_t *Bs, const Unit &u,
                                           Publish &&publish) {
     uint32_t acc[Q + 2];
+    uint32_t cnt = 0;
     uint64_t cacc[Q];  // unused by the chain form
     uint32_t ccar[Q];
 #pragma unroll
@@ -229,6 +241,7 @@ __device__ __forceinline__ void conv_unit(const uint32_t *As, const uint32_t *Bs
     // After a window's last block: publish it and start the next one, whose
     // upper chunk goes to the buffer the next block reads as "upper".
     auto finish = [&](uint32_t (&next_hi)[Q]) {
+        fold_count<Q>(acc, cnt);
         publish(k, acc);
 #pragma unroll
         for (int q = 0; q < Q + 2; ++q) acc[q] = 0;
@@ -242,12 +255,12 @@ __device__ __forceinline__ void conv_unit(const uint32_t *As, const uint32_t *Bs
     };
     for (uint32_t b = 0; b < total; b += 2) {
         ld_words<Q>(Bs, k - i0, c0);
-        window_block<Q, false>(As, i0, c0, c1, acc, cacc, ccar);
+        window_block<Q, false>(As, i0, c0, c1, acc, cnt, cacc, ccar);
         i0 += Q;
         if (--left == 0) finish(c0);
         if (b + 1 == total) break;
         ld_words<Q>(Bs, k - i0, c1);
-        window_block<Q, false>(As, i0, c1, c0, acc, cacc, ccar);
+        window_block<Q, false>(As, i0, c1, c0, acc, cnt, cacc, ccar);
         i0 += Q;
         if (--left == 0) finish(c1);
     }
