@@ -623,7 +623,8 @@ def run_e2e(args, torch, bn, ops, hosts, dev, world=1):
             plans[o.label].execute_host_async(pa, pb, pinned_out[(o.bits, o.nout)],
                                               stream=streams[i % len(streams)])
 
-    step()  # allocates staging buffers
+    for _ in range(2):  # the first allocates staging buffers; both warm the copy paths
+        step()
     torch.cuda.synchronize()
     steps = max(1, min(args.steps, args.e2e_steps))
     barrier(world)
@@ -768,7 +769,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="3 sizes only (smoke runs)")
     ap.add_argument("--only", default="", help="comma list of op names/labels to keep")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-step-budget", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
