@@ -11,24 +11,26 @@
 // the recombined coefficients are exact.
 //
 // Why 32-bit primes on this GPU: a field element is one 32-bit word, so a
-// Montgomery product (R = 2^32) is two 32x32 multiplies for the product and
-// two for the reduction (the 64-bit fields take six 32x32->64 multiply-adds),
-// and both spectra of a 16384-point transform fit in shared memory, so every
-// size up to 256K-bit operands runs as one transform (no split).  Elements are
-// kept lazily in [0, 2p): with p < 2^30, 4p < 2^32 leaves room for the DIF
-// butterfly's unreduced difference u - v + 2p.
+// product by a constant (twiddles, the digit reduction, the 1/N scale) is
+// three 32x32 multiplies by Shoup's method and a product of two variables
+// (pointwise) four by Montgomery's (R = 2^32), where the 64-bit fields take
+// six 32x32->64 multiply-adds; and both spectra of a 16384-point transform
+// fit in shared memory, so every size up to 256K-bit operands runs as one
+// transform (no split).  Elements are kept lazily in [0, 2p): with p < 2^30,
+// 4p < 2^32 leaves room for the DIF butterfly's unreduced difference
+// u - v + 2p.
 //
 // Work mapping as in mul_ntt.cu: one CTA per integer pair at a time (a
 // persistent grid), forward transforms decimation-in-frequency and the
 // inverse decimation-in-time (no bit-reversal pass), radix-8 register passes.
-// The kernels are instantiated for every transform length (log2 N = 1 .. 14,
-// ntt3_device.cuh and mul_ntt32_k*.cu), so the passes run with compile-time
-// strides; this file holds the host side: tables, plans and launches.
 // For each prime: digits -> A, B (reduced into the field), forward transforms,
 // pointwise product, inverse, scale by 1/N.  The residues modulo p0 and p1 go
 // to a per-CTA scratch slot (L2-resident), the residues modulo p2 stay in
 // shared memory, and the normalisation recombines and carries them into
-// limbs.
+// limbs.  The kernels are instantiated for every transform length (log2 N =
+// 1 .. 14; ntt3_device.cuh and mul_ntt32_k*.cu), so the passes run with
+// compile-time strides; this file holds the host side: tables, plans and
+// launches.
 #include <cuda_runtime.h>
 
 #include <cstring>
