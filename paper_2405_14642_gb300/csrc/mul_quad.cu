@@ -16,10 +16,13 @@
 //     S = sum_{q<Q} C_{k+q} 2^{32q}
 // in Q+2 registers (it stays below 2^{32(Q+2)} since nb < 2^32) and adds
 // A_i * (B_{k-i}, ..., B_{k-i+Q-1}) for each i with one mad.lo carry chain
-// and one mad.hi carry chain: about two multiply-adds per word product.
-// Operands are read from shared memory as 16-byte vectors, Q at a time; the
-// B window slides down one word per step and is assembled from two
-// consecutive Q-word chunks held in registers.
+// and one mad.hi carry chain (the low chain's final carry is counted in a
+// register and folded in once per window): about two multiply-adds per word
+// product.  Operands are read from shared memory as 16-byte vectors, Q at a
+// time; the B window slides down one word per step and is assembled from two
+// consecutive Q-word chunks held in registers.  Every unit is R + 1 blocks of
+// Q steps, and its windows run as one loop over them, so the lanes of a warp
+// share one trip count whatever their windows (quad_device.cuh, conv_unit).
 //
 // Recombination (Fig. 4/5).  Each window's low Q words go to L (the result
 // range [k, k+Q)), its two high words to H at k+Q and k+Q+1; windows are Q
