@@ -742,7 +742,11 @@ def dist_env():
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
-        dist.barrier()
+        if dist.get_backend() == "nccl":
+            import torch
+            dist.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            dist.barrier()
 
 
 def allreduce_max(x: float, world: int, dev):
@@ -792,6 +796,8 @@ def main(argv=None):
         if world > 1:
             import torch
             import torch.distributed as dist
+            if torch.cuda.is_available():
+                torch.cuda.set_device(local_rank)  # before NCCL binds the rank to a device
             dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         res = run_gpu(args, rank, world, local_rank)
         if world > 1:
