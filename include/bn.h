@@ -95,7 +95,9 @@ typedef enum bn_op {
 typedef struct bn_tuning {
     uint32_t limbs_per_thread;  /* add: limbs per thread (multiple of the vector width);
                                    quad: result limbs per window (4 or 8) */
-    uint32_t cta_threads;       /* threads per CTA (multiple of 32, <= 1024) */
+    uint32_t cta_threads;       /* threads per CTA (multiple of 32, <= 1024); the three-prime
+                                   transform's kernels are compiled for one count per
+                                   length (N/8 within 32..1024) and refuse any other */
     uint32_t variant;           /* quad: 1 = carry-chain accumulation, 2 = per-column
                                    64-bit sums with carry counts; other ops: 0 */
     uint32_t reserved;          /* must be zero */
