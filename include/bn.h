@@ -83,7 +83,17 @@ typedef enum bn_op {
      * power of two >= na + nb, at most 16384 (na + nb <= 16384).  Field
      * elements are single 32-bit words.  Plans and one-shot calls only (not a
      * batch item op). */
-    BN_OP_MUL_NTT3 = 5
+    BN_OP_MUL_NTT3 = 5,
+    /* Section 3's classical product (every word product, summed by column,
+     * Eq. (1)) computed one level down on bytes as an exact contraction on
+     * the tensor cores: fp16 byte digits, f32 sums of at most 128 byte
+     * products (below 2^23, exact), per-thread integer column sums, then the
+     * normalisation into limbs with the Section 2 carry scan.  Operands cut
+     * into 128-byte blocks; per block J of the shorter operand one MMA chain
+     * of M = 128, K = 128 against all blocks of the longer one.
+     * na, nb <= BN_MUL_MAX_LIMBS; no tuning fields.  Plans and one-shot
+     * calls only (not a batch item op). */
+    BN_OP_MUL_QUAD_TC = 6
 } bn_op;
 
 /* Largest limb counts per operand (256K bits for the products, 512K bits for
@@ -167,6 +177,18 @@ bn_status bn_mul_ntt(const uint32_t *a, const uint32_t *b, uint32_t *c,
  * result (na + nb limbs) and errors as bn_mul_ntt. */
 bn_status bn_mul_ntt3(const uint32_t *a, const uint32_t *b, uint32_t *c,
                       uint32_t na, uint32_t nb, uint64_t batch, void *stream);
+/* One-shot BN_OP_MUL_QUAD_TC (schoolbook on the tensor cores): same
+ * arguments, layout, ownership and errors as bn_mul_quad. */
+bn_status bn_mul_quad_tc(const uint32_t *a, const uint32_t *b, uint32_t *c,
+                         uint32_t na, uint32_t nb, uint64_t batch, void *stream);
+
+/* Tensor-core kernels wait for their MMAs with a time limit (1 s per wait);
+ * one that gives up skips the rest of its work, leaves its results
+ * incomplete and raises a device flag.  This call synchronises the device,
+ * reads and clears the flag: BN_ETIMEOUT if it was raised since the last
+ * call, BN_ECUDA on a CUDA error, else BN_OK. */
+bn_status bn_tc_check(void);
+
 /* One-shot BN_OP_MUL_AUTO: c = a * b by the fastest product for the sizes
  * (schoolbook for small operands, the three-prime transform from about 8K
  * bits on GB300); arguments, layout, result and errors as bn_mul_quad. */

@@ -16,7 +16,8 @@ import numpy as np
 from . import _build
 
 BN_OK, BN_EINVAL, BN_ENOMEM, BN_ECUDA, BN_EUNSUPPORTED, BN_ETIMEOUT = range(6)
-BN_OP_ADD, BN_OP_MUL_QUAD, BN_OP_MUL_NTT64, BN_OP_MUL_NTT_CRT, BN_OP_MUL_AUTO, BN_OP_MUL_NTT3 = range(6)
+(BN_OP_ADD, BN_OP_MUL_QUAD, BN_OP_MUL_NTT64, BN_OP_MUL_NTT_CRT, BN_OP_MUL_AUTO, BN_OP_MUL_NTT3,
+ BN_OP_MUL_QUAD_TC) = range(7)
 BN_BATCH_AUTOTUNE, BN_BATCH_PLAIN = 1, 2
 # Layout of struct bn_batch_item (include/bn.h), 40 bytes.
 BATCH_ITEM_DTYPE = np.dtype([("op", "<u4"), ("na", "<u4"), ("nb", "<u4"), ("reserved", "<u4"),
@@ -102,6 +103,8 @@ def load(build_if_missing: bool = False):
         "bn_mul_ntt": ([u32p, u32p, u32p, u32, u32, u64, ctypes.c_int, vp], st),
         "bn_mul_ntt3": ([u32p, u32p, u32p, u32, u32, u64, vp], st),
         "bn_mul": ([u32p, u32p, u32p, u32, u32, u64, vp], st),
+        "bn_mul_quad_tc": ([u32p, u32p, u32p, u32, u32, u64, vp], st),
+        "bn_tc_check": ([], st),
         "bn_plan_op": ([vp], ctypes.c_int),
         "bn_status_str": ([ctypes.c_int], ctypes.c_char_p),
         "bn_last_error": ([], ctypes.c_char_p),
@@ -236,6 +239,24 @@ def bn_mul_ntt3(a, b, out=None, stream=None):
     _check(lib.bn_mul_ntt3(_ptr(a), _ptr(b), _ptr(out), na, nb, batch,
                            _stream_handle(stream, a.device)), "bn_mul_ntt3")
     return out
+
+
+def bn_mul_quad_tc(a, b, out=None, stream=None):
+    """c = a * b per row by the classical method computed on bytes as an exact
+    fp16 contraction on the tensor cores (Section 3's column sums); na + nb limbs."""
+    lib = load()
+    a, b = _pair(a, b)
+    batch, na, nb = a.shape[0], a.shape[1], b.shape[1]
+    out = _out(out, batch, na + nb, a)
+    _check(lib.bn_mul_quad_tc(_ptr(a), _ptr(b), _ptr(out), na, nb, batch,
+                              _stream_handle(stream, a.device)), "bn_mul_quad_tc")
+    return out
+
+
+def bn_tc_check():
+    """Synchronise the device and raise BnError (BN_ETIMEOUT) if a tensor-core
+    kernel gave up waiting for its MMAs since the last check."""
+    _check(load().bn_tc_check(), "bn_tc_check")
 
 
 def _same_length(name, a, b, out, stream):

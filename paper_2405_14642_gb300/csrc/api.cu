@@ -21,6 +21,7 @@ struct bn_plan_s {
     bn::QuadConfig quad;
     bn::NttPlan *ntt = nullptr;
     bn::Ntt3Plan *ntt3 = nullptr;
+    bn::QuadTcPlan *qtc = nullptr;
     // Device staging for bn_plan_execute_host (allocated on first use).
     uint32_t *d_a = nullptr, *d_b = nullptr, *d_c = nullptr;
     uint64_t staged_batch = 0;
@@ -61,6 +62,9 @@ bn_status configure(bn_plan_s *p, const bn_tuning *t) {
     case BN_OP_MUL_NTT_CRT:
         return bn::ntt_create(&p->ntt, p->op == BN_OP_MUL_NTT_CRT, p->na, p->nb, t);
     case BN_OP_MUL_NTT3: return bn::ntt3_create(&p->ntt3, p->na, p->nb, t);
+    case BN_OP_MUL_QUAD_TC:
+        if (t && (t->limbs_per_thread || t->cta_threads)) return BN_EINVAL;  // fixed geometry
+        return bn::quad_tc_create(&p->qtc, p->na, p->nb);
     default: break;
     }
     return BN_EINVAL;
@@ -89,6 +93,7 @@ bn_status launch(bn_plan_s *p, const uint32_t *a, const uint32_t *b, uint32_t *c
     case BN_OP_MUL_NTT64:
     case BN_OP_MUL_NTT_CRT: e = bn::ntt_launch(p->ntt, a, b, c, batch, st); break;
     case BN_OP_MUL_NTT3: e = bn::ntt3_launch(p->ntt3, a, b, c, batch, st); break;
+    case BN_OP_MUL_QUAD_TC: e = bn::quad_tc_launch(p->qtc, a, b, c, batch, st); break;
     default: e = cudaErrorInvalidValue; break;
     }
     return cuda_status("kernel launch", e);
@@ -191,7 +196,7 @@ bn_status bn_plan_create(bn_plan *out, bn_op op, uint32_t na, uint32_t nb, uint6
     }
     *out = nullptr;
     if (op != BN_OP_ADD && op != BN_OP_MUL_QUAD && op != BN_OP_MUL_NTT64 && op != BN_OP_MUL_NTT_CRT &&
-        op != BN_OP_MUL_NTT3 && op != BN_OP_MUL_AUTO) {
+        op != BN_OP_MUL_NTT3 && op != BN_OP_MUL_AUTO && op != BN_OP_MUL_QUAD_TC) {
         set_error_text("unknown op");
         return BN_EINVAL;
     }
@@ -312,6 +317,7 @@ bn_status bn_plan_destroy(bn_plan plan) {
     cudaFree(plan->d_c);
     if (plan->ntt) bn::ntt_destroy(plan->ntt);
     if (plan->ntt3) bn::ntt3_destroy(plan->ntt3);
+    if (plan->qtc) bn::quad_tc_destroy(plan->qtc);
     delete plan;
     return cuda_status("cudaDeviceSynchronize", e);
 }
@@ -322,6 +328,7 @@ int bn_plan_op(bn_plan plan) { return plan ? (int)plan->op : -1; }
 
 size_t bn_plan_scratch_bytes(bn_plan plan) {
     if (plan && plan->ntt3) return bn::ntt3_scratch_bytes(plan->ntt3);
+    if (plan && plan->qtc) return bn::quad_tc_scratch_bytes(plan->qtc);
     return (plan && plan->ntt) ? bn::ntt_scratch_bytes(plan->ntt) : 0;
 }
 
@@ -348,6 +355,22 @@ bn_status bn_mul_ntt(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_t
 bn_status bn_mul_ntt3(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_t na, uint32_t nb,
                       uint64_t batch, void *stream) {
     return one_shot(BN_OP_MUL_NTT3, a, b, c, na, nb, batch, stream);
+}
+
+bn_status bn_mul_quad_tc(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_t na, uint32_t nb,
+                         uint64_t batch, void *stream) {
+    return one_shot(BN_OP_MUL_QUAD_TC, a, b, c, na, nb, batch, stream);
+}
+
+bn_status bn_tc_check(void) {
+    uint32_t flag = 0;
+    cudaError_t e = bn::tc_fault_take(&flag);
+    if (e != cudaSuccess) return cuda_status("tensor-core status", e);
+    if (flag) {
+        set_error_text("a tensor-core kernel gave up waiting for its MMAs");
+        return BN_ETIMEOUT;
+    }
+    return BN_OK;
 }
 
 bn_status bn_mul(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_t na, uint32_t nb,

@@ -118,4 +118,14 @@ cudaError_t ntt3_batch_launch(Ntt3Plan *p, const BatchItem *items, uint32_t coun
 cudaError_t ntt3_launch_sized(Ntt3Plan *p, uint32_t na, uint32_t nb, const uint32_t *a, const uint32_t *b,
                               uint32_t *c, cudaStream_t st);
 
+// Schoolbook product on the tensor cores (mul_quad_tc.cu).
+struct QuadTcPlan;  // opaque
+bn_status quad_tc_create(QuadTcPlan **out, uint32_t na, uint32_t nb);
+void quad_tc_destroy(QuadTcPlan *p);
+cudaError_t quad_tc_launch(QuadTcPlan *p, const uint32_t *a, const uint32_t *b, uint32_t *c, uint64_t batch,
+                           cudaStream_t st);
+size_t quad_tc_scratch_bytes(const QuadTcPlan *p);
+// Reads and clears the tensor-core kernels' timeout flag (synchronises the device).
+cudaError_t tc_fault_take(uint32_t *flag);
+
 }  // namespace bn

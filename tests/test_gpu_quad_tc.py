@@ -1,0 +1,97 @@
+"""Parity of bn_mul_quad_tc (Section 3's column sums computed on bytes as an
+exact fp16 contraction on the tensor cores) with the CPU oracle, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_limbs_equal, to_dev, to_host, torch_cuda
+from paper_2405_14642_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+# 32 limbs = one 128-byte block; 4096 limbs of output = one tile of 128 blocks.
+SHAPES = [(1, 1), (1, 2), (2, 1), (3, 5), (31, 33), (32, 32), (33, 31), (64, 64), (100, 3),
+          (3, 100), (128, 128), (129, 130), (500, 20), (777, 1000), (1024, 1024), (2047, 2049),
+          (2048, 2048), (4096, 4096), (4097, 4000), (5000, 3001), (8192, 8192), (8192, 1),
+          (1, 8192), (8192, 100), (100, 8192)]
+
+
+def _tc(a, b):
+    import paper_2405_14642_gb300 as bn
+    got = to_host(bn.bn_mul_quad_tc(to_dev(a), to_dev(b)))
+    bn.bn_tc_check()
+    return got
+
+
+@pytest.mark.parametrize("na,nb", SHAPES)
+def test_quad_tc_matches_oracle(na, nb):
+    torch_cuda()
+    batch = 37 if max(na, nb) <= 2048 else 7
+    a, b = workloads.pair_batch(batch, na, nb, seed=workloads.seed_for(9, na * 7 + nb))
+    assert_limbs_equal(_tc(a, b), oracle.mul(a, b), f"quad_tc {na}x{nb}")
+
+
+def test_quad_tc_closed_forms():
+    """(2^N - 1)^2: every byte 255, so every MMA sum is at its maximum
+    128 * 255^2 < 2^23 and the column sums and carries are the largest."""
+    torch_cuda()
+    for n in [1, 7, 32, 33, 1000, 4096, 8192]:
+        ones = np.full((2, n), 0xFFFFFFFF, np.uint32)
+        want = np.zeros((2, 2 * n), np.uint32)
+        want[:, 0] = 1
+        want[:, n] = 0xFFFFFFFE
+        want[:, n + 1:] = 0xFFFFFFFF
+        assert_limbs_equal(_tc(ones, ones), want, f"(2^N-1)^2 n={n}")
+
+
+def test_quad_tc_edges_and_many_ctas():
+    """More pairs than CTAs (each CTA loops over instances, reusing its tensor
+    memory and mbarriers), with the 5% edge cases, through a plan."""
+    torch_cuda()
+    import paper_2405_14642_gb300 as bn
+    a, b = workloads.pair_batch(700, 300, 260, seed=workloads.seed_for(9, 77), edges=True)
+    with bn.Plan(bn.BN_OP_MUL_QUAD_TC, 300, 260, 700) as plan:
+        assert plan.op == bn.BN_OP_MUL_QUAD_TC
+        assert plan.scratch_bytes > 0
+        got = to_host(plan.execute(to_dev(a), to_dev(b)))
+    bn.bn_tc_check()
+    assert_limbs_equal(got, oracle.mul(a, b), "quad_tc plan 700 x 300x260")
+
+
+def test_quad_tc_equals_integer_schoolbook():
+    torch_cuda()
+    import paper_2405_14642_gb300 as bn
+    for na, nb in [(4096, 4096), (3000, 1234)]:
+        a, b = workloads.pair_batch(300, na, nb, seed=workloads.seed_for(9, na + nb))
+        da, db = to_dev(a), to_dev(b)
+        assert_limbs_equal(_tc(a, b), to_host(bn.bn_mul_quad(da, db)), f"tc vs quad {na}x{nb}")
+
+
+@pytest.mark.parametrize("bits", [16384, 65536, 262144])
+def test_quad_tc_full_size_sampled(bits):
+    """A size-sweep batch (64 MiB per side), launched as the benchmark launches
+    it, checked against the oracle on sampled rows."""
+    torch_cuda()
+    p = [q for q in workloads.sweep_points() if q.bits == bits][0]
+    a, b = workloads.pair_batch(p.batch, p.limbs, seed=p.seed, edges=True)
+    got = _tc(a, b)
+    rows = np.union1d(np.random.default_rng(bits).choice(p.batch, 5, replace=False), [19, 39])
+    assert_limbs_equal(got[rows], oracle.mul(a[rows], b[rows]), f"quad_tc {bits} sampled")
+
+
+def test_quad_tc_errors():
+    torch = torch_cuda()
+    import paper_2405_14642_gb300 as bn
+    big = torch.zeros((1, 8193), dtype=torch.int32, device="cuda")
+    one = torch.zeros((1, 4), dtype=torch.int32, device="cuda")
+    with pytest.raises(bn.BnError):
+        bn.bn_mul_quad_tc(big, one)
+    with pytest.raises(bn.BnError):
+        bn.Plan(bn.BN_OP_MUL_QUAD_TC, 64, 64, 4, limbs_per_thread=4)
+    x = torch.zeros((2, 16), dtype=torch.int32, device="cuda")
+    out = torch.zeros((2, 32), dtype=torch.int32, device="cuda")
+    with pytest.raises(bn.BnError):
+        bn.bn_mul_quad_tc(out.view(-1)[:32].view(2, 16), x, out=out)  # result overlaps an operand
+    empty = torch.zeros((0, 16), dtype=torch.int32, device="cuda")
+    assert bn.bn_mul_quad_tc(empty, empty).shape == (0, 32)
+    bn.bn_tc_check()
