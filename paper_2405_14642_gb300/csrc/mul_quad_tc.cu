@@ -40,18 +40,21 @@ __device__ uint32_t g_tc_fault;  // set when an MMA wait timed out
 
 namespace {
 
-constexpr uint32_t kThreads = 640;   // warp 0 issues the MMAs, 1-3 build W, 4-19 read D
-constexpr uint32_t kBuilders = 3, kEpiWarps = 16;
+constexpr uint32_t kThreads = 640;   // warp 0 issues the MMAs, warps 1-3 build W, warps 4-19 read D
+constexpr uint32_t kBuildWarps = 3;
+constexpr uint32_t kEpiWarps = 16;   // four per group of 32 tensor-memory lanes
 constexpr uint32_t kBlk = 128;       // bytes per block: rows of W, K of a step
 constexpr uint32_t kTile = 256;      // output blocks per tile (D columns, the MMA's N)
 constexpr uint32_t kPad = 32;        // zero blocks on each side of X
 constexpr uint32_t kTmemCols = 512;  // two D slots of 256 columns
-constexpr uint32_t kDSlots = 2;      // D slots in tensor memory (256 columns each)
+constexpr uint32_t kDSlots = 2;      // D slots in tensor memory
 constexpr uint32_t kWSlots = 3;      // W slots in shared memory
-constexpr uint32_t kWBytes = 128 * 128 * 2;  // one W_J in fp16: 16 K-chunks x 16 row groups x 128 B
-constexpr uint32_t kWLbo = 2048, kWSbo = 128;  // W: K-chunk stride, 8-row-group stride
-constexpr uint64_t kWaitNs = 1000000000ull;   // 1 s per wait
-constexpr uint32_t kMinSmem = 116 * 1024;     // one CTA per SM (the whole tensor memory each)
+constexpr uint32_t kWBytes = 128 * 128 * 2;     // one W_J in fp16: 16 K-chunks x 16 row groups x 128 B
+constexpr uint32_t kWLbo = 2048, kWSbo = 128;   // W: K-chunk stride, 8-row-group stride
+constexpr uint32_t kMaxSteps = 2 * (BN_MUL_MAX_LIMBS / 32 + 1);  // two tiles of at most mb + 1 steps
+constexpr uint64_t kWaitNs = 1000000000ull;     // 1 s per wait
+constexpr uint32_t kMinSmem = 116 * 1024;       // one CTA per SM (the whole tensor memory each)
+constexpr uint32_t kEpiBar = 1;                 // named barrier of the epilogue warps
 
 struct TcArgs {
     const uint32_t *a, *b;  // na >= nb (the host orders the operands)
@@ -61,70 +64,113 @@ struct TcArgs {
     uint32_t *scratch;        // per CTA: 128 (ma + mb) byte-column sums
     uint64_t scratch_stride;  // words per CTA
     uint32_t xs;              // bytes per chunk row of X: (ma + 2 kPad) * 16
-    uint32_t w_off, braw_off, spill_off, flags_off, bar_off;  // shared-memory byte offsets
+    uint32_t w_off, ca_off, cb_off, braw_off, sched_off, spill_off, flags_off, bar_off;  // shared-memory offsets
 };
 
-__device__ __forceinline__ int jlo(const TcArgs &g, int t) {
-    const int v = (int)(kTile * t) - (int)g.ma + 1;
-    return v > 0 ? v : 0;
+// A step (tile t, block J of b): the D chunks (32 columns) it writes are
+// [clo, chi), the columns s of tile t with 0 <= s - J < ma rounded out to
+// whole chunks (X's zero blocks cover the rest); `last` marks the tile's last step.
+struct Step {
+    uint32_t J, t, clo, chi, last;
+};
+__device__ __forceinline__ uint32_t step_pack(Step x) {
+    return x.J | (x.t << 10) | (x.clo << 12) | (x.chi << 16) | (x.last << 20);
 }
-__device__ __forceinline__ int jhi(const TcArgs &g, int t) {
-    const int v = (int)(kTile * t + kTile - 1);
-    return v < (int)g.mb ? v : (int)g.mb;
-}
-
-// D chunks (32 columns each) of tile t that step J writes: the columns s with
-// 0 <= s - J < ma, rounded out to whole chunks (X's zero blocks cover the rest).
-__device__ __forceinline__ void chunk_range(const TcArgs &g, int t, int J, int &clo, int &chi) {
-    const int s0 = (int)(kTile * t);
-    const int lo = (J > s0 ? J : s0) - s0;
-    const int e = J + (int)g.ma, hi = (e < s0 + (int)kTile ? e : s0 + (int)kTile) - s0;
-    clo = lo >> 5;
-    chi = (hi + 31) >> 5;
+__device__ __forceinline__ Step step_unpack(uint32_t w) {
+    return Step{w & 1023u, (w >> 10) & 3u, (w >> 12) & 15u, (w >> 16) & 15u, (w >> 20) & 1u};
 }
 
-__device__ __forceinline__ bool step_next(const TcArgs &g, int &t, int &J) {
-    if (J < jhi(g, t)) {
-        ++J;
-        return true;
+// The steps of one product, in order: for each tile, J from the first block of
+// b that reaches it to the last.  Depends only on the sizes.
+__device__ uint32_t make_schedule(const TcArgs &g, uint32_t *sched) {
+    uint32_t n = 0;
+    for (uint32_t t = 0; t < g.tiles; ++t) {
+        const int s0 = (int)(kTile * t);
+        const int lo = s0 - (int)g.ma + 1 > 0 ? s0 - (int)g.ma + 1 : 0;
+        const int hi = s0 + (int)kTile - 1 < (int)g.mb ? s0 + (int)kTile - 1 : (int)g.mb;
+        for (int J = lo; J <= hi; ++J) {
+            const int c0 = (J > s0 ? J : s0) - s0;
+            const int e = J + (int)g.ma, c1 = (e < s0 + (int)kTile ? e : s0 + (int)kTile) - s0;
+            sched[n++] = step_pack(Step{(uint32_t)J, t, (uint32_t)(c0 >> 5), (uint32_t)((c1 + 31) >> 5),
+                                        J == hi ? 1u : 0u});
+        }
     }
-    if (t + 1 < (int)g.tiles) {
-        ++t;
-        J = jlo(g, t);
-        return true;
-    }
-    return false;
+    return n;
 }
 
-// Row r of W_J, words 32 h .. 32 h + 31, into the W slot at
-// `w` (shared memory, the MMA's A operand: K-major without swizzle, the 16-byte
-// piece of row r and K-chunk q at (r / 8) * 128 + q * 2048 + (r % 8) * 16).
-// Word k of row r holds the fp16 pair (W_J[r][2k], W_J[r][2k+1]) =
-// (b-byte (v - 2k), b-byte (v - 2k - 1)), v = 128 J + r; braw holds b's bytes
-// at offset 128 + index, zero outside b.
-__device__ __forceinline__ void build_w(const uint32_t *braw, int J, uint32_t r, uint32_t h, uint8_t *w) {
-    const int e = 65 + 128 * J + (int)r - 64 * (int)h;  // lowest byte offset this thread reads
+// Row r of W_J, words 16 u .. 16 u + 15 (K-chunks 4 u .. 4 u + 3), into the
+// W slot at `w` (shared memory, the MMA's A operand: K-major without swizzle,
+// the 16-byte piece of row r and K-chunk q at (r / 8) * 128 + q * 2048 +
+// (r % 8) * 16).  Word k of row r holds the fp16 pair (W_J[r][2k], W_J[r][2k+1])
+// = (b-byte (v - 2k), b-byte (v - 2k - 1)), v = 128 J + r; braw holds b's
+// bytes at offset 128 + index, zero outside b (bytes are denser in shared
+// memory than fp16, which halves these reads).
+__device__ __forceinline__ void build_w(const uint32_t *braw, uint32_t J, uint32_t r, uint32_t u, uint8_t *w) {
+    const uint32_t e = 97 + 128 * J + r - 32 * u;  // lowest byte offset this thread reads
     const uint32_t *bw = braw + (e >> 2);
-    const uint32_t sh = (uint32_t)e & 3u;
-    uint32_t wv[17];
+    const uint32_t sh = e & 3u;
+    uint32_t wv[9];
 #pragma unroll
-    for (int j = 0; j < 17; ++j) wv[j] = bw[j];
-    // bytes at offsets e + 63 - 4g, e + 62 - 4g, e + 61 - 4g, e + 60 - 4g
+    for (int j = 0; j < 9; ++j) wv[j] = bw[j];
+    // words 2g, 2g + 1: bytes at offsets e + 31 - 4g, e + 30 - 4g, e + 29 - 4g, e + 28 - 4g
     const uint32_t sel = (sh + 3) | ((sh + 2) << 4) | ((sh + 1) << 8) | (sh << 12);
-    uint8_t *row = w + (r >> 3) * kWSbo + (r & 7) * 16 + 8 * h * kWLbo;
+    uint8_t *row = w + (r >> 3) * kWSbo + (r & 7) * 16 + 4 * u * kWLbo;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {  // K-chunk 8 h + q: words 4 q .. 4 q + 3 of this half
-        const uint32_t r0 = __byte_perm(wv[15 - 2 * q], wv[16 - 2 * q], sel);
-        const uint32_t r1 = __byte_perm(wv[14 - 2 * q], wv[15 - 2 * q], sel);
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t r0 = __byte_perm(wv[7 - 2 * q], wv[8 - 2 * q], sel);
+        const uint32_t r1 = __byte_perm(wv[6 - 2 * q], wv[7 - 2 * q], sel);
         *reinterpret_cast<uint4 *>(row + q * kWLbo) =
             make_uint4(tc::bytes01_f16x2(r0), tc::bytes23_f16x2(r0), tc::bytes01_f16x2(r1), tc::bytes23_f16x2(r1));
     }
 }
 
-// Exact integer of an f32 holding an integer v in [0, 2^23): v + 2^23 has
-// exponent 23, so its mantissa bits are v.
-__device__ __forceinline__ uint32_t f32_int(uint32_t bits) {
-    return __float_as_uint(__fadd_rn(__uint_as_float(bits), 8388608.0f)) - 0x4b000000u;
+// build_w for the quarter rows x0 and x1 (row = x & 127, quarter = x >> 7),
+// both rows' source words loaded before either is converted and stored.
+__device__ __forceinline__ void build_w2(const uint32_t *braw, uint32_t J, uint32_t x0, uint32_t x1, uint8_t *w) {
+    uint32_t wv[2][9], sel[2];
+    uint8_t *row[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const uint32_t x = i ? x1 : x0, r = x & 127, u = x >> 7;
+        const uint32_t e = 97 + 128 * J + r - 32 * u;
+        const uint32_t *bw = braw + (e >> 2);
+        const uint32_t sh = e & 3u;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) wv[i][j] = bw[j];
+        sel[i] = (sh + 3) | ((sh + 2) << 4) | ((sh + 1) << 8) | (sh << 12);
+        row[i] = w + (r >> 3) * kWSbo + (r & 7) * 16 + 4 * u * kWLbo;
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t r0 = __byte_perm(wv[i][7 - 2 * q], wv[i][8 - 2 * q], sel[i]);
+            const uint32_t r1 = __byte_perm(wv[i][6 - 2 * q], wv[i][7 - 2 * q], sel[i]);
+            *reinterpret_cast<uint4 *>(row[i] + q * kWLbo) = make_uint4(
+                tc::bytes01_f16x2(r0), tc::bytes23_f16x2(r0), tc::bytes01_f16x2(r1), tc::bytes23_f16x2(r1));
+        }
+}
+
+// Every D starts at 2^23 (a first MMA multiplies 2048 by 4096 into each
+// element); the byte products add an integer v < 2^23, so D = 2^23 + v is
+// exact in f32 and, having exponent 23, its bit pattern is 0x4b000000 + v.
+constexpr uint32_t kBiasBits = 0x4b000000u;
+constexpr uint16_t kF16_2048 = 0x6800u, kF16_4096 = 0x6c00u;
+constexpr uint32_t kCaBytes = 128 * 16 * 2, kCbBytes = 256 * 16 * 2;  // the bias MMA's A (M x 16) and B (N x 16)
+constexpr uint32_t kCbLbo = 4096;
+
+// Named barrier of the `count` threads of warps 1-16, OR-reducing `pred`.
+__device__ __forceinline__ bool epi_barrier_or(bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\t"
+        "setp.ne.u32 pi, %1, 0;\n\t"
+        "barrier.red.or.pred po, %2, %3, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "n"(kEpiBar), "n"(32 * kEpiWarps)
+        : "memory");
+    return r != 0;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
@@ -132,26 +178,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
     uint8_t *X = sm;  // X and the W slots double as the normalisation's staging row
     uint8_t *W = sm + g.w_off;
     uint32_t *braw = reinterpret_cast<uint32_t *>(sm + g.braw_off);
+    uint32_t *sched = reinterpret_cast<uint32_t *>(sm + g.sched_off);
     uint64_t *spill = reinterpret_cast<uint64_t *>(sm + g.spill_off);
     uint32_t *flags = reinterpret_cast<uint32_t *>(sm + g.flags_off);
-    uint64_t *wfull = reinterpret_cast<uint64_t *>(sm + g.bar_off);  // [kWSlots], builder arrivals
+    uint64_t *wfull = reinterpret_cast<uint64_t *>(sm + g.bar_off);  // [kWSlots], one arrival per builder warp
     uint64_t *wempty = wfull + kWSlots;                                 // [kWSlots], MMA commits
     uint64_t *dfull = wempty + kWSlots;                                 // [kDSlots], MMA commits
-    uint64_t *dempty = dfull + kDSlots;                                 // [kDSlots], epilogue arrivals
+    uint64_t *dempty = dfull + kDSlots;                                 // [kDSlots], one arrival per warp
     uint32_t *slot = reinterpret_cast<uint32_t *>(dempty + kDSlots);
     volatile uint32_t *abortf = slot + 1;
+    uint32_t *nsteps = slot + 2;
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lq = warp & 3;  // the tensor-memory lanes this warp may move
     if (warp == 0) tc::tmem_alloc(slot, kTmemCols);
+    if (tid == 32) *nsteps = make_schedule(g, sched);
+    {  // the bias MMA's operands: A[r][0] = 2048, B[n][0] = 4096, zero elsewhere
+        uint16_t *ca = reinterpret_cast<uint16_t *>(sm + g.ca_off), *cb = reinterpret_cast<uint16_t *>(sm + g.cb_off);
+        for (uint32_t x = tid; x < kCaBytes / 2; x += kThreads) ca[x] = (x % 8 == 0 && x < 128 * 8) ? kF16_2048 : 0;
+        for (uint32_t x = tid; x < kCbBytes / 2; x += kThreads) cb[x] = (x % 8 == 0 && x < 256 * 8) ? kF16_4096 : 0;
+        tc::fence_proxy_async();
+    }
     if (tid == 0) {
         for (uint32_t k = 0; k < kWSlots; ++k) {
-            tc::mbar_init(&wfull[k], 32 * kBuilders);
+            tc::mbar_init(&wfull[k], kBuildWarps);
             tc::mbar_init(&wempty[k], 1);
         }
         for (uint32_t k = 0; k < kDSlots; ++k) {
             tc::mbar_init(&dfull[k], 1);
-            tc::mbar_init(&dempty[k], 32 * kEpiWarps);
+            tc::mbar_init(&dempty[k], kEpiWarps);
         }
         *abortf = 0;
         tc::fence_mbar_init();
@@ -159,12 +214,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tbase = *slot;
+    const uint32_t tbase = *slot, S = *nsteps;
     const uint32_t lane_off = (32 * lq) << 16;
     const uint32_t x_s = tc::smem_u32(X), w_s = tc::smem_u32(W);
     const uint32_t out_blocks = g.ma + g.mb;
     uint32_t *cols = g.scratch + blockIdx.x * g.scratch_stride;
-    uint32_t gs = 0;  // this thread's step count over all instances (slots and phases)
+    uint32_t gs = 0;  // steps done by this CTA over all instances (slots and phases)
     bool fail = false;
 
     for (uint64_t inst = blockIdx.x; inst < g.batch; inst += gridDim.x) {
@@ -189,101 +244,104 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
         tc::fence_proxy_async();
         __syncthreads();
 
-        // ---- the steps (tile, J), one role per warp group
-        int t = 0, J = jlo(g, 0);
         if (warp == 0) {
-            // one thread issues each step's 8 MMAs (K = 16 each) and commits them
-            do {
+            // the warp waits and computes each step's descriptors together (so
+            // they stay in uniform registers); one elected lane issues the 8
+            // MMAs (K = 16 each) and commits them
+            for (uint32_t i = 0; i < S; ++i, ++gs) {
                 const uint32_t k = gs % kWSlots, d = gs % kDSlots, ud = gs / kDSlots;
-                if (lane == 0) {
-                    bool ok = tc::mbar_wait(&wfull[k], (gs / kWSlots) & 1u, kWaitNs, abortf);
-                    if (ok && ud > 0) ok = tc::mbar_wait(&dempty[d], (ud - 1) & 1u, kWaitNs, abortf);
-                    if (ok) {
-                        tc::fence_after_sync();
-                        int clo, chi;
-                        chunk_range(g, t, J, clo, chi);
-                        const uint32_t idesc = tc::idesc_f16_f32(128, 32u * (uint32_t)(chi - clo));
-                        const int i0 = (int)(kTile * t) + 32 * clo - J + (int)kPad;  // padded block of column 0
-                        const uint32_t dt = tbase + kTile * d + 32 * (uint32_t)clo;
-                        const uint32_t ws = w_s + k * kWBytes;
-#pragma unroll
-                        for (uint32_t kk = 0; kk < 8; ++kk) {
-                            const uint64_t bd = tc::smem_desc(x_s + 2 * kk * g.xs + (uint32_t)i0 * 16, g.xs, 128);
-                            const uint64_t ad = tc::smem_desc(ws + 2 * kk * kWLbo, kWLbo, kWSbo);
-                            tc::mma_f16_ss(dt, ad, bd, idesc, kk > 0);
-                        }
-                        tc::mma_commit(&dfull[d]);
-                        tc::mma_commit(&wempty[k]);
-                    } else {
-                        *abortf = 1;
-                    }
+                bool ok = tc::mbar_wait(&wfull[k], (gs / kWSlots) & 1u, kWaitNs, abortf);
+                if (ok && ud > 0) ok = tc::mbar_wait(&dempty[d], (ud - 1) & 1u, kWaitNs, abortf);
+                if (!__all_sync(FULL_MASK, ok)) {
+                    *abortf = 1;
+                    break;
                 }
-                ++gs;
-                if (__shfl_sync(FULL_MASK, (uint32_t)*abortf, 0)) break;
-            } while (step_next(g, t, J));
-        } else if (warp <= kBuilders) {
-            // builders: W_J into a W slot once the MMA that last read it is done;
-            // the 256 pieces (row, half) are spread over the 96 builder threads
+                tc::fence_after_sync();
+                const Step st = step_unpack(sched[i]);
+                const uint32_t idesc = tc::idesc_f16_f32(128, 32u * (st.chi - st.clo));
+                // padded block of D column 0: s - J with s = 256 t + 32 clo
+                const uint32_t i0 = kTile * st.t + 32 * st.clo + kPad - st.J;
+                const uint32_t dt = tbase + kTile * d + 32 * st.clo;
+                const uint64_t bd = tc::smem_desc(x_s + i0 * 16, g.xs, 128), bstep = (2 * g.xs) >> 4;
+                const uint64_t ad = tc::smem_desc(w_s + k * kWBytes, kWLbo, kWSbo), astep = (2 * kWLbo) >> 4;
+                const uint64_t cad = tc::smem_desc(x_s + g.ca_off, kWLbo, kWSbo), cbd = tc::smem_desc(x_s + g.cb_off, kCbLbo, 128);
+                if (tc::elect_one()) {
+                    tc::mma_f16_ss(dt, cad, cbd, idesc, 0);  // D = 2^23
+#pragma unroll
+                    for (uint32_t kk = 0; kk < 8; ++kk) tc::mma_f16_ss(dt, ad + kk * astep, bd + kk * bstep, idesc, 1);
+                    tc::mma_commit(&dfull[d]);
+                    tc::mma_commit(&wempty[k]);
+                }
+                __syncwarp();
+            }
+        } else if (warp <= kBuildWarps) {
+            // builders: W of each step into a W slot once the MMA that last read
+            // it is done; the 512 quarter rows are spread over the 96 threads
             const uint32_t bt = tid - 32;
-            do {
+            for (uint32_t i = 0; i < S; ++i, ++gs) {
                 const uint32_t k = gs % kWSlots, use = gs / kWSlots;
                 if (use > 0 &&
                     !__all_sync(FULL_MASK, tc::mbar_wait(&wempty[k], (use - 1) & 1u, kWaitNs, abortf))) {
                     *abortf = 1;
                     break;
                 }
+                const uint32_t J = sched[i] & 1023u;
                 uint8_t *wk = W + k * kWBytes;
-                for (uint32_t i = bt; i < 256; i += 32 * kBuilders) build_w(braw, J, i & 127, i >> 7, wk);
+                uint32_t x = bt;
+                for (; x + 32 * kBuildWarps < 512; x += 64 * kBuildWarps) build_w2(braw, J, x, x + 32 * kBuildWarps, wk);
+                if (x < 512) build_w(braw, J, x & 127, x >> 7, wk);
                 tc::fence_proxy_async();
-                tc::mbar_arrive(&wfull[k]);
-                ++gs;
-            } while (step_next(g, t, J));
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&wfull[k]);
+            }
         } else {
-            // epilogue: D of each step into the integer column sums of the tile
+            // epilogue: each finished D into the integer column sums of its tile
             // (the 4 warps of lane group lq own chunks 2m, 2m + 1, m = 0..3)
-            const uint32_t m = (warp - 1 - kBuilders) >> 2;  // warps 4..19: m = 0..3
+            const uint32_t m = (warp - 1 - kBuildWarps) >> 2;
             uint32_t acc[2][32];
 #pragma unroll
             for (int c = 0; c < 2; ++c)
 #pragma unroll
                 for (int i = 0; i < 32; ++i) acc[c][i] = 0;
-            do {
+            for (uint32_t i = 0; i < S; ++i, ++gs) {
                 const uint32_t d = gs % kDSlots;
-                if (!__all_sync(FULL_MASK, tc::mbar_wait(&dfull[d], (gs / kDSlots) & 1u, kWaitNs, abortf))) {
+                bool bad = false;
+                if (warp == 1 + kBuildWarps)  // one warp polls, the others sleep in the barrier
+                    bad = !__all_sync(FULL_MASK, tc::mbar_wait(&dfull[d], (gs / kDSlots) & 1u, kWaitNs, abortf));
+                if (epi_barrier_or(bad)) {
                     *abortf = 1;
                     break;
                 }
                 tc::fence_after_sync();
-                int clo, chi;
-                chunk_range(g, t, J, clo, chi);
+                const Step st = step_unpack(sched[i]);
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    const int ch = 2 * (int)m + c;
-                    if (ch >= clo && ch < chi) {
+                    const uint32_t ch = 2 * m + c;
+                    if (ch >= st.clo && ch < st.chi) {
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh) {
                             uint32_t v[16];
-                            tc::tmem_ld16(tbase + lane_off + kTile * d + 32 * (uint32_t)ch + 16 * hh, v);
+                            tc::tmem_ld16(tbase + lane_off + kTile * d + 32 * ch + 16 * hh, v);
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) acc[c][16 * hh + i] += f32_int(v[i]);
+                            for (int j = 0; j < 16; ++j) acc[c][16 * hh + j] += v[j] - kBiasBits;
                         }
                     }
                 }
                 tc::fence_before_sync();
-                tc::mbar_arrive(&dempty[d]);
-                ++gs;
-                if (J == jhi(g, t)) {  // tile complete: publish its column sums
-                    const uint32_t s0 = kTile * (uint32_t)t, r = 32 * lq + lane;
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&dempty[d]);
+                if (st.last) {  // tile complete: publish its column sums
+                    const uint32_t s0 = kTile * st.t, r = 32 * lq + lane;
 #pragma unroll
                     for (int c = 0; c < 2; ++c)
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const uint32_t s = s0 + 32 * (2 * m + c) + i;
-                            if (s < out_blocks) cols[kBlk * s + r] = acc[c][i];
-                            acc[c][i] = 0;
+                        for (int j = 0; j < 32; ++j) {
+                            const uint32_t s = s0 + 32 * (2 * m + c) + j;
+                            if (s < out_blocks) cols[kBlk * s + r] = acc[c][j];
+                            acc[c][j] = 0;
                         }
                 }
-            } while (step_next(g, t, J));
+            }
         }
         __syncthreads();
         fail = *abortf != 0;
@@ -310,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
 }
 
 struct TcGeometry {
-    uint32_t na, nb, ma, mb, tiles, xs, w_off, braw_off, spill_off, flags_off, bar_off, smem;
+    uint32_t na, nb, ma, mb, tiles, xs, w_off, ca_off, cb_off, braw_off, sched_off, spill_off, flags_off, bar_off, smem;
     bool swap;
 };
 
@@ -326,18 +384,23 @@ TcGeometry geometry(uint32_t na, uint32_t nb) {
     const uint32_t nout = q.na + q.nb;
     const uint32_t stage_bytes = 4 * ((nout - 1) + ((nout - 1) >> 4) + 1);
     q.w_off = 16 * q.xs;  // a multiple of 16
+    q.spill_off = q.w_off;  // the normalisation's spill words reuse the W slots
     uint32_t off = q.w_off + kWSlots * kWBytes;
     if (off < stage_bytes) off = stage_bytes;
     off = (off + 15) & ~15u;
+    q.ca_off = off;
+    off += kCaBytes;
+    q.cb_off = off;
+    off += kCbBytes;
     q.braw_off = off;
     off += 4 * (32 * (q.mb + 2) + 4);
     off = (off + 15) & ~15u;
-    q.spill_off = off;
-    off += 8 * kThreads;
+    q.sched_off = off;
+    off += 4 * kMaxSteps;
     q.flags_off = off;
     off += 4 * (kThreads / 32);
     q.bar_off = (off + 15) & ~15u;
-    off = q.bar_off + 8 * (2 * kWSlots + 2 * kDSlots) + 8;
+    off = q.bar_off + 8 * (2 * kWSlots + 2 * kDSlots) + 16;
     q.smem = off > kMinSmem ? off : kMinSmem;
     return q;
 }
@@ -405,7 +468,10 @@ cudaError_t quad_tc_launch(QuadTcPlan *p, const uint32_t *a, const uint32_t *b, 
     g.scratch_stride = p->stride;
     g.xs = q.xs;
     g.w_off = q.w_off;
+    g.ca_off = q.ca_off;
+    g.cb_off = q.cb_off;
     g.braw_off = q.braw_off;
+    g.sched_off = q.sched_off;
     g.spill_off = q.spill_off;
     g.flags_off = q.flags_off;
     g.bar_off = q.bar_off;

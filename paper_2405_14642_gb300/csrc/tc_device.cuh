@@ -102,7 +102,9 @@ __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.
 
 // Shared-memory descriptor without swizzle: start address, leading byte offset
 // (core matrices adjacent in K), stride byte offset (adjacent in M/N); bits
-// 46..48 hold the descriptor version 1.
+// 46..48 hold the descriptor version 1.  The start address sits in the low 14
+// bits as address / 16, so adding n to a descriptor moves it by 16 n bytes
+// (within the 256 KB window).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     return (uint64_t)((saddr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
@@ -147,6 +149,17 @@ __device__ __forceinline__ void mma_f16_ss(uint32_t d_tmem, uint64_t a_desc, uin
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                  ::"r"(smem_u32(bar)) : "memory");
+}
+
+// True in exactly one active lane of the warp (all lanes must call it).
+__device__ __forceinline__ bool elect_one() {
+    uint32_t pred = 0;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "elect.sync _|p, 0xffffffff;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(pred));
+    return pred != 0;
 }
 
 // ---- mbarriers ---------------------------------------------------------------
@@ -202,20 +215,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
 
 // ---- digits as fp16 ------------------------------------------------------------
 
-// Bytes 0 and 1 of w as the fp16 pair (byte0, byte1), exact: 0x64xx is the
-// fp16 number 1024 + xx, and subtracting 1024 is exact.
-__device__ __forceinline__ uint32_t bytes01_f16x2(uint32_t w) {
-    const uint32_t t = __byte_perm(w, 0x64646464u, 0x4140);
+// Two bytes of w as an fp16 pair, exact: `sel` (a byte_perm selector) places
+// the byte meant for the low half in byte 0 and the other in byte 2, with 0x64
+// above each (0x64xx is the fp16 number 1024 + xx); subtracting 1024 is exact.
+__device__ __forceinline__ uint32_t bytes_f16x2(uint32_t w, uint32_t sel) {
+    const uint32_t t = __byte_perm(w, 0x64646464u, sel);
     uint32_t r;
     asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(t), "r"(0x64006400u));
     return r;
 }
-__device__ __forceinline__ uint32_t bytes23_f16x2(uint32_t w) {
-    const uint32_t t = __byte_perm(w, 0x64646464u, 0x4342);
-    uint32_t r;
-    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(t), "r"(0x64006400u));
-    return r;
-}
+// Bytes (0, 1) and (2, 3) of w.
+__device__ __forceinline__ uint32_t bytes01_f16x2(uint32_t w) { return bytes_f16x2(w, 0x4140u); }
+__device__ __forceinline__ uint32_t bytes23_f16x2(uint32_t w) { return bytes_f16x2(w, 0x4342u); }
 
 }  // namespace tc
 }  // namespace bn
