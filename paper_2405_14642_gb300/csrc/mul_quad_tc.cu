@@ -40,18 +40,19 @@ __device__ uint32_t g_tc_fault;  // set when an MMA wait timed out
 
 namespace {
 
-constexpr uint32_t kThreads = 640;   // warp 0 issues the MMAs, warps 1-3 build W, warps 4-19 read D
-constexpr uint32_t kBuildWarps = 3;
-constexpr uint32_t kEpiWarps = 16;   // four per group of 32 tensor-memory lanes
+constexpr uint32_t kThreads = 640;   // warp 0 issues the MMAs, warps 1-7 build W, warps 8-19 read D
+constexpr uint32_t kBuildWarps = 7;
+constexpr uint32_t kEpiWarps = 12;   // three per group of 32 tensor-memory lanes, two D chunks each
 constexpr uint32_t kBlk = 128;       // bytes per block: rows of W, K of a step
-constexpr uint32_t kTile = 256;      // output blocks per tile (D columns, the MMA's N)
+constexpr uint32_t kTile = 192;      // output blocks per tile (D columns, the MMA's N)
 constexpr uint32_t kPad = 32;        // zero blocks on each side of X
-constexpr uint32_t kTmemCols = 512;  // two D slots of 256 columns
+constexpr uint32_t kTmemCols = 512;  // two D slots of 192 columns (allocations are powers of two)
 constexpr uint32_t kDSlots = 2;      // D slots in tensor memory
 constexpr uint32_t kWSlots = 3;      // W slots in shared memory
 constexpr uint32_t kWBytes = 128 * 128 * 2;     // one W_J in fp16: 16 K-chunks x 16 row groups x 128 B
 constexpr uint32_t kWLbo = 2048, kWSbo = 128;   // W: K-chunk stride, 8-row-group stride
-constexpr uint32_t kMaxSteps = 2 * (BN_MUL_MAX_LIMBS / 32 + 1);  // two tiles of at most mb + 1 steps
+constexpr uint32_t kTilesMax = (2 * BN_MUL_MAX_LIMBS / 32 + kTile - 1) / kTile;
+constexpr uint32_t kMaxSteps = kTilesMax * (BN_MUL_MAX_LIMBS / 32 + 1);  // tiles x at most mb + 1 steps
 constexpr uint64_t kWaitNs = 1000000000ull;     // 1 s per wait
 constexpr uint32_t kMinSmem = 116 * 1024;       // one CTA per SM (the whole tensor memory each)
 constexpr uint32_t kEpiBar = 1;                 // named barrier of the epilogue warps
@@ -156,8 +157,8 @@ __device__ __forceinline__ void build_w2(const uint32_t *braw, uint32_t J, uint3
 // exact in f32 and, having exponent 23, its bit pattern is 0x4b000000 + v.
 constexpr uint32_t kBiasBits = 0x4b000000u;
 constexpr uint16_t kF16_2048 = 0x6800u, kF16_4096 = 0x6c00u;
-constexpr uint32_t kCaBytes = 128 * 16 * 2, kCbBytes = 256 * 16 * 2;  // the bias MMA's A (M x 16) and B (N x 16)
-constexpr uint32_t kCbLbo = 4096;
+constexpr uint32_t kCaBytes = 128 * 16 * 2, kCbBytes = kTile * 16 * 2;  // the bias MMA's A (M x 16) and B (N x 16)
+constexpr uint32_t kCbLbo = kTile * 16;
 
 // Named barrier of the `count` threads of warps 1-16, OR-reducing `pred`.
 __device__ __forceinline__ bool epi_barrier_or(bool pred) {
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
     {  // the bias MMA's operands: A[r][0] = 2048, B[n][0] = 4096, zero elsewhere
         uint16_t *ca = reinterpret_cast<uint16_t *>(sm + g.ca_off), *cb = reinterpret_cast<uint16_t *>(sm + g.cb_off);
         for (uint32_t x = tid; x < kCaBytes / 2; x += kThreads) ca[x] = (x % 8 == 0 && x < 128 * 8) ? kF16_2048 : 0;
-        for (uint32_t x = tid; x < kCbBytes / 2; x += kThreads) cb[x] = (x % 8 == 0 && x < 256 * 8) ? kF16_4096 : 0;
+        for (uint32_t x = tid; x < kCbBytes / 2; x += kThreads) cb[x] = (x % 8 == 0 && x < kTile * 8) ? kF16_4096 : 0;
         tc::fence_proxy_async();
     }
     if (tid == 0) {
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
                 tc::fence_after_sync();
                 const Step st = step_unpack(sched[i]);
                 const uint32_t idesc = tc::idesc_f16_f32(128, 32u * (st.chi - st.clo));
-                // padded block of D column 0: s - J with s = 256 t + 32 clo
+                // padded block of D column 0: s - J with s = kTile t + 32 clo
                 const uint32_t i0 = kTile * st.t + 32 * st.clo + kPad - st.J;
                 const uint32_t dt = tbase + kTile * d + 32 * st.clo;
                 const uint64_t bd = tc::smem_desc(x_s + i0 * 16, g.xs, 128), bstep = (2 * g.xs) >> 4;
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
             }
         } else {
             // epilogue: each finished D into the integer column sums of its tile
-            // (the 4 warps of lane group lq own chunks 2m, 2m + 1, m = 0..3)
+            // (the 3 warps of lane group lq own chunks 2m, 2m + 1, m = 0..2)
             const uint32_t m = (warp - 1 - kBuildWarps) >> 2;
             uint32_t acc[2][32];
 #pragma unroll
