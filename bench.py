@@ -66,8 +66,17 @@ class Op:
 
 
 OPCODES = {"add": lambda bn: bn.BN_OP_ADD, "quad": lambda bn: bn.BN_OP_MUL_QUAD,
+           "quadtc": lambda bn: bn.BN_OP_MUL_QUAD_TC,
            "ntt64": lambda bn: bn.BN_OP_MUL_NTT64, "crt": lambda bn: bn.BN_OP_MUL_NTT_CRT,
            "ntt3": lambda bn: bn.BN_OP_MUL_NTT3}
+
+# The schoolbook product runs on the integer pipes below this size and on the
+# tensor cores (byte digits, exact f32 sums) from it up, where that kernel is
+# the faster schoolbook on GB300; both compute every word product.
+TC_MIN_BITS = 32768
+# fp16-equivalent FLOP of one 32x32-bit word product on the tensor cores:
+# 16 byte products, 2 FLOP each.
+TC_FLOP_PER_WORD_PRODUCT = 32
 
 
 def ntt_lengths(n: int):
@@ -79,7 +88,7 @@ def ntt_lengths(n: int):
     return n64, ncrt, modmuls(n64), 2 * modmuls(ncrt)
 
 
-def build_ops(quick: bool = False):
+def build_ops(quick: bool = False, integer_schoolbook: bool = False):
     pts = workloads.sweep_points()
     if quick:
         pts = [p for p in pts if p.bits in (1024, 32768, 262144)]
@@ -88,8 +97,9 @@ def build_ops(quick: bool = False):
         n = p.limbs
         ops.append(Op("add", p.bits, n, n, p.batch, p.seed, mults=0,
                       bytes=4 * (3 * n + 1) * p.batch))
-        ops.append(Op("quad", p.bits, n, n, p.batch, p.seed, mults=p.batch,
-                      bytes=4 * 4 * n * p.batch, prods=n * n * p.batch))
+        tc = p.bits >= TC_MIN_BITS and not integer_schoolbook
+        ops.append(Op("quadtc" if tc else "quad", p.bits, n, n, p.batch, p.seed,
+                      mults=p.batch, bytes=4 * 4 * n * p.batch, prods=n * n * p.batch))
     for p in pts:
         if p.bits not in workloads.NTT_BITS:
             continue
@@ -111,7 +121,8 @@ def build_ops(quick: bool = False):
 def workload_config(ops, world: int):
     bits = sorted({o.bits for o in ops})
     return {
-        "workload": "size sweep 1K-256K bits: add + schoolbook mul at 9 sizes, NTT mul "
+        "workload": "size sweep 1K-256K bits: add + schoolbook mul at 9 sizes (integer-pipe "
+                    "kernel below 32K bits, tensor-core kernel from 32K bits), NTT mul "
                     "(1x64-bit prime/16-bit digits, 2-prime CRT/32-bit digits and 3x32-bit "
                     "primes/32-bit digits) at 16K-256K; 64 MiB of u32 operand limbs per side "
                     "per size",
@@ -241,6 +252,19 @@ def kernel_traffic(op_label: str):
     return entry["dram_bytes"]
 
 
+def read_tensor_peak():
+    """Dense bf16 TFLOP/s sustained over a long run (the figure for a kernel
+    timed inside a long step); fp16 has the same nominal tensor rate."""
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        try:
+            d = json.loads(p.read_text())
+            return float(d["bf16_tflops_sustained"]), "measured (cuBLAS bf16, sustained)"
+        except (ValueError, KeyError):
+            pass
+    return 1700.0, "fallback (sustained)"
+
+
 def read_measured_peaks():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
@@ -259,7 +283,7 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device(f"cuda:{local_rank}")
     torch.cuda.set_device(dev)
     bn.load()
-    ops = build_ops(args.quick)
+    ops = build_ops(args.quick, args.integer_schoolbook)
     if args.only:
         keep = set(args.only.split(","))
         ops = [o for o in ops if o.name in keep or o.label in keep]
@@ -338,6 +362,8 @@ def run_gpu(args, rank, world, local_rank):
         return None
     # Per-GPU sections, on rank 0 only.
     isolated = run_isolated(args, torch, ops, plans, inputs, outs, stream, dev) if args.isolated_reps else None
+    schoolbook = (run_schoolbook_compare(args, torch, bn, ops, inputs, outs, stream, dev)
+                  if args.isolated_reps else None)
     fused = None
     if args.fused_reps > 0:
         fused = run_fused(args, torch, bn, dev, inputs, peak_info)
@@ -348,6 +374,7 @@ def run_gpu(args, rank, world, local_rank):
     if args.serve_requests > 0:
         serving = run_serving(args, torch, bn, dev, rank)
     hbm_peak, hbm_kind = read_measured_peaks()
+    tc_peak, tc_kind = read_tensor_peak()
     rows, rooflines = [], []
     for o in ops:
         ms = float(np.mean(o.times_ms))
@@ -358,6 +385,15 @@ def run_gpu(args, rank, world, local_rank):
             rooflines.append({"op": o.label, "bound": "hbm", "achieved": round(gbs, 1),
                               "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
                               "peak_kind": hbm_kind, "traffic": None})
+        elif o.name == "quadtc":
+            gp = o.prods / (ms * 1e-3) / 1e12
+            tf = TC_FLOP_PER_WORD_PRODUCT * gp
+            row.update(mults_per_s=o.batch / (ms * 1e-3), word_tprods=round(gp, 3), tflops=round(tf, 1))
+            rooflines.append({"op": o.label, "bound": "tensor", "achieved": round(tf, 1),
+                              "peak": tc_peak, "unit": "TFLOP/s", "frac": round(tf / tc_peak, 4),
+                              "peak_kind": tc_kind + "; FLOP = 2 per byte product, 16 byte products "
+                                           "per word product (the exact fp16 contraction's useful work)",
+                              "traffic": None})
         else:
             gp = o.prods / (ms * 1e-3) / 1e12
             peak_t = peak_info["peak_word_products_per_s"] / 1e12
@@ -394,6 +430,7 @@ def run_gpu(args, rank, world, local_rank):
         "imad_probe": peak_info, "clocks": clocks, "gpu_launches": gpu_launches,
         "e2e": e2e, "cpu_baseline": cpu, "impl": "ours", "skipped_ops": skipped,
         "mixed": mixed, "serving": serving, "fused": fused, "isolated": isolated,
+        "schoolbook": schoolbook,
     }
 
 
@@ -431,6 +468,40 @@ def run_isolated(args, torch, ops, plans, inputs, outs, stream, dev):
     return {"how": "median of %d launches, each after a read-only pass over 256 MiB (L2 holds "
                    "no dirty lines from other kernels)" % args.isolated_reps,
             "add_gbs": round(add_gbs, 1) if add_gbs else None, "ops": rows}
+
+
+def run_schoolbook_compare(args, torch, bn, ops, inputs, outs, stream, dev):
+    """The two schoolbook kernels side by side at the sizes where the step
+    uses the tensor-core one: each timed alone (median of the isolated
+    repetitions, L2 cleaned before each launch), word products per second."""
+    clean_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    rows = []
+    for o in ops:
+        if o.name != "quadtc":
+            continue
+        ta, tb = inputs[o.bits]
+        out = outs[(o.bits, o.nout)]
+        row = {"bits": o.bits, "batch": o.batch}
+        for name, opcode in (("integer", bn.BN_OP_MUL_QUAD), ("tensor", bn.BN_OP_MUL_QUAD_TC)):
+            with bn.Plan(opcode, o.na, o.nb, o.batch) as plan:
+                plan.execute(ta, tb, out=out, stream=stream)
+                ts = []
+                for _ in range(args.isolated_reps):
+                    clean_buf.sum(dtype=torch.int64)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    plan.execute(ta, tb, out=out, stream=stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+            ms = float(np.median(ts))
+            row[name + "_ms"] = round(ms, 4)
+            row[name + "_word_tprods"] = round(o.prods / (ms * 1e-3) / 1e12, 3)
+        row["speedup"] = round(row["integer_ms"] / row["tensor_ms"], 3)
+        rows.append(row)
+    bn.bn_tc_check()
+    return {"how": "each kernel alone, median of %d launches after a read-only pass over 256 MiB"
+                   % args.isolated_reps, "sizes": rows}
 
 
 def run_fused(args, torch, bn, dev, inputs, peak_info):
@@ -706,7 +777,7 @@ def run_reference(args, rank, world):
         return None
     import oracle
     oracle.build()
-    ops = build_ops(args.quick)
+    ops = build_ops(args.quick, getattr(args, "integer_schoolbook", False))
     threads = oracle.default_threads()
     counts, _ = sample_counts(ops, args.ref_step_budget, threads)
     for _ in range(args.warmup):
@@ -773,6 +844,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="3 sizes only (smoke runs)")
     ap.add_argument("--only", default="", help="comma list of op names/labels to keep")
+    ap.add_argument("--integer-schoolbook", action="store_true",
+                    help="the integer-pipe schoolbook at every size (for profiling that kernel)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-step-budget", type=float, default=4.0)
