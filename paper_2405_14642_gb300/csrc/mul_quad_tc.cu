@@ -17,15 +17,21 @@
 // column sums (below 2^31: no rounding anywhere); the column sums are folded
 // into limbs by the transform products' normalisation (carry scan included).
 //
-// Per CTA and instance: X is staged once in shared memory as fp16 in the
-// tensor core's core-matrix layout (the longer operand, with 32 zero blocks on
-// each side); b stays as raw bytes.  The output is processed in tiles of 128
-// blocks, each tile in steps J.  Three roles run as a pipeline linked by
-// mbarriers: four warps build W_J (one row per thread) into one of four W
-// slots in tensor memory, one thread issues the step's 8 MMAs of K = 16 into
-// one of two D slots and commits them, and eight warps (two per group of 32
-// lanes) add each finished D into their integer column sums and publish them
-// at the end of the tile.
+// Per CTA (one per SM, persistent over the products) and product: the longer
+// operand is staged in shared memory as fp16 in the tensor core's core-matrix
+// layout (X, with 32 zero blocks on each side), the shorter one as raw bytes.
+// The output is processed in tiles of 192 blocks (the MMA's N), each tile in
+// steps J, and three roles form a pipeline linked by mbarriers:
+//  * warps 1-7 build W_J in shared memory (fp16, the MMA's A operand) into one
+//    of three slots;
+//  * warp 0 issues each step's MMAs into one of two 192-column D slots in
+//    tensor memory: first a bias MMA (2048 x 4096 into every element, so D
+//    starts at 2^23), then 8 MMAs of K = 16 over the block's 128 bytes;
+//  * warps 8-19 read D: D = 2^23 + v with v < 2^23, so its bit pattern minus
+//    0x4b000000 is v, which they add into per-thread integer column sums
+//    (three warps per group of 32 lanes, two 32-column chunks each) and
+//    publish to a per-CTA scratch row at the end of the tile.
+// Every wait is bounded; a timeout raises a device flag (bn_tc_check).
 #include <cuda_runtime.h>
 
 #include <new>
