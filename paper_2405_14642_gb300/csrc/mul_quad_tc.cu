@@ -20,16 +20,16 @@
 // Per CTA (one per SM, persistent over the products) and product: the longer
 // operand is staged in shared memory as fp16 in the tensor core's core-matrix
 // layout (X, with 32 zero blocks on each side), the shorter one as raw bytes.
-// The output is processed in tiles of 192 blocks (the MMA's N), each tile in
+// The output is processed in tiles of 256 blocks (the MMA's N), each tile in
 // steps J, and three roles form a pipeline linked by mbarriers:
 //  * warps 1-7 build W_J in shared memory (fp16, the MMA's A operand) into one
 //    of three slots;
-//  * warp 0 issues each step's MMAs into one of two 192-column D slots in
+//  * warp 0 issues each step's MMAs into one of two 256-column D slots in
 //    tensor memory: first a bias MMA (2048 x 4096 into every element, so D
 //    starts at 2^23), then 8 MMAs of K = 16 over the block's 128 bytes;
-//  * warps 8-19 read D: D = 2^23 + v with v < 2^23, so its bit pattern minus
+//  * warps 8-23 read D: D = 2^23 + v with v < 2^23, so its bit pattern minus
 //    0x4b000000 is v, which they add into per-thread integer column sums
-//    (three warps per group of 32 lanes, two 32-column chunks each) and
+//    (four warps per group of 32 lanes, two 32-column chunks each) and
 //    publish to a per-CTA scratch row at the end of the tile.
 // Every wait is bounded; a timeout raises a device flag (bn_tc_check).
 #include <cuda_runtime.h>
@@ -46,13 +46,13 @@ __device__ uint32_t g_tc_fault;  // set when an MMA wait timed out
 
 namespace {
 
-constexpr uint32_t kThreads = 640;   // warp 0 issues the MMAs, warps 1-7 build W, warps 8-19 read D
+constexpr uint32_t kThreads = 768;   // warp 0 issues the MMAs, warps 1-7 build W, warps 8-23 read D
 constexpr uint32_t kBuildWarps = 7;
-constexpr uint32_t kEpiWarps = 12;   // three per group of 32 tensor-memory lanes, two D chunks each
+constexpr uint32_t kEpiWarps = 16;   // four per group of 32 tensor-memory lanes, two D chunks each
 constexpr uint32_t kBlk = 128;       // bytes per block: rows of W, K of a step
-constexpr uint32_t kTile = 192;      // output blocks per tile (D columns, the MMA's N)
+constexpr uint32_t kTile = 256;      // output blocks per tile (D columns, the MMA's N)
 constexpr uint32_t kPad = 32;        // zero blocks on each side of X
-constexpr uint32_t kTmemCols = 512;  // two D slots of 192 columns (allocations are powers of two)
+constexpr uint32_t kTmemCols = 512;  // two D slots of 256 columns
 constexpr uint32_t kDSlots = 2;      // D slots in tensor memory
 constexpr uint32_t kWSlots = 3;      // W slots in shared memory
 constexpr uint32_t kWBytes = 128 * 128 * 2;     // one W_J in fp16: 16 K-chunks x 16 row groups x 128 B
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
             }
         } else {
             // epilogue: each finished D into the integer column sums of its tile
-            // (the 3 warps of lane group lq own chunks 2m, 2m + 1, m = 0..2)
+            // (the 4 warps of lane group lq own chunks 2m, 2m + 1, m = 0..3)
             const uint32_t m = (warp - 1 - kBuildWarps) >> 2;
             uint32_t acc[2][32];
 #pragma unroll
@@ -326,11 +326,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
                     const uint32_t ch = 2 * m + c;
                     if (ch >= st.clo && ch < st.chi) {
 #pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            uint32_t v[16];
-                            tc::tmem_ld16(tbase + lane_off + kTile * d + 32 * ch + 16 * hh, v);
+                        for (int hh = 0; hh < 4; ++hh) {  // 8 columns at a time: the register cap is 80
+                            uint32_t v[8];
+                            tc::tmem_ld8(tbase + lane_off + kTile * d + 32 * ch + 8 * hh, v);
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) acc[c][16 * hh + j] += v[j] - kBiasBits;
+                            for (int j = 0; j < 8; ++j) acc[c][8 * hh + j] += v[j] - kBiasBits;
                         }
                     }
                 }
