@@ -189,6 +189,14 @@ bn_status bn_mul_quad_tc(const uint32_t *a, const uint32_t *b, uint32_t *c,
  * call, BN_ECUDA on a CUDA error, else BN_OK. */
 bn_status bn_tc_check(void);
 
+/* Diagnostic of the bounded waits above: launches one small kernel whose
+ * mbarrier wait has no arrival coming, so it must give up after limit_us
+ * microseconds (a second waiter watching the shared abort flag must give up
+ * with it), and reads the device flag.  Returns BN_ETIMEOUT when the waits
+ * gave up as designed (the flag is left clear), BN_OK if they did not,
+ * BN_ECUDA on a CUDA error.  Synchronises the device. */
+bn_status bn_tc_wait_selftest(uint32_t limit_us);
+
 /* One-shot BN_OP_MUL_AUTO: c = a * b by the fastest product for the sizes
  * (schoolbook for small operands, the three-prime transform from about 8K
  * bits on GB300); arguments, layout, result and errors as bn_mul_quad. */

@@ -105,6 +105,7 @@ def load(build_if_missing: bool = False):
         "bn_mul": ([u32p, u32p, u32p, u32, u32, u64, vp], st),
         "bn_mul_quad_tc": ([u32p, u32p, u32p, u32, u32, u64, vp], st),
         "bn_tc_check": ([], st),
+        "bn_tc_wait_selftest": ([u32], st),
         "bn_plan_op": ([vp], ctypes.c_int),
         "bn_status_str": ([ctypes.c_int], ctypes.c_char_p),
         "bn_last_error": ([], ctypes.c_char_p),
@@ -257,6 +258,12 @@ def bn_tc_check():
     """Synchronise the device and raise BnError (BN_ETIMEOUT) if a tensor-core
     kernel gave up waiting for its MMAs since the last check."""
     _check(load().bn_tc_check(), "bn_tc_check")
+
+
+def bn_tc_wait_selftest(limit_us: int = 20000) -> int:
+    """Run the bounded-wait diagnostic; returns the bn_status (BN_ETIMEOUT when
+    the waits gave up as designed)."""
+    return load().bn_tc_wait_selftest(int(limit_us))
 
 
 def _same_length(name, a, b, out, stream):

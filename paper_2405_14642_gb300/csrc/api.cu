@@ -373,6 +373,19 @@ bn_status bn_tc_check(void) {
     return BN_OK;
 }
 
+bn_status bn_tc_wait_selftest(uint32_t limit_us) {
+    uint32_t flag = 0;
+    cudaError_t e = bn::tc_fault_take(&flag);  // start from a clear flag
+    if (e == cudaSuccess) e = bn::tc_wait_selftest(limit_us);
+    if (e == cudaSuccess) e = bn::tc_fault_take(&flag);
+    if (e != cudaSuccess) return cuda_status("tensor-core wait self-test", e);
+    if (!flag) {
+        set_error_text("the self-test's wait did not give up");
+        return BN_OK;
+    }
+    return BN_ETIMEOUT;
+}
+
 bn_status bn_mul(const uint32_t *a, const uint32_t *b, uint32_t *c, uint32_t na, uint32_t nb,
                  uint64_t batch, void *stream) {
     return one_shot(BN_OP_MUL_AUTO, a, b, c, na, nb, batch, stream);

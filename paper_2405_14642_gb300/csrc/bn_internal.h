@@ -127,5 +127,7 @@ cudaError_t quad_tc_launch(QuadTcPlan *p, const uint32_t *a, const uint32_t *b, 
 size_t quad_tc_scratch_bytes(const QuadTcPlan *p);
 // Reads and clears the tensor-core kernels' timeout flag (synchronises the device).
 cudaError_t tc_fault_take(uint32_t *flag);
+// One launch whose mbarrier wait must time out after limit_us (raises the flag).
+cudaError_t tc_wait_selftest(uint32_t limit_us);
 
 }  // namespace bn

@@ -487,6 +487,36 @@ cudaError_t quad_tc_launch(QuadTcPlan *p, const uint32_t *a, const uint32_t *b, 
     return cudaGetLastError();
 }
 
+namespace {
+
+// The bounded-wait machinery on its own: warp 0 waits for an mbarrier that
+// nobody arrives on, gives up after limit_ns and raises the abort flag; warp 1
+// waits on it with a 10 s limit but watches the abort flag, so it gives up as
+// soon as warp 0 does.  Either giving up raises the device flag.
+__global__ void k_tc_wait_selftest(uint64_t limit_ns) {
+    __shared__ uint64_t bar;
+    __shared__ uint32_t abortf;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        abortf = 0;
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    const bool w0 = threadIdx.x < 32;
+    const bool ok = tc::mbar_wait(&bar, 0, w0 ? limit_ns : 10000000000ull, &abortf);
+    if (!__all_sync(FULL_MASK, ok)) {
+        if (w0) *(volatile uint32_t *)&abortf = 1;
+        if ((threadIdx.x & 31) == 0) atomicOr(&g_tc_fault, 1u);
+    }
+}
+
+}  // namespace
+
+cudaError_t tc_wait_selftest(uint32_t limit_us) {
+    k_tc_wait_selftest<<<1, 64>>>(1000ull * limit_us);
+    return cudaGetLastError();
+}
+
 // Reads and clears the flag that a tensor-core kernel sets when an MMA wait
 // timed out (synchronises the device).
 cudaError_t tc_fault_take(uint32_t *flag) {

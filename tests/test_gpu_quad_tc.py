@@ -95,3 +95,17 @@ def test_quad_tc_errors():
     empty = torch.zeros((0, 16), dtype=torch.int32, device="cuda")
     assert bn.bn_mul_quad_tc(empty, empty).shape == (0, 32)
     bn.bn_tc_check()
+
+
+def test_tc_bounded_wait_gives_up():
+    """A wait with no arrival coming gives up after its limit, a second waiter
+    watching the abort flag gives up with it, and the device flag reports it."""
+    import time
+    torch_cuda()
+    import paper_2405_14642_gb300 as bn
+    t0 = time.perf_counter()
+    status = bn.bn_tc_wait_selftest(20000)  # 20 ms
+    elapsed = time.perf_counter() - t0
+    assert status == bn.BN_ETIMEOUT
+    assert elapsed < 5.0  # not the second waiter's own 10 s limit
+    bn.bn_tc_check()      # the self-test leaves the flag clear
