@@ -21,7 +21,17 @@
 // operand is staged in shared memory as fp16 in the tensor core's core-matrix
 // layout (X, with 32 zero blocks on each side), the shorter one as raw bytes.
 // The output is processed in tiles of 256 blocks (the MMA's N), each tile in
-// steps J, and three roles form a pipeline linked by mbarriers:
+// steps J.  When the output is wider than one tile (a longer than 128 blocks,
+// at most 256), D is instead circular: column n (0 <= n < ma) holds output
+// block n while J <= n and block n + ma afterwards, so one D of ma columns
+// covers every output block and each W_J is built and multiplied once.  X is
+// then staged twice in a row (XX[I] = a-block I mod ma), so that step J's
+// columns are the window of XX starting at block ma - J: one MMA per K-chunk.
+// Once step J is added, block J is complete and the epilogue stores column J
+// and starts it over as block J + ma.  (To fit XX, that form keeps two W
+// slots, no step table, and the bias MMA's constant operands as one core
+// matrix each, repeated over the rows by a zero stride.)  Three roles form a
+// pipeline linked by mbarriers:
 //  * warps 1-7 build W_J in shared memory (fp16, the MMA's A operand) into one
 //    of three slots;
 //  * warp 0 issues each step's MMAs into one of two 256-column D slots in
@@ -67,6 +77,7 @@ struct TcArgs {
     const uint32_t *a, *b;  // na >= nb (the host orders the operands)
     uint32_t *c;
     uint32_t na, nb, nout, ma, mb, tiles;
+    uint32_t circ, ma16;      // circular D (one tile of ma columns); ma rounded up to 16
     uint64_t batch;
     uint32_t *scratch;        // per CTA: 128 (ma + mb) byte-column sums
     uint64_t scratch_stride;  // words per CTA
@@ -103,6 +114,16 @@ __device__ uint32_t make_schedule(const TcArgs &g, uint32_t *sched) {
         }
     }
     return n;
+}
+
+// Step i of a product: the table's entry, or for the circular form J = i
+// (0..mb: block mb holds the top of b's last block shifted up) over all of D.
+template <bool CIRC>
+__device__ __forceinline__ Step step_at(const TcArgs &g, const uint32_t *sched, uint32_t i) {
+    if constexpr (CIRC)
+        return Step{i, 0, 0, (g.ma + 31) >> 5, i == g.mb ? 1u : 0u};
+    else
+        return step_unpack(sched[i]);
 }
 
 // Row r of W_J, words 16 u .. 16 u + 15 (K-chunks 4 u .. 4 u + 3), into the
@@ -165,8 +186,9 @@ constexpr uint32_t kBiasBits = 0x4b000000u;
 constexpr uint16_t kF16_2048 = 0x6800u, kF16_4096 = 0x6c00u;
 constexpr uint32_t kCaBytes = 128 * 16 * 2, kCbBytes = kTile * 16 * 2;  // the bias MMA's A (M x 16) and B (N x 16)
 constexpr uint32_t kCbLbo = kTile * 16;
+constexpr uint32_t kBiasTiny = 256;  // circular form: each bias operand as one core matrix per K-chunk
 
-// Named barrier of the `count` threads of warps 1-16, OR-reducing `pred`.
+// Named barrier of the epilogue warps, OR-reducing `pred`.
 __device__ __forceinline__ bool epi_barrier_or(bool pred) {
     uint32_t r;
     asm volatile(
@@ -180,6 +202,9 @@ __device__ __forceinline__ bool epi_barrier_or(bool pred) {
     return r != 0;
 }
 
+// CIRC: the circular D (outputs wider than one tile); a separate instantiation
+// so that the one-tile form keeps its own register allocation.
+template <bool CIRC>
 __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *X = sm;  // X and the W slots double as the normalisation's staging row
@@ -188,8 +213,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
     uint32_t *sched = reinterpret_cast<uint32_t *>(sm + g.sched_off);
     uint64_t *spill = reinterpret_cast<uint64_t *>(sm + g.spill_off);
     uint32_t *flags = reinterpret_cast<uint32_t *>(sm + g.flags_off);
-    uint64_t *wfull = reinterpret_cast<uint64_t *>(sm + g.bar_off);  // [kWSlots], one arrival per builder warp
-    uint64_t *wempty = wfull + kWSlots;                                 // [kWSlots], MMA commits
+    constexpr uint32_t kWS = CIRC ? 2 : kWSlots;                       // W slots in use
+    uint64_t *wfull = reinterpret_cast<uint64_t *>(sm + g.bar_off);  // [kWS], one arrival per builder warp
+    uint64_t *wempty = wfull + kWSlots;                                 // [kWS], MMA commits
     uint64_t *dfull = wempty + kWSlots;                                 // [kDSlots], MMA commits
     uint64_t *dempty = dfull + kDSlots;                                 // [kDSlots], one arrival per warp
     uint32_t *slot = reinterpret_cast<uint32_t *>(dempty + kDSlots);
@@ -199,15 +225,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lq = warp & 3;  // the tensor-memory lanes this warp may move
     if (warp == 0) tc::tmem_alloc(slot, kTmemCols);
-    if (tid == 32) *nsteps = make_schedule(g, sched);
+    if (tid == 32) *nsteps = CIRC ? g.mb + 1 : make_schedule(g, sched);
     {  // the bias MMA's operands: A[r][0] = 2048, B[n][0] = 4096, zero elsewhere
         uint16_t *ca = reinterpret_cast<uint16_t *>(sm + g.ca_off), *cb = reinterpret_cast<uint16_t *>(sm + g.cb_off);
-        for (uint32_t x = tid; x < kCaBytes / 2; x += kThreads) ca[x] = (x % 8 == 0 && x < 128 * 8) ? kF16_2048 : 0;
-        for (uint32_t x = tid; x < kCbBytes / 2; x += kThreads) cb[x] = (x % 8 == 0 && x < kTile * 8) ? kF16_4096 : 0;
+        if constexpr (CIRC) {  // one core matrix per K-chunk: 8 rows, then 128 zero bytes
+            if (tid < kBiasTiny / 2) {
+                ca[tid] = (tid % 8 == 0 && tid < 64) ? kF16_2048 : 0;
+                cb[tid] = (tid % 8 == 0 && tid < 64) ? kF16_4096 : 0;
+            }
+        } else {
+            for (uint32_t x = tid; x < kCaBytes / 2; x += kThreads) ca[x] = (x % 8 == 0 && x < 128 * 8) ? kF16_2048 : 0;
+            for (uint32_t x = tid; x < kCbBytes / 2; x += kThreads) cb[x] = (x % 8 == 0 && x < kTile * 8) ? kF16_4096 : 0;
+        }
         tc::fence_proxy_async();
     }
     if (tid == 0) {
-        for (uint32_t k = 0; k < kWSlots; ++k) {
+        for (uint32_t k = 0; k < kWS; ++k) {
             tc::mbar_init(&wfull[k], kBuildWarps);
             tc::mbar_init(&wempty[k], 1);
         }
@@ -238,12 +271,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
             const uint32_t v = w0 + 1 < g.na ? __ldg(arow + w0 + 1) : 0u;
             const uint4 f = make_uint4(tc::bytes01_f16x2(u), tc::bytes23_f16x2(u), tc::bytes01_f16x2(v),
                                        tc::bytes23_f16x2(v));
-            *reinterpret_cast<uint4 *>(X + q * g.xs + (I + kPad) * 16) = f;
+            if constexpr (CIRC) {  // XX: blocks I and I + ma
+                *reinterpret_cast<uint4 *>(X + q * g.xs + I * 16) = f;
+                *reinterpret_cast<uint4 *>(X + q * g.xs + (I + g.ma) * 16) = f;
+            } else {
+                *reinterpret_cast<uint4 *>(X + q * g.xs + (I + kPad) * 16) = f;
+            }
         }
-        for (uint32_t x = tid; x < 16 * 2 * kPad; x += kThreads) {
-            const uint32_t q = x / (2 * kPad), p = x % (2 * kPad);
-            const uint32_t I = p < kPad ? p : g.ma + p;  // padded index (kPad offset included)
-            *reinterpret_cast<uint4 *>(X + q * g.xs + I * 16) = make_uint4(0, 0, 0, 0);
+        if constexpr (CIRC) {  // zero blocks after XX up to D's width rounded to 16
+            const uint32_t zb = g.ma16 - g.ma;
+            for (uint32_t x = tid; x < 16 * zb; x += kThreads)
+                *reinterpret_cast<uint4 *>(X + (x / zb) * g.xs + (2 * g.ma + x % zb) * 16) = make_uint4(0, 0, 0, 0);
+        } else {
+            for (uint32_t x = tid; x < 16 * 2 * kPad; x += kThreads) {
+                const uint32_t q = x / (2 * kPad), p = x % (2 * kPad);
+                const uint32_t I = p < kPad ? p : g.ma + p;  // padded index (kPad offset included)
+                *reinterpret_cast<uint4 *>(X + q * g.xs + I * 16) = make_uint4(0, 0, 0, 0);
+            }
         }
         const uint32_t bwords = 32 * (g.mb + 2) + 4;
         for (uint32_t x = tid; x < bwords; x += kThreads)
@@ -256,43 +300,63 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
             // they stay in uniform registers); one elected lane issues the 8
             // MMAs (K = 16 each) and commits them
             for (uint32_t i = 0; i < S; ++i, ++gs) {
-                const uint32_t k = gs % kWSlots, d = gs % kDSlots, ud = gs / kDSlots;
-                bool ok = tc::mbar_wait(&wfull[k], (gs / kWSlots) & 1u, kWaitNs, abortf);
+                const uint32_t k = gs % kWS, d = gs % kDSlots, ud = gs / kDSlots;
+                bool ok = tc::mbar_wait(&wfull[k], (gs / kWS) & 1u, kWaitNs, abortf);
                 if (ok && ud > 0) ok = tc::mbar_wait(&dempty[d], (ud - 1) & 1u, kWaitNs, abortf);
                 if (!__all_sync(FULL_MASK, ok)) {
                     *abortf = 1;
                     break;
                 }
                 tc::fence_after_sync();
-                const Step st = step_unpack(sched[i]);
-                const uint32_t idesc = tc::idesc_f16_f32(128, 32u * (st.chi - st.clo));
-                // padded block of D column 0: s - J with s = kTile t + 32 clo
-                const uint32_t i0 = kTile * st.t + 32 * st.clo + kPad - st.J;
-                const uint32_t dt = tbase + kTile * d + 32 * st.clo;
-                const uint64_t bd = tc::smem_desc(x_s + i0 * 16, g.xs, 128), bstep = (2 * g.xs) >> 4;
+                const Step st = step_at<CIRC>(g, sched, i);
+                const uint64_t bstep = (2 * g.xs) >> 4;
                 const uint64_t ad = tc::smem_desc(w_s + k * kWBytes, kWLbo, kWSbo), astep = (2 * kWLbo) >> 4;
                 const uint64_t cad = tc::smem_desc(x_s + g.ca_off, kWLbo, kWSbo), cbd = tc::smem_desc(x_s + g.cb_off, kCbLbo, 128);
-                if (tc::elect_one()) {
-                    tc::mma_f16_ss(dt, cad, cbd, idesc, 0);  // D = 2^23
+                if constexpr (CIRC) {
+                    // all of D: column n is XX block ma - J + n, i.e. a-block n - J
+                    // for n >= J and n - J + ma below (columns from ma on unused)
+                    const uint32_t dt = tbase + kTile * d;
+                    const uint32_t idesc = tc::idesc_f16_f32(128, g.ma16);
+                    const uint64_t bd = tc::smem_desc(x_s + (g.ma - st.J) * 16, g.xs, 128);
+                    // the bias operands' core matrix repeats over all row groups (stride 0)
+                    const uint64_t tad = tc::smem_desc(x_s + g.ca_off, 128, 0), tbd = tc::smem_desc(x_s + g.cb_off, 128, 0);
+                    if (tc::elect_one()) {
+                        tc::mma_f16_ss(dt, tad, tbd, idesc, 0);  // D = 2^23
 #pragma unroll
-                    for (uint32_t kk = 0; kk < 8; ++kk) tc::mma_f16_ss(dt, ad + kk * astep, bd + kk * bstep, idesc, 1);
-                    tc::mma_commit(&dfull[d]);
-                    tc::mma_commit(&wempty[k]);
+                        for (uint32_t kk = 0; kk < 8; ++kk)
+                            tc::mma_f16_ss(dt, ad + kk * astep, bd + kk * bstep, idesc, 1);
+                        tc::mma_commit(&dfull[d]);
+                        tc::mma_commit(&wempty[k]);
+                    }
+                } else {
+                    const uint32_t idesc = tc::idesc_f16_f32(128, 32u * (st.chi - st.clo));
+                    // padded block of D column 0: s - J with s = kTile t + 32 clo
+                    const uint32_t i0 = kTile * st.t + 32 * st.clo + kPad - st.J;
+                    const uint32_t dt = tbase + kTile * d + 32 * st.clo;
+                    const uint64_t bd = tc::smem_desc(x_s + i0 * 16, g.xs, 128);
+                    if (tc::elect_one()) {
+                        tc::mma_f16_ss(dt, cad, cbd, idesc, 0);  // D = 2^23
+#pragma unroll
+                        for (uint32_t kk = 0; kk < 8; ++kk)
+                            tc::mma_f16_ss(dt, ad + kk * astep, bd + kk * bstep, idesc, 1);
+                        tc::mma_commit(&dfull[d]);
+                        tc::mma_commit(&wempty[k]);
+                    }
                 }
                 __syncwarp();
             }
         } else if (warp <= kBuildWarps) {
             // builders: W of each step into a W slot once the MMA that last read
-            // it is done; the 512 quarter rows are spread over the 96 threads
+            // it is done; the 512 quarter rows are spread over the builder threads
             const uint32_t bt = tid - 32;
             for (uint32_t i = 0; i < S; ++i, ++gs) {
-                const uint32_t k = gs % kWSlots, use = gs / kWSlots;
+                const uint32_t k = gs % kWS, use = gs / kWS;
                 if (use > 0 &&
                     !__all_sync(FULL_MASK, tc::mbar_wait(&wempty[k], (use - 1) & 1u, kWaitNs, abortf))) {
                     *abortf = 1;
                     break;
                 }
-                const uint32_t J = sched[i] & 1023u;
+                const uint32_t J = step_at<CIRC>(g, sched, i).J;
                 uint8_t *wk = W + k * kWBytes;
                 uint32_t x = bt;
                 for (; x + 32 * kBuildWarps < 512; x += 64 * kBuildWarps) build_w2(braw, J, x, x + 32 * kBuildWarps, wk);
@@ -305,6 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
             // epilogue: each finished D into the integer column sums of its tile
             // (the 4 warps of lane group lq own chunks 2m, 2m + 1, m = 0..3)
             const uint32_t m = (warp - 1 - kBuildWarps) >> 2;
+            uint32_t *const colr = cols + 32 * lq + lane;  // this thread's row of every column block
             uint32_t acc[2][32];
 #pragma unroll
             for (int c = 0; c < 2; ++c)
@@ -320,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
                     break;
                 }
                 tc::fence_after_sync();
-                const Step st = step_unpack(sched[i]);
+                const Step st = step_at<CIRC>(g, sched, i);
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     const uint32_t ch = 2 * m + c;
@@ -337,14 +402,50 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&dempty[d]);
+                if (CIRC && !st.last) {
+                    // circular D: column J now holds all of block J; store it and
+                    // start the column over as block J + ma
+                    const uint32_t f = st.J - 64 * m;  // warp-uniform
+                    if (f < 64u) {
+                        switch (f) {
+#define BN_TC_FLUSH(x)                                    \
+    case x:                                               \
+        colr[kBlk * (64 * m + x)] = acc[x >> 5][x & 31];  \
+        acc[x >> 5][x & 31] = 0;                          \
+        break;
+                            BN_TC_FLUSH(0) BN_TC_FLUSH(1) BN_TC_FLUSH(2) BN_TC_FLUSH(3) BN_TC_FLUSH(4)
+                            BN_TC_FLUSH(5) BN_TC_FLUSH(6) BN_TC_FLUSH(7) BN_TC_FLUSH(8) BN_TC_FLUSH(9)
+                            BN_TC_FLUSH(10) BN_TC_FLUSH(11) BN_TC_FLUSH(12) BN_TC_FLUSH(13) BN_TC_FLUSH(14)
+                            BN_TC_FLUSH(15) BN_TC_FLUSH(16) BN_TC_FLUSH(17) BN_TC_FLUSH(18) BN_TC_FLUSH(19)
+                            BN_TC_FLUSH(20) BN_TC_FLUSH(21) BN_TC_FLUSH(22) BN_TC_FLUSH(23) BN_TC_FLUSH(24)
+                            BN_TC_FLUSH(25) BN_TC_FLUSH(26) BN_TC_FLUSH(27) BN_TC_FLUSH(28) BN_TC_FLUSH(29)
+                            BN_TC_FLUSH(30) BN_TC_FLUSH(31) BN_TC_FLUSH(32) BN_TC_FLUSH(33) BN_TC_FLUSH(34)
+                            BN_TC_FLUSH(35) BN_TC_FLUSH(36) BN_TC_FLUSH(37) BN_TC_FLUSH(38) BN_TC_FLUSH(39)
+                            BN_TC_FLUSH(40) BN_TC_FLUSH(41) BN_TC_FLUSH(42) BN_TC_FLUSH(43) BN_TC_FLUSH(44)
+                            BN_TC_FLUSH(45) BN_TC_FLUSH(46) BN_TC_FLUSH(47) BN_TC_FLUSH(48) BN_TC_FLUSH(49)
+                            BN_TC_FLUSH(50) BN_TC_FLUSH(51) BN_TC_FLUSH(52) BN_TC_FLUSH(53) BN_TC_FLUSH(54)
+                            BN_TC_FLUSH(55) BN_TC_FLUSH(56) BN_TC_FLUSH(57) BN_TC_FLUSH(58) BN_TC_FLUSH(59)
+                            BN_TC_FLUSH(60) BN_TC_FLUSH(61) BN_TC_FLUSH(62) BN_TC_FLUSH(63)
+#undef BN_TC_FLUSH
+                        }
+                    }
+                }
                 if (st.last) {  // tile complete: publish its column sums
-                    const uint32_t s0 = kTile * st.t, r = 32 * lq + lane;
+                    const uint32_t s0 = kTile * st.t;
 #pragma unroll
                     for (int c = 0; c < 2; ++c)
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
-                            const uint32_t s = s0 + 32 * (2 * m + c) + j;
-                            if (s < out_blocks) cols[kBlk * s + r] = acc[c][j];
+                            const uint32_t n = 32 * (2 * m + c) + j;
+                            if constexpr (CIRC) {
+                                // columns n < mb moved on to block n + ma after step n (the
+                                // flag is read at run time here: it compiles without spills)
+                                const uint32_t s = g.circ ? (n < g.mb ? n + g.ma : n) : s0 + n;
+                                if (s < out_blocks && (!g.circ || n < g.ma)) colr[kBlk * s] = acc[c][j];
+                            } else {
+                                const uint32_t s = s0 + n;
+                                if (s < out_blocks) colr[kBlk * s] = acc[c][j];
+                            }
                             acc[c][j] = 0;
                         }
                 }
@@ -387,23 +488,24 @@ TcGeometry geometry(uint32_t na, uint32_t nb) {
     q.ma = (q.na + 31) / 32;
     q.mb = (q.nb + 31) / 32;
     q.tiles = (q.ma + q.mb + kTile - 1) / kTile;
-    q.xs = (q.ma + 2 * kPad) * 16;
+    const bool circ = q.tiles > 1;  // circular D: XX of 2 ma blocks rounded up to 16, two W slots, no bias MMA
+    q.xs = (circ ? 2 * q.ma + ((q.ma + 15) & ~15u) - q.ma : q.ma + 2 * kPad) * 16;
     const uint32_t nout = q.na + q.nb;
     const uint32_t stage_bytes = 4 * ((nout - 1) + ((nout - 1) >> 4) + 1);
     q.w_off = 16 * q.xs;  // a multiple of 16
     q.spill_off = q.w_off;  // the normalisation's spill words reuse the W slots
-    uint32_t off = q.w_off + kWSlots * kWBytes;
+    uint32_t off = q.w_off + (circ ? 2 : kWSlots) * kWBytes;
     if (off < stage_bytes) off = stage_bytes;
     off = (off + 15) & ~15u;
     q.ca_off = off;
-    off += kCaBytes;
+    off += circ ? kBiasTiny : kCaBytes;
     q.cb_off = off;
-    off += kCbBytes;
+    off += circ ? kBiasTiny : kCbBytes;
     q.braw_off = off;
     off += 4 * (32 * (q.mb + 2) + 4);
     off = (off + 15) & ~15u;
     q.sched_off = off;
-    off += 4 * kMaxSteps;
+    if (!circ) off += 4 * kMaxSteps;
     q.flags_off = off;
     off += 4 * (kThreads / 32);
     q.bar_off = (off + 15) & ~15u;
@@ -432,7 +534,8 @@ bn_status quad_tc_create(QuadTcPlan **out, uint32_t na, uint32_t nb) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc<false>);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc<true>);
     if (e != cudaSuccess) {
         delete p;
         return BN_ECUDA;
@@ -470,6 +573,8 @@ cudaError_t quad_tc_launch(QuadTcPlan *p, const uint32_t *a, const uint32_t *b, 
     g.ma = q.ma;
     g.mb = q.mb;
     g.tiles = q.tiles;
+    g.circ = q.tiles > 1 ? 1u : 0u;
+    g.ma16 = (q.ma + 15) & ~15u;
     g.batch = batch;
     g.scratch = p->scratch;
     g.scratch_stride = p->stride;
@@ -483,7 +588,10 @@ cudaError_t quad_tc_launch(QuadTcPlan *p, const uint32_t *a, const uint32_t *b, 
     g.flags_off = q.flags_off;
     g.bar_off = q.bar_off;
     const uint32_t grid = batch < p->ctas ? (uint32_t)batch : p->ctas;
-    k_mul_quad_tc<<<grid, kThreads, q.smem, st>>>(g);
+    if (g.circ)
+        k_mul_quad_tc<true><<<grid, kThreads, q.smem, st>>>(g);
+    else
+        k_mul_quad_tc<false><<<grid, kThreads, q.smem, st>>>(g);
     return cudaGetLastError();
 }
 

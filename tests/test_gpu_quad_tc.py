@@ -9,11 +9,15 @@ from paper_2405_14642_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
 
-# 32 limbs = one 128-byte block; 4096 limbs of output = one tile of 128 blocks.
+# 32 limbs = one 128-byte block; 8192 limbs of output = one tile of 256 blocks.
+# Outputs wider than one tile use the circular D (the longer operand's blocks
+# as D's columns): (4097, 4097) onwards, incl. lengths that are not a multiple
+# of 16 blocks (4500: 141 blocks, 6000: 188, 8000: 250) and a one-block operand.
 SHAPES = [(1, 1), (1, 2), (2, 1), (3, 5), (31, 33), (32, 32), (33, 31), (64, 64), (100, 3),
           (3, 100), (128, 128), (129, 130), (500, 20), (777, 1000), (1024, 1024), (2047, 2049),
           (2048, 2048), (4096, 4096), (4097, 4000), (5000, 3001), (8192, 8192), (8192, 1),
-          (1, 8192), (8192, 100), (100, 8192)]
+          (1, 8192), (8192, 100), (100, 8192), (4097, 4097), (4500, 4500), (6000, 5000),
+          (8000, 300), (8191, 8191), (8192, 4097), (7777, 8000), (8192, 32), (8192, 33)]
 
 
 def _tc(a, b):
