@@ -6,41 +6,37 @@
 // is an exact fp16 integer, a byte product is below 2^16, and 128 of them sum
 // below 2^23, where f32 arithmetic is exact whatever the order of the sums.
 //
-// Cut both operands into blocks of 128 bytes (a: blocks I < ma, b: J < mb) and
-// let W_J be the 128 x 128 Toeplitz matrix W_J[r][c] = b-byte (128 J + r - c)
-// (zero outside b).  Byte column 128 s + r of the product is then
+// Cut both operands into blocks of 128 bytes (a, the longer: blocks I < ma;
+// b: J < mb) and let W_J be the 128 x 128 Toeplitz matrix W_J[r][c] =
+// b-byte (128 J + r - c) (zero outside b).  Byte column 128 s + r of the
+// product is then
 //     sum_J  sum_c  W_J[r][c] * a-byte (128 (s - J) + c),
-// so for each J the contribution to the output blocks s is D_J = W_J X^T,
-// where row I of X is block I of a: one MMA chain with M = 128 (r), K = 128
-// (c) and N = the output blocks s with 0 <= s - J < ma.  D_J is read from
-// tensor memory, turned into integers and added into per-thread integer
-// column sums (below 2^31: no rounding anywhere); the column sums are folded
-// into limbs by the transform products' normalisation (carry scan included).
+// J = 0..mb (block mb carries the top of b's last block).  Step J computes
+// D_J = W_J X^T, one MMA chain with M = 128 (r), K = 128 (c) and N = ma:
+// D's columns are circular, column n holding output block n while J <= n and
+// block n + ma afterwards, so that D_J's column n is a-block n - J, or
+// n - J + ma below J.  X is staged twice in a row (XX[I] = a-block I mod ma),
+// which makes step J's B operand the window of XX starting at block ma - J.
+// D_J is read from tensor memory, turned into integers and added into
+// per-thread integer column sums (below 2^31: no rounding anywhere); once step
+// J is added, column J holds all of block J, which is stored before the
+// column starts over as block J + ma.  The column sums are folded into limbs
+// by the transform products' normalisation (carry scan included).
 //
-// Per CTA (one per SM, persistent over the products) and product: the longer
-// operand is staged in shared memory as fp16 in the tensor core's core-matrix
-// layout (X, with 32 zero blocks on each side), the shorter one as raw bytes.
-// The output is processed in tiles of 256 blocks (the MMA's N), each tile in
-// steps J.  When the output is wider than one tile (a longer than 128 blocks,
-// at most 256), D is instead circular: column n (0 <= n < ma) holds output
-// block n while J <= n and block n + ma afterwards, so one D of ma columns
-// covers every output block and each W_J is built and multiplied once.  X is
-// then staged twice in a row (XX[I] = a-block I mod ma), so that step J's
-// columns are the window of XX starting at block ma - J: one MMA per K-chunk.
-// Once step J is added, block J is complete and the epilogue stores column J
-// and starts it over as block J + ma.  (To fit XX, that form keeps two W
-// slots, no step table, and the bias MMA's constant operands as one core
-// matrix each, repeated over the rows by a zero stride.)  Three roles form a
-// pipeline linked by mbarriers:
+// Per CTA (one per SM, persistent over the products) and product: XX in
+// shared memory as fp16 in the tensor core's core-matrix layout, b as raw
+// bytes.  Three roles form a pipeline linked by mbarriers:
 //  * warps 1-7 build W_J in shared memory (fp16, the MMA's A operand) into one
-//    of three slots;
-//  * warp 0 issues each step's MMAs into one of two 256-column D slots in
-//    tensor memory: first a bias MMA (2048 x 4096 into every element, so D
-//    starts at 2^23), then 8 MMAs of K = 16 over the block's 128 bytes;
+//    of two or three slots;
+//  * warp 0 issues each step's MMAs into a D slot in tensor memory (two of 256
+//    columns when ma > 128, else four of 128): first a bias MMA (2048 x 4096
+//    into every element, so D starts at 2^23; its constant operands are one
+//    core matrix each, repeated over the rows by a zero stride), then 8 MMAs
+//    of K = 16 over the block's 128 bytes;
 //  * warps 8-23 read D: D = 2^23 + v with v < 2^23, so its bit pattern minus
 //    0x4b000000 is v, which they add into per-thread integer column sums
-//    (four warps per group of 32 lanes, two 32-column chunks each) and
-//    publish to a per-CTA scratch row at the end of the tile.
+//    (four warps per group of 32 lanes, each a quarter of the slot's columns)
+//    and publish to a per-CTA scratch row.
 // Every wait is bounded; a timeout raises a device flag (bn_tc_check).
 #include <cuda_runtime.h>
 
@@ -58,17 +54,12 @@ namespace {
 
 constexpr uint32_t kThreads = 768;   // warp 0 issues the MMAs, warps 1-7 build W, warps 8-23 read D
 constexpr uint32_t kBuildWarps = 7;
-constexpr uint32_t kEpiWarps = 16;   // four per group of 32 tensor-memory lanes, two D chunks each
+constexpr uint32_t kEpiWarps = 16;   // four per group of 32 tensor-memory lanes
 constexpr uint32_t kBlk = 128;       // bytes per block: rows of W, K of a step
-constexpr uint32_t kTile = 256;      // output blocks per tile (D columns, the MMA's N)
-constexpr uint32_t kPad = 32;        // zero blocks on each side of X
-constexpr uint32_t kTmemCols = 512;  // two D slots of 256 columns
-constexpr uint32_t kDSlots = 2;      // D slots in tensor memory
-constexpr uint32_t kWSlots = 3;      // W slots in shared memory
+constexpr uint32_t kTmemCols = 512;  // the D slots
+constexpr uint32_t kWSlotsMax = 3, kDSlotsMax = 4;
 constexpr uint32_t kWBytes = 128 * 128 * 2;     // one W_J in fp16: 16 K-chunks x 16 row groups x 128 B
 constexpr uint32_t kWLbo = 2048, kWSbo = 128;   // W: K-chunk stride, 8-row-group stride
-constexpr uint32_t kTilesMax = (2 * BN_MUL_MAX_LIMBS / 32 + kTile - 1) / kTile;
-constexpr uint32_t kMaxSteps = kTilesMax * (BN_MUL_MAX_LIMBS / 32 + 1);  // tiles x at most mb + 1 steps
 constexpr uint64_t kWaitNs = 1000000000ull;     // 1 s per wait
 constexpr uint32_t kMinSmem = 116 * 1024;       // one CTA per SM (the whole tensor memory each)
 constexpr uint32_t kEpiBar = 1;                 // named barrier of the epilogue warps
@@ -76,55 +67,14 @@ constexpr uint32_t kEpiBar = 1;                 // named barrier of the epilogue
 struct TcArgs {
     const uint32_t *a, *b;  // na >= nb (the host orders the operands)
     uint32_t *c;
-    uint32_t na, nb, nout, ma, mb, tiles;
-    uint32_t circ, ma16;      // circular D (one tile of ma columns); ma rounded up to 16
+    uint32_t na, nb, nout, ma, mb;
+    uint32_t ma16;            // ma rounded up to 16: D's width (the MMA's N)
     uint64_t batch;
     uint32_t *scratch;        // per CTA: 128 (ma + mb) byte-column sums
     uint64_t scratch_stride;  // words per CTA
-    uint32_t xs;              // bytes per chunk row of X: (ma + 2 kPad) * 16
-    uint32_t w_off, ca_off, cb_off, braw_off, sched_off, spill_off, flags_off, bar_off;  // shared-memory offsets
+    uint32_t xs;              // bytes per K-chunk row of XX: (2 ma + ma16 - ma) * 16
+    uint32_t w_off, ca_off, cb_off, braw_off, spill_off, flags_off, bar_off;  // shared-memory offsets
 };
-
-// A step (tile t, block J of b): the D chunks (32 columns) it writes are
-// [clo, chi), the columns s of tile t with 0 <= s - J < ma rounded out to
-// whole chunks (X's zero blocks cover the rest); `last` marks the tile's last step.
-struct Step {
-    uint32_t J, t, clo, chi, last;
-};
-__device__ __forceinline__ uint32_t step_pack(Step x) {
-    return x.J | (x.t << 10) | (x.clo << 12) | (x.chi << 16) | (x.last << 20);
-}
-__device__ __forceinline__ Step step_unpack(uint32_t w) {
-    return Step{w & 1023u, (w >> 10) & 3u, (w >> 12) & 15u, (w >> 16) & 15u, (w >> 20) & 1u};
-}
-
-// The steps of one product, in order: for each tile, J from the first block of
-// b that reaches it to the last.  Depends only on the sizes.
-__device__ uint32_t make_schedule(const TcArgs &g, uint32_t *sched) {
-    uint32_t n = 0;
-    for (uint32_t t = 0; t < g.tiles; ++t) {
-        const int s0 = (int)(kTile * t);
-        const int lo = s0 - (int)g.ma + 1 > 0 ? s0 - (int)g.ma + 1 : 0;
-        const int hi = s0 + (int)kTile - 1 < (int)g.mb ? s0 + (int)kTile - 1 : (int)g.mb;
-        for (int J = lo; J <= hi; ++J) {
-            const int c0 = (J > s0 ? J : s0) - s0;
-            const int e = J + (int)g.ma, c1 = (e < s0 + (int)kTile ? e : s0 + (int)kTile) - s0;
-            sched[n++] = step_pack(Step{(uint32_t)J, t, (uint32_t)(c0 >> 5), (uint32_t)((c1 + 31) >> 5),
-                                        J == hi ? 1u : 0u});
-        }
-    }
-    return n;
-}
-
-// Step i of a product: the table's entry, or for the circular form J = i
-// (0..mb: block mb holds the top of b's last block shifted up) over all of D.
-template <bool CIRC>
-__device__ __forceinline__ Step step_at(const TcArgs &g, const uint32_t *sched, uint32_t i) {
-    if constexpr (CIRC)
-        return Step{i, 0, 0, (g.ma + 31) >> 5, i == g.mb ? 1u : 0u};
-    else
-        return step_unpack(sched[i]);
-}
 
 // Row r of W_J, words 16 u .. 16 u + 15 (K-chunks 4 u .. 4 u + 3), into the
 // W slot at `w` (shared memory, the MMA's A operand: K-major without swizzle,
@@ -184,9 +134,7 @@ __device__ __forceinline__ void build_w2(const uint32_t *braw, uint32_t J, uint3
 // exact in f32 and, having exponent 23, its bit pattern is 0x4b000000 + v.
 constexpr uint32_t kBiasBits = 0x4b000000u;
 constexpr uint16_t kF16_2048 = 0x6800u, kF16_4096 = 0x6c00u;
-constexpr uint32_t kCaBytes = 128 * 16 * 2, kCbBytes = kTile * 16 * 2;  // the bias MMA's A (M x 16) and B (N x 16)
-constexpr uint32_t kCbLbo = kTile * 16;
-constexpr uint32_t kBiasTiny = 256;  // circular form: each bias operand as one core matrix per K-chunk
+constexpr uint32_t kBiasBytes = 256;  // each bias operand: one core matrix per K-chunk (8 rows, then zeros)
 
 // Named barrier of the epilogue warps, OR-reducing `pred`.
 __device__ __forceinline__ bool epi_barrier_or(bool pred) {
@@ -202,49 +150,49 @@ __device__ __forceinline__ bool epi_barrier_or(bool pred) {
     return r != 0;
 }
 
-// CIRC: the circular D (outputs wider than one tile); a separate instantiation
-// so that the one-tile form keeps its own register allocation.
-template <bool CIRC>
+#define BN_TC_FLUSH(x)                                   \
+    case x:                                              \
+        colr[kBlk * (n0 + (x))] = acc[(x) >> 5][(x) & 31]; \
+        acc[(x) >> 5][(x) & 31] = 0;                     \
+        break;
+#define BN_TC_FLUSH8(x)                                                                      \
+    BN_TC_FLUSH(x) BN_TC_FLUSH(x + 1) BN_TC_FLUSH(x + 2) BN_TC_FLUSH(x + 3) BN_TC_FLUSH(x + 4) \
+        BN_TC_FLUSH(x + 5) BN_TC_FLUSH(x + 6) BN_TC_FLUSH(x + 7)
+
+// SLOTC: columns per D slot, 256 (two slots, ma > 128) or 128 (four slots);
+// an epilogue warp owns SLOTC / 4 columns of its 32 lanes.
+template <uint32_t SLOTC>
 __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
+    constexpr uint32_t kDS = kTmemCols / SLOTC;     // D slots
+    constexpr uint32_t kCPW = SLOTC / 128;          // 32-column chunks per epilogue warp
+    constexpr uint32_t kWS = SLOTC == 256 ? 2 : 3;  // W slots (two leave room for XX at 256K bits)
     extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t *X = sm;  // X and the W slots double as the normalisation's staging row
+    uint8_t *X = sm;  // XX and the W slots double as the normalisation's staging row
     uint8_t *W = sm + g.w_off;
     uint32_t *braw = reinterpret_cast<uint32_t *>(sm + g.braw_off);
-    uint32_t *sched = reinterpret_cast<uint32_t *>(sm + g.sched_off);
     uint64_t *spill = reinterpret_cast<uint64_t *>(sm + g.spill_off);
     uint32_t *flags = reinterpret_cast<uint32_t *>(sm + g.flags_off);
-    constexpr uint32_t kWS = CIRC ? 2 : kWSlots;                       // W slots in use
     uint64_t *wfull = reinterpret_cast<uint64_t *>(sm + g.bar_off);  // [kWS], one arrival per builder warp
-    uint64_t *wempty = wfull + kWSlots;                                 // [kWS], MMA commits
-    uint64_t *dfull = wempty + kWSlots;                                 // [kDSlots], MMA commits
-    uint64_t *dempty = dfull + kDSlots;                                 // [kDSlots], one arrival per warp
-    uint32_t *slot = reinterpret_cast<uint32_t *>(dempty + kDSlots);
+    uint64_t *wempty = wfull + kWSlotsMax;                              // [kWS], MMA commits
+    uint64_t *dfull = wempty + kWSlotsMax;                              // [kDS], MMA commits
+    uint64_t *dempty = dfull + kDSlotsMax;                              // [kDS], one arrival per warp
+    uint32_t *slot = reinterpret_cast<uint32_t *>(dempty + kDSlotsMax);
     volatile uint32_t *abortf = slot + 1;
-    uint32_t *nsteps = slot + 2;
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lq = warp & 3;  // the tensor-memory lanes this warp may move
     if (warp == 0) tc::tmem_alloc(slot, kTmemCols);
-    if (tid == 32) *nsteps = CIRC ? g.mb + 1 : make_schedule(g, sched);
-    {  // the bias MMA's operands: A[r][0] = 2048, B[n][0] = 4096, zero elsewhere
-        uint16_t *ca = reinterpret_cast<uint16_t *>(sm + g.ca_off), *cb = reinterpret_cast<uint16_t *>(sm + g.cb_off);
-        if constexpr (CIRC) {  // one core matrix per K-chunk: 8 rows, then 128 zero bytes
-            if (tid < kBiasTiny / 2) {
-                ca[tid] = (tid % 8 == 0 && tid < 64) ? kF16_2048 : 0;
-                cb[tid] = (tid % 8 == 0 && tid < 64) ? kF16_4096 : 0;
-            }
-        } else {
-            for (uint32_t x = tid; x < kCaBytes / 2; x += kThreads) ca[x] = (x % 8 == 0 && x < 128 * 8) ? kF16_2048 : 0;
-            for (uint32_t x = tid; x < kCbBytes / 2; x += kThreads) cb[x] = (x % 8 == 0 && x < kTile * 8) ? kF16_4096 : 0;
-        }
-        tc::fence_proxy_async();
+    if (tid < kBiasBytes / 2) {  // the bias MMA's operands: A[r][0] = 2048, B[n][0] = 4096, zero elsewhere
+        reinterpret_cast<uint16_t *>(sm + g.ca_off)[tid] = (tid % 8 == 0 && tid < 64) ? kF16_2048 : 0;
+        reinterpret_cast<uint16_t *>(sm + g.cb_off)[tid] = (tid % 8 == 0 && tid < 64) ? kF16_4096 : 0;
     }
+    tc::fence_proxy_async();
     if (tid == 0) {
         for (uint32_t k = 0; k < kWS; ++k) {
             tc::mbar_init(&wfull[k], kBuildWarps);
             tc::mbar_init(&wempty[k], 1);
         }
-        for (uint32_t k = 0; k < kDSlots; ++k) {
+        for (uint32_t k = 0; k < kDS; ++k) {
             tc::mbar_init(&dfull[k], 1);
             tc::mbar_init(&dempty[k], kEpiWarps);
         }
@@ -254,41 +202,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tbase = *slot, S = *nsteps;
+    const uint32_t tbase = *slot, S = g.mb + 1;  // steps J = 0..mb
     const uint32_t lane_off = (32 * lq) << 16;
     const uint32_t x_s = tc::smem_u32(X), w_s = tc::smem_u32(W);
-    const uint32_t out_blocks = g.ma + g.mb;
     uint32_t *cols = g.scratch + blockIdx.x * g.scratch_stride;
     uint32_t gs = 0;  // steps done by this CTA over all instances (slots and phases)
     bool fail = false;
 
     for (uint64_t inst = blockIdx.x; inst < g.batch; inst += gridDim.x) {
         const uint32_t *arow = g.a + inst * g.na, *brow = g.b + inst * g.nb;
-        // ---- stage X (fp16, core-matrix layout) and b's bytes
+        // ---- stage XX (fp16, core-matrix layout: a-block I at blocks I and
+        // I + ma), its zero blocks up to D's width, and b's bytes
         for (uint32_t x = tid; x < 16 * g.ma; x += kThreads) {
             const uint32_t I = x >> 4, q = x & 15, w0 = 32 * I + 2 * q;
             const uint32_t u = w0 < g.na ? __ldg(arow + w0) : 0u;
             const uint32_t v = w0 + 1 < g.na ? __ldg(arow + w0 + 1) : 0u;
             const uint4 f = make_uint4(tc::bytes01_f16x2(u), tc::bytes23_f16x2(u), tc::bytes01_f16x2(v),
                                        tc::bytes23_f16x2(v));
-            if constexpr (CIRC) {  // XX: blocks I and I + ma
-                *reinterpret_cast<uint4 *>(X + q * g.xs + I * 16) = f;
-                *reinterpret_cast<uint4 *>(X + q * g.xs + (I + g.ma) * 16) = f;
-            } else {
-                *reinterpret_cast<uint4 *>(X + q * g.xs + (I + kPad) * 16) = f;
-            }
+            *reinterpret_cast<uint4 *>(X + q * g.xs + I * 16) = f;
+            *reinterpret_cast<uint4 *>(X + q * g.xs + (I + g.ma) * 16) = f;
         }
-        if constexpr (CIRC) {  // zero blocks after XX up to D's width rounded to 16
-            const uint32_t zb = g.ma16 - g.ma;
-            for (uint32_t x = tid; x < 16 * zb; x += kThreads)
-                *reinterpret_cast<uint4 *>(X + (x / zb) * g.xs + (2 * g.ma + x % zb) * 16) = make_uint4(0, 0, 0, 0);
-        } else {
-            for (uint32_t x = tid; x < 16 * 2 * kPad; x += kThreads) {
-                const uint32_t q = x / (2 * kPad), p = x % (2 * kPad);
-                const uint32_t I = p < kPad ? p : g.ma + p;  // padded index (kPad offset included)
-                *reinterpret_cast<uint4 *>(X + q * g.xs + I * 16) = make_uint4(0, 0, 0, 0);
-            }
-        }
+        const uint32_t zb = g.ma16 - g.ma;
+        for (uint32_t x = tid; x < 16 * zb; x += kThreads)
+            *reinterpret_cast<uint4 *>(X + (x / zb) * g.xs + (2 * g.ma + x % zb) * 16) = make_uint4(0, 0, 0, 0);
         const uint32_t bwords = 32 * (g.mb + 2) + 4;
         for (uint32_t x = tid; x < bwords; x += kThreads)
             braw[x] = (x >= 32 && x - 32 < g.nb) ? __ldg(brow + x - 32) : 0u;
@@ -297,10 +233,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
 
         if (warp == 0) {
             // the warp waits and computes each step's descriptors together (so
-            // they stay in uniform registers); one elected lane issues the 8
-            // MMAs (K = 16 each) and commits them
-            for (uint32_t i = 0; i < S; ++i, ++gs) {
-                const uint32_t k = gs % kWS, d = gs % kDSlots, ud = gs / kDSlots;
+            // they stay in uniform registers); one elected lane issues the
+            // MMAs and commits them
+            const uint32_t idesc = tc::idesc_f16_f32(128, g.ma16);
+            const uint64_t bstep = (2 * g.xs) >> 4, astep = (2 * kWLbo) >> 4;
+            for (uint32_t J = 0; J < S; ++J, ++gs) {
+                const uint32_t k = gs % kWS, d = gs % kDS, ud = gs / kDS;
                 bool ok = tc::mbar_wait(&wfull[k], (gs / kWS) & 1u, kWaitNs, abortf);
                 if (ok && ud > 0) ok = tc::mbar_wait(&dempty[d], (ud - 1) & 1u, kWaitNs, abortf);
                 if (!__all_sync(FULL_MASK, ok)) {
@@ -308,40 +246,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
                     break;
                 }
                 tc::fence_after_sync();
-                const Step st = step_at<CIRC>(g, sched, i);
-                const uint64_t bstep = (2 * g.xs) >> 4;
-                const uint64_t ad = tc::smem_desc(w_s + k * kWBytes, kWLbo, kWSbo), astep = (2 * kWLbo) >> 4;
-                const uint64_t cad = tc::smem_desc(x_s + g.ca_off, kWLbo, kWSbo), cbd = tc::smem_desc(x_s + g.cb_off, kCbLbo, 128);
-                if constexpr (CIRC) {
-                    // all of D: column n is XX block ma - J + n, i.e. a-block n - J
-                    // for n >= J and n - J + ma below (columns from ma on unused)
-                    const uint32_t dt = tbase + kTile * d;
-                    const uint32_t idesc = tc::idesc_f16_f32(128, g.ma16);
-                    const uint64_t bd = tc::smem_desc(x_s + (g.ma - st.J) * 16, g.xs, 128);
-                    // the bias operands' core matrix repeats over all row groups (stride 0)
-                    const uint64_t tad = tc::smem_desc(x_s + g.ca_off, 128, 0), tbd = tc::smem_desc(x_s + g.cb_off, 128, 0);
-                    if (tc::elect_one()) {
-                        tc::mma_f16_ss(dt, tad, tbd, idesc, 0);  // D = 2^23
+                const uint32_t dt = tbase + SLOTC * d;
+                const uint64_t ad = tc::smem_desc(w_s + k * kWBytes, kWLbo, kWSbo);
+                const uint64_t bd = tc::smem_desc(x_s + (g.ma - J) * 16, g.xs, 128);  // XX from block ma - J
+                // the bias operands' core matrix repeats over all row groups (stride 0)
+                const uint64_t cad = tc::smem_desc(x_s + g.ca_off, 128, 0);
+                const uint64_t cbd = tc::smem_desc(x_s + g.cb_off, 128, 0);
+                if (tc::elect_one()) {
+                    tc::mma_f16_ss(dt, cad, cbd, idesc, 0);  // D = 2^23
 #pragma unroll
-                        for (uint32_t kk = 0; kk < 8; ++kk)
-                            tc::mma_f16_ss(dt, ad + kk * astep, bd + kk * bstep, idesc, 1);
-                        tc::mma_commit(&dfull[d]);
-                        tc::mma_commit(&wempty[k]);
-                    }
-                } else {
-                    const uint32_t idesc = tc::idesc_f16_f32(128, 32u * (st.chi - st.clo));
-                    // padded block of D column 0: s - J with s = kTile t + 32 clo
-                    const uint32_t i0 = kTile * st.t + 32 * st.clo + kPad - st.J;
-                    const uint32_t dt = tbase + kTile * d + 32 * st.clo;
-                    const uint64_t bd = tc::smem_desc(x_s + i0 * 16, g.xs, 128);
-                    if (tc::elect_one()) {
-                        tc::mma_f16_ss(dt, cad, cbd, idesc, 0);  // D = 2^23
-#pragma unroll
-                        for (uint32_t kk = 0; kk < 8; ++kk)
-                            tc::mma_f16_ss(dt, ad + kk * astep, bd + kk * bstep, idesc, 1);
-                        tc::mma_commit(&dfull[d]);
-                        tc::mma_commit(&wempty[k]);
-                    }
+                    for (uint32_t kk = 0; kk < 8; ++kk) tc::mma_f16_ss(dt, ad + kk * astep, bd + kk * bstep, idesc, 1);
+                    tc::mma_commit(&dfull[d]);
+                    tc::mma_commit(&wempty[k]);
                 }
                 __syncwarp();
             }
@@ -349,14 +265,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
             // builders: W of each step into a W slot once the MMA that last read
             // it is done; the 512 quarter rows are spread over the builder threads
             const uint32_t bt = tid - 32;
-            for (uint32_t i = 0; i < S; ++i, ++gs) {
+            for (uint32_t J = 0; J < S; ++J, ++gs) {
                 const uint32_t k = gs % kWS, use = gs / kWS;
                 if (use > 0 &&
                     !__all_sync(FULL_MASK, tc::mbar_wait(&wempty[k], (use - 1) & 1u, kWaitNs, abortf))) {
                     *abortf = 1;
                     break;
                 }
-                const uint32_t J = step_at<CIRC>(g, sched, i).J;
                 uint8_t *wk = W + k * kWBytes;
                 uint32_t x = bt;
                 for (; x + 32 * kBuildWarps < 512; x += 64 * kBuildWarps) build_w2(braw, J, x, x + 32 * kBuildWarps, wk);
@@ -366,90 +281,73 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
                 if (lane == 0) tc::mbar_arrive(&wfull[k]);
             }
         } else {
-            // epilogue: each finished D into the integer column sums of its tile
-            // (the 4 warps of lane group lq own chunks 2m, 2m + 1, m = 0..3)
-            const uint32_t m = (warp - 1 - kBuildWarps) >> 2;
+            // epilogue: each finished D into the integer column sums; the 4 warps
+            // of lane group lq own the columns [n0, n0 + SLOTC / 4)
+            const uint32_t m = (warp - 1 - kBuildWarps) >> 2, n0 = 32 * kCPW * m;
+            const uint32_t chi = (g.ma + 31) >> 5;        // chunks that hold D's ma columns
             uint32_t *const colr = cols + 32 * lq + lane;  // this thread's row of every column block
-            uint32_t acc[2][32];
+            uint32_t acc[kCPW][32];
 #pragma unroll
-            for (int c = 0; c < 2; ++c)
+            for (int c = 0; c < (int)kCPW; ++c)
 #pragma unroll
                 for (int i = 0; i < 32; ++i) acc[c][i] = 0;
-            for (uint32_t i = 0; i < S; ++i, ++gs) {
-                const uint32_t d = gs % kDSlots;
+            for (uint32_t J = 0; J < S; ++J, ++gs) {
+                const uint32_t d = gs % kDS;
                 bool bad = false;
                 if (warp == 1 + kBuildWarps)  // one warp polls, the others sleep in the barrier
-                    bad = !__all_sync(FULL_MASK, tc::mbar_wait(&dfull[d], (gs / kDSlots) & 1u, kWaitNs, abortf));
+                    bad = !__all_sync(FULL_MASK, tc::mbar_wait(&dfull[d], (gs / kDS) & 1u, kWaitNs, abortf));
                 if (epi_barrier_or(bad)) {
                     *abortf = 1;
                     break;
                 }
                 tc::fence_after_sync();
-                const Step st = step_at<CIRC>(g, sched, i);
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const uint32_t ch = 2 * m + c;
-                    if (ch >= st.clo && ch < st.chi) {
+                for (int c = 0; c < (int)kCPW; ++c) {
+                    const uint32_t ch = kCPW * m + c;
+                    if (ch < chi) {
+                        const uint32_t ta = tbase + lane_off + SLOTC * d + 32 * ch;
+                        if constexpr (kCPW == 1) {  // the warp's 32 columns in one load
+                            uint32_t v[32];
+                            tc::tmem_ld32(ta, v);
 #pragma unroll
-                        for (int hh = 0; hh < 4; ++hh) {  // 8 columns at a time: the register cap is 80
-                            uint32_t v[8];
-                            tc::tmem_ld8(tbase + lane_off + kTile * d + 32 * ch + 8 * hh, v);
+                            for (int j = 0; j < 32; ++j) acc[c][j] += v[j] - kBiasBits;
+                        } else {
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) acc[c][8 * hh + j] += v[j] - kBiasBits;
+                            for (int hh = 0; hh < 4; ++hh) {  // 8 columns at a time: the register cap is 80
+                                uint32_t v[8];
+                                tc::tmem_ld8(ta + 8 * hh, v);
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) acc[c][8 * hh + j] += v[j] - kBiasBits;
+                            }
                         }
                     }
                 }
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&dempty[d]);
-                if (CIRC && !st.last) {
-                    // circular D: column J now holds all of block J; store it and
-                    // start the column over as block J + ma
-                    const uint32_t f = st.J - 64 * m;  // warp-uniform
-                    if (f < 64u) {
+                // column J now holds all of block J: store it and start the column
+                // over as block J + ma (after the last step, J = mb, every column
+                // is published below instead)
+                const uint32_t f = J - n0;  // warp-uniform
+                if (J < g.mb && f < 32 * kCPW) {
+                    if constexpr (kCPW == 2) {
                         switch (f) {
-#define BN_TC_FLUSH(x)                                    \
-    case x:                                               \
-        colr[kBlk * (64 * m + x)] = acc[x >> 5][x & 31];  \
-        acc[x >> 5][x & 31] = 0;                          \
-        break;
-                            BN_TC_FLUSH(0) BN_TC_FLUSH(1) BN_TC_FLUSH(2) BN_TC_FLUSH(3) BN_TC_FLUSH(4)
-                            BN_TC_FLUSH(5) BN_TC_FLUSH(6) BN_TC_FLUSH(7) BN_TC_FLUSH(8) BN_TC_FLUSH(9)
-                            BN_TC_FLUSH(10) BN_TC_FLUSH(11) BN_TC_FLUSH(12) BN_TC_FLUSH(13) BN_TC_FLUSH(14)
-                            BN_TC_FLUSH(15) BN_TC_FLUSH(16) BN_TC_FLUSH(17) BN_TC_FLUSH(18) BN_TC_FLUSH(19)
-                            BN_TC_FLUSH(20) BN_TC_FLUSH(21) BN_TC_FLUSH(22) BN_TC_FLUSH(23) BN_TC_FLUSH(24)
-                            BN_TC_FLUSH(25) BN_TC_FLUSH(26) BN_TC_FLUSH(27) BN_TC_FLUSH(28) BN_TC_FLUSH(29)
-                            BN_TC_FLUSH(30) BN_TC_FLUSH(31) BN_TC_FLUSH(32) BN_TC_FLUSH(33) BN_TC_FLUSH(34)
-                            BN_TC_FLUSH(35) BN_TC_FLUSH(36) BN_TC_FLUSH(37) BN_TC_FLUSH(38) BN_TC_FLUSH(39)
-                            BN_TC_FLUSH(40) BN_TC_FLUSH(41) BN_TC_FLUSH(42) BN_TC_FLUSH(43) BN_TC_FLUSH(44)
-                            BN_TC_FLUSH(45) BN_TC_FLUSH(46) BN_TC_FLUSH(47) BN_TC_FLUSH(48) BN_TC_FLUSH(49)
-                            BN_TC_FLUSH(50) BN_TC_FLUSH(51) BN_TC_FLUSH(52) BN_TC_FLUSH(53) BN_TC_FLUSH(54)
-                            BN_TC_FLUSH(55) BN_TC_FLUSH(56) BN_TC_FLUSH(57) BN_TC_FLUSH(58) BN_TC_FLUSH(59)
-                            BN_TC_FLUSH(60) BN_TC_FLUSH(61) BN_TC_FLUSH(62) BN_TC_FLUSH(63)
-#undef BN_TC_FLUSH
+                            BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) BN_TC_FLUSH8(16) BN_TC_FLUSH8(24)
+                            BN_TC_FLUSH8(32) BN_TC_FLUSH8(40) BN_TC_FLUSH8(48) BN_TC_FLUSH8(56)
                         }
+                    } else {
+                        switch (f) { BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) BN_TC_FLUSH8(16) BN_TC_FLUSH8(24) }
                     }
                 }
-                if (st.last) {  // tile complete: publish its column sums
-                    const uint32_t s0 = kTile * st.t;
-#pragma unroll
-                    for (int c = 0; c < 2; ++c)
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const uint32_t n = 32 * (2 * m + c) + j;
-                            if constexpr (CIRC) {
-                                // columns n < mb moved on to block n + ma after step n (the
-                                // flag is read at run time here: it compiles without spills)
-                                const uint32_t s = g.circ ? (n < g.mb ? n + g.ma : n) : s0 + n;
-                                if (s < out_blocks && (!g.circ || n < g.ma)) colr[kBlk * s] = acc[c][j];
-                            } else {
-                                const uint32_t s = s0 + n;
-                                if (s < out_blocks) colr[kBlk * s] = acc[c][j];
-                            }
-                            acc[c][j] = 0;
-                        }
-                }
             }
+            // publish: column n < mb went on to block n + ma after step n
+#pragma unroll
+            for (int c = 0; c < (int)kCPW; ++c)
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const uint32_t n = n0 + 32 * c + j;
+                    if (n < g.ma) colr[kBlk * (n < g.mb ? n + g.ma : n)] = acc[c][j];
+                }
         }
         __syncthreads();
         fail = *abortf != 0;
@@ -466,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
         // wind down: give the MMAs issued last a bounded time to finish
         if (gs > 0) {
             const uint32_t last = gs - 1;
-            tc::mbar_wait(&dfull[last % kDSlots], (last / kDSlots) & 1u, kWaitNs);
+            tc::mbar_wait(&dfull[last % kDS], (last / kDS) & 1u, kWaitNs);
         }
         atomicOr(&g_tc_fault, 1u);
     }
@@ -474,9 +372,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
 }
+#undef BN_TC_FLUSH8
+#undef BN_TC_FLUSH
 
 struct TcGeometry {
-    uint32_t na, nb, ma, mb, tiles, xs, w_off, ca_off, cb_off, braw_off, sched_off, spill_off, flags_off, bar_off, smem;
+    uint32_t na, nb, ma, mb, ma16, slotc, xs, w_off, ca_off, cb_off, braw_off, spill_off, flags_off, bar_off, smem;
     bool swap;
 };
 
@@ -487,29 +387,27 @@ TcGeometry geometry(uint32_t na, uint32_t nb) {
     q.nb = q.swap ? na : nb;
     q.ma = (q.na + 31) / 32;
     q.mb = (q.nb + 31) / 32;
-    q.tiles = (q.ma + q.mb + kTile - 1) / kTile;
-    const bool circ = q.tiles > 1;  // circular D: XX of 2 ma blocks rounded up to 16, two W slots, no bias MMA
-    q.xs = (circ ? 2 * q.ma + ((q.ma + 15) & ~15u) - q.ma : q.ma + 2 * kPad) * 16;
+    q.ma16 = (q.ma + 15) & ~15u;
+    q.slotc = q.ma16 > 128 ? 256 : 128;
+    q.xs = (2 * q.ma + (q.ma16 - q.ma)) * 16;
     const uint32_t nout = q.na + q.nb;
     const uint32_t stage_bytes = 4 * ((nout - 1) + ((nout - 1) >> 4) + 1);
-    q.w_off = 16 * q.xs;  // a multiple of 16
+    q.w_off = 16 * q.xs;    // a multiple of 256
     q.spill_off = q.w_off;  // the normalisation's spill words reuse the W slots
-    uint32_t off = q.w_off + (circ ? 2 : kWSlots) * kWBytes;
+    uint32_t off = q.w_off + (q.slotc == 256 ? 2 : 3) * kWBytes;
     if (off < stage_bytes) off = stage_bytes;
     off = (off + 15) & ~15u;
     q.ca_off = off;
-    off += circ ? kBiasTiny : kCaBytes;
+    off += kBiasBytes;
     q.cb_off = off;
-    off += circ ? kBiasTiny : kCbBytes;
+    off += kBiasBytes;
     q.braw_off = off;
     off += 4 * (32 * (q.mb + 2) + 4);
     off = (off + 15) & ~15u;
-    q.sched_off = off;
-    if (!circ) off += 4 * kMaxSteps;
     q.flags_off = off;
     off += 4 * (kThreads / 32);
     q.bar_off = (off + 15) & ~15u;
-    off = q.bar_off + 8 * (2 * kWSlots + 2 * kDSlots) + 16;
+    off = q.bar_off + 8 * (2 * kWSlotsMax + 2 * kDSlotsMax) + 16;
     q.smem = off > kMinSmem ? off : kMinSmem;
     return q;
 }
@@ -534,8 +432,8 @@ bn_status quad_tc_create(QuadTcPlan **out, uint32_t na, uint32_t nb) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc<false>);
-    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc<true>);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc<256>);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc<128>);
     if (e != cudaSuccess) {
         delete p;
         return BN_ECUDA;
@@ -572,9 +470,7 @@ cudaError_t quad_tc_launch(QuadTcPlan *p, const uint32_t *a, const uint32_t *b, 
     g.nout = p->nout;
     g.ma = q.ma;
     g.mb = q.mb;
-    g.tiles = q.tiles;
-    g.circ = q.tiles > 1 ? 1u : 0u;
-    g.ma16 = (q.ma + 15) & ~15u;
+    g.ma16 = q.ma16;
     g.batch = batch;
     g.scratch = p->scratch;
     g.scratch_stride = p->stride;
@@ -583,15 +479,14 @@ cudaError_t quad_tc_launch(QuadTcPlan *p, const uint32_t *a, const uint32_t *b, 
     g.ca_off = q.ca_off;
     g.cb_off = q.cb_off;
     g.braw_off = q.braw_off;
-    g.sched_off = q.sched_off;
     g.spill_off = q.spill_off;
     g.flags_off = q.flags_off;
     g.bar_off = q.bar_off;
     const uint32_t grid = batch < p->ctas ? (uint32_t)batch : p->ctas;
-    if (g.circ)
-        k_mul_quad_tc<true><<<grid, kThreads, q.smem, st>>>(g);
+    if (q.slotc == 256)
+        k_mul_quad_tc<256><<<grid, kThreads, q.smem, st>>>(g);
     else
-        k_mul_quad_tc<false><<<grid, kThreads, q.smem, st>>>(g);
+        k_mul_quad_tc<128><<<grid, kThreads, q.smem, st>>>(g);
     return cudaGetLastError();
 }
 
