@@ -190,6 +190,17 @@ __device__ __forceinline__ void inverse_sub(const NttArgs &p, const uint64_t *tw
     else inverse<F>(p.L, p.logL, tw, B);
 }
 
+// Drops a per-CTA scratch region from L2 after its last read: its lines are
+// dead, and writing them back to memory when they are evicted would only add
+// DRAM traffic.  Whole CTA, after a barrier that follows the last read; a
+// region that is not whole 128-byte lines is left alone.
+__device__ __forceinline__ void discard_scratch(const uint64_t *ptr, uint32_t words) {
+    const size_t g = __cvta_generic_to_global(ptr), bytes = 8ull * words;
+    if ((g | bytes) & 127u) return;
+    for (size_t off = 128ull * threadIdx.x; off < bytes; off += 128ull * blockDim.x)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(g + off) : "memory");
+}
+
 // Coefficients of a*b mod the field's prime, scaled by 1/N.  With keep and
 // S == 1 they stay in B (padded layout); otherwise they go to dest[0 .. N).
 template <class F>
@@ -230,6 +241,8 @@ __device__ void prime_product(const NttArgs &p, const PrimeTab &tb, const uint32
                 dest[j + r * p.L] = F::canon(acc);
             }
         }
+        __syncthreads();
+        discard_scratch(Z, p.N);  // the partial results are consumed
     }
     __syncthreads();
 }
@@ -285,6 +298,8 @@ __global__ void __launch_bounds__(1024) k_mul_ntt(NttArgs p) {
             prime_product<FieldP1>(p, p.t1, arow, brow, A, B, Z, Cs, keep);
         }
         normalize<CRT>(p, inst, reinterpret_cast<uint32_t *>(A), B, keep, C1, Cs, spill, flags);
+        if (CRT) discard_scratch(C1, p.N);  // the coefficients are consumed
+        if (!keep) discard_scratch(Cs, p.N);
     }
 }
 
@@ -329,6 +344,8 @@ __global__ void __launch_bounds__(1024)
             prime_product<FieldP1>(q, q.t1, q.a, q.b, A, B, Z, Cs, keep);
         }
         normalize<CRT>(q, 0, reinterpret_cast<uint32_t *>(A), B, keep, C1, Cs, spill, flags);
+        if (CRT) discard_scratch(C1, q.N);  // the coefficients are consumed
+        if (!keep) discard_scratch(Cs, q.N);
     }
 }
 
