@@ -28,7 +28,8 @@
 // bytes.  Three roles form a pipeline linked by mbarriers:
 //  * warps 1-7 build W_J in shared memory (fp16, the MMA's A operand) into one
 //    of two or three slots;
-//  * warp 0 issues each step's MMAs into a D slot in tensor memory (two of 256
+//  * warp 0 (which polls its mbarriers without sleeping: its wake-up is on the
+//    critical path) issues each step's MMAs into a D slot in tensor memory (two of 256
 //    columns when ma > 128, else four of 128): first a bias MMA (2048 x 4096
 //    into every element, so D starts at 2^23; its constant operands are one
 //    core matrix each, repeated over the rows by a zero stride), then 8 MMAs
@@ -62,7 +63,6 @@ constexpr uint32_t kWBytes = 128 * 128 * 2;     // one W_J in fp16: 16 K-chunks 
 constexpr uint32_t kWLbo = 2048, kWSbo = 128;   // W: K-chunk stride, 8-row-group stride
 constexpr uint64_t kWaitNs = 1000000000ull;     // 1 s per wait
 constexpr uint32_t kMinSmem = 116 * 1024;       // one CTA per SM (the whole tensor memory each)
-constexpr uint32_t kEpiBar = 1;                 // named barrier of the epilogue warps
 
 struct TcArgs {
     const uint32_t *a, *b;  // na >= nb (the host orders the operands)
@@ -135,20 +135,6 @@ __device__ __forceinline__ void build_w2(const uint32_t *braw, uint32_t J, uint3
 constexpr uint32_t kBiasBits = 0x4b000000u;
 constexpr uint16_t kF16_2048 = 0x6800u, kF16_4096 = 0x6c00u;
 constexpr uint32_t kBiasBytes = 256;  // each bias operand: one core matrix per K-chunk (8 rows, then zeros)
-
-// Named barrier of the epilogue warps, OR-reducing `pred`.
-__device__ __forceinline__ bool epi_barrier_or(bool pred) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred pi, po;\n\t"
-        "setp.ne.u32 pi, %1, 0;\n\t"
-        "barrier.red.or.pred po, %2, %3, pi;\n\t"
-        "selp.u32 %0, 1, 0, po;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)pred), "n"(kEpiBar), "n"(32 * kEpiWarps)
-        : "memory");
-    return r != 0;
-}
 
 #define BN_TC_FLUSH(x)                                   \
     case x:                                              \
@@ -239,8 +225,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
             const uint64_t bstep = (2 * g.xs) >> 4, astep = (2 * kWLbo) >> 4;
             for (uint32_t J = 0; J < S; ++J, ++gs) {
                 const uint32_t k = gs % kWS, d = gs % kDS, ud = gs / kDS;
-                bool ok = tc::mbar_wait(&wfull[k], (gs / kWS) & 1u, kWaitNs, abortf);
-                if (ok && ud > 0) ok = tc::mbar_wait(&dempty[d], (ud - 1) & 1u, kWaitNs, abortf);
+                bool ok = tc::mbar_wait_spin(&wfull[k], (gs / kWS) & 1u, kWaitNs, abortf);
+                if (ok && ud > 0) ok = tc::mbar_wait_spin(&dempty[d], (ud - 1) & 1u, kWaitNs, abortf);
                 if (!__all_sync(FULL_MASK, ok)) {
                     *abortf = 1;
                     break;
@@ -293,10 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
                 for (int i = 0; i < 32; ++i) acc[c][i] = 0;
             for (uint32_t J = 0; J < S; ++J, ++gs) {
                 const uint32_t d = gs % kDS;
-                bool bad = false;
-                if (warp == 1 + kBuildWarps)  // one warp polls, the others sleep in the barrier
-                    bad = !__all_sync(FULL_MASK, tc::mbar_wait(&dfull[d], (gs / kDS) & 1u, kWaitNs, abortf));
-                if (epi_barrier_or(bad)) {
+                if (!__all_sync(FULL_MASK, tc::mbar_wait(&dfull[d], (gs / kDS) & 1u, kWaitNs, abortf))) {
                     *abortf = 1;
                     break;
                 }

@@ -223,6 +223,32 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
     }
 }
 
+// One non-blocking test of the phase (mbarrier at shared address addr).
+__device__ __forceinline__ bool mbar_test(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// As mbar_wait, but polling without suspending the thread (for the one warp
+// whose wake-up latency is on the critical path); same limits.
+__device__ __forceinline__ bool mbar_wait_spin(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                               const volatile uint32_t *abort = nullptr) {
+    const uint32_t addr = smem_u32(bar);
+    if (mbar_test(addr, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 64; ++i)  // the limits are checked every 64 polls
+            if (mbar_test(addr, parity)) return true;
+        if ((abort && *abort) || global_ns() - t0 > limit_ns) return false;
+    }
+}
+
 // ---- digits as fp16 ------------------------------------------------------------
 
 // Two bytes of w as an fp16 pair, exact: `sel` (a byte_perm selector) places
