@@ -102,6 +102,28 @@ __device__ __forceinline__ void build_w(const uint32_t *braw, uint32_t J, uint32
     }
 }
 
+// Quarter u of row r of W_J (words 16 u .. 16 u + 15, the same values as
+// build_w) into registers, for a store to tensor memory.
+__device__ __forceinline__ void build_w_regs(const uint32_t *braw, uint32_t J, uint32_t r, uint32_t u,
+                                             uint32_t (&out)[16]) {
+    const uint32_t e = 97 + 128 * J + r - 32 * u;  // lowest byte offset this thread reads
+    const uint32_t *bw = braw + (e >> 2);
+    const uint32_t sh = e & 3u;
+    uint32_t wv[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) wv[j] = bw[j];
+    const uint32_t sel = (sh + 3) | ((sh + 2) << 4) | ((sh + 1) << 8) | (sh << 12);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t r0 = __byte_perm(wv[7 - 2 * q], wv[8 - 2 * q], sel);
+        const uint32_t r1 = __byte_perm(wv[6 - 2 * q], wv[7 - 2 * q], sel);
+        out[4 * q] = tc::bytes01_f16x2(r0);
+        out[4 * q + 1] = tc::bytes23_f16x2(r0);
+        out[4 * q + 2] = tc::bytes01_f16x2(r1);
+        out[4 * q + 3] = tc::bytes23_f16x2(r1);
+    }
+}
+
 // build_w for the quarter rows x0 and x1 (row = x & 127, quarter = x >> 7),
 // both rows' source words loaded before either is converted and stored.
 __device__ __forceinline__ void build_w2(const uint32_t *braw, uint32_t J, uint32_t x0, uint32_t x1, uint8_t *w) {
@@ -355,12 +377,197 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
 }
+
+// Products whose longer operand has at most 128 blocks (up to 128K bits): D is
+// at most 128 columns wide, so tensor memory holds three D slots and, beside
+// them, two W slots (W_J as the MMA's A operand: 128 lanes x 64 columns of
+// fp16 pairs).  The epilogue warps build W themselves: W_J's slot is free
+// exactly when the step that read it last (J - 2) has delivered its D, which
+// those warps wait for anyway.  No W goes through shared memory, which then
+// only carries XX (the MMAs' B operand) and b's bytes.  17 warps: warp 0
+// issues the MMAs; warps 1-16, four per group of 32 tensor-memory lanes, each
+// build a quarter of their lanes' W rows (16 columns), read 32 columns of D
+// (one load) and keep those columns' sums.
+constexpr uint32_t kThreadsTw = 544;
+constexpr uint32_t kDSlotsTw = 3, kWSlotsTw = 2;
+constexpr uint32_t kDColsTw = 128, kWColsTw = 64;  // tensor-memory columns per D slot, per W slot
+
+__global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t *X = sm;  // XX doubles as the normalisation's staging row
+    uint32_t *braw = reinterpret_cast<uint32_t *>(sm + g.braw_off);
+    uint64_t *spill = reinterpret_cast<uint64_t *>(sm + g.spill_off);
+    uint32_t *flags = reinterpret_cast<uint32_t *>(sm + g.flags_off);
+    uint64_t *wfull = reinterpret_cast<uint64_t *>(sm + g.bar_off);  // [2], one arrival per epilogue warp
+    uint64_t *dfull = wfull + kWSlotsTw;                                // [3], MMA commits
+    uint64_t *dempty = dfull + kDSlotsTw;                               // [3], one arrival per epilogue warp
+    uint32_t *slot = reinterpret_cast<uint32_t *>(dempty + kDSlotsTw);
+    volatile uint32_t *abortf = slot + 1;
+
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t lq = warp & 3;  // the tensor-memory lanes this warp may move
+    if (warp == 0) tc::tmem_alloc(slot, kTmemCols);
+    if (tid < kBiasBytes / 2) {  // the bias MMA's operands: A[r][0] = 2048, B[n][0] = 4096, zero elsewhere
+        reinterpret_cast<uint16_t *>(sm + g.ca_off)[tid] = (tid % 8 == 0 && tid < 64) ? kF16_2048 : 0;
+        reinterpret_cast<uint16_t *>(sm + g.cb_off)[tid] = (tid % 8 == 0 && tid < 64) ? kF16_4096 : 0;
+    }
+    tc::fence_proxy_async();
+    if (tid == 0) {
+        for (uint32_t k = 0; k < kWSlotsTw; ++k) tc::mbar_init(&wfull[k], kEpiWarps);
+        for (uint32_t k = 0; k < kDSlotsTw; ++k) {
+            tc::mbar_init(&dfull[k], 1);
+            tc::mbar_init(&dempty[k], kEpiWarps);
+        }
+        *abortf = 0;
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *slot, S = g.mb + 1;  // steps J = 0..mb
+    const uint32_t wbase = tbase + kDSlotsTw * kDColsTw;  // W slot k at column wbase + 64 k
+    const uint32_t lane_off = (32 * lq) << 16;
+    const uint32_t x_s = tc::smem_u32(X);
+    uint32_t *cols = g.scratch + blockIdx.x * g.scratch_stride;
+    uint32_t gs = 0;  // steps done by this CTA over all instances (slots and phases)
+    bool fail = false;
+
+    for (uint64_t inst = blockIdx.x; inst < g.batch; inst += gridDim.x) {
+        const uint32_t *arow = g.a + inst * g.na, *brow = g.b + inst * g.nb;
+        // ---- stage XX (a-block I at blocks I and I + ma), its zero blocks up
+        // to D's width, and b's bytes
+        for (uint32_t x = tid; x < 16 * g.ma; x += kThreadsTw) {
+            const uint32_t I = x >> 4, q = x & 15, w0 = 32 * I + 2 * q;
+            const uint32_t u = w0 < g.na ? __ldg(arow + w0) : 0u;
+            const uint32_t v = w0 + 1 < g.na ? __ldg(arow + w0 + 1) : 0u;
+            const uint4 f = make_uint4(tc::bytes01_f16x2(u), tc::bytes23_f16x2(u), tc::bytes01_f16x2(v),
+                                       tc::bytes23_f16x2(v));
+            *reinterpret_cast<uint4 *>(X + q * g.xs + I * 16) = f;
+            *reinterpret_cast<uint4 *>(X + q * g.xs + (I + g.ma) * 16) = f;
+        }
+        const uint32_t zb = g.ma16 - g.ma;
+        for (uint32_t x = tid; x < 16 * zb; x += kThreadsTw)
+            *reinterpret_cast<uint4 *>(X + (x / zb) * g.xs + (2 * g.ma + x % zb) * 16) = make_uint4(0, 0, 0, 0);
+        const uint32_t bwords = 32 * (g.mb + 2) + 4;
+        for (uint32_t x = tid; x < bwords; x += kThreadsTw)
+            braw[x] = (x >= 32 && x - 32 < g.nb) ? __ldg(brow + x - 32) : 0u;
+        tc::fence_proxy_async();
+        __syncthreads();
+
+        if (warp == 0) {
+            const uint32_t idesc = tc::idesc_f16_f32(128, g.ma16);
+            const uint64_t bstep = (2 * g.xs) >> 4;
+            const uint64_t cad = tc::smem_desc(x_s + g.ca_off, 128, 0), cbd = tc::smem_desc(x_s + g.cb_off, 128, 0);
+            for (uint32_t J = 0; J < S; ++J, ++gs) {
+                const uint32_t k = gs % kWSlotsTw, d = gs % kDSlotsTw, ud = gs / kDSlotsTw;
+                bool ok = tc::mbar_wait_spin(&wfull[k], (gs / kWSlotsTw) & 1u, kWaitNs, abortf);
+                if (ok && ud > 0) ok = tc::mbar_wait_spin(&dempty[d], (ud - 1) & 1u, kWaitNs, abortf);
+                if (!__all_sync(FULL_MASK, ok)) {
+                    *abortf = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t dt = tbase + kDColsTw * d, at = wbase + kWColsTw * k;
+                const uint64_t bd = tc::smem_desc(x_s + (g.ma - J) * 16, g.xs, 128);  // XX from block ma - J
+                if (tc::elect_one()) {
+                    tc::mma_f16_ss(dt, cad, cbd, idesc, 0);  // D = 2^23
+#pragma unroll
+                    for (uint32_t kk = 0; kk < 8; ++kk) tc::mma_f16_ts(dt, at + 8 * kk, bd + kk * bstep, idesc, 1);
+                    tc::mma_commit(&dfull[d]);
+                }
+                __syncwarp();
+            }
+        } else {
+            // column quarter m: D columns [32 m, 32 m + 32), W columns [16 m, 16 m + 16)
+            const uint32_t m = (warp - 1) >> 2, n0 = 32 * m, r = 32 * lq + lane;
+            const uint32_t chi = (g.ma + 31) >> 5;  // chunks that hold D's ma columns
+            uint32_t *const colr = cols + r;        // this thread's row of every column block
+            uint32_t acc[1][32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) acc[0][i] = 0;
+            // W_0 and W_1 (their slots are free: every earlier MMA has delivered its D)
+            for (uint32_t J = 0; J < 2 && J < S; ++J) {
+                uint32_t w16[16];
+                build_w_regs(braw, J, r, m, w16);
+                tc::tmem_st16(wbase + lane_off + kWColsTw * ((gs + J) % kWSlotsTw) + 16 * m, w16);
+                tc::tmem_st_wait();
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&wfull[(gs + J) % kWSlotsTw]);
+            }
+            for (uint32_t J = 0; J < S; ++J, ++gs) {
+                const uint32_t d = gs % kDSlotsTw;
+                if (!__all_sync(FULL_MASK, tc::mbar_wait(&dfull[d], (gs / kDSlotsTw) & 1u, kWaitNs, abortf))) {
+                    *abortf = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                // W_{J+2} into the slot step J has finished reading
+                const bool more = J + 2 < S;
+                if (more) {
+                    uint32_t w16[16];
+                    build_w_regs(braw, J + 2, r, m, w16);
+                    tc::tmem_st16(wbase + lane_off + kWColsTw * (gs % kWSlotsTw) + 16 * m, w16);
+                    tc::tmem_st_wait();
+                }
+                if (m < chi) {  // the warp's 32 columns of D in one load
+                    uint32_t v[32];
+                    tc::tmem_ld32(tbase + lane_off + kDColsTw * d + n0, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) acc[0][j] += v[j] - kBiasBits;
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) {
+                    if (more) tc::mbar_arrive(&wfull[gs % kWSlotsTw]);
+                    tc::mbar_arrive(&dempty[d]);
+                }
+                // column J now holds all of block J: store it and start the column
+                // over as block J + ma
+                const uint32_t f = J - n0;  // warp-uniform
+                if (J < g.mb && f < 32) {
+                    switch (f) { BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) BN_TC_FLUSH8(16) BN_TC_FLUSH8(24) }
+                }
+            }
+            // publish: column n < mb went on to block n + ma after step n (two
+            // loops with one destination each: this form compiles without spills)
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (n0 + j >= g.mb && n0 + j < g.ma) colr[kBlk * (n0 + j)] = acc[0][j];
+            uint32_t *const colr_hi = colr + kBlk * g.ma;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (n0 + j < g.mb) colr_hi[kBlk * (n0 + j)] = acc[0][j];
+        }
+        __syncthreads();
+        fail = *abortf != 0;
+        if (fail) break;
+        // ---- column sums -> limbs (Section 2 carry scan inside)
+        ntt::normalize_limbs(g.nout, g.c + inst * g.nout, reinterpret_cast<uint32_t *>(X), spill, flags,
+                             [&](uint32_t k) {
+                                 const uint4 q = *reinterpret_cast<const uint4 *>(cols + 4 * k);
+                                 return (ntt::u128)((uint64_t)q.x + ((uint64_t)q.y << 8) +
+                                                    ((uint64_t)q.z << 16) + ((uint64_t)q.w << 24));
+                             });
+    }
+    if (fail && tid == 0) {
+        // wind down: give the MMAs issued last a bounded time to finish
+        if (gs > 0) {
+            const uint32_t last = gs - 1;
+            tc::mbar_wait(&dfull[last % kDSlotsTw], (last / kDSlotsTw) & 1u, kWaitNs);
+        }
+        atomicOr(&g_tc_fault, 1u);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
+}
 #undef BN_TC_FLUSH8
 #undef BN_TC_FLUSH
 
 struct TcGeometry {
     uint32_t na, nb, ma, mb, ma16, slotc, xs, w_off, ca_off, cb_off, braw_off, spill_off, flags_off, bar_off, smem;
-    bool swap;
+    bool swap, tw;  // tw: W in tensor memory (k_mul_quad_tc_tw, ma <= 128)
 };
 
 TcGeometry geometry(uint32_t na, uint32_t nb) {
@@ -372,13 +579,22 @@ TcGeometry geometry(uint32_t na, uint32_t nb) {
     q.mb = (q.nb + 31) / 32;
     q.ma16 = (q.ma + 15) & ~15u;
     q.slotc = q.ma16 > 128 ? 256 : 128;
+    q.tw = q.slotc == 128;
     q.xs = (2 * q.ma + (q.ma16 - q.ma)) * 16;
     const uint32_t nout = q.na + q.nb;
     const uint32_t stage_bytes = 4 * ((nout - 1) + ((nout - 1) >> 4) + 1);
-    q.w_off = 16 * q.xs;    // a multiple of 256
-    q.spill_off = q.w_off;  // the normalisation's spill words reuse the W slots
-    uint32_t off = q.w_off + (q.slotc == 256 ? 2 : 3) * kWBytes;
-    if (off < stage_bytes) off = stage_bytes;
+    q.w_off = 16 * q.xs;  // a multiple of 256
+    uint32_t off;
+    if (q.tw) {  // no W in shared memory; the spill words after the staging row
+        off = q.w_off > stage_bytes ? q.w_off : stage_bytes;
+        off = (off + 15) & ~15u;
+        q.spill_off = off;
+        off += 8 * kThreadsTw;
+    } else {
+        q.spill_off = q.w_off;  // the normalisation's spill words reuse the W slots
+        off = q.w_off + 2 * kWBytes;
+        if (off < stage_bytes) off = stage_bytes;
+    }
     off = (off + 15) & ~15u;
     q.ca_off = off;
     off += kBiasBytes;
@@ -388,7 +604,7 @@ TcGeometry geometry(uint32_t na, uint32_t nb) {
     off += 4 * (32 * (q.mb + 2) + 4);
     off = (off + 15) & ~15u;
     q.flags_off = off;
-    off += 4 * (kThreads / 32);
+    off += 4 * (kThreads / 32);  // at least one word per warp of either kernel
     q.bar_off = (off + 15) & ~15u;
     off = q.bar_off + 8 * (2 * kWSlotsMax + 2 * kDSlotsMax) + 16;
     q.smem = off > kMinSmem ? off : kMinSmem;
@@ -416,7 +632,7 @@ bn_status quad_tc_create(QuadTcPlan **out, uint32_t na, uint32_t nb) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc<256>);
-    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc<128>);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc_tw);
     if (e != cudaSuccess) {
         delete p;
         return BN_ECUDA;
@@ -466,10 +682,10 @@ cudaError_t quad_tc_launch(QuadTcPlan *p, const uint32_t *a, const uint32_t *b, 
     g.flags_off = q.flags_off;
     g.bar_off = q.bar_off;
     const uint32_t grid = batch < p->ctas ? (uint32_t)batch : p->ctas;
-    if (q.slotc == 256)
-        k_mul_quad_tc<256><<<grid, kThreads, q.smem, st>>>(g);
+    if (q.tw)
+        k_mul_quad_tc_tw<<<grid, kThreadsTw, q.smem, st>>>(g);
     else
-        k_mul_quad_tc<128><<<grid, kThreads, q.smem, st>>>(g);
+        k_mul_quad_tc<256><<<grid, kThreads, q.smem, st>>>(g);
     return cudaGetLastError();
 }
 
