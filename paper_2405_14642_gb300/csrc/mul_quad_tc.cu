@@ -25,20 +25,21 @@
 //
 // Per CTA (one per SM, persistent over the products) and product: XX in
 // shared memory as fp16 in the tensor core's core-matrix layout, b as raw
-// bytes.  Three roles form a pipeline linked by mbarriers:
-//  * warps 1-7 build W_J in shared memory (fp16, the MMA's A operand) into one
-//    of two or three slots;
-//  * warp 0 (which polls its mbarriers without sleeping: its wake-up is on the
-//    critical path) issues each step's MMAs into a D slot in tensor memory (two of 256
-//    columns when ma > 128, else four of 128): first a bias MMA (2048 x 4096
-//    into every element, so D starts at 2^23; its constant operands are one
-//    core matrix each, repeated over the rows by a zero stride), then 8 MMAs
-//    of K = 16 over the block's 128 bytes;
-//  * warps 8-23 read D: D = 2^23 + v with v < 2^23, so its bit pattern minus
-//    0x4b000000 is v, which they add into per-thread integer column sums
-//    (four warps per group of 32 lanes, each a quarter of the slot's columns)
-//    and publish to a per-CTA scratch row.
-// Every wait is bounded; a timeout raises a device flag (bn_tc_check).
+// bytes.  Each step is a bias MMA (2048 x 4096 into every element, so D
+// starts at 2^23; its constant operands are one core matrix each, repeated
+// over the rows by a zero stride) and 8 MMAs of K = 16 over the block's 128
+// bytes.  D = 2^23 + v with v < 2^23, so its bit pattern minus 0x4b000000 is
+// v, which the epilogue warps add into per-thread integer column sums (four
+// warps per group of 32 tensor-memory lanes, each a quarter of D's columns)
+// and publish to a per-CTA scratch row.  Two kernels, by the width of D:
+//  * k_mul_quad_tc (ma > 128): two D slots of 256 columns; warps 1-7 build
+//    W_J in shared memory (the MMA's A operand) into one of two slots, warps
+//    8-23 read D, warp 0 issues the MMAs;
+//  * k_mul_quad_tc_tw (ma <= 128): three D slots of 128 columns and two W
+//    slots in tensor memory, W built by the 16 epilogue warps (see there).
+// Warp 0 polls its mbarriers without sleeping (its wake-up is on the
+// critical path).  Every wait is bounded; a timeout raises a device flag
+// (bn_tc_check).
 #include <cuda_runtime.h>
 
 #include <new>
@@ -58,7 +59,7 @@ constexpr uint32_t kBuildWarps = 7;
 constexpr uint32_t kEpiWarps = 16;   // four per group of 32 tensor-memory lanes
 constexpr uint32_t kBlk = 128;       // bytes per block: rows of W, K of a step
 constexpr uint32_t kTmemCols = 512;  // the D slots
-constexpr uint32_t kWSlotsMax = 3, kDSlotsMax = 4;
+constexpr uint32_t kWSlotsMax = 2, kDSlotsMax = 3;  // mbarrier room for either kernel
 constexpr uint32_t kWBytes = 128 * 128 * 2;     // one W_J in fp16: 16 K-chunks x 16 row groups x 128 B
 constexpr uint32_t kWLbo = 2048, kWSbo = 128;   // W: K-chunk stride, 8-row-group stride
 constexpr uint64_t kWaitNs = 1000000000ull;     // 1 s per wait
@@ -167,13 +168,13 @@ constexpr uint32_t kBiasBytes = 256;  // each bias operand: one core matrix per 
     BN_TC_FLUSH(x) BN_TC_FLUSH(x + 1) BN_TC_FLUSH(x + 2) BN_TC_FLUSH(x + 3) BN_TC_FLUSH(x + 4) \
         BN_TC_FLUSH(x + 5) BN_TC_FLUSH(x + 6) BN_TC_FLUSH(x + 7)
 
-// SLOTC: columns per D slot, 256 (two slots, ma > 128) or 128 (four slots);
-// an epilogue warp owns SLOTC / 4 columns of its 32 lanes.
-template <uint32_t SLOTC>
+// Products whose longer operand has more than 128 blocks: two D slots of
+// SLOTC = 256 columns; an epilogue warp owns 64 columns of its 32 lanes.
 __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
-    constexpr uint32_t kDS = kTmemCols / SLOTC;     // D slots
-    constexpr uint32_t kCPW = SLOTC / 128;          // 32-column chunks per epilogue warp
-    constexpr uint32_t kWS = SLOTC == 256 ? 2 : 3;  // W slots (two leave room for XX at 256K bits)
+    constexpr uint32_t SLOTC = 256;
+    constexpr uint32_t kDS = kTmemCols / SLOTC;  // D slots
+    constexpr uint32_t kCPW = SLOTC / 128;       // 32-column chunks per epilogue warp
+    constexpr uint32_t kWS = 2;                  // W slots (two leave room for XX at 256K bits)
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *X = sm;  // XX and the W slots double as the normalisation's staging row
     uint8_t *W = sm + g.w_off;
@@ -311,19 +312,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
                     const uint32_t ch = kCPW * m + c;
                     if (ch < chi) {
                         const uint32_t ta = tbase + lane_off + SLOTC * d + 32 * ch;
-                        if constexpr (kCPW == 1) {  // the warp's 32 columns in one load
-                            uint32_t v[32];
-                            tc::tmem_ld32(ta, v);
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) acc[c][j] += v[j] - kBiasBits;
-                        } else {
+                        for (int hh = 0; hh < 4; ++hh) {  // 8 columns at a time: the register cap is 80
+                            uint32_t v[8];
+                            tc::tmem_ld8(ta + 8 * hh, v);
 #pragma unroll
-                            for (int hh = 0; hh < 4; ++hh) {  // 8 columns at a time: the register cap is 80
-                                uint32_t v[8];
-                                tc::tmem_ld8(ta + 8 * hh, v);
-#pragma unroll
-                                for (int j = 0; j < 8; ++j) acc[c][8 * hh + j] += v[j] - kBiasBits;
-                            }
+                            for (int j = 0; j < 8; ++j) acc[c][8 * hh + j] += v[j] - kBiasBits;
                         }
                     }
                 }
@@ -335,13 +329,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
                 // is published below instead)
                 const uint32_t f = J - n0;  // warp-uniform
                 if (J < g.mb && f < 32 * kCPW) {
-                    if constexpr (kCPW == 2) {
-                        switch (f) {
-                            BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) BN_TC_FLUSH8(16) BN_TC_FLUSH8(24)
-                            BN_TC_FLUSH8(32) BN_TC_FLUSH8(40) BN_TC_FLUSH8(48) BN_TC_FLUSH8(56)
-                        }
-                    } else {
-                        switch (f) { BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) BN_TC_FLUSH8(16) BN_TC_FLUSH8(24) }
+                    switch (f) {
+                        BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) BN_TC_FLUSH8(16) BN_TC_FLUSH8(24)
+                        BN_TC_FLUSH8(32) BN_TC_FLUSH8(40) BN_TC_FLUSH8(48) BN_TC_FLUSH8(56)
                     }
                 }
             }
@@ -566,7 +556,7 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
 #undef BN_TC_FLUSH
 
 struct TcGeometry {
-    uint32_t na, nb, ma, mb, ma16, slotc, xs, w_off, ca_off, cb_off, braw_off, spill_off, flags_off, bar_off, smem;
+    uint32_t na, nb, ma, mb, ma16, xs, w_off, ca_off, cb_off, braw_off, spill_off, flags_off, bar_off, smem;
     bool swap, tw;  // tw: W in tensor memory (k_mul_quad_tc_tw, ma <= 128)
 };
 
@@ -578,8 +568,7 @@ TcGeometry geometry(uint32_t na, uint32_t nb) {
     q.ma = (q.na + 31) / 32;
     q.mb = (q.nb + 31) / 32;
     q.ma16 = (q.ma + 15) & ~15u;
-    q.slotc = q.ma16 > 128 ? 256 : 128;
-    q.tw = q.slotc == 128;
+    q.tw = q.ma16 <= 128;
     q.xs = (2 * q.ma + (q.ma16 - q.ma)) * 16;
     const uint32_t nout = q.na + q.nb;
     const uint32_t stage_bytes = 4 * ((nout - 1) + ((nout - 1) >> 4) + 1);
@@ -631,7 +620,7 @@ bn_status quad_tc_create(QuadTcPlan **out, uint32_t na, uint32_t nb) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc<256>);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc);
     if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc_tw);
     if (e != cudaSuccess) {
         delete p;
@@ -685,7 +674,7 @@ cudaError_t quad_tc_launch(QuadTcPlan *p, const uint32_t *a, const uint32_t *b, 
     if (q.tw)
         k_mul_quad_tc_tw<<<grid, kThreadsTw, q.smem, st>>>(g);
     else
-        k_mul_quad_tc<256><<<grid, kThreads, q.smem, st>>>(g);
+        k_mul_quad_tc<<<grid, kThreads, q.smem, st>>>(g);
     return cudaGetLastError();
 }
 
