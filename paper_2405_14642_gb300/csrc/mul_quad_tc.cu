@@ -492,13 +492,16 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
                     break;
                 }
                 tc::fence_after_sync();
-                // W_{J+2} into the slot step J has finished reading
-                const bool more = J + 2 < S;
-                if (more) {
+                // W_{J+2} into the slot step J has finished reading, released to
+                // the MMA warp before D is read (it gates the MMAs two steps on)
+                if (J + 2 < S) {
                     uint32_t w16[16];
                     build_w_regs(braw, J + 2, r, m, w16);
                     tc::tmem_st16(wbase + lane_off + kWColsTw * (gs % kWSlotsTw) + 16 * m, w16);
                     tc::tmem_st_wait();
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&wfull[gs % kWSlotsTw]);
                 }
                 if (m < chi) {  // the warp's 32 columns of D in one load
                     uint32_t v[32];
@@ -508,10 +511,7 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
                 }
                 tc::fence_before_sync();
                 __syncwarp();
-                if (lane == 0) {
-                    if (more) tc::mbar_arrive(&wfull[gs % kWSlotsTw]);
-                    tc::mbar_arrive(&dempty[d]);
-                }
+                if (lane == 0) tc::mbar_arrive(&dempty[d]);
                 // column J now holds all of block J: store it and start the column
                 // over as block J + ma
                 const uint32_t f = J - n0;  // warp-uniform
