@@ -153,10 +153,33 @@ __device__ __forceinline__ uint64_t digit(const uint32_t *row, uint32_t ndig, ui
 }
 
 // Sub-problem s of the forward transform: y_s[j] = w_N^{js} sum_r x[j + rL] w_S^{rs}.
+// For S = 2 and 4 the inner sum is a radix-S butterfly: w_2 = w_4^2 = -1, so
+// only w_4 (times x1 - x3) takes a product, and w_N^0 = 1 takes none.
 template <class F>
 __device__ void load_fold(const NttArgs &p, const PrimeTab &tb, const uint32_t *row, uint32_t n,
                           uint32_t s, uint64_t *buf) {
     const uint32_t ndig = p.digit_bits == 16 ? 2 * n : n;
+    if (p.S == 2 || p.S == 4) {
+        for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) {
+            const uint64_t x0 = digit(row, ndig, j, p.digit_bits), x1 = digit(row, ndig, j + p.L, p.digit_bits);
+            uint64_t acc;
+            if (p.S == 2) {
+                acc = s == 0 ? F::add(x0, x1) : F::sub(x0, x1);
+            } else {
+                const uint64_t x2 = digit(row, ndig, j + 2 * p.L, p.digit_bits);
+                const uint64_t x3 = digit(row, ndig, j + 3 * p.L, p.digit_bits);
+                if (s == 0) acc = F::add(F::add(x0, x2), F::add(x1, x3));
+                else if (s == 2) acc = F::sub(F::add(x0, x2), F::add(x1, x3));
+                else {
+                    const uint64_t o = F::sub(x0, x2), q = F::mul(F::sub(x1, x3), tb.ws[1]);
+                    acc = s == 1 ? F::add(o, q) : F::sub(o, q);
+                }
+            }
+            if (s != 0) acc = F::mul(acc, tb.ffold[s * p.L + j]);
+            buf[phys(j)] = acc;
+        }
+        return;
+    }
     for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) {
         uint64_t acc = digit(row, ndig, j, p.digit_bits);
         if (p.S > 1) {
@@ -228,10 +251,25 @@ __device__ void prime_product(const NttArgs &p, const PrimeTab &tb, const uint32
             else dest[j] = v;
         }
     } else {
-        // Last radix-S inverse stage: c[j + rL] = sum_s w_S^{-rs} (scale w_N^{-js} z_s[j]).
+        // Last radix-S inverse stage: c[j + rL] = sum_s w_S^{-rs} (scale w_N^{-js} z_s[j]);
+        // for S = 2 and 4 a radix-S butterfly with one product, by w_4^-1.
         for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) {
             uint64_t u[4];
             for (uint32_t s = 0; s < p.S; ++s) u[s] = F::mul(Z[s * p.L + j], tb.ifold[s * p.L + j]);
+            if (p.S == 2) {
+                dest[j] = F::canon(F::add(u[0], u[1]));
+                dest[j + p.L] = F::canon(F::sub(u[0], u[1]));
+                continue;
+            }
+            if (p.S == 4) {
+                const uint64_t e0 = F::add(u[0], u[2]), e1 = F::add(u[1], u[3]);
+                const uint64_t o0 = F::sub(u[0], u[2]), o1 = F::mul(F::sub(u[1], u[3]), tb.iws[1]);
+                dest[j] = F::canon(F::add(e0, e1));
+                dest[j + p.L] = F::canon(F::add(o0, o1));
+                dest[j + 2 * p.L] = F::canon(F::sub(e0, e1));
+                dest[j + 3 * p.L] = F::canon(F::sub(o0, o1));
+                continue;
+            }
             for (uint32_t r = 0; r < p.S; ++r) {
                 uint64_t acc = u[0];
                 for (uint32_t s = 1; s < p.S; ++s) {
