@@ -85,7 +85,8 @@ __device__ __forceinline__ uint32_t tw_index(uint32_t base, uint32_t m, uint32_t
 }
 
 // KK decimation-in-frequency stages with half-sizes H, H/2, ..., H >> (KK-1).
-// UNIT: the group step is 1, so the last stage's twiddle is 1.  The
+// UNIT: the group step is 1, so the last stage's twiddle is 1, and so is that
+// of every group's element 0 in the other stages.  The
 // difference u - v + 2P (< 4P) goes to the twiddle multiply unreduced.
 template <class F, int KK, bool UNIT>
 __device__ __forceinline__ void dif_pass(typename F::Elem *buf, uint32_t L, uint32_t H,
@@ -109,13 +110,16 @@ __device__ __forceinline__ void dif_pass(typename F::Elem *buf, uint32_t L, uint
             const bool trivial = UNIT && hm == 1;
             W w[E / 2];
 #pragma unroll
-            for (int m = 0; m < (int)hm; ++m) w[m] = trivial ? W{} : __ldg(tw + tw_index(base, m, step, h));
+            for (int m = 0; m < (int)hm; ++m)
+                w[m] = (trivial || (UNIT && m == 0)) ? W{} : __ldg(tw + tw_index(base, m, step, h));
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 if (m & hm) continue;
+                // UNIT: base is a multiple of E, so element m's twiddle is w_{2h}^(m mod hm): 1 for m mod hm = 0
+                const bool one = UNIT && (m & (hm - 1)) == 0;
                 const T u = x[m], v = x[m + hm];
                 x[m] = F::add(u, v);
-                x[m + hm] = trivial ? F::sub(u, v) : F::twiddle(u + F::TWO_P - v, w[m & (hm - 1)]);
+                x[m + hm] = one ? F::sub(u, v) : F::twiddle(u + F::TWO_P - v, w[m & (hm - 1)]);
             }
         }
         if constexpr (UNIT) store_run<T, E>(buf, base, x);
@@ -127,7 +131,8 @@ __device__ __forceinline__ void dif_pass(typename F::Elem *buf, uint32_t L, uint
 }
 
 // KK decimation-in-time stages with half-sizes h0, 2 h0, ..., h0 << (KK-1).
-// UNIT: h0 = 1, so the first stage's twiddle is 1.
+// UNIT: h0 = 1, so the first stage's twiddle is 1 (and every group's element
+// 0 has twiddle 1 in the other stages).
 template <class F, int KK, bool UNIT>
 __device__ __forceinline__ void dit_pass(typename F::Elem *buf, uint32_t L, uint32_t h0,
                                          const typename F::Tw *tw) {
@@ -150,12 +155,14 @@ __device__ __forceinline__ void dit_pass(typename F::Elem *buf, uint32_t L, uint
             const bool trivial = UNIT && hm == 1;
             W w[E / 2];
 #pragma unroll
-            for (int m = 0; m < (int)hm; ++m) w[m] = trivial ? W{} : __ldg(tw + tw_index(base, m, step, h));
+            for (int m = 0; m < (int)hm; ++m)
+                w[m] = (trivial || (UNIT && m == 0)) ? W{} : __ldg(tw + tw_index(base, m, step, h));
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 if (m & hm) continue;
+                const bool one = UNIT && (m & (hm - 1)) == 0;  // twiddle w_{2h}^0 = 1 (as in dif_pass)
                 const T u = x[m];
-                const T v = trivial ? x[m + hm] : F::twiddle_lazy(x[m + hm], w[m & (hm - 1)]);
+                const T v = one ? x[m + hm] : F::twiddle_lazy(x[m + hm], w[m & (hm - 1)]);
                 x[m] = F::add(u, v);
                 x[m + hm] = F::sub(u, v);
             }
@@ -266,7 +273,8 @@ __host__ __device__ constexpr uint32_t pidx_c(uint32_t i) {
 
 // KK stages over groups of E = 2^KK elements base + m*STEP; DIF: half-sizes
 // STEP*E/2 .. STEP (decimation in frequency), else STEP .. STEP*E/2
-// (decimation in time).  UNIT (STEP = 1): the trivial stage has twiddle 1.
+// (decimation in time).  UNIT (STEP = 1): the trivial stage has twiddle 1, and
+// so has element 0 of every group in the other stages.
 template <class F, int KK, bool UNIT, uint32_t STEP, uint32_t L, uint32_t NT, bool DIF>
 __device__ __forceinline__ void pass_c(typename F::Elem *buf, const typename F::Tw *tw) {
     using T = typename F::Elem;
@@ -295,17 +303,19 @@ __device__ __forceinline__ void pass_c(typename F::Elem *buf, const typename F::
             const bool trivial = UNIT && hm == 1;
             W w[E / 2];
 #pragma unroll
-            for (int m = 0; m < (int)hm; ++m) w[m] = trivial ? W{} : __ldg(twj + (hm + m) * STEP);
+            for (int m = 0; m < (int)hm; ++m) w[m] = (trivial || (UNIT && m == 0)) ? W{} : __ldg(twj + (hm + m) * STEP);
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 if (m & hm) continue;
+                // UNIT: j0 = 0, so element m's twiddle is tw[hm + m mod hm]: 1 for m mod hm = 0
+                const bool one = UNIT && (m & (hm - 1)) == 0;
                 if constexpr (DIF) {
                     const T u = x[m], v = x[m + hm];
                     x[m] = F::add(u, v);
-                    x[m + hm] = trivial ? F::sub(u, v) : F::twiddle(u + F::TWO_P - v, w[m & (hm - 1)]);
+                    x[m + hm] = one ? F::sub(u, v) : F::twiddle(u + F::TWO_P - v, w[m & (hm - 1)]);
                 } else {
                     const T u = x[m];
-                    const T v = trivial ? x[m + hm] : F::twiddle_lazy(x[m + hm], w[m & (hm - 1)]);
+                    const T v = one ? x[m + hm] : F::twiddle_lazy(x[m + hm], w[m & (hm - 1)]);
                     x[m] = F::add(u, v);
                     x[m + hm] = F::sub(u, v);
                 }
