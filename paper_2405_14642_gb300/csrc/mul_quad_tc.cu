@@ -59,7 +59,7 @@ constexpr uint32_t kBuildWarps = 7;
 constexpr uint32_t kEpiWarps = 16;   // four per group of 32 tensor-memory lanes
 constexpr uint32_t kBlk = 128;       // bytes per block: rows of W, K of a step
 constexpr uint32_t kTmemCols = 512;  // the D slots
-constexpr uint32_t kWSlotsMax = 2, kDSlotsMax = 3;  // mbarrier room for either kernel
+constexpr uint32_t kWSlotsMax = 4, kDSlotsMax = 4;  // mbarrier room for any of the kernels
 constexpr uint32_t kWBytes = 128 * 128 * 2;     // one W_J in fp16: 16 K-chunks x 16 row groups x 128 B
 constexpr uint32_t kWLbo = 2048, kWSbo = 128;   // W: K-chunk stride, 8-row-group stride
 constexpr uint64_t kWaitNs = 1000000000ull;     // 1 s per wait
@@ -378,20 +378,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
 // issues the MMAs; warps 1-16, four per group of 32 tensor-memory lanes, each
 // build a quarter of their lanes' W rows (16 columns), read 32 columns of D
 // (one load) and keep those columns' sums.
+//
+// DW = 64 (ma <= 64, up to 64K bits): four D slots of 64 columns and four W
+// slots, and the MMA warp issues the steps in pairs (J, J + 1), their MMAs
+// interleaved: two accumulation chains in flight instead of one, while the
+// epilogue warps build the next pair's W's.
 constexpr uint32_t kThreadsTw = 544;
-constexpr uint32_t kDSlotsTw = 3, kWSlotsTw = 2;
-constexpr uint32_t kDColsTw = 128, kWColsTw = 64;  // tensor-memory columns per D slot, per W slot
+constexpr uint32_t kWColsTw = 64;  // tensor-memory columns per W slot
 
+template <uint32_t DW>
 __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
+    constexpr uint32_t kDSlotsTw = DW == 128 ? 3 : 4, kWSlotsTw = DW == 128 ? 2 : 4;
+    constexpr uint32_t kDColsTw = DW;       // tensor-memory columns per D slot
+    constexpr uint32_t kCW = DW / 4;        // D columns per epilogue warp
+    constexpr bool kPair = DW == 64;        // MMAs of two steps interleaved
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *X = sm;  // XX doubles as the normalisation's staging row
     uint32_t *braw = reinterpret_cast<uint32_t *>(sm + g.braw_off);
     uint64_t *spill = reinterpret_cast<uint64_t *>(sm + g.spill_off);
     uint32_t *flags = reinterpret_cast<uint32_t *>(sm + g.flags_off);
-    uint64_t *wfull = reinterpret_cast<uint64_t *>(sm + g.bar_off);  // [2], one arrival per epilogue warp
-    uint64_t *dfull = wfull + kWSlotsTw;                                // [3], MMA commits
-    uint64_t *dempty = dfull + kDSlotsTw;                               // [3], one arrival per epilogue warp
-    uint32_t *slot = reinterpret_cast<uint32_t *>(dempty + kDSlotsTw);
+    uint64_t *wfull = reinterpret_cast<uint64_t *>(sm + g.bar_off);  // [kWSlotsTw], one arrival per epilogue warp
+    uint64_t *dfull = wfull + kWSlotsMax;                               // [kDSlotsTw], MMA commits
+    uint64_t *dempty = dfull + kDSlotsMax;                              // [kDSlotsTw], one arrival per epilogue warp
+    uint32_t *slot = reinterpret_cast<uint32_t *>(dempty + kDSlotsMax);
     volatile uint32_t *abortf = slot + 1;
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -415,7 +424,7 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = *slot, S = g.mb + 1;  // steps J = 0..mb
-    const uint32_t wbase = tbase + kDSlotsTw * kDColsTw;  // W slot k at column wbase + 64 k
+    const uint32_t wbase = tbase + kDSlotsTw * kDColsTw;  // W slot k at column wbase + 64 k (ends at 512)
     const uint32_t lane_off = (32 * lq) << 16;
     const uint32_t x_s = tc::smem_u32(X);
     uint32_t *cols = g.scratch + blockIdx.x * g.scratch_stride;
@@ -448,35 +457,51 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
             const uint32_t idesc = tc::idesc_f16_f32(128, g.ma16);
             const uint64_t bstep = (2 * g.xs) >> 4;
             const uint64_t cad = tc::smem_desc(x_s + g.ca_off, 128, 0), cbd = tc::smem_desc(x_s + g.cb_off, 128, 0);
-            for (uint32_t J = 0; J < S; ++J, ++gs) {
-                const uint32_t k = gs % kWSlotsTw, d = gs % kDSlotsTw, ud = gs / kDSlotsTw;
-                bool ok = tc::mbar_wait_spin(&wfull[k], (gs / kWSlotsTw) & 1u, kWaitNs, abortf);
-                if (ok && ud > 0) ok = tc::mbar_wait_spin(&dempty[d], (ud - 1) & 1u, kWaitNs, abortf);
+            constexpr uint32_t kStepsPerIssue = kPair ? 2 : 1;
+            for (uint32_t J = 0; J < S; J += kStepsPerIssue) {
+                const uint32_t n = J + 1 < S ? kStepsPerIssue : 1;  // steps issued together
+                bool ok = true;
+                for (uint32_t h = 0; h < n && ok; ++h) {
+                    const uint32_t gh = gs + h, ud = gh / kDSlotsTw;
+                    ok = tc::mbar_wait_spin(&wfull[gh % kWSlotsTw], (gh / kWSlotsTw) & 1u, kWaitNs, abortf);
+                    if (ok && ud > 0)
+                        ok = tc::mbar_wait_spin(&dempty[gh % kDSlotsTw], (ud - 1) & 1u, kWaitNs, abortf);
+                }
                 if (!__all_sync(FULL_MASK, ok)) {
                     *abortf = 1;
                     break;
                 }
                 tc::fence_after_sync();
-                const uint32_t dt = tbase + kDColsTw * d, at = wbase + kWColsTw * k;
-                const uint64_t bd = tc::smem_desc(x_s + (g.ma - J) * 16, g.xs, 128);  // XX from block ma - J
+                const uint32_t d0 = gs % kDSlotsTw, d1 = (gs + 1) % kDSlotsTw;
+                const uint32_t dt0 = tbase + kDColsTw * d0, dt1 = tbase + kDColsTw * d1;
+                const uint32_t at0 = wbase + kWColsTw * (gs % kWSlotsTw);
+                const uint32_t at1 = wbase + kWColsTw * ((gs + 1) % kWSlotsTw);
+                const uint64_t bd0 = tc::smem_desc(x_s + (g.ma - J) * 16, g.xs, 128);  // XX from block ma - J
+                const uint64_t bd1 = bd0 - 1;  // step J + 1: one block (16 bytes) lower
                 if (tc::elect_one()) {
-                    tc::mma_f16_ss(dt, cad, cbd, idesc, 0);  // D = 2^23
+                    tc::mma_f16_ss(dt0, cad, cbd, idesc, 0);  // D = 2^23
+                    if (n == 2) tc::mma_f16_ss(dt1, cad, cbd, idesc, 0);
 #pragma unroll
-                    for (uint32_t kk = 0; kk < 8; ++kk) tc::mma_f16_ts(dt, at + 8 * kk, bd + kk * bstep, idesc, 1);
-                    tc::mma_commit(&dfull[d]);
+                    for (uint32_t kk = 0; kk < 8; ++kk) {
+                        tc::mma_f16_ts(dt0, at0 + 8 * kk, bd0 + kk * bstep, idesc, 1);
+                        if (n == 2) tc::mma_f16_ts(dt1, at1 + 8 * kk, bd1 + kk * bstep, idesc, 1);
+                    }
+                    tc::mma_commit(&dfull[d0]);
+                    if (n == 2) tc::mma_commit(&dfull[d1]);
                 }
                 __syncwarp();
+                gs += n;
             }
         } else {
-            // column quarter m: D columns [32 m, 32 m + 32), W columns [16 m, 16 m + 16)
-            const uint32_t m = (warp - 1) >> 2, n0 = 32 * m, r = 32 * lq + lane;
-            const uint32_t chi = (g.ma + 31) >> 5;  // chunks that hold D's ma columns
-            uint32_t *const colr = cols + r;        // this thread's row of every column block
-            uint32_t acc[1][32];
+            // column quarter m: D columns [kCW m, kCW m + kCW), W columns [16 m, 16 m + 16)
+            const uint32_t m = (warp - 1) >> 2, n0 = kCW * m, r = 32 * lq + lane;
+            uint32_t *const colr = cols + r;  // this thread's row of every column block
+            uint32_t acc[1][kCW];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) acc[0][i] = 0;
-            // W_0 and W_1 (their slots are free: every earlier MMA has delivered its D)
-            for (uint32_t J = 0; J < 2 && J < S; ++J) {
+            for (int i = 0; i < (int)kCW; ++i) acc[0][i] = 0;
+            // W_0 .. W_{kWSlotsTw - 1} (their slots are free: every earlier MMA
+            // has delivered its D)
+            for (uint32_t J = 0; J < kWSlotsTw && J < S; ++J) {
                 uint32_t w16[16];
                 build_w_regs(braw, J, r, m, w16);
                 tc::tmem_st16(wbase + lane_off + kWColsTw * ((gs + J) % kWSlotsTw) + 16 * m, w16);
@@ -492,22 +517,23 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
                     break;
                 }
                 tc::fence_after_sync();
-                // W_{J+2} into the slot step J has finished reading, released to
-                // the MMA warp before D is read (it gates the MMAs two steps on)
-                if (J + 2 < S) {
+                // W_{J+kWSlotsTw} into the slot step J has finished reading,
+                // released to the MMA warp before D is read (it gates later MMAs)
+                if (J + kWSlotsTw < S) {
                     uint32_t w16[16];
-                    build_w_regs(braw, J + 2, r, m, w16);
+                    build_w_regs(braw, J + kWSlotsTw, r, m, w16);
                     tc::tmem_st16(wbase + lane_off + kWColsTw * (gs % kWSlotsTw) + 16 * m, w16);
                     tc::tmem_st_wait();
                     tc::fence_before_sync();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&wfull[gs % kWSlotsTw]);
                 }
-                if (m < chi) {  // the warp's 32 columns of D in one load
-                    uint32_t v[32];
-                    tc::tmem_ld32(tbase + lane_off + kDColsTw * d + n0, v);
+                if (n0 < g.ma) {  // the warp's kCW columns of D in one load
+                    uint32_t v[kCW];
+                    if constexpr (kCW == 32) tc::tmem_ld32(tbase + lane_off + kDColsTw * d + n0, v);
+                    else tc::tmem_ld16(tbase + lane_off + kDColsTw * d + n0, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[0][j] += v[j] - kBiasBits;
+                    for (int j = 0; j < (int)kCW; ++j) acc[0][j] += v[j] - kBiasBits;
                 }
                 tc::fence_before_sync();
                 __syncwarp();
@@ -515,18 +541,22 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
                 // column J now holds all of block J: store it and start the column
                 // over as block J + ma
                 const uint32_t f = J - n0;  // warp-uniform
-                if (J < g.mb && f < 32) {
-                    switch (f) { BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) BN_TC_FLUSH8(16) BN_TC_FLUSH8(24) }
+                if (J < g.mb && f < kCW) {
+                    if constexpr (kCW == 32) {
+                        switch (f) { BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) BN_TC_FLUSH8(16) BN_TC_FLUSH8(24) }
+                    } else {
+                        switch (f) { BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) }
+                    }
                 }
             }
             // publish: column n < mb went on to block n + ma after step n (two
             // loops with one destination each: this form compiles without spills)
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
+            for (int j = 0; j < (int)kCW; ++j)
                 if (n0 + j >= g.mb && n0 + j < g.ma) colr[kBlk * (n0 + j)] = acc[0][j];
             uint32_t *const colr_hi = colr + kBlk * g.ma;
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
+            for (int j = 0; j < (int)kCW; ++j)
                 if (n0 + j < g.mb) colr_hi[kBlk * (n0 + j)] = acc[0][j];
         }
         __syncthreads();
@@ -558,6 +588,7 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
 struct TcGeometry {
     uint32_t na, nb, ma, mb, ma16, xs, w_off, ca_off, cb_off, braw_off, spill_off, flags_off, bar_off, smem;
     bool swap, tw;  // tw: W in tensor memory (k_mul_quad_tc_tw, ma <= 128)
+    uint32_t dw;    // its D slot width: 64 (ma <= 64) or 128
 };
 
 TcGeometry geometry(uint32_t na, uint32_t nb) {
@@ -569,6 +600,7 @@ TcGeometry geometry(uint32_t na, uint32_t nb) {
     q.mb = (q.nb + 31) / 32;
     q.ma16 = (q.ma + 15) & ~15u;
     q.tw = q.ma16 <= 128;
+    q.dw = q.ma16 <= 64 ? 64 : 128;
     q.xs = (2 * q.ma + (q.ma16 - q.ma)) * 16;
     const uint32_t nout = q.na + q.nb;
     const uint32_t stage_bytes = 4 * ((nout - 1) + ((nout - 1) >> 4) + 1);
@@ -621,7 +653,8 @@ bn_status quad_tc_create(QuadTcPlan **out, uint32_t na, uint32_t nb) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc);
-    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc_tw);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc_tw<128>);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc_tw<64>);
     if (e != cudaSuccess) {
         delete p;
         return BN_ECUDA;
@@ -671,8 +704,10 @@ cudaError_t quad_tc_launch(QuadTcPlan *p, const uint32_t *a, const uint32_t *b, 
     g.flags_off = q.flags_off;
     g.bar_off = q.bar_off;
     const uint32_t grid = batch < p->ctas ? (uint32_t)batch : p->ctas;
-    if (q.tw)
-        k_mul_quad_tc_tw<<<grid, kThreadsTw, q.smem, st>>>(g);
+    if (q.tw && q.dw == 64)
+        k_mul_quad_tc_tw<64><<<grid, kThreadsTw, q.smem, st>>>(g);
+    else if (q.tw)
+        k_mul_quad_tc_tw<128><<<grid, kThreadsTw, q.smem, st>>>(g);
     else
         k_mul_quad_tc<<<grid, kThreads, q.smem, st>>>(g);
     return cudaGetLastError();
