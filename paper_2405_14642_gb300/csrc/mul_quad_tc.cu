@@ -35,8 +35,10 @@
 //  * k_mul_quad_tc (ma > 128): two D slots of 256 columns; warps 1-7 build
 //    W_J in shared memory (the MMA's A operand) into one of two slots, warps
 //    8-23 read D, warp 0 issues the MMAs;
-//  * k_mul_quad_tc_tw (ma <= 128): three D slots of 128 columns and two W
-//    slots in tensor memory, W built by the 16 epilogue warps (see there).
+//  * k_mul_quad_tc_tw (ma <= 128): W in tensor memory, built by the 16
+//    epilogue warps; three D slots of 128 columns and two W slots, or, when
+//    ma <= 64, four of each with 64-column D slots and the steps issued in
+//    interleaved pairs (see there).
 // Warp 0 polls its mbarriers without sleeping (its wake-up is on the
 // critical path).  Every wait is bounded; a timeout raises a device flag
 // (bn_tc_check).
