@@ -4,17 +4,25 @@
 One step = one pass of the whole hot path over the size-sweep workload:
   * addition and schoolbook multiplication of 1K .. 256K-bit integers
     (u32 limbs), each size a batch holding 64 MiB of operand limbs per side;
-  * transform multiplication (one 64-bit prime with 16-bit digits, and two
-    primes with 32-bit digits and CRT) at 16K .. 256K bits, same batches.
+  * transform multiplication (one 64-bit prime with 16-bit digits, two
+    64-bit primes with 32-bit digits and CRT, three 32-bit primes) at
+    16K .. 256K bits, same batches.
 Each operation is one kernel launch through the library's C ABI (plans).
 
-Printed: one JSON line (rank 0).  `value` is multiplications completed per
-second over the step (inputs resident in HBM); the addition throughput, the
-per-operation breakdown, the roofline of the dominant kernel, the clocks seen
-during the timed region, an end-to-end figure through the host-buffer entry
-point, and the CPU oracle timed on a bounded sample are reported beside it.
+Printed on stdout: one compact JSON line (rank 0, at most about 3 KB).
+`value` is multiplications completed per second over the step (inputs
+resident in HBM); beside it the addition throughput, the roofline of the
+dominant kernel, the clocks seen during the timed region, an end-to-end
+figure through the host-buffer entry point, the CPU oracle timed on a bounded
+sample, and summary figures of the off-step sections (roofline fractions of
+the kernels at their key sizes, the transform/schoolbook crossover sizes, the
+mixed-size batch against the plain per-class and per-item launches, the
+serving loop's latencies).  The full detail (per-op breakdown and rooflines,
+every product form timed alone at every size, the fused programs, the mixed
+and serving runs) goes to the file named by --detail, else to stderr.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--detail PATH]
 Under torchrun each rank runs the same per-rank workload (weak scaling).
 """
 from __future__ import annotations
@@ -121,15 +129,15 @@ def build_ops(quick: bool = False, integer_schoolbook: bool = False):
 def workload_config(ops, world: int):
     bits = sorted({o.bits for o in ops})
     return {
-        "workload": "size sweep 1K-256K bits: add + schoolbook mul at 9 sizes (integer-pipe "
+        "workload": "size sweep 1K-256K bits: add + schoolbook mul at every size (integer-pipe "
                     "kernel below 32K bits, tensor-core kernel from 32K bits), NTT mul "
-                    "(1x64-bit prime/16-bit digits, 2-prime CRT/32-bit digits and 3x32-bit "
-                    "primes/32-bit digits) at 16K-256K; 64 MiB of u32 operand limbs per side "
-                    "per size",
+                    "(1x64-bit prime/16-bit digits, 2x64-bit primes CRT/32-bit digits, "
+                    "3x32-bit primes/32-bit digits) at 16K-256K; 64 MiB of u32 operand limbs "
+                    "per side per size",
         "sizes_bits": bits,
         "batch_per_size": {str(b): next(o.batch for o in ops if o.bits == b) for b in bits},
-        "ops_per_step": [o.label for o in ops],
-        "cache": "inputs larger than L2 (>= 128 MiB of operands per launch)",
+        "ops_per_step": len(ops),
+        "cache": "inputs larger than L2 (>= 128 MiB of operands per launch), no flush",
         "per_rank": "each rank runs the full workload (weak scaling)",
         "ranks": world,
     }
@@ -361,9 +369,8 @@ def run_gpu(args, rank, world, local_rank):
     if rank != 0:
         return None
     # Per-GPU sections, on rank 0 only.
-    isolated = run_isolated(args, torch, ops, plans, inputs, outs, stream, dev) if args.isolated_reps else None
-    schoolbook = (run_schoolbook_compare(args, torch, bn, ops, inputs, outs, stream, dev)
-                  if args.isolated_reps else None)
+    forms = (run_forms(args, torch, bn, ops, inputs, outs, stream, dev)
+             if args.isolated_reps else None)
     fused = None
     if args.fused_reps > 0:
         fused = run_fused(args, torch, bn, dev, inputs, peak_info)
@@ -379,41 +386,19 @@ def run_gpu(args, rank, world, local_rank):
     for o in ops:
         ms = float(np.mean(o.times_ms))
         row = {"op": o.label, "ms": round(ms, 4), "batch": o.batch}
+        rf = roofline_of(o, ms, hbm_peak, hbm_kind, tc_peak, tc_kind, peak_info)
         if o.name == "add":
-            gbs = o.bytes / (ms * 1e-3) / 1e9
-            row.update(gbs=round(gbs, 1), adds_per_s=o.batch / (ms * 1e-3))
-            rooflines.append({"op": o.label, "bound": "hbm", "achieved": round(gbs, 1),
-                              "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
-                              "peak_kind": hbm_kind, "traffic": None})
-        elif o.name == "quadtc":
-            gp = o.prods / (ms * 1e-3) / 1e12
-            tf = TC_FLOP_PER_WORD_PRODUCT * gp
-            row.update(mults_per_s=o.batch / (ms * 1e-3), word_tprods=round(gp, 3), tflops=round(tf, 1))
-            rooflines.append({"op": o.label, "bound": "tensor", "achieved": round(tf, 1),
-                              "peak": tc_peak, "unit": "TFLOP/s", "frac": round(tf / tc_peak, 4),
-                              "peak_kind": tc_kind + "; FLOP = 2 per byte product, 16 byte products "
-                                           "per word product (the exact fp16 contraction's useful work)",
-                              "traffic": None})
+            row.update(gbs=rf["achieved"], adds_per_s=o.batch / (ms * 1e-3))
         else:
-            gp = o.prods / (ms * 1e-3) / 1e12
-            peak_t = peak_info["peak_word_products_per_s"] / 1e12
-            row.update(mults_per_s=o.batch / (ms * 1e-3), word_tprods=round(gp, 3))
-            rooflines.append({"op": o.label, "bound": "alu", "achieved": round(gp, 3),
-                              "peak": round(peak_t, 3), "unit": "T word-products/s",
-                              "frac": round(gp / peak_t, 4),
-                              "peak_kind": "derived: 1/(1/%d + 1/%d) = %.2f word products/clk/SM "
-                                           "(mad.lo, mad.hi rates from the probe) x %d SMs x %.0f MHz"
-                                           % (peak_info["mad_lo_per_clk_per_sm"],
-                                              peak_info["mad_hi_per_clk_per_sm"],
-                                              peak_info["word_products_per_clk_per_sm"],
-                                              peak_info["sms"], SM_MAX_MHZ_NOMINAL),
-                              "traffic": None})
+            row.update(mults_per_s=o.batch / (ms * 1e-3), word_tprods=round(o.prods / (ms * 1e-3) / 1e12, 3))
+        rooflines.append(rf)
         rows.append(row)
     total_ms = [sum(o.times_ms[k] for o in ops) for k in range(args.steps)]
     dom = max(range(len(ops)), key=lambda i: np.mean(ops[i].times_ms))
     roof = dict(rooflines[dom])
     roof["traffic"] = kernel_traffic(ops[dom].label)
     roof["kernel_share_of_step"] = round(float(np.mean(ops[dom].times_ms)) / float(np.mean(total_ms)), 4)
+    roof["ms"] = round(float(np.mean(ops[dom].times_ms)), 4)
     add_ops = [o for o in ops if o.name == "add"]
     add_gbs = (sum(o.bytes for o in add_ops) / (sum(np.mean(o.times_ms) for o in add_ops) * 1e-3) / 1e9
                if add_ops else None)
@@ -429,61 +414,79 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": roof, "rooflines": rooflines, "breakdown": rows,
         "imad_probe": peak_info, "clocks": clocks, "gpu_launches": gpu_launches,
         "e2e": e2e, "cpu_baseline": cpu, "impl": "ours", "skipped_ops": skipped,
-        "mixed": mixed, "serving": serving, "fused": fused, "isolated": isolated,
-        "schoolbook": schoolbook,
+        "mixed": mixed, "serving": serving, "fused": fused, "forms": forms,
     }
 
 
-def run_isolated(args, torch, ops, plans, inputs, outs, stream, dev):
-    """Each op of the step timed alone, outside the timed region: before every
-    launch a read-only pass over 256 MiB evicts whatever the previous kernel
-    left dirty in L2 (inside the step, an op pays for writing back the
-    previous op's result, up to 128 MiB).  Results still in L2 when the timed
-    launch ends are written back after it, so these are per-kernel figures,
-    not a substitute for the step time."""
-    clean_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    rows = []
-    for o in ops:
-        ta, tb = inputs[o.bits]
-        out = outs[(o.bits, o.nout)]
-        ts = []
-        for _ in range(args.isolated_reps):
-            clean_buf.sum(dtype=torch.int64)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            plans[o.label].execute(ta, tb, out=out, stream=stream)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        ms = float(np.median(ts))
-        row = {"op": o.label, "ms": round(ms, 4)}
-        if o.name == "add":
-            row["gbs"] = round(o.bytes / (ms * 1e-3) / 1e9, 1)
-        else:
-            row["word_tprods"] = round(o.prods / (ms * 1e-3) / 1e12, 3)
-        rows.append(row)
-    add_rows = [(o, r) for o, r in zip(ops, rows) if o.name == "add"]
-    add_gbs = (sum(o.bytes for o, _ in add_rows) / (sum(r["ms"] for _, r in add_rows) * 1e-3) / 1e9
-               if add_rows else None)
-    return {"how": "median of %d launches, each after a read-only pass over 256 MiB (L2 holds "
-                   "no dirty lines from other kernels)" % args.isolated_reps,
-            "add_gbs": round(add_gbs, 1) if add_gbs else None, "ops": rows}
+def roofline_of(o, ms, hbm_peak, hbm_kind, tc_peak, tc_kind, peak_info):
+    """Roofline entry of one op from its mean event time: algorithmic bytes
+    (add) against measured HBM, fp16-equivalent FLOP (tensor-core schoolbook)
+    against the measured sustained tensor peak, word products (integer-pipe
+    products) against the derived word-product ceiling."""
+    if o.name == "add":
+        gbs = o.bytes / (ms * 1e-3) / 1e9
+        return {"op": o.label, "bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(gbs / hbm_peak, 4), "peak_kind": hbm_kind + " copy",
+                "traffic": None}
+    gp = o.prods / (ms * 1e-3) / 1e12
+    if o.name == "quadtc":
+        tf = TC_FLOP_PER_WORD_PRODUCT * gp
+        return {"op": o.label, "bound": "tensor", "achieved": round(tf, 1), "peak": tc_peak,
+                "unit": "TFLOP/s", "frac": round(tf / tc_peak, 4),
+                "peak_kind": tc_kind + "; 32 fp16 FLOP per word product", "traffic": None}
+    peak_t = peak_info["peak_word_products_per_s"] / 1e12
+    return {"op": o.label, "bound": "alu", "achieved": round(gp, 3), "peak": round(peak_t, 3),
+            "unit": "T word-products/s", "frac": round(gp / peak_t, 4),
+            "peak_kind": "derived: 1/(1/%d+1/%d) word products/clk/SM x %d SMs x %.0f MHz"
+                         % (peak_info["mad_lo_per_clk_per_sm"], peak_info["mad_hi_per_clk_per_sm"],
+                            peak_info["sms"], SM_MAX_MHZ_NOMINAL),
+            "traffic": None}
 
 
-def run_schoolbook_compare(args, torch, bn, ops, inputs, outs, stream, dev):
-    """The two schoolbook kernels side by side at the sizes where the step
-    uses the tensor-core one: each timed alone (median of the isolated
-    repetitions, L2 cleaned before each launch), word products per second."""
+FORMS = ("quad", "quadtc", "ntt64", "crt", "ntt3")
+
+
+def crossover_bits(table, form):
+    """Smallest size from which `form` is faster than the better of the two
+    schoolbook kernels at that size and at every larger size timed (None if
+    it is not faster at the largest size)."""
+    sizes = sorted(table)
+    best = None
+    for bits in reversed(sizes):
+        row = table[bits]
+        school = [row[f] for f in ("quad", "quadtc") if row.get(f)]
+        if not row.get(form) or not school or row[form] >= min(school):
+            break
+        best = bits
+    return best
+
+
+def run_forms(args, torch, bn, ops, inputs, outs, stream, dev):
+    """Every product form alone at every size of the sweep, on the step's
+    operands: the integer-pipe and tensor-core schoolbooks and the three
+    transform forms (plus the addition), each the median of the isolated
+    repetitions, each launch after a read-only pass over 256 MiB so that L2
+    holds no dirty lines from another kernel.  From this table, the
+    transform/schoolbook crossover size of each transform form."""
     clean_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    rows = []
-    for o in ops:
-        if o.name != "quadtc":
-            continue
-        ta, tb = inputs[o.bits]
-        out = outs[(o.bits, o.nout)]
-        row = {"bits": o.bits, "batch": o.batch}
-        for name, opcode in (("integer", bn.BN_OP_MUL_QUAD), ("tensor", bn.BN_OP_MUL_QUAD_TC)):
-            with bn.Plan(opcode, o.na, o.nb, o.batch) as plan:
+    table, rows = {}, []
+    for bits in sorted(inputs):
+        ta, tb = inputs[bits]
+        batch, n = ta.shape
+        table[bits] = {}
+        for name in ("add",) + FORMS:
+            nout = n + 1 if name == "add" else 2 * n
+            out = outs.get((bits, nout))
+            if out is None:
+                out = torch.empty((batch, nout), dtype=torch.int32, device=dev)
+                outs[(bits, nout)] = out
+            try:
+                plan = bn.Plan(OPCODES[name](bn), n, n, batch)
+            except bn.BnError as e:
+                if e.status != 4:
+                    raise
+                continue
+            with plan:
                 plan.execute(ta, tb, out=out, stream=stream)
                 ts = []
                 for _ in range(args.isolated_reps):
@@ -495,13 +498,14 @@ def run_schoolbook_compare(args, torch, bn, ops, inputs, outs, stream, dev):
                     torch.cuda.synchronize()
                     ts.append(e0.elapsed_time(e1))
             ms = float(np.median(ts))
-            row[name + "_ms"] = round(ms, 4)
-            row[name + "_word_tprods"] = round(o.prods / (ms * 1e-3) / 1e12, 3)
-        row["speedup"] = round(row["integer_ms"] / row["tensor_ms"], 3)
-        rows.append(row)
+            table[bits][name] = ms
+            rows.append({"op": f"{name}@{bits // 1024}K", "ms": round(ms, 4)})
     bn.bn_tc_check()
-    return {"how": "each kernel alone, median of %d launches after a read-only pass over 256 MiB"
-                   % args.isolated_reps, "sizes": rows}
+    cross = {f: crossover_bits(table, f) for f in ("ntt64", "crt", "ntt3")}
+    return {"how": "each (form, size) alone, median of %d launches after a read-only pass over "
+                   "256 MiB" % args.isolated_reps,
+            "crossover_bits": cross, "ops": rows,
+            "table_ms": {str(k): {f: round(v, 4) for f, v in r.items()} for k, r in table.items()}}
 
 
 def run_fused(args, torch, bn, dev, inputs, peak_info):
@@ -555,8 +559,10 @@ def run_fused(args, torch, bn, dev, inputs, peak_info):
 def run_mixed(args, torch, bn, dev, rank):
     """Mixed-size batch (200k operations by default, 70% products / 30% sums,
     limb counts log-uniform in 32..8192 for each operand, 5% edge cases):
-    the batched graph (autotuned) against plain per-item launches of the same
-    items, same kernels; results must be identical."""
+    the batched graph (autotuned) against two plain baselines over the same
+    items and kernel choices: per size class one padded ordinary launch
+    (gather, launch, scatter; the paper's one-size-per-launch method) and one
+    ordinary launch per item.  Results must be identical."""
     items, a, b, c_limbs = workloads.mixed_workload(args.mixed_items,
                                                     seed=workloads.seed_for(3, 0) + 7919 * rank)
     ta = torch.from_numpy(a.view(np.int32)).to(dev)
@@ -566,7 +572,9 @@ def run_mixed(args, torch, bn, dev, rank):
     stream = torch.cuda.current_stream(dev)
     out, results = {}, {}
     for name, flags, steps in (("batched", bn.BN_BATCH_AUTOTUNE, args.mixed_steps),
-                               ("plain", bn.BN_BATCH_PLAIN, 1)):
+                               ("plain_class", bn.BN_BATCH_AUTOTUNE | bn.BN_BATCH_PLAIN_CLASSES,
+                                args.mixed_steps),
+                               ("plain_item", bn.BN_BATCH_AUTOTUNE | bn.BN_BATCH_PLAIN, 1)):
         t = time.perf_counter()
         batch = bn.Batch(items, flags)
         create_ms = (time.perf_counter() - t) * 1e3
@@ -589,11 +597,15 @@ def run_mixed(args, torch, bn, dev, rank):
                      "items_by_kernel": {k: info[k] for k in ("items_add", "items_quad",
                                                               "items_ntt64", "items_crt",
                                                               "items_ntt3")}}
-    identical = bool(torch.equal(results["batched"], results["plain"]))
+    identical = bool(torch.equal(results["batched"], results["plain_class"])
+                     and torch.equal(results["batched"], results["plain_item"]))
+    del results
     return {"workload": f"{len(items)} ops, 70% mul (auto quad/NTT) / 30% add, limbs log-uniform "
                         "32..8192 per operand, 5% edge cases",
-            "batched": out["batched"], "plain": out["plain"],
-            "speedup": round(out["plain"]["ms"] / out["batched"]["ms"], 2),
+            "batched": out["batched"], "plain_class": out["plain_class"],
+            "plain_item": out["plain_item"],
+            "speedup_vs_class": round(out["plain_class"]["ms"] / out["batched"]["ms"], 2),
+            "speedup_vs_item": round(out["plain_item"]["ms"] / out["batched"]["ms"], 2),
             "results_identical": identical}
 
 
@@ -646,9 +658,12 @@ def run_serving(args, torch, bn, dev, rank):
     out = {"workload": "products, limbs log-uniform 32..8192 per operand (1K-256K bits), "
                        "Poisson arrivals, operands device-resident, 8 GiB result pool",
            "runs": []}
+    # The batched server at both ends of the offered range; the one-at-a-time
+    # baseline at a rate below its capacity (about 15k requests/s), so that
+    # its percentiles are latencies rather than a growing queue.
     plan = [("batched", rate, args.serve_requests if rate >= 100000 else args.serve_requests // 5)
             for rate in (50000, 500000)]
-    plan.append(("sequential", 50000, max(200, args.serve_requests // 100)))
+    plan.append(("sequential", args.seq_rate, max(200, args.serve_requests // 50)))
     for mode, rate, count in plan:
         reqs = make(count)
         arrivals = np.cumsum(rng.exponential(1e6 / rate, size=count)) + 2000.0
@@ -663,7 +678,7 @@ def run_serving(args, torch, bn, dev, rank):
                             "throughput_per_s": round(count / span_s, 1),
                             "p50_us": round(float(np.percentile(lat, 50)), 1),
                             "p99_us": round(float(np.percentile(lat, 99)), 1),
-                            "batches": st["batches"] - (0 if mode == "sequential" else 0),
+                            "batches": st["batches"],
                             "max_inflight": st["max_inflight_seen"]})
     return out
 
@@ -743,7 +758,8 @@ def oracle_time_op(o: Op, count: int, threads: int):
 
 
 def sample_counts(ops, budget_s: float, threads: int):
-    """Pairs per op so the whole sample takes about budget_s on `threads` cores.
+    """Pairs per op so the whole sample takes about budget_s on `threads` cores:
+    the same fraction of every op's batch (at least one pair per thread).
     Each op's per-pair cost is calibrated on a small run of that op."""
     per_pair = {}
     for o in ops:
@@ -755,52 +771,134 @@ def sample_counts(ops, budget_s: float, threads: int):
     return {o.label: int(min(o.batch, max(threads, round(o.batch * frac)))) for o in ops}, frac
 
 
-def cpu_baseline(ops, budget_s=15.0, counts=None):
-    import oracle
-    threads = oracle.default_threads()
-    if counts is None:
-        counts, _ = sample_counts(ops, budget_s, threads)
-    total_s = 0.0
+def sample_text(ops, counts, frac):
+    big = max(ops, key=lambda o: o.na * o.nb if o.mults else 0)
+    return ("%.3g%% of every op's pairs (at least one per core), e.g. %s %d of %d; ops timed in "
+            "turn, multiplications counted over the sample's measured time"
+            % (100 * frac, big.label, counts[big.label], big.batch))
+
+
+def oracle_sample_step(ops, counts, threads):
+    """One sampled step of the oracle: every op on its sample, in turn.
+    Returns (seconds measured over the whole sample, the same seconds
+    extrapolated to every op's full batch)."""
+    t0 = time.perf_counter()
+    full = 0.0
     for o in ops:
         c = counts[o.label]
-        total_s += oracle_time_op(o, c, threads) * (o.batch / c)
-    mults = sum(o.mults for o in ops)
-    sample = ", ".join(f"{o.label}:{counts[o.label]}/{o.batch}" for o in ops)
-    return {"value": mults / total_s, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "pairs timed per op, each scaled to its full batch: " + sample,
-            "extrapolated_step_s": round(total_s, 3)}
+        full += oracle_time_op(o, c, threads) * (o.batch / c)
+    return time.perf_counter() - t0, full
+
+
+def cpu_baseline(ops, budget_s=15.0):
+    """The oracle as it stands, on all host cores, over one bounded sample of
+    the step's workload: value = multiplications in the sample / its time."""
+    import oracle
+    threads = oracle.default_threads()
+    counts, frac = sample_counts(ops, budget_s, threads)
+    wall, full = oracle_sample_step(ops, counts, threads)
+    mults = sum(counts[o.label] for o in ops if o.mults)
+    return {"value": mults / wall, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": sample_text(ops, counts, frac), "sample_s": round(wall, 3),
+            "extrapolated_full_step_s": round(full, 3)}
 
 
 def run_reference(args, rank, world):
-    """The oracle, as it stands, on the host cores: each step a bounded sample."""
+    """The oracle, as it stands, on the host cores: each step one bounded
+    sample of the step's workload (the same fraction of every op), timed as a
+    whole; ms_per_step is that measured time and value the sample's
+    multiplications over it."""
     if rank != 0:
         return None
     import oracle
     oracle.build()
     ops = build_ops(args.quick, getattr(args, "integer_schoolbook", False))
     threads = oracle.default_threads()
-    counts, _ = sample_counts(ops, args.ref_step_budget, threads)
+    counts, frac = sample_counts(ops, args.ref_step_budget, threads)
     for _ in range(args.warmup):
-        cpu_baseline(ops, counts=counts)
-    vals, step_s = [], []
-    wall = time.perf_counter()
+        oracle_sample_step(ops, counts, threads)
+    walls, fulls = [], []
+    t_all = time.perf_counter()
     for _ in range(args.steps):
-        r = cpu_baseline(ops, counts=counts)
-        vals.append(r["value"])
-        step_s.append(r["extrapolated_step_s"])
-    wall = time.perf_counter() - wall
-    value = float(np.mean(vals))
-    sample = r["sample"]
+        w, f = oracle_sample_step(ops, counts, threads)
+        walls.append(w)
+        fulls.append(f)
+    t_all = time.perf_counter() - t_all
+    mults = sum(counts[o.label] for o in ops if o.mults)
+    value = mults * args.steps / sum(walls)
+    cpu = {"value": value, "unit": UNIT, "kind": "oracle", "cores": threads,
+           "sample": sample_text(ops, counts, frac)}
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(float(np.mean(step_s)) * 1e3, 3),
+        "warmup": args.warmup, "ms_per_step": round(float(np.mean(walls)) * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "config": workload_config(ops, world), "impl": "reference",
-        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": threads,
-                         "sample": sample},
+        "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "wall_s": round(wall, 2),
+        "timed_s": round(t_all, 4),
+        "extrapolated_full_step_s": round(float(np.mean(fulls)), 3),
     }
+
+
+# ---- the printed line ------------------------------------------------------
+
+# Kernels whose roofline fractions the compact line carries (the targets the
+# design tracks), by op label.
+KEY_OPS = ("add@256K", "add@128K", "quad@1K", "quad@2K", "quadtc@32K", "quadtc@64K",
+           "quadtc@256K", "ntt64@256K", "crt@256K", "ntt3@256K")
+
+
+def compact(full: dict) -> dict:
+    """The printed line: the contract's keys plus summary scalars of every
+    section; the per-op detail stays in the full record."""
+    keep = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+            "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "impl",
+            "e2e", "cpu_baseline", "clocks", "gpu_launches", "add_gbs", "roofline", "timed_s",
+            "extrapolated_full_step_s", "skipped_ops")
+    out = {k: full[k] for k in keep if k in full}
+    if isinstance(out.get("e2e"), dict) and "api" in out["e2e"]:
+        out["e2e"] = dict(out["e2e"], api="bn_plan_execute_host_async, pinned host buffers, "
+                                          "3 streams")
+    if isinstance(out.get("roofline"), dict):
+        out["roofline"] = dict(out["roofline"])
+    if full.get("rooflines"):
+        fr = {r["op"]: r["frac"] for r in full["rooflines"]}
+        out["frac"] = {k: fr[k] for k in KEY_OPS if k in fr}
+    if full.get("forms"):
+        out["crossover_bits"] = full["forms"]["crossover_bits"]
+    m = full.get("mixed")
+    if m:
+        out["mixed"] = {"batched_ms": m["batched"]["ms"], "plain_class_ms": m["plain_class"]["ms"],
+                        "plain_item_ms": m["plain_item"]["ms"],
+                        "speedup_vs_class": m["speedup_vs_class"],
+                        "speedup_vs_item": m["speedup_vs_item"],
+                        "results_identical": m["results_identical"]}
+    sv = full.get("serving")
+    if sv:
+        out["serving"] = {("%s@%dk" % (r["mode"], r["offered_per_s"] // 1000)):
+                          [round(r["throughput_per_s"]), r["p50_us"], r["p99_us"]]
+                          for r in sv["runs"]}
+        out["serving"]["fields"] = "served/s, p50 us, p99 us"
+    f = full.get("fused")
+    if f and f.get("sizes"):
+        last = f["sizes"][-1]
+        out["fused_256K"] = {"add6_over_add": last["add6_over_add"],
+                             "poly_over_mul_low": last["poly_over_mul_low"]}
+    return out
+
+
+def emit(full: dict, detail_path: str):
+    """Full record to the detail file (or stderr), compact line to stdout."""
+    text = json.dumps(full)
+    if detail_path:
+        Path(detail_path).parent.mkdir(parents=True, exist_ok=True)
+        Path(detail_path).write_text(text + "\n")
+    else:
+        print(text, file=sys.stderr, flush=True)
+    line = compact(full)
+    if detail_path:
+        line["detail"] = detail_path
+    print(json.dumps(line), flush=True)
 
 
 # ---- distributed plumbing --------------------------------------------------
@@ -859,6 +957,10 @@ def main(argv=None):
                     help="timed repetitions of each fused program per size (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=50000,
                     help="requests per serving run at 500k/s (0 = skip the serving runs)")
+    ap.add_argument("--seq-rate", type=int, default=5000,
+                    help="offered rate (requests/s) of the one-at-a-time serving baseline")
+    ap.add_argument("--detail", default="",
+                    help="file for the full JSON record (default: stderr)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -877,7 +979,7 @@ def main(argv=None):
             import torch.distributed as dist
             dist.destroy_process_group()
     if res is not None:
-        print(json.dumps(res), flush=True)
+        emit(res, args.detail)
 
 
 if __name__ == "__main__":

@@ -223,11 +223,17 @@ bn_status bn_mul(const uint32_t *a, const uint32_t *b, uint32_t *c,
  *
  * The first call on a device sets that device up (looks up the arrays'
  * device addresses, raises the kernel's shared-memory cap), so make that
- * first call before any stream capture.  Every call shares the arrays and
- * they keep the last call's contents (nothing in them has to start at zero:
- * each call writes every scratch and table word before reading it), so
- * calls that overlap on the GPU (different streams, other host threads)
- * race and give wrong results: serialise them on one stream. */
+ * first call before any stream capture: a first call made while `stream` is
+ * capturing returns BN_EINVAL.  Every call shares the arrays and they keep
+ * the last call's contents (nothing in them has to start at zero: each call
+ * writes every scratch and table word before reading it), so calls that
+ * overlap on the GPU (different streams, other host threads) race and give
+ * wrong results: serialise them on one stream.  Eager calls skip the table
+ * kernel when the tables already hold their (field, length); a call made
+ * while `stream` is capturing always records the table kernel, and after
+ * the first such call every later call on that device regenerates its
+ * tables too (a replay may have rewritten them).  The per-device set-up is
+ * never redone: after cudaDeviceReset use a fresh process. */
 #define BN_NOALLOC_SCRATCH_BYTES (32ull << 20)
 #define BN_NOALLOC_MAX_LIMBS 8192u
 bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, uint32_t *c,
@@ -284,8 +290,16 @@ bn_status bn_add6(const uint32_t *a, const uint32_t *b, uint32_t *c,
  * bn_batch_execute binds the flat arrays and enqueues the graph on `stream`;
  * it must not overlap another execution of the same batch.
  * BN_BATCH_PLAIN executes the same item list as one ordinary launch per
- * item (same kernel choices, no graph), the baseline the batched form is
- * measured against. */
+ * item (same kernel choices, no graph).  BN_BATCH_PLAIN_CLASSES executes it
+ * the way the paper's per-size launches would (Section 6 runs one size per
+ * launch): per size class, in turn, a gather kernel copies the items'
+ * operands into contiguous rows zero-padded to the class's largest sizes
+ * (longer operand first for products), one ordinary batched launch of the
+ * class's kernel computes all of them, and a scatter kernel copies each
+ * item's result limbs back; three launches per class and device buffers for
+ * the padded rows, allocated at creation.  Both are baselines the batched
+ * form is measured against; they give bit-identical results and exclude
+ * each other (BN_EINVAL). */
 typedef struct bn_batch_item {
     uint32_t op;         /* bn_op */
     uint32_t na, nb;     /* limb counts */
@@ -305,6 +319,7 @@ typedef struct bn_batch_s *bn_batch;
 
 #define BN_BATCH_AUTOTUNE 1u
 #define BN_BATCH_PLAIN 2u
+#define BN_BATCH_PLAIN_CLASSES 4u
 
 bn_status bn_batch_create(bn_batch *out, const bn_batch_item *items, uint64_t count,
                           uint32_t flags);

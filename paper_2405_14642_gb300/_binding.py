@@ -18,7 +18,7 @@ from . import _build
 BN_OK, BN_EINVAL, BN_ENOMEM, BN_ECUDA, BN_EUNSUPPORTED, BN_ETIMEOUT = range(6)
 (BN_OP_ADD, BN_OP_MUL_QUAD, BN_OP_MUL_NTT64, BN_OP_MUL_NTT_CRT, BN_OP_MUL_AUTO, BN_OP_MUL_NTT3,
  BN_OP_MUL_QUAD_TC) = range(7)
-BN_BATCH_AUTOTUNE, BN_BATCH_PLAIN = 1, 2
+BN_BATCH_AUTOTUNE, BN_BATCH_PLAIN, BN_BATCH_PLAIN_CLASSES = 1, 2, 4
 # Layout of struct bn_batch_item (include/bn.h), 40 bytes.
 BATCH_ITEM_DTYPE = np.dtype([("op", "<u4"), ("na", "<u4"), ("nb", "<u4"), ("reserved", "<u4"),
                              ("a_offset", "<u8"), ("b_offset", "<u8"), ("c_offset", "<u8")])
@@ -305,8 +305,10 @@ def bn_mul_ntt_noalloc(a, b, crt: bool = False, out=None, stream=None):
     a, b = _pair(a, b)
     batch, na, nb = a.shape[0], a.shape[1], b.shape[1]
     out = _out(out, batch, na + nb, a)
-    _check(lib.bn_mul_ntt_noalloc(_ptr(a), _ptr(b), _ptr(out), na, nb, batch, int(bool(crt)),
-                                  _stream_handle(stream, a.device)), "bn_mul_ntt_noalloc")
+    # The library keys its arrays on the current device: make it a's device.
+    with _torch().cuda.device(a.device):
+        _check(lib.bn_mul_ntt_noalloc(_ptr(a), _ptr(b), _ptr(out), na, nb, batch, int(bool(crt)),
+                                      _stream_handle(stream, a.device)), "bn_mul_ntt_noalloc")
     return out
 
 
@@ -422,7 +424,8 @@ class Batch:
 
     ``items`` is a numpy array of BATCH_ITEM_DTYPE (op, na, nb, offsets in
     limbs into the flat a, b, c arrays).  ``execute`` runs them as one CUDA
-    graph (or, with BN_BATCH_PLAIN, as one launch per item)."""
+    graph (or, with BN_BATCH_PLAIN, as one launch per item; with
+    BN_BATCH_PLAIN_CLASSES, as one padded plain launch per size class)."""
 
     def __init__(self, items: np.ndarray, flags: int = 0):
         lib = load()

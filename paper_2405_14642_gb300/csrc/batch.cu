@@ -16,6 +16,13 @@
 // BN_BATCH_AUTOTUNE re-measures them for the classes present, on synthetic
 // items at each class's largest size, and also picks each schoolbook class's
 // window size Q and CTA size.
+//
+// Baselines.  BN_BATCH_PLAIN runs every item as its own ordinary launch.
+// BN_BATCH_PLAIN_CLASSES runs the plain method the way a caller of the
+// per-size entry points would: per class, the items' operands are gathered
+// into contiguous rows zero-padded to the class's largest sizes (products
+// take the longer operand first), one ordinary batched launch computes the
+// class, and the low limbs of each padded result are scattered back.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,6 +63,47 @@ struct Class {
     bn::Ntt3Plan *ntt3 = nullptr;
 };
 
+// One item of a padded plain class: operand x (the longer one for products)
+// and y, taken from the flat a or b array, and the result limbs to keep.
+struct PlainItem {
+    uint64_t off_x, off_y, off_c;
+    uint32_t nx, ny, nout, x_from_b;
+};
+
+struct PlainClass {
+    Kind kind;
+    uint32_t first = 0, count = 0;     // range in the sorted item array
+    uint32_t pad_x = 0, pad_y = 0, out = 0;
+    uint32_t *X = nullptr, *Y = nullptr, *C = nullptr;  // count x pad_x / pad_y / out
+    bn::AddConfig add;
+    bn::QuadConfig quad;
+    bn::NttPlan *ntt = nullptr;
+    bn::Ntt3Plan *ntt3 = nullptr;
+};
+
+// Copies each item's operands into its zero-padded rows of X and Y.
+__global__ void k_plain_gather(const PlainItem *items, uint32_t count, uint32_t pad_x, uint32_t pad_y,
+                               const uint32_t *a, const uint32_t *b, uint32_t *X, uint32_t *Y) {
+    for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+        const PlainItem it = items[i];
+        const uint32_t *sx = it.x_from_b ? b + it.off_x : a + it.off_x;
+        const uint32_t *sy = it.x_from_b ? a + it.off_y : b + it.off_y;
+        uint32_t *dx = X + (size_t)i * pad_x, *dy = Y + (size_t)i * pad_y;
+        for (uint32_t k = threadIdx.x; k < pad_x; k += blockDim.x) dx[k] = k < it.nx ? sx[k] : 0u;
+        for (uint32_t k = threadIdx.x; k < pad_y; k += blockDim.x) dy[k] = k < it.ny ? sy[k] : 0u;
+    }
+}
+
+// Copies the low nout limbs of each padded result row to the item's result.
+__global__ void k_plain_scatter(const PlainItem *items, uint32_t count, uint32_t out,
+                                const uint32_t *C, uint32_t *c) {
+    for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+        const PlainItem it = items[i];
+        const uint32_t *src = C + (size_t)i * out;
+        for (uint32_t k = threadIdx.x; k < it.nout; k += blockDim.x) c[it.off_c + k] = src[k];
+    }
+}
+
 }  // namespace
 
 struct bn_batch_s {
@@ -63,6 +111,7 @@ struct bn_batch_s {
     uint32_t flags = 0;
     std::vector<bn::BatchItem> items;  // sorted by class, then cost (host copy)
     std::vector<Kind> kinds;           // per sorted item (plain mode)
+    std::vector<uint32_t> class_of;    // per sorted item: its class (plain mode)
     std::vector<Class> classes;
     bn::BatchItem *d_items = nullptr;
     uint32_t *d_queues = nullptr;
@@ -73,6 +122,9 @@ struct bn_batch_s {
     cudaGraphExec_t exec = nullptr;
     bn_batch_info info{};
     std::map<uint32_t, bn::QuadConfig> plain_quad;  // (na << 16 | nb) -> config
+    std::vector<PlainClass> plain;     // BN_BATCH_PLAIN_CLASSES
+    PlainItem *d_plain_items = nullptr;
+    uint32_t *d_plain_buf = nullptr;
 };
 
 namespace {
@@ -87,6 +139,12 @@ void release(bn_batch_s *b) {
         if (c.ntt) bn::ntt_destroy(c.ntt);
         if (c.ntt3) bn::ntt3_destroy(c.ntt3);
     }
+    for (auto &c : b->plain) {
+        if (c.ntt) bn::ntt_destroy(c.ntt);
+        if (c.ntt3) bn::ntt3_destroy(c.ntt3);
+    }
+    cudaFree(b->d_plain_items);
+    cudaFree(b->d_plain_buf);
     cudaFree(b->d_items);
     cudaFree(b->d_queues);
     cudaFree(b->d_bind);
@@ -380,6 +438,7 @@ bn_status bn_batch_create(bn_batch *out, const bn_batch_item *items, uint64_t co
         for (size_t k = i; k < j; ++k) {
             b->items.push_back(tmp[k].item);
             b->kinds.push_back(tmp[k].kind);
+            b->class_of.push_back((uint32_t)(b->classes.size() - 1));
             switch (tmp[k].kind) {
             case K_ADD: ++b->info.items_add; break;
             case K_QUAD: ++b->info.items_quad; break;
@@ -403,8 +462,61 @@ bn_status bn_batch_create(bn_batch *out, const bn_batch_item *items, uint64_t co
                    cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(b, BN_ECUDA, "batch item upload");
 
+    if ((flags & BN_BATCH_PLAIN) && (flags & BN_BATCH_PLAIN_CLASSES))
+        return fail(b, BN_EINVAL, "BN_BATCH_PLAIN and BN_BATCH_PLAIN_CLASSES exclude each other");
     if (flags & BN_BATCH_PLAIN) {
         b->info.launches = (uint32_t)b->items.size();
+    } else if (flags & BN_BATCH_PLAIN_CLASSES) {
+        // Per class: padded sizes, a plain plan for them, and the rows.
+        std::vector<PlainItem> pitems(b->items.size());
+        size_t words = 0;
+        for (const Class &c : b->classes) {
+            PlainClass pc;
+            pc.kind = c.kind;
+            pc.first = c.first;
+            pc.count = c.count;
+            for (uint32_t i = c.first; i < c.first + c.count; ++i) {
+                const bn::BatchItem &it = b->items[i];
+                PlainItem &q = pitems[i];
+                const bool swap = c.kind != K_ADD && it.nb > it.na;  // longer operand first
+                q.off_x = swap ? it.off_b : it.off_a;
+                q.off_y = swap ? it.off_a : it.off_b;
+                q.off_c = it.off_c;
+                q.nx = swap ? it.nb : it.na;
+                q.ny = swap ? it.na : it.nb;
+                q.x_from_b = swap;
+                q.nout = c.kind == K_ADD ? std::max(it.na, it.nb) + 1 : it.na + it.nb;
+                pc.pad_x = std::max(pc.pad_x, c.kind == K_ADD ? std::max(q.nx, q.ny) : q.nx);
+                pc.pad_y = std::max(pc.pad_y, c.kind == K_ADD ? std::max(q.nx, q.ny) : q.ny);
+            }
+            pc.out = c.kind == K_ADD ? pc.pad_x + 1 : pc.pad_x + pc.pad_y;
+            bn_status st = BN_OK;
+            switch (c.kind) {
+            case K_ADD: st = add_configure(pc.add, pc.pad_x, pc.pad_y, nullptr); break;
+            case K_QUAD: st = quad_configure(pc.quad, pc.pad_x, pc.pad_y, nullptr); break;
+            case K_NTT3: st = ntt3_create(&pc.ntt3, pc.pad_x, pc.pad_y, nullptr); break;
+            default: st = ntt_create(&pc.ntt, c.kind == K_CRT, pc.pad_x, pc.pad_y, nullptr); break;
+            }
+            b->plain.push_back(pc);
+            if (st != BN_OK) return fail(b, st, "could not set up a plain class");
+            words += (size_t)c.count * (pc.pad_x + pc.pad_y + pc.out);
+        }
+        if (cudaMalloc(&b->d_plain_items, std::max<size_t>(pitems.size(), 1) * sizeof(PlainItem)) ||
+            cudaMalloc(&b->d_plain_buf, std::max<size_t>(words, 1) * 4))
+            return fail(b, BN_ENOMEM, "plain class buffers");
+        if (!pitems.empty() && cudaMemcpy(b->d_plain_items, pitems.data(), pitems.size() * sizeof(PlainItem),
+                                          cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(b, BN_ECUDA, "plain item upload");
+        size_t off = 0;
+        for (PlainClass &pc : b->plain) {
+            pc.X = b->d_plain_buf + off;
+            off += (size_t)pc.count * pc.pad_x;
+            pc.Y = b->d_plain_buf + off;
+            off += (size_t)pc.count * pc.pad_y;
+            pc.C = b->d_plain_buf + off;
+            off += (size_t)pc.count * pc.out;
+        }
+        b->info.launches = 3u * (uint32_t)b->plain.size();
     } else if (!b->classes.empty()) {
         // Capture: zero the queues, fork to the streams, one launch per class
         // (largest estimated classes first, round robin), join.
@@ -487,14 +599,38 @@ bn_status bn_batch_execute(bn_batch b, const uint32_t *a, const uint32_t *bb, ui
                 }
                 e = quad_launch(f->second, pa, pb, pc, 1, st);
             } else {
-                const Class *cls = nullptr;
-                for (const auto &cl : b->classes)
-                    if (i >= cl.first && i < cl.first + cl.count) cls = &cl;
-                e = cls->ntt3 ? ntt3_launch_sized(cls->ntt3, it.na, it.nb, pa, pb, pc, st)
-                              : ntt_launch_sized(cls->ntt, it.na, it.nb, pa, pb, pc, st);
+                const Class &cls = b->classes[b->class_of[i]];
+                e = cls.ntt3 ? ntt3_launch_sized(cls.ntt3, it.na, it.nb, pa, pb, pc, st)
+                             : ntt_launch_sized(cls.ntt, it.na, it.nb, pa, pb, pc, st);
             }
             if (e != cudaSuccess) {
                 record_error("plain batch launch failed");
+                return BN_ECUDA;
+            }
+        }
+        return BN_OK;
+    }
+    if (b->flags & BN_BATCH_PLAIN_CLASSES) {
+        // Per class, in order: gather into padded rows, one plain launch, scatter.
+        for (const PlainClass &pc : b->plain) {
+            const PlainItem *pi = b->d_plain_items + pc.first;
+            const unsigned grid = std::min<uint32_t>(pc.count, 65535u);
+            k_plain_gather<<<grid, 256, 0, st>>>(pi, pc.count, pc.pad_x, pc.pad_y, a, bb, pc.X, pc.Y);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) {
+                switch (pc.kind) {
+                case K_ADD: e = add_launch(pc.add, pc.X, pc.Y, pc.C, pc.count, st); break;
+                case K_QUAD: e = quad_launch(pc.quad, pc.X, pc.Y, pc.C, pc.count, st); break;
+                case K_NTT3: e = ntt3_launch(pc.ntt3, pc.X, pc.Y, pc.C, pc.count, st); break;
+                default: e = ntt_launch(pc.ntt, pc.X, pc.Y, pc.C, pc.count, st); break;
+                }
+            }
+            if (e == cudaSuccess) {
+                k_plain_scatter<<<grid, 256, 0, st>>>(pi, pc.count, pc.out, pc.C, c);
+                e = cudaGetLastError();
+            }
+            if (e != cudaSuccess) {
+                record_error("plain class launch failed");
                 return BN_ECUDA;
             }
         }

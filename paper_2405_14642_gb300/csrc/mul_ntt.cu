@@ -696,6 +696,10 @@ struct NoAllocDevice {
     bool have_tables = false;  // the table array holds (crt, N)
     bool crt = false;
     uint32_t N = 0;
+    // Set once a call has been captured into a graph: a replay of that graph
+    // rewrites the table array at a time the host cannot see, so from then
+    // on every call regenerates its tables.
+    bool captured = false;
 };
 NoAllocDevice g_noalloc_devices[kNoAllocMaxDevices];
 std::mutex g_noalloc_mutex;
@@ -828,8 +832,18 @@ extern "C" bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, ui
         record_error("no usable current device for bn_mul_ntt_noalloc");
         return BN_ECUDA;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) {
+        record_error("bn_mul_ntt_noalloc: cudaStreamIsCapturing failed on the stream");
+        return BN_ECUDA;
+    }
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     NoAllocDevice &d = g_noalloc_devices[dev];
+    if (!d.ready && capturing) {
+        record_error("bn_mul_ntt_noalloc: the first call on a device must come before stream capture");
+        return BN_EINVAL;
+    }
     if (!d.ready) {  // once per device, with that device current
         void *ps = nullptr, *pt = nullptr;
         int optin = 0;
@@ -860,7 +874,11 @@ extern "C" bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, ui
 
     const NoAllocPrime c1 = noalloc_prime(field_p1(), N, S, d.tables);
     const NoAllocPrime c2 = noalloc_prime(field_p2(), N, S, d.tables + noalloc_prime_words(N, S));
-    if (!d.have_tables || d.crt != crt || d.N != N) {
+    // A captured call records its own table kernel (replays regenerate the
+    // tables they read) and leaves the host's record of the table contents
+    // unusable for every later call.
+    if (capturing) d.captured = true;
+    if (capturing || d.captured || !d.have_tables || d.crt != crt || d.N != N) {
         const uint32_t words = (uint32_t)noalloc_prime_words(N, S);
         const unsigned blocks = (words + 255) / 256 < 1024 ? (words + 255) / 256 : 1024;
         k_noalloc_tables<FieldP1><<<blocks, 256, 0, st>>>(d.tables, L, S, c1.one, c1.wL, c1.wLi,
@@ -873,7 +891,7 @@ extern "C" bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, ui
             record_error("bn_mul_ntt_noalloc table kernel launch failed");
             return BN_ECUDA;
         }
-        d.have_tables = true;
+        d.have_tables = !d.captured;
         d.crt = crt;
         d.N = N;
     }

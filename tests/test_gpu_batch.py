@@ -1,5 +1,6 @@
 """Mixed-size batches (bn_batch_*): every item of a batch equals the oracle,
-bit for bit, in the graph form, the plain per-item form and after autotuning."""
+bit for bit, in the graph form, the plain per-item form, the padded
+per-class plain form and after autotuning."""
 import numpy as np
 import pytest
 
@@ -36,7 +37,7 @@ def run(items, a, b, c_limbs, flags=0):
     return to_host(tc), info
 
 
-@pytest.mark.parametrize("flags", [0, 2, 1], ids=["graph", "plain", "autotune"])
+@pytest.mark.parametrize("flags", [0, 2, 4, 1], ids=["graph", "plain", "plain_classes", "autotune"])
 def test_mixed_small_sizes_all_items(flags):
     torch_cuda()
     items, a, b, c_limbs = workloads.mixed_workload(700, seed=workloads.seed_for(3, 1), lo=1, hi=700)
@@ -46,12 +47,13 @@ def test_mixed_small_sizes_all_items(flags):
     check_items(items, a, b, c)
 
 
+@pytest.mark.parametrize("flags", [0, 4], ids=["graph", "plain_classes"])
 @pytest.mark.parametrize("op", [1, 2, 3], ids=["quad", "ntt64", "crt"])
-def test_forced_kinds(op):
+def test_forced_kinds(op, flags):
     torch_cuda()
     items, a, b, c_limbs = workloads.mixed_workload(150, seed=workloads.seed_for(3, 10 + op), lo=3,
                                                     hi=3000, mul_frac=1.0, mul_op=op)
-    c, info = run(items, a, b, c_limbs)
+    c, info = run(items, a, b, c_limbs, flags)
     key = {1: "items_quad", 2: "items_ntt64", 3: "items_crt"}[op]
     assert info[key] == 150
     check_items(items, a, b, c)
@@ -59,20 +61,24 @@ def test_forced_kinds(op):
 
 def test_full_range_sampled_and_plain_equals_graph():
     """Sizes log-uniform over 32..8192 limbs (the paper's whole range): the
-    graph and the plain per-item form give identical results; sampled items
-    and every 20th (edge-case) item against the oracle."""
+    graph, the plain per-item form and the padded per-class form give
+    identical results; sampled items and every 20th (edge-case) item against
+    the oracle."""
     torch_cuda()
     items, a, b, c_limbs = workloads.mixed_workload(1500, seed=workloads.seed_for(3, 2))
     c_graph, info = run(items, a, b, c_limbs)
     c_plain, info_p = run(items, a, b, c_limbs, flags=2)
+    c_cls, info_c = run(items, a, b, c_limbs, flags=4)
     assert np.array_equal(c_graph, c_plain)
+    assert np.array_equal(c_graph, c_cls)
     assert info["launches"] == info["classes"] and info_p["launches"] == 1500
+    assert info_c["launches"] == 3 * info_c["classes"]
     rng = np.random.default_rng(5)
     sample = np.union1d(rng.choice(1500, 60, replace=False), np.arange(19, 1500, 20)[:40])
     check_items(items, a, b, c_graph, sample)
 
 
-@pytest.mark.parametrize("flags", [0, 2, 1], ids=["graph", "plain", "autotune"])
+@pytest.mark.parametrize("flags", [0, 2, 4, 1], ids=["graph", "plain", "plain_classes", "autotune"])
 def test_auto_large_products_take_three_primes(flags):
     """Products of 1024..8192 limbs: the cost model sends them to the
     three-prime transform (the fastest form there), with exact results."""
@@ -117,3 +123,9 @@ def test_batch_rejects_bad_items():
     empty = np.zeros(0, bn.BATCH_ITEM_DTYPE)
     with bn.Batch(empty) as batch:
         assert batch.info["classes"] == 0
+    with bn.Batch(empty, bn.BN_BATCH_PLAIN_CLASSES) as batch:
+        assert batch.info["launches"] == 0
+    items["na"] = [4, 4]
+    with pytest.raises(bn.BnError) as e:
+        bn.Batch(items, bn.BN_BATCH_PLAIN | bn.BN_BATCH_PLAIN_CLASSES)
+    assert e.value.status == 1
