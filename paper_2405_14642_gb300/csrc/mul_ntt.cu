@@ -11,35 +11,44 @@
 // cyclic convolution does not wrap (inputs are zero-padded).
 //
 // Arithmetic.  Section 4.1's field multiplies with a full-width modulo; here
-// both primes use a lazy Montgomery multiplication (R = 2^64, values kept in
-// [0, 2p)) that is cheap because each prime's low 32-bit word is 1 (see
-// MontField).  Twiddles are stored in Montgomery form so that
-// mul(x, form(w)) = x*w; the pointwise product and the final 1/N scale absorb
-// Montgomery's extra 1/R.
+// the butterflies multiply by twiddles with Shoup's method (each table entry
+// is a pair (w, floor(w 2^64 / p)), so a product costs one high and two low
+// 64-bit multiplies and no division) and keep Harvey's lazy ranges: the
+// forward (decimation-in-frequency) passes hold values in [0, 2p), the
+// inverse (decimation-in-time) passes in [0, 4p), one conditional
+// subtraction per butterfly (both primes are below 2^62, so 4p < 2^64).
+// The pointwise product of two spectra is a Montgomery product (R = 2^64),
+// cheap because each prime's low 32-bit word is 1; the final scale by 1/N
+// also cancels its 1/R.
 //
-// Work mapping.  One CTA transforms one integer pair at a time in shared
-// memory (a persistent grid walks the batch).  Forward transforms are
-// decimation-in-frequency (natural order in, bit-reversed out), the inverse
-// is decimation-in-time (bit-reversed in, natural out), so no permutation
-// pass is needed (Section 4.2's fft reorders first).  Stages are grouped into
-// radix-8 passes: a thread loads 8 elements, runs 3 butterfly stages in
-// registers and stores them back, one barrier per pass instead of one per
-// stage.
+// Work mapping.  A transform of up to 8192 points is one CTA's: both spectra
+// in shared memory, forward transforms natural order in / bit-reversed out,
+// the inverse bit-reversed in / natural out (no permutation pass; Section
+// 4.2's fft reorders first), stages grouped into radix-8 passes (a thread
+// loads 8 elements, runs 3 stages in registers, stores them back: one
+// barrier per 3 stages).  A persistent grid walks the batch.
 //
-// Sizes beyond shared memory.  Both spectra of a sub-transform of length L
-// must fit (L <= 8192 u64 each).  A longer transform, N = S*L with S in
-// {2, 4}, is split into S independent length-L problems: the first radix-S
-// decimation-in-frequency stage is folded into the digit load (sub-problem s
-// transforms y_s[j] = w_N^{js} sum_r x[j + rL] w_S^{rs}), each sub-problem is
-// multiplied pointwise and inverted on its own, and the last radix-S inverse
-// stage is folded into the final combine, reading the S partial results back
-// from a per-CTA scratch slot (L2-resident, since the grid is persistent).
+// Longer transforms (N = S*L, S in {2, 4}, L = 8192) run on a cluster of S
+// CTAs that share their shared memory.  CTA s of the cluster owns
+// sub-problem s: the first radix-S decimation-in-frequency stage is folded
+// into its digit load (y_s[j] = w_N^{js} sum_r x[j + rL] w_S^{rs}, from the
+// operand rows in global memory), then its forward transforms, pointwise
+// product and inverse run as above, and the last radix-S inverse stage's
+// factor N^-1 w_N^{-js} is applied in place.  The remaining radix-S
+// butterfly is evaluated during the normalisation: CTA r owns the
+// coefficients rL .. rL + L - 1, each the sum over s of w_S^{-rs} z_s[j],
+// read from the S CTAs' shared memory.  Nothing goes through global scratch.
+// The two-prime form keeps the first prime's coefficients in a third
+// shared buffer while the second prime runs (in global scratch, L2-resident,
+// only for short one-CTA transforms, where a third buffer would cost
+// occupancy).
 //
 // Normalisation (Section 4.2's splitFftReg/baddRegMul2Fft, here with whole
 // 16/32-bit digits).  Each thread folds the coefficients of its window of
 // limbs into limbs plus a carried spill, the spill is added into the next
-// window, and the remaining one-bit carries are resolved with the Section 2
-// carry scan across threads.
+// window (across CTAs of a cluster through shared memory), and the
+// remaining one-bit carries are resolved with the Section 2 carry scan
+// across threads and then across the cluster's CTAs.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -57,37 +66,92 @@ namespace {
 using namespace ntt;
 
 constexpr uint32_t kMaxSubLength = 8192;  // both spectra in shared memory
+constexpr uint32_t kMaxSplit = 4;         // N <= 32768
+
+// ---- clusters ---------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_index() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// Every thread of every CTA of the cluster; orders shared-memory writes
+// before the barrier before reads after it, across the cluster.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Address of `p` (this CTA's shared memory) in the shared memory of the
+// cluster's CTA `rank`, for ld.shared::cluster.
+__device__ __forceinline__ uint32_t dsmem_addr(const void *p, uint32_t rank) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t r;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ uint64_t ld_dsmem_u64(uint32_t addr) {
+    uint64_t v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_dsmem_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
 
 // ---- device fields ---------------------------------------------------------
 
+// Shoup pair of a constant w < P: (w, floor(w 2^64 / P)).
+typedef ulonglong2 Tw64;
+
 // Z_P for a prime P = k 2^m + 1 with m >= 32 (so P's low 32-bit word is 1)
-// and P < 2^62, in Montgomery form with R = 2^64.  Elements are kept lazily
-// in [0, 2P); canon() maps to [0, P).
-//   * mul: for a, b < 2P the 128-bit product comes from four 32x32->64
-//     multiply-adds with no carry handling (a, b < 2^63 keep the cross sum
-//     below 2^64).  Reduction: -P^-1 = P - 2 (mod 2^64), so the quotient
-//     m = t_lo (P - 2) has words (-x0, x0*P_hi - x1 - borrow); m*P needs two
-//     more multiply-adds since P's low word is 1; the result is < 2P because
-//     4P < 2^64.
+// and P < 2^62 (so 4P < 2^64).
+//   * shoup(x, (w, w')): for any 64-bit x, q = hi64(x w') and x w - q P lies
+//     in [0, 2P) and is x w mod P up to one P (Shoup; exact in 64-bit
+//     arithmetic since the result is below 2^64).
+//   * mont(a, b) for a, b < 2^63: a b / 2^64 mod P in [0, 2P).  The 128-bit
+//     product comes from four 32x32->64 multiply-adds with no carry handling
+//     (a, b < 2^63 keep the cross sum below 2^64).  Reduction: -P^-1 = P - 2
+//     (mod 2^64), so the quotient m = t_lo (P - 2) has words (-x0, x0*P_hi -
+//     x1 - borrow); m*P needs two more multiply-adds since P's low word is 1;
+//     the result is < 2P because 4P < 2^64.
+//   * Butterflies (Harvey's lazy ranges): dif on u, v < 2P gives u + v
+//     reduced into [0, 2P) and (u - v + 2P) w by Shoup, in [0, 2P); dit on
+//     u, v < 4P reduces u into [0, 2P), takes t = v w in [0, 2P) and gives
+//     u + t and u - t + 2P, both in [0, 4P).  One conditional subtraction
+//     each.
 template <uint64_t P>
-struct MontField {
+struct Field64 {
     using Elem = uint64_t;
-    using Tw = uint64_t;  // twiddles in Montgomery form
+    using Tw = Tw64;
     static constexpr uint64_t P_VALUE = P;
     static constexpr uint32_t PH = (uint32_t)(P >> 32);
     static constexpr uint64_t TWO_P = 2 * P;
     static_assert((P & 0xffffffffull) == 1 && P < (1ull << 62), "P = k 2^m + 1, m >= 32, P < 2^62");
-    __device__ static __forceinline__ uint64_t add(uint64_t a, uint64_t b) {
-        const uint64_t r = a + b;
-        return r >= TWO_P ? r - TWO_P : r;
+    // r < 4P into [0, 2P): r - 2P wraps above r exactly when r < 2P.
+    __device__ static __forceinline__ uint64_t red(uint64_t r) {
+        const uint64_t t = r - TWO_P;
+        return t < r ? t : r;
     }
-    __device__ static __forceinline__ uint64_t sub(uint64_t a, uint64_t b) {
-        const uint64_t r = a + TWO_P - b;
-        return r >= TWO_P ? r - TWO_P : r;
-    }
+    __device__ static __forceinline__ uint64_t add(uint64_t a, uint64_t b) { return red(a + b); }
+    __device__ static __forceinline__ uint64_t sub(uint64_t a, uint64_t b) { return red(a + TWO_P - b); }
     __device__ static __forceinline__ uint64_t canon(uint64_t a) { return a >= P ? a - P : a; }
-    // a * b / 2^64 mod P, inputs and output in [0, 2P).
-    __device__ static __forceinline__ uint64_t mul(uint64_t a, uint64_t b) {
+    __device__ static __forceinline__ uint64_t shoup(uint64_t x, Tw64 w) {
+        const uint64_t q = __umul64hi(x, w.y);
+        const uint64_t qp = q + ((uint64_t)((uint32_t)q * PH) << 32);  // q * P mod 2^64
+        return x * w.x - qp;
+    }
+    __device__ static __forceinline__ uint64_t mont(uint64_t a, uint64_t b) {
         const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
         const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
         const uint64_t p00 = (uint64_t)a0 * b0;
@@ -101,37 +165,38 @@ struct MontField {
         const uint64_t h = (uint64_t)m1 * PH + (sm >> 32);
         return hi + h + ((x0 | x1) != 0u);
     }
-    // a * b / 2^64 mod P for any 64-bit a and a canonical b < P (a twiddle):
-    // a*b < P 2^64 keeps the result in [0, 2P); the cross sum takes one more
-    // add because a's high word may use all 32 bits.
-    __device__ static __forceinline__ uint64_t mulw(uint64_t a, uint64_t b) {
-        const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
-        const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
-        const uint64_t p00 = (uint64_t)a0 * b0;
-        const uint64_t t1 = (uint64_t)a1 * b0 + (p00 >> 32);
-        const uint64_t t2 = (uint64_t)a0 * b1 + (uint32_t)t1;
-        const uint64_t hi = (uint64_t)a1 * b1 + (t1 >> 32) + (t2 >> 32);
-        const uint32_t x0 = (uint32_t)p00, x1 = (uint32_t)t2;
-        const uint32_t m0 = 0u - x0;
-        const uint32_t m1 = x0 * PH - x1 - (x0 != 0u);
-        const uint64_t sm = (uint64_t)m0 * PH + m1;
-        const uint64_t h = (uint64_t)m1 * PH + (sm >> 32);
-        return hi + h + ((x0 | x1) != 0u);
+    __device__ static __forceinline__ void dif(uint64_t &u, uint64_t &v, Tw64 w) {
+        const uint64_t x = u, y = v;
+        u = add(x, y);
+        v = shoup(x + TWO_P - y, w);
     }
-    __device__ static __forceinline__ uint64_t twiddle(uint64_t a, uint64_t w) { return mulw(a, w); }
-    __device__ static __forceinline__ uint64_t twiddle_lazy(uint64_t a, uint64_t w) { return mul(a, w); }
+    __device__ static __forceinline__ void dif1(uint64_t &u, uint64_t &v) {
+        const uint64_t x = u, y = v;
+        u = add(x, y);
+        v = sub(x, y);
+    }
+    __device__ static __forceinline__ void dit(uint64_t &u, uint64_t &v, Tw64 w) {
+        const uint64_t x = red(u), t = shoup(v, w);
+        u = x + t;
+        v = x + TWO_P - t;
+    }
+    __device__ static __forceinline__ void dit1(uint64_t &u, uint64_t &v) {
+        const uint64_t x = red(u), t = red(v);
+        u = x + t;
+        v = x + TWO_P - t;
+    }
 };
 
-using FieldP1 = MontField<4179340454199820289ull>;  // 29 * 2^57 + 1 (PrimeField64)
-using FieldP2 = MontField<1945555039024054273ull>;  // 27 * 2^56 + 1
+using FieldP1 = Field64<4179340454199820289ull>;  // 29 * 2^57 + 1 (PrimeField64)
+using FieldP2 = Field64<1945555039024054273ull>;  // 27 * 2^56 + 1
 
 struct PrimeTab {
-    const uint64_t *twf;    // [L]: twf[h + j] = w_{2h}^j (h = 1 .. L/2, j < h)
-    const uint64_t *twi;    // [L]: w_{2h}^-j
-    const uint64_t *ffold;  // [S*L]: w_N^{js}            (S > 1)
-    const uint64_t *ifold;  // [S*L]: scale * w_N^{-js}   (S > 1)
-    uint64_t ws[4], iws[4]; // w_S^k, w_S^-k
-    uint64_t scale;         // N^-1 (times R for p1), S == 1
+    const Tw64 *twf;    // [L]: twf[h + j] = w_{2h}^j (h = 1 .. L/2, j < h)
+    const Tw64 *twi;    // [L]: w_{2h}^-j
+    const Tw64 *ffold;  // [S*L]: w_N^{js}                 (S > 1)
+    const Tw64 *ifold;  // [S*L]: N^-1 R w_N^{-js}          (S > 1)
+    Tw64 w4, iw4;       // w_4 and w_4^-1                   (S = 4)
+    Tw64 scale;         // N^-1 R                           (S = 1)
 };
 
 struct NttArgs {
@@ -139,60 +204,115 @@ struct NttArgs {
     uint32_t *c;
     uint32_t na, nb, nout;
     uint32_t N, L, logL, S, digit_bits;
+    uint32_t zk_smem;         // two primes: the first prime's coefficients in shared memory
     uint64_t batch;
-    uint64_t *scratch;
+    uint64_t *scratch;        // two primes, zk_smem == 0: one slot per CTA
     uint64_t scratch_stride;  // u64 words per CTA
-    uint64_t garner_inv;      // p1^-1 mod p2
+    Tw64 garner;              // p1^-1 mod p2
     PrimeTab t1, t2;
 };
 
-__device__ __forceinline__ uint64_t digit(const uint32_t *row, uint32_t ndig, uint32_t m,
-                                          uint32_t bits) {
-    if (m >= ndig) return 0;
-    return bits == 16 ? (row[m >> 1] >> ((m & 1u) << 4)) & 0xFFFFu : row[m];
+__host__ __device__ constexpr uint32_t buf_words(uint32_t L) { return (phys_words(L) + 1) & ~1u; }
+
+// Dynamic shared memory of one CTA: `bufs` padded length-L buffers, one
+// spill word per thread, the warp flags, the cluster carry word and the
+// batch queue slot.
+__host__ __device__ constexpr uint32_t smem_bytes(uint32_t L, uint32_t bufs, uint32_t threads) {
+    return 8u * (bufs * buf_words(L) + threads) + 4u * (32u + 2u);
 }
 
-// Sub-problem s of the forward transform: y_s[j] = w_N^{js} sum_r x[j + rL] w_S^{rs}.
-// For S = 2 and 4 the inner sum is a radix-S butterfly: w_2 = w_4^2 = -1, so
-// only w_4 (times x1 - x3) takes a product, and w_N^0 = 1 takes none.
-template <class F>
-__device__ void load_fold(const NttArgs &p, const PrimeTab &tb, const uint32_t *row, uint32_t n,
-                          uint32_t s, uint64_t *buf) {
-    const uint32_t ndig = p.digit_bits == 16 ? 2 * n : n;
-    if (p.S == 2 || p.S == 4) {
-        for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) {
-            const uint64_t x0 = digit(row, ndig, j, p.digit_bits), x1 = digit(row, ndig, j + p.L, p.digit_bits);
-            uint64_t acc;
-            if (p.S == 2) {
-                acc = s == 0 ? F::add(x0, x1) : F::sub(x0, x1);
-            } else {
-                const uint64_t x2 = digit(row, ndig, j + 2 * p.L, p.digit_bits);
-                const uint64_t x3 = digit(row, ndig, j + 3 * p.L, p.digit_bits);
-                if (s == 0) acc = F::add(F::add(x0, x2), F::add(x1, x3));
-                else if (s == 2) acc = F::sub(F::add(x0, x2), F::add(x1, x3));
-                else {
-                    const uint64_t o = F::sub(x0, x2), q = F::mul(F::sub(x1, x3), tb.ws[1]);
-                    acc = s == 1 ? F::add(o, q) : F::sub(o, q);
-                }
-            }
-            if (s != 0) acc = F::mul(acc, tb.ffold[s * p.L + j]);
-            buf[phys(j)] = acc;
-        }
-        return;
+struct Smem64 {
+    uint64_t *A, *B, *Z;  // Z: the first prime's coefficients (two primes, zk_smem)
+    uint64_t *spill;
+    uint32_t *flags, *xflag, *next;
+};
+
+template <bool CRT>
+__device__ __forceinline__ Smem64 smem64(const NttArgs &p, uint64_t *sm) {
+    const uint32_t W = buf_words(p.L);
+    Smem64 s;
+    s.A = sm;
+    s.B = sm + W;
+    s.Z = (CRT && p.zk_smem) ? sm + 2 * W : nullptr;
+    s.spill = sm + ((CRT && p.zk_smem) ? 3 : 2) * W;
+    s.flags = reinterpret_cast<uint32_t *>(s.spill + blockDim.x);
+    s.xflag = s.flags + 32;
+    s.next = s.xflag + 1;
+    return s;
+}
+
+// The radix-S fold of sub-problem s (S = 1, 2, 4) over digits x[r] =
+// x_{j + rL}: sum_r x_r w_S^{rs}, for which w_2 = w_4^2 = -1, so only w_4
+// (times x1 - x3) takes a product.  Values in [0, 2P).
+template <class F, uint32_t S>
+__device__ __forceinline__ uint64_t fold(const uint64_t (&x)[S], uint32_t s, Tw64 w4) {
+    if constexpr (S == 1) return x[0];
+    else if constexpr (S == 2) return s == 0 ? F::add(x[0], x[1]) : F::sub(x[0], x[1]);
+    else {
+    if (s == 0) return F::add(F::add(x[0], x[2]), F::add(x[1], x[3]));
+    if (s == 2) return F::sub(F::add(x[0], x[2]), F::add(x[1], x[3]));
+    const uint64_t o = F::sub(x[0], x[2]), q = F::shoup(F::sub(x[1], x[3]), w4);
+    return s == 1 ? F::add(o, q) : F::sub(o, q);
     }
-    for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) {
-        uint64_t acc = digit(row, ndig, j, p.digit_bits);
-        if (p.S > 1) {
-            for (uint32_t r = 1; r < p.S; ++r) {
+}
+
+// n1 for sub-problem s of both operands: y_s[j] = w_N^{js} sum_r x[j + rL]
+// w_S^{rs} into A (from arow) and B (from brow), values in [0, 2P).  Each
+// thread takes positions j, j + 1 (j even): with 16-bit digits one 32-bit
+// word of each row quarter holds both.  All global loads of U iterations
+// are issued before any is used.
+template <class F, uint32_t S>
+__device__ void load_fold(const NttArgs &p, const PrimeTab &tb, const uint32_t *arow, const uint32_t *brow,
+                          uint32_t s, uint64_t *A, uint64_t *B) {
+    const bool d16 = p.digit_bits == 16;
+    const uint32_t wa = p.na, wb = p.nb;  // 32-bit words per row
+    const uint32_t half = p.L / 2;
+    // word index of digit position m; 16-bit digits: position pairs share one word
+    auto word = [&](const uint32_t *row, uint32_t nw, uint32_t m) -> uint32_t {
+        const uint32_t w = d16 ? m >> 1 : m;
+        return w < nw ? __ldg(row + w) : 0u;
+    };
+    constexpr int U = S == 1 ? 2 : 1;
+    for (uint32_t q0 = threadIdx.x; q0 < half; q0 += U * blockDim.x) {
+        uint32_t ra[U][S][2], rb[U][S][2];
+        Tw64 f[U][2];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t j = 2 * (q0 + u * blockDim.x);
+#pragma unroll
+            for (uint32_t r = 0; r < S; ++r) {
+                const bool live = j < p.L;
                 const uint32_t m = j + r * p.L;
-                if (m >= ndig) break;
-                const uint64_t d = digit(row, ndig, m, p.digit_bits);
-                const uint32_t k = (r * s) & (p.S - 1);
-                acc = F::add(acc, k == 0 ? d : F::mul(d, tb.ws[k]));
+                ra[u][r][0] = live ? word(arow, wa, m) : 0u;
+                rb[u][r][0] = live ? word(brow, wb, m) : 0u;
+                ra[u][r][1] = live && !d16 ? word(arow, wa, m + 1) : 0u;
+                rb[u][r][1] = live && !d16 ? word(brow, wb, m + 1) : 0u;
             }
-            acc = F::mul(acc, tb.ffold[s * p.L + j]);
+            const bool tw = S > 1 && j < p.L && s != 0;
+            f[u][0] = tw ? __ldg(tb.ffold + s * p.L + j) : make_ulonglong2(0, 0);
+            f[u][1] = tw ? __ldg(tb.ffold + s * p.L + j + 1) : make_ulonglong2(0, 0);
         }
-        buf[phys(j)] = acc;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t j = 2 * (q0 + u * blockDim.x);
+            if (j >= p.L) break;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                uint64_t xa[S], xb[S];
+#pragma unroll
+                for (uint32_t r = 0; r < S; ++r) {
+                    xa[r] = d16 ? (ra[u][r][0] >> (16 * e)) & 0xFFFFu : ra[u][r][e];
+                    xb[r] = d16 ? (rb[u][r][0] >> (16 * e)) & 0xFFFFu : rb[u][r][e];
+                }
+                uint64_t ya = fold<F, S>(xa, s, tb.w4), yb = fold<F, S>(xb, s, tb.w4);
+                if (S > 1 && s != 0) {
+                    ya = F::shoup(ya, f[u][e]);
+                    yb = F::shoup(yb, f[u][e]);
+                }
+                A[phys(j + e)] = ya;
+                B[phys(j + e)] = yb;
+            }
+        }
     }
 }
 
@@ -200,14 +320,14 @@ __device__ void load_fold(const NttArgs &p, const PrimeTab &tb, const uint32_t *
 // the lengths the 16K..256K-bit range uses most (L = 4096 and 8192 with their
 // default thread counts; 7-8% faster), the runtime passes otherwise.
 template <class F>
-__device__ __forceinline__ void forward_sub(const NttArgs &p, const uint64_t *tw, uint64_t *A, uint64_t *B) {
+__device__ __forceinline__ void forward_sub(const NttArgs &p, const Tw64 *tw, uint64_t *A, uint64_t *B) {
     if (p.logL == 13 && blockDim.x == 1024) forward2_c<F, 13, 1024>(tw, A, B);
     else if (p.logL == 12 && blockDim.x == 512) forward2_c<F, 12, 512>(tw, A, B);
     else forward2<F>(p.L, p.logL, tw, A, B);
 }
 
 template <class F>
-__device__ __forceinline__ void inverse_sub(const NttArgs &p, const uint64_t *tw, uint64_t *B) {
+__device__ __forceinline__ void inverse_sub(const NttArgs &p, const Tw64 *tw, uint64_t *B) {
     if (p.logL == 13 && blockDim.x == 1024) inverse_c<F, 13, 1024>(tw, B);
     else if (p.logL == 12 && blockDim.x == 512) inverse_c<F, 12, 512>(tw, B);
     else inverse<F>(p.L, p.logL, tw, B);
@@ -224,166 +344,252 @@ __device__ __forceinline__ void discard_scratch(const uint64_t *ptr, uint32_t wo
         asm volatile("discard.global.L2 [%0], 128;" ::"l"(g + off) : "memory");
 }
 
-// Coefficients of a*b mod the field's prime, scaled by 1/N.  With keep and
-// S == 1 they stay in B (padded layout); otherwise they go to dest[0 .. N).
-template <class F>
-__device__ void prime_product(const NttArgs &p, const PrimeTab &tb, const uint32_t *arow,
-                              const uint32_t *brow, uint64_t *A, uint64_t *B, uint64_t *Z,
-                              uint64_t *dest, bool keep) {
-    for (uint32_t s = 0; s < p.S; ++s) {
-        load_fold<F>(p, tb, arow, p.na, s, A);   // n1: digits (and the folded first stage)
-        load_fold<F>(p, tb, brow, p.nb, s, B);
-        __syncthreads();
-        forward_sub<F>(p, tb.twf, A, B);          // n2: forward transforms
-        for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x)   // n3: pointwise
-            B[phys(j)] = F::mul(A[phys(j)], B[phys(j)]);
-        __syncthreads();
-        inverse_sub<F>(p, tb.twi, B);             // n4: inverse transform (unscaled)
-        if (p.S > 1) {
-            for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) Z[s * p.L + j] = B[phys(j)];
-            __syncthreads();
-        }
-    }
-    if (p.S == 1) {
-        for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) {
-            const uint64_t v = F::canon(F::mul(B[phys(j)], tb.scale));
-            if (keep) B[phys(j)] = v;
-            else dest[j] = v;
-        }
-    } else {
-        // Last radix-S inverse stage: c[j + rL] = sum_s w_S^{-rs} (scale w_N^{-js} z_s[j]);
-        // for S = 2 and 4 a radix-S butterfly with one product, by w_4^-1.
-        for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) {
-            uint64_t u[4];
-            for (uint32_t s = 0; s < p.S; ++s) u[s] = F::mul(Z[s * p.L + j], tb.ifold[s * p.L + j]);
-            if (p.S == 2) {
-                dest[j] = F::canon(F::add(u[0], u[1]));
-                dest[j + p.L] = F::canon(F::sub(u[0], u[1]));
-                continue;
-            }
-            if (p.S == 4) {
-                const uint64_t e0 = F::add(u[0], u[2]), e1 = F::add(u[1], u[3]);
-                const uint64_t o0 = F::sub(u[0], u[2]), o1 = F::mul(F::sub(u[1], u[3]), tb.iws[1]);
-                dest[j] = F::canon(F::add(e0, e1));
-                dest[j + p.L] = F::canon(F::add(o0, o1));
-                dest[j + 2 * p.L] = F::canon(F::sub(e0, e1));
-                dest[j + 3 * p.L] = F::canon(F::sub(o0, o1));
-                continue;
-            }
-            for (uint32_t r = 0; r < p.S; ++r) {
-                uint64_t acc = u[0];
-                for (uint32_t s = 1; s < p.S; ++s) {
-                    const uint32_t k = (r * s) & (p.S - 1);
-                    acc = F::add(acc, k == 0 ? u[s] : F::mul(u[s], tb.iws[k]));
-                }
-                dest[j + r * p.L] = F::canon(acc);
-            }
-        }
-        __syncthreads();
-        discard_scratch(Z, p.N);  // the partial results are consumed
+// Sub-problem s of a*b mod the field's prime (n1..n4): z_s scaled by the last
+// inverse stage's factor (N^-1 R w_N^{-js}; N^-1 R when S = 1), canonical, to
+// dest (padded layout; dest may be B).  Ends with a barrier.
+template <class F, uint32_t S>
+__device__ void sub_product(const NttArgs &p, const PrimeTab &tb, const uint32_t *arow,
+                            const uint32_t *brow, uint32_t s, uint64_t *A, uint64_t *B, uint64_t *dest) {
+    load_fold<F, S>(p, tb, arow, brow, s, A, B);  // n1: digits (and the folded first stage)
+    __syncthreads();
+    forward_sub<F>(p, tb.twf, A, B);              // n2: forward transforms
+    for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x)   // n3: pointwise
+        B[phys(j)] = F::mont(A[phys(j)], B[phys(j)]);
+    __syncthreads();
+    inverse_sub<F>(p, tb.twi, B);                 // n4: inverse transform (unscaled)
+#pragma unroll 4
+    for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) {
+        const Tw64 f = S > 1 ? __ldg(tb.ifold + s * p.L + j) : tb.scale;
+        dest[phys(j)] = F::canon(F::shoup(B[phys(j)], f));
     }
     __syncthreads();
 }
 
-// Limb k's share of the product: the digit coefficients that start in limb k.
-template <bool CRT>
-__device__ __forceinline__ u128 limb_value(const NttArgs &p, uint32_t k, const uint64_t *B,
-                                           bool in_smem, const uint64_t *C1, const uint64_t *Cs) {
-    if constexpr (!CRT) {
-        const uint64_t c0 = in_smem ? B[phys(2 * k)] : Cs[2 * k];
-        const uint64_t c1 = in_smem ? B[phys(2 * k + 1)] : Cs[2 * k + 1];
-        return (u128)(c0 + (c1 << 16));  // < 2^46 + 2^62
-    } else {
-        const uint64_t r1 = C1[k];                     // canonical mod p1
-        const uint64_t r2 = in_smem ? B[phys(k)] : Cs[k];  // canonical mod p2
-        // Garner: c = r1 + p1 * ((r2 - r1) p1^-1 mod p2), exact since c < p1 p2.
-        uint64_t r1m = r1;                             // r1 mod p2 (p1 < 3 p2)
-        if (r1m >= FieldP2::P_VALUE) r1m -= FieldP2::P_VALUE;
-        if (r1m >= FieldP2::P_VALUE) r1m -= FieldP2::P_VALUE;
-        const uint64_t d = r2 >= r1m ? r2 - r1m : r2 + FieldP2::P_VALUE - r1m;
-        const uint64_t v = FieldP2::canon(FieldP2::mul(d, p.garner_inv));
-        return (u128)r1 + (u128)v * FieldP1::P_VALUE;
+// Addresses of a buffer in the shared memory of each CTA of the cluster.
+struct Remote {
+    uint32_t base[kMaxSplit];
+};
+
+__device__ __forceinline__ Remote remote(const uint64_t *buf, uint32_t S) {
+    Remote v;
+    for (uint32_t s = 0; s < kMaxSplit; ++s) v.base[s] = s < S ? dsmem_addr(buf, s) : 0u;
+    return v;
+}
+
+// Coefficient rL + j (canonical) from the sub-problems' scaled results of
+// the cluster's CTAs (S > 1): the last radix-S inverse stage,
+// sum_s w_S^{-rs} z_s[j].
+template <class F, uint32_t S>
+__device__ __forceinline__ uint64_t coefficient(const PrimeTab &tb, const Remote &zv, uint32_t r, uint32_t j) {
+    const uint32_t off = 8u * phys(j);
+    const uint64_t z0 = ld_dsmem_u64(zv.base[0] + off), z1 = ld_dsmem_u64(zv.base[1] + off);
+    if constexpr (S == 2) return F::canon(r == 0 ? F::add(z0, z1) : F::sub(z0, z1));
+    const uint64_t z2 = ld_dsmem_u64(zv.base[2] + off), z3 = ld_dsmem_u64(zv.base[3] + off);
+    if ((r & 1u) == 0) {
+        const uint64_t e0 = F::add(z0, z2), e1 = F::add(z1, z3);
+        return F::canon(r == 0 ? F::add(e0, e1) : F::sub(e0, e1));
     }
+    const uint64_t o0 = F::sub(z0, z2), o1 = F::shoup(F::sub(z1, z3), tb.iw4);
+    return F::canon(r == 1 ? F::add(o0, o1) : F::sub(o0, o1));
+}
+
+// Garner's step: v = (r2 - r1) p1^-1 mod p2 for r1 < p1, r2 < p2 canonical;
+// the coefficient is r1 + v p1 (exact, since it is below p1 p2).
+__device__ __forceinline__ uint64_t garner_v(const NttArgs &p, uint64_t r1, uint64_t r2) {
+    uint64_t r1m = r1;  // r1 mod p2 (p1 < 3 p2)
+    if (r1m >= FieldP2::P_VALUE) r1m -= FieldP2::P_VALUE;
+    if (r1m >= FieldP2::P_VALUE) r1m -= FieldP2::P_VALUE;
+    const uint64_t d = r2 >= r1m ? r2 - r1m : r2 + FieldP2::P_VALUE - r1m;
+    return FieldP2::canon(FieldP2::shoup(d, p.garner));
+}
+
+// The carry into this thread's window: the Section 2 scan of (g, p) over the
+// CTA's threads, then over the cluster's CTAs in rank order (a carry-in to
+// the CTA enters its thread 0 and passes every thread whose prefix is all
+// ones).  S = 1 is the plain CTA-wide scan.  Every thread of the cluster.
+__device__ uint32_t cluster_carry_in(uint32_t g, uint32_t p, uint32_t rank, uint32_t S, uint32_t *flags,
+                                     uint32_t *xflag) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const RowFlags f{__ballot_sync(FULL_MASK, g), __ballot_sync(FULL_MASK, p)};
+    uint32_t wc;
+    row_carries(f, 0, wc);
+    if (lane == 0) flags[warp] = wc | ((f.P == FULL_MASK) << 1);
+    __syncthreads();
+    const uint32_t sw = lane < nw ? flags[lane] : 2u;  // missing warps pass a carry through
+    const RowFlags fw{__ballot_sync(FULL_MASK, sw & 1u), __ballot_sync(FULL_MASK, (sw >> 1) & 1u)};
+    uint32_t cin = 0, unused;
+    if (S > 1) {
+        uint32_t blk_g;
+        row_carries(fw, 0, blk_g);
+        if (threadIdx.x == 0) *xflag = blk_g | ((fw.P == FULL_MASK) << 1);
+        cluster_sync();
+        for (uint32_t q = 0; q < rank; ++q) {
+            const uint32_t x = ld_dsmem_u32(dsmem_addr(xflag, q));
+            cin = (x & 1u) | ((x >> 1) & cin);
+        }
+    }
+    const uint32_t wcin = (row_carries(fw, cin, unused) >> warp) & 1u;
+    return (row_carries(f, wcin, unused) >> lane) & 1u;
+}
+
+// n6 for the limbs [rank*part, rank*part + part) of the product (clipped to
+// nout): limb(k) gives the part of the product that starts in limb k.  Each
+// thread folds the limbs of its window, carrying inside the window; the
+// window's carry spills into the next window (the first window of a CTA
+// takes the last spill of the previous rank's CTA); the remaining one-bit
+// carries are resolved by cluster_carry_in.  Limbs are assembled in the
+// shared staging row out_s (limb k_lo + i at i + i/16: the windows fall in
+// distinct banks) and copied to crow.  Every thread of the cluster.
+template <class LimbFn>
+__device__ void normalize_part(uint32_t nout, uint32_t part, uint32_t rank, uint32_t S, uint32_t *crow,
+                               uint32_t *out_s, uint64_t *spill, uint32_t *flags, uint32_t *xflag,
+                               LimbFn &&limb) {
+    const uint32_t T = blockDim.x, t = threadIdx.x;
+    const uint32_t k_lo = rank * part < nout ? rank * part : nout;
+    const uint32_t k_hi = k_lo + part < nout ? k_lo + part : nout;
+    uint32_t QN = (part + T - 1) / T;
+    if (QN < 2) QN = 2;  // a window must absorb a two-word spill
+    const uint32_t k0 = k_lo + t * QN < k_hi ? k_lo + t * QN : k_hi;
+    const uint32_t k1 = k0 + QN < k_hi ? k0 + QN : k_hi;
+    u128 carry = 0;
+    for (uint32_t k = k0; k < k1; ++k) {
+        const u128 v = limb(k) + carry;
+        out_s[stage_index(k - k_lo)] = (uint32_t)v;
+        carry = v >> 32;
+    }
+    spill[t] = (uint64_t)carry;  // < 2^64: the coefficients are below 2^96
+    __syncthreads();
+    if (S > 1) cluster_sync();
+    uint64_t c = t > 0 ? spill[t - 1] : (rank > 0 ? ld_dsmem_u64(dsmem_addr(spill + T - 1, rank - 1)) : 0);
+    uint32_t all = 0xffffffffu;
+    for (uint32_t k = k0; k < k1; ++k) {
+        const uint64_t v = (uint64_t)out_s[stage_index(k - k_lo)] + (c & 0xffffffffu);
+        out_s[stage_index(k - k_lo)] = (uint32_t)v;
+        c = (c >> 32) + (v >> 32);
+        all &= (uint32_t)v;
+    }
+    const bool owns = k0 < k1;
+    const uint32_t cin = cluster_carry_in(owns && c != 0, owns && all == 0xffffffffu, rank, S, flags, xflag);
+    if (cin)
+        for (uint32_t k = k0; k < k1; ++k)
+            if (++out_s[stage_index(k - k_lo)] != 0) break;
+    __syncthreads();
+    for (uint32_t x = k_lo + t; x < k_hi; x += T) st_stream(crow + x, out_s[stage_index(x - k_lo)]);
+    __syncthreads();
+}
+
+// One product by a CTA (S = 1) or a cluster of S CTAs (this one of rank
+// `rank`).  zk: where the first prime's coefficients go (two primes).
+//
+// In a cluster, CTA r first gathers its coefficients rL .. rL + L - 1 into
+// its own A (thread-consecutive positions, so each warp reads whole runs of
+// the other CTAs' buffers); two primes: the first prime's into A, then
+// Garner's v into its Z.  Only then is it normalised, from local memory,
+// with B (no longer read by any CTA) as the staging row.
+template <bool CRT, uint32_t S>
+__device__ void pair_product(const NttArgs &p, const uint32_t *arow, const uint32_t *brow, uint32_t *crow,
+                             const Smem64 &s, uint64_t *zk, uint32_t rank) {
+    if constexpr (CRT) {
+        sub_product<FieldP1, S>(p, p.t1, arow, brow, rank, s.A, s.B, zk);
+        sub_product<FieldP2, S>(p, p.t2, arow, brow, rank, s.A, s.B, s.B);
+    } else {
+        sub_product<FieldP1, S>(p, p.t1, arow, brow, rank, s.A, s.B, s.B);
+    }
+    const uint32_t r = rank;
+    // c1 / v: the (first prime's) coefficients and Garner's v of this CTA's
+    // part, in padded layout; out_s: the staging row.
+    const uint64_t *c1 = CRT ? zk : s.B;
+    const uint64_t *gv = s.B;
+    uint32_t *out_s = reinterpret_cast<uint32_t *>(s.A);
+    if constexpr (S > 1) {
+        cluster_sync();  // every sub-problem's result is in place
+        if constexpr (!CRT) {
+            const Remote zb = remote(s.B, S);
+#pragma unroll 2
+            for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x)
+                s.A[phys(j)] = coefficient<FieldP1, S>(p.t1, zb, r, j);
+        } else {
+            const Remote z1 = remote(zk, S), z2 = remote(s.B, S);
+#pragma unroll 2
+            for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x)
+                s.A[phys(j)] = coefficient<FieldP1, S>(p.t1, z1, r, j);
+            cluster_sync();  // no CTA reads Z any more: it takes Garner's v
+#pragma unroll 2
+            for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x)
+                zk[phys(j)] = garner_v(p, s.A[phys(j)], coefficient<FieldP2, S>(p.t2, z2, r, j));
+        }
+        cluster_sync();  // no CTA reads B any more: it becomes the staging row
+        c1 = s.A;
+        gv = zk;
+        out_s = reinterpret_cast<uint32_t *>(s.B);
+    }
+    const uint32_t base = r * p.L;
+    if constexpr (!CRT) {
+        // 16-bit digits: limb k holds coefficients 2k and 2k + 1 (< 2^46 + 2^62).
+        const uint32_t part = S > 1 ? p.L / 2 : p.nout;
+        normalize_part(p.nout, part, r, S, crow, out_s, s.spill, s.flags, s.xflag, [&](uint32_t k) {
+            const uint32_t j = 2 * k - base;
+            return (u128)(c1[phys(j)] + (c1[phys(j + 1)] << 16));
+        });
+    } else {
+        const uint32_t part = S > 1 ? p.L : p.nout;
+        normalize_part(p.nout, part, r, S, crow, out_s, s.spill, s.flags, s.xflag, [&](uint32_t k) {
+            const uint32_t j = k - base;
+            const uint64_t r1 = c1[phys(j)];
+            const uint64_t v = S > 1 ? gv[phys(j)] : garner_v(p, r1, s.B[phys(j)]);
+            return (u128)r1 + (u128)v * FieldP1::P_VALUE;
+        });
+        if (!p.zk_smem) discard_scratch(zk, buf_words(p.L));  // consumed
+    }
+    if constexpr (S > 1) cluster_sync();  // no CTA reuses its buffers while another may read them
 }
 
 template <bool CRT>
-__device__ void normalize(const NttArgs &p, uint64_t inst, uint32_t *out_s, const uint64_t *B,
-                          bool in_smem, const uint64_t *C1, const uint64_t *Cs, uint64_t *spill,
-                          uint32_t *flags) {
-    normalize_limbs(p.nout, p.c + inst * p.nout, out_s, spill, flags,
-                    [&](uint32_t k) { return limb_value<CRT>(p, k, B, in_smem, C1, Cs); });
+__device__ __forceinline__ uint64_t *zk_slot(const NttArgs &p, const Smem64 &s) {
+    if constexpr (!CRT) return nullptr;
+    return p.zk_smem ? s.Z : p.scratch + blockIdx.x * p.scratch_stride;
 }
 
-template <bool CRT>
+template <bool CRT, uint32_t S>
 __global__ void __launch_bounds__(1024) k_mul_ntt(NttArgs p) {
     extern __shared__ __align__(16) uint64_t sm64[];
-    const uint32_t Lp = phys_words(p.L);
-    uint64_t *A = sm64;
-    uint64_t *B = sm64 + ((Lp + 1) & ~1u);
-    uint64_t *spill = B + ((Lp + 1) & ~1u);
-    uint32_t *flags = reinterpret_cast<uint32_t *>(spill + blockDim.x);
-    uint64_t *scr = p.scratch + blockIdx.x * p.scratch_stride;
-    uint64_t *Z = scr;                                  // [N] partial results (S > 1)
-    uint64_t *C1 = scr + (p.S > 1 ? p.N : 0);           // [N] p1 coefficients (CRT)
-    uint64_t *Cs = C1 + (CRT ? p.N : 0);                // [N] final-prime coefficients (S > 1)
-    for (uint64_t inst = blockIdx.x; inst < p.batch; inst += gridDim.x) {
-        const uint32_t *arow = p.a + inst * p.na, *brow = p.b + inst * p.nb;
-        const bool keep = p.S == 1;
-        if constexpr (CRT) {
-            prime_product<FieldP1>(p, p.t1, arow, brow, A, B, Z, C1, false);
-            prime_product<FieldP2>(p, p.t2, arow, brow, A, B, Z, Cs, keep);
-        } else {
-            prime_product<FieldP1>(p, p.t1, arow, brow, A, B, Z, Cs, keep);
-        }
-        normalize<CRT>(p, inst, reinterpret_cast<uint32_t *>(A), B, keep, C1, Cs, spill, flags);
-        if (CRT) discard_scratch(C1, p.N);  // the coefficients are consumed
-        if (!keep) discard_scratch(Cs, p.N);
-    }
+    const Smem64 s = smem64<CRT>(p, sm64);
+    uint64_t *zk = zk_slot<CRT>(p, s);
+    constexpr bool cl = S > 1;
+    const uint32_t rank = cl ? cluster_rank() : 0u;
+    const uint64_t first = cl ? cluster_index() : blockIdx.x, stride = cl ? cluster_count() : gridDim.x;
+    for (uint64_t inst = first; inst < p.batch; inst += stride)
+        pair_product<CRT, S>(p, p.a + inst * p.na, p.b + inst * p.nb, p.c + inst * p.nout, s, zk, rank);
 }
 
 // Mixed-size batch of products that share the transform length N (and so
-// the tables and geometry in p): the CTA takes the next item from the work
-// queue, largest items first, and uses that item's sizes and rows.
-template <bool CRT>
+// the tables and geometry in p): the CTA (or the cluster, through its rank 0)
+// takes the next item from the work queue, largest items first, and uses
+// that item's sizes and rows.
+template <bool CRT, uint32_t S>
 __global__ void __launch_bounds__(1024)
     k_mul_ntt_batch(NttArgs p, const BatchItem *items, uint32_t count, uint32_t *queue,
                     const BatchBinding *bind) {
     extern __shared__ __align__(16) uint64_t sm64[];
-    __shared__ uint32_t next;
-    const uint32_t Lp = phys_words(p.L);
-    uint64_t *A = sm64;
-    uint64_t *B = sm64 + ((Lp + 1) & ~1u);
-    uint64_t *spill = B + ((Lp + 1) & ~1u);
-    uint32_t *flags = reinterpret_cast<uint32_t *>(spill + blockDim.x);
-    uint64_t *scr = p.scratch + blockIdx.x * p.scratch_stride;
-    uint64_t *Z = scr;
-    uint64_t *C1 = scr + (p.S > 1 ? p.N : 0);
-    uint64_t *Cs = C1 + (CRT ? p.N : 0);
+    const Smem64 s = smem64<CRT>(p, sm64);
+    uint64_t *zk = zk_slot<CRT>(p, s);
+    constexpr bool cl = S > 1;
+    const uint32_t rank = cl ? cluster_rank() : 0u;
     for (;;) {
-        __syncthreads();  // the previous item is stored before `next` moves on
-        if (threadIdx.x == 0) next = atomicAdd(queue, 1u);
-        __syncthreads();
-        const uint32_t i = next;
+        if (rank == 0 && threadIdx.x == 0) *s.next = atomicAdd(queue, 1u);
+        if (cl) cluster_sync();
+        else __syncthreads();
+        const uint32_t i = rank == 0 ? *s.next : ld_dsmem_u32(dsmem_addr(s.next, 0));
+        if (cl) cluster_sync();  // rank 0 neither moves on nor exits before every rank has read
+        else __syncthreads();
         if (i >= count) break;
         const BatchItem it = items[i];
         NttArgs q = p;
-        q.a = bind->a + it.off_a;
-        q.b = bind->b + it.off_b;
-        q.c = bind->c + it.off_c;
         q.na = it.na;
         q.nb = it.nb;
         q.nout = it.na + it.nb;
         q.batch = 1;
-        const bool keep = q.S == 1;
-        if constexpr (CRT) {
-            prime_product<FieldP1>(q, q.t1, q.a, q.b, A, B, Z, C1, false);
-            prime_product<FieldP2>(q, q.t2, q.a, q.b, A, B, Z, Cs, keep);
-        } else {
-            prime_product<FieldP1>(q, q.t1, q.a, q.b, A, B, Z, Cs, keep);
-        }
-        normalize<CRT>(q, 0, reinterpret_cast<uint32_t *>(A), B, keep, C1, Cs, spill, flags);
-        if (CRT) discard_scratch(C1, q.N);  // the coefficients are consumed
-        if (!keep) discard_scratch(Cs, q.N);
+        pair_product<CRT, S>(q, bind->a + it.off_a, bind->b + it.off_b, bind->c + it.off_c, s, zk, rank);
     }
 }
 
@@ -392,7 +598,6 @@ __global__ void __launch_bounds__(1024)
 struct HostField {
     uint64_t p, g;  // g has order exactly 2^n
     uint32_t n;
-    bool montgomery;
 };
 
 uint64_t hmul(uint64_t a, uint64_t b, uint64_t p) { return (uint64_t)((u128)a * b % p); }
@@ -410,24 +615,34 @@ uint64_t hpow(uint64_t a, uint64_t e, uint64_t p) {
 
 uint64_t hinv(uint64_t a, uint64_t p) { return hpow(a, p - 2, p); }
 
-HostField field_p1() { return {FieldP1::P_VALUE, 21, 57, true}; }  // Section 4.1
+HostField field_p1() { return {FieldP1::P_VALUE, 21, 57}; }  // Section 4.1
 
 HostField field_p2() {
     const uint64_t p = FieldP2::P_VALUE;  // 27 * 2^56 + 1; 5^27 has order 2^56
-    return {p, hpow(5, 27, p), 56, true};
+    return {p, hpow(5, 27, p), 56};
 }
 
-// The form in which the device keeps constants: mul(x, form(w)) = x*w.
-uint64_t to_form(const HostField &f, uint64_t x) {
-    return f.montgomery ? (uint64_t)((((u128)x) << 64) % f.p) : x;
+Tw64 shoup_pair(uint64_t w, uint64_t p) {
+    w %= p;
+    return make_ulonglong2(w, (uint64_t)(((u128)w << 64) / p));
 }
+
+// Montgomery form x R mod p (R = 2^64): the device's table generator works in it.
+uint64_t mont_form(uint64_t x, uint64_t p) { return (uint64_t)((((u128)(x % p)) << 64) % p); }
 
 uint64_t root_of_unity(const HostField &f, uint64_t m) { return hpow(f.g, (1ull << f.n) / m, f.p); }
 
-// Host copy of one prime's tables; offsets are in u64 words.
+// N^-1 R mod p: the final scale, which also cancels the 1/R of the
+// Montgomery pointwise product.
+uint64_t final_scale(const HostField &f, uint32_t N) {
+    const uint64_t R = (uint64_t)(((u128)1 << 64) % f.p);
+    return hmul(hinv(N % f.p, f.p), R, f.p);
+}
+
+// Host copy of one prime's tables.
 struct HostTables {
-    std::vector<uint64_t> twf, twi, ffold, ifold;
-    uint64_t ws[4] = {0, 0, 0, 0}, iws[4] = {0, 0, 0, 0}, scale = 0;
+    std::vector<Tw64> twf, twi, ffold, ifold;
+    Tw64 w4{0, 0}, iw4{0, 0}, scale{0, 0};
 };
 
 HostTables make_tables(const HostField &f, uint32_t N, uint32_t S) {
@@ -435,40 +650,36 @@ HostTables make_tables(const HostField &f, uint32_t N, uint32_t S) {
     HostTables t;
     const uint64_t wN = root_of_unity(f, N), wL = hpow(wN, S, f.p);
     const uint64_t wLi = hinv(wL, f.p), wNi = hinv(wN, f.p);
-    t.twf.assign(L, 0);
-    t.twi.assign(L, 0);
+    t.twf.assign(L, make_ulonglong2(0, 0));
+    t.twi.assign(L, make_ulonglong2(0, 0));
     for (uint32_t h = 1; h < L; h <<= 1) {
         const uint64_t w = hpow(wL, L / (2 * h), f.p), wi = hpow(wLi, L / (2 * h), f.p);
         uint64_t x = 1, xi = 1;
         for (uint32_t j = 0; j < h; ++j) {
-            t.twf[h + j] = to_form(f, x);
-            t.twi[h + j] = to_form(f, xi);
+            t.twf[h + j] = shoup_pair(x, f.p);
+            t.twi[h + j] = shoup_pair(xi, f.p);
             x = hmul(x, w, f.p);
             xi = hmul(xi, wi, f.p);
         }
     }
-    // 1/N, times R for Montgomery fields (the pointwise product divided by R).
-    const uint64_t R = f.montgomery ? (uint64_t)(((u128)1 << 64) % f.p) : 1;
-    const uint64_t scale = hmul(hinv(N % f.p, f.p), R, f.p);
-    t.scale = to_form(f, scale);
+    const uint64_t scale = final_scale(f, N);
+    t.scale = shoup_pair(scale, f.p);
     if (S > 1) {
-        t.ffold.assign((size_t)S * L, 0);
-        t.ifold.assign((size_t)S * L, 0);
+        t.ffold.assign((size_t)S * L, make_ulonglong2(0, 0));
+        t.ifold.assign((size_t)S * L, make_ulonglong2(0, 0));
         for (uint32_t s = 0; s < S; ++s) {
             const uint64_t ws = hpow(wN, s, f.p), wsi = hpow(wNi, s, f.p);
             uint64_t x = 1, xi = scale;
             for (uint32_t j = 0; j < L; ++j) {
-                t.ffold[(size_t)s * L + j] = to_form(f, x);
-                t.ifold[(size_t)s * L + j] = to_form(f, xi);
+                t.ffold[(size_t)s * L + j] = shoup_pair(x, f.p);
+                t.ifold[(size_t)s * L + j] = shoup_pair(xi, f.p);
                 x = hmul(x, ws, f.p);
                 xi = hmul(xi, wsi, f.p);
             }
         }
-        const uint64_t wS = hpow(wN, N / S, f.p), wSi = hinv(wS, f.p);
-        for (uint32_t k = 0; k < S; ++k) {
-            t.ws[k] = to_form(f, hpow(wS, k, f.p));
-            t.iws[k] = to_form(f, hpow(wSi, k, f.p));
-        }
+        const uint64_t w4 = hpow(wN, N / 4, f.p);  // used when S = 4
+        t.w4 = shoup_pair(w4, f.p);
+        t.iw4 = shoup_pair(hinv(w4, f.p), f.p);
     }
     return t;
 }
@@ -479,18 +690,99 @@ uint32_t next_pow2(uint32_t x) {
     return t;
 }
 
+// Geometry of a transform product of na x nb limbs.
+struct Geometry {
+    uint32_t N, S, L, logL, T;
+};
+
+Geometry geometry(bool crt, uint32_t na, uint32_t nb, uint32_t cta) {
+    Geometry g{};
+    const uint32_t digits = crt ? na + nb : 2 * (na + nb);
+    g.N = next_pow2(digits < 2 ? 2 : digits);
+    g.S = g.N > kMaxSubLength ? g.N / kMaxSubLength : 1;
+    g.L = g.N / g.S;
+    while ((1u << g.logL) < g.L) ++g.logL;
+    uint32_t T = g.L / 8;
+    if (T < 32) T = 32;
+    if (T > 1024) T = 1024;
+    g.T = cta ? cta : T;
+    return g;
+}
+
+using PlainKernel = void (*)(NttArgs);
+using BatchKernel = void (*)(NttArgs, const BatchItem *, uint32_t, uint32_t *, const BatchBinding *);
+
+// The kernels of a form and split: two primes never split more than in two
+// (32-bit digits, N <= 16384).
+PlainKernel plain_kernel(bool crt, uint32_t S) {
+    if (crt) return S == 1 ? k_mul_ntt<true, 1> : k_mul_ntt<true, 2>;
+    return S == 1 ? k_mul_ntt<false, 1> : (S == 2 ? k_mul_ntt<false, 2> : k_mul_ntt<false, 4>);
+}
+BatchKernel batch_kernel(bool crt, uint32_t S) {
+    if (crt) return S == 1 ? k_mul_ntt_batch<true, 1> : k_mul_ntt_batch<true, 2>;
+    return S == 1 ? k_mul_ntt_batch<false, 1> : (S == 2 ? k_mul_ntt_batch<false, 2> : k_mul_ntt_batch<false, 4>);
+}
+
+// Largest co-resident grid of the plain kernel for the geometry (a multiple
+// of S); 0 if it does not fit.
+cudaError_t max_grid_of(const void *kern, const Geometry &g, uint32_t smem, int sms, uint32_t *grid) {
+    *grid = 0;
+    if (g.S == 1) {
+        int per_sm = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)g.T, smem);
+        if (e == cudaSuccess) *grid = (uint32_t)(sms * per_sm);
+        return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = g.S;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(g.S * (uint32_t)sms, 1, 1);
+    cfg.blockDim = dim3(g.T, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+    if (e == cudaSuccess) *grid = (uint32_t)clusters * g.S;
+    return e;
+}
+
+// Launch with a cluster of S CTAs when S > 1.
+template <class... Args>
+cudaError_t launch(void (*kern)(Args...), uint32_t grid, uint32_t threads, uint32_t smem, uint32_t S,
+                   cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    if (S > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = S;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 }  // namespace
 
 struct NttPlan {
     bool crt = false;
     uint32_t na = 0, nb = 0, nout = 0, N = 0, L = 0, logL = 0, S = 1, threads = 0;
-    uint32_t smem = 0, max_grid = 0;
+    uint32_t smem = 0, max_grid = 0, zk_smem = 0;
     uint64_t scratch_stride = 0;
     size_t scratch_bytes = 0;
-    uint64_t *dev = nullptr;      // tables followed by scratch
+    void *dev = nullptr;          // tables followed by scratch
     uint64_t *scratch = nullptr;  // max_grid slots of scratch_stride words
     PrimeTab t1{}, t2{};
-    uint64_t garner_inv = 0;
+    Tw64 garner{0, 0};
 };
 
 bn_status ntt_create(NttPlan **out, bool crt, uint32_t na, uint32_t nb, const bn_tuning *tun) {
@@ -503,61 +795,66 @@ bn_status ntt_create(NttPlan **out, bool crt, uint32_t na, uint32_t nb, const bn
         if (tun->cta_threads && (tun->cta_threads % 32 || tun->cta_threads > 1024)) return BN_EINVAL;
         cta = tun->cta_threads;
     }
+    const Geometry g = geometry(crt, na, nb, cta);
     NttPlan *p = new (std::nothrow) NttPlan();
     if (!p) return BN_ENOMEM;
     p->crt = crt;
     p->na = na;
     p->nb = nb;
     p->nout = na + nb;
-    const uint32_t digits = crt ? na + nb : 2 * (na + nb);
-    p->N = next_pow2(digits < 2 ? 2 : digits);
-    p->S = p->N > kMaxSubLength ? p->N / kMaxSubLength : 1;
-    p->L = p->N / p->S;
-    while ((1u << p->logL) < p->L) ++p->logL;
-    uint32_t T = p->L / 8;
-    if (T < 32) T = 32;
-    if (T > 1024) T = 1024;
-    if (cta) T = cta;
-    p->threads = T;
-    const uint32_t Lp2 = (phys_words(p->L) + 1) & ~1u;
-    p->smem = 8u * (2u * Lp2 + T) + 4u * 32u;
+    p->N = g.N;
+    p->S = g.S;
+    p->L = g.L;
+    p->logL = g.logL;
+    p->threads = g.T;
 
     cudaError_t e;
-    auto *kern = crt ? k_mul_ntt<true> : k_mul_ntt<false>;
-    e = allow_max_smem((const void *)kern);
-    int dev = 0, sms = 0, per_sm = 0;
+    const void *kern = (const void *)plain_kernel(crt, g.S);
+    e = allow_max_smem(kern);
+    int dev = 0, sms = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)T, p->smem);
-    if (e != cudaSuccess || per_sm == 0) {
+    // Two primes: the first prime's coefficients stay in shared memory when a
+    // third buffer costs no occupancy (and always in a cluster).
+    uint32_t grid2 = 0, grid3 = 0;
+    if (e == cudaSuccess) e = max_grid_of(kern, g, smem_bytes(g.L, 2, g.T), sms, &grid2);
+    if (e == cudaSuccess && crt) e = max_grid_of(kern, g, smem_bytes(g.L, 3, g.T), sms, &grid3);
+    if (e != cudaSuccess) {
         delete p;
-        return e == cudaSuccess ? BN_EUNSUPPORTED : BN_ECUDA;
+        return BN_ECUDA;
     }
-    p->max_grid = (uint32_t)(sms * per_sm);
-    p->scratch_stride = (p->S > 1 ? 2ull * p->N : 0ull) + (crt ? (uint64_t)p->N : 0ull);
+    p->zk_smem = crt && (g.S > 1 || grid3 >= grid2) ? 1u : 0u;
+    p->smem = smem_bytes(g.L, p->zk_smem ? 3 : 2, g.T);
+    p->max_grid = p->zk_smem ? grid3 : grid2;
+    if (p->max_grid == 0) {
+        delete p;
+        return BN_EUNSUPPORTED;
+    }
+    p->scratch_stride = crt && !p->zk_smem ? buf_words(g.L) : 0;
 
     // Tables for each prime, then scratch, in one allocation.
     std::vector<HostTables> tabs;
     tabs.push_back(make_tables(field_p1(), p->N, p->S));
     if (crt) tabs.push_back(make_tables(field_p2(), p->N, p->S));
-    size_t words = 0;
-    for (auto &t : tabs) words += t.twf.size() + t.twi.size() + t.ffold.size() + t.ifold.size();
-    const size_t table_words = (words + 31) & ~size_t(31);
+    size_t entries = 0;
+    for (auto &t : tabs) entries += t.twf.size() + t.twi.size() + t.ffold.size() + t.ifold.size();
+    const size_t table_bytes = (entries * sizeof(Tw64) + 255) & ~size_t(255);
     p->scratch_bytes = (size_t)p->max_grid * p->scratch_stride * 8u;
-    e = cudaMalloc(&p->dev, table_words * 8u + p->scratch_bytes);
+    e = cudaMalloc(&p->dev, table_bytes + p->scratch_bytes);
     if (e != cudaSuccess) {
         delete p;
         return e == cudaErrorMemoryAllocation ? BN_ENOMEM : BN_ECUDA;
     }
-    std::vector<uint64_t> host(table_words, 0);
+    std::vector<Tw64> host(table_bytes / sizeof(Tw64), make_ulonglong2(0, 0));
     size_t off = 0;
+    Tw64 *dtab = static_cast<Tw64 *>(p->dev);
     for (size_t i = 0; i < tabs.size(); ++i) {
         HostTables &t = tabs[i];
         PrimeTab &pt = i == 0 ? p->t1 : p->t2;
-        auto put = [&](const std::vector<uint64_t> &v) -> const uint64_t * {
+        auto put = [&](const std::vector<Tw64> &v) -> const Tw64 * {
             if (v.empty()) return nullptr;
-            std::memcpy(host.data() + off, v.data(), v.size() * 8u);
-            const uint64_t *d = p->dev + off;
+            std::memcpy(host.data() + off, v.data(), v.size() * sizeof(Tw64));
+            const Tw64 *d = dtab + off;
             off += v.size();
             return d;
         };
@@ -565,19 +862,19 @@ bn_status ntt_create(NttPlan **out, bool crt, uint32_t na, uint32_t nb, const bn
         pt.twi = put(t.twi);
         pt.ffold = put(t.ffold);
         pt.ifold = put(t.ifold);
-        std::memcpy(pt.ws, t.ws, sizeof pt.ws);
-        std::memcpy(pt.iws, t.iws, sizeof pt.iws);
+        pt.w4 = t.w4;
+        pt.iw4 = t.iw4;
         pt.scale = t.scale;
     }
-    e = cudaMemcpy(p->dev, host.data(), table_words * 8u, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(p->dev, host.data(), table_bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(p->dev);
         delete p;
         return BN_ECUDA;
     }
-    p->scratch = p->dev + table_words;
+    p->scratch = reinterpret_cast<uint64_t *>(static_cast<char *>(p->dev) + table_bytes);
     const HostField f1 = field_p1(), f2 = field_p2();
-    p->garner_inv = to_form(f2, hinv(f1.p % f2.p, f2.p));
+    p->garner = shoup_pair(hinv(f1.p % f2.p, f2.p), f2.p);
     *out = p;
     return BN_OK;
 }
@@ -604,12 +901,19 @@ NttArgs plan_args(const NttPlan *p) {
     args.logL = p->logL;
     args.S = p->S;
     args.digit_bits = p->crt ? 32 : 16;
+    args.zk_smem = p->zk_smem;
     args.scratch = p->scratch;
     args.scratch_stride = p->scratch_stride;
-    args.garner_inv = p->garner_inv;
+    args.garner = p->garner;
     args.t1 = p->t1;
     args.t2 = p->t2;
     return args;
+}
+
+// Grid for `units` products: persistent, at most max_grid CTAs, whole clusters.
+uint32_t grid_for(const NttPlan *p, uint64_t units) {
+    const uint64_t ctas = units * p->S;
+    return (uint32_t)(ctas < p->max_grid ? ctas : p->max_grid);
 }
 
 }  // namespace
@@ -622,10 +926,8 @@ cudaError_t ntt_launch(NttPlan *p, const uint32_t *a, const uint32_t *b, uint32_
     args.b = b;
     args.c = c;
     args.batch = batch;
-    const uint64_t grid = batch < p->max_grid ? batch : p->max_grid;
-    if (p->crt) k_mul_ntt<true><<<(unsigned)grid, p->threads, p->smem, st>>>(args);
-    else k_mul_ntt<false><<<(unsigned)grid, p->threads, p->smem, st>>>(args);
-    return cudaGetLastError();
+    const uint32_t grid = grid_for(p, batch);
+    return launch(plain_kernel(p->crt, p->S), grid, p->threads, p->smem, p->S, st, args);
 }
 
 cudaError_t ntt_launch_sized(NttPlan *p, uint32_t na, uint32_t nb, const uint32_t *a,
@@ -638,9 +940,7 @@ cudaError_t ntt_launch_sized(NttPlan *p, uint32_t na, uint32_t nb, const uint32_
     args.nb = nb;
     args.nout = na + nb;
     args.batch = 1;
-    if (p->crt) k_mul_ntt<true><<<1, p->threads, p->smem, st>>>(args);
-    else k_mul_ntt<false><<<1, p->threads, p->smem, st>>>(args);
-    return cudaGetLastError();
+    return launch(plain_kernel(p->crt, p->S), p->S, p->threads, p->smem, p->S, st, args);
 }
 
 bn_status ntt_batch_plan(NttPlan **out, bool crt, uint32_t N) {
@@ -648,25 +948,24 @@ bn_status ntt_batch_plan(NttPlan **out, bool crt, uint32_t N) {
     if (N < 4 || (N & (N - 1))) return BN_EINVAL;
     const uint32_t per_side = crt ? N / 2 : N / 4;
     if (per_side > BN_MUL_MAX_LIMBS) return BN_EUNSUPPORTED;
-    cudaError_t e = allow_max_smem((const void *)k_mul_ntt_batch<true>);
-    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_ntt_batch<false>);
-    if (e != cudaSuccess) return BN_ECUDA;
-    return ntt_create(out, crt, per_side, per_side, nullptr);
+    const bn_status st = ntt_create(out, crt, per_side, per_side, nullptr);
+    if (st != BN_OK) return st;
+    if (allow_max_smem((const void *)batch_kernel(crt, (*out)->S)) != cudaSuccess) {
+        ntt_destroy(*out);
+        *out = nullptr;
+        return BN_ECUDA;
+    }
+    return BN_OK;
 }
 
 cudaError_t ntt_batch_launch(NttPlan *p, const BatchItem *items, uint32_t count, uint32_t *queue,
                              const BatchBinding *bind, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
     const NttArgs args = plan_args(p);
-    const uint32_t grid = count < p->max_grid ? count : p->max_grid;
-    if (p->crt) {
-        if (cudaError_t e = allow_max_smem((const void *)k_mul_ntt_batch<true>)) return e;
-        k_mul_ntt_batch<true><<<grid, p->threads, p->smem, st>>>(args, items, count, queue, bind);
-    } else {
-        if (cudaError_t e = allow_max_smem((const void *)k_mul_ntt_batch<false>)) return e;
-        k_mul_ntt_batch<false><<<grid, p->threads, p->smem, st>>>(args, items, count, queue, bind);
-    }
-    return cudaGetLastError();
+    const uint32_t grid = grid_for(p, count);
+    const BatchKernel kern = batch_kernel(p->crt, p->S);
+    if (cudaError_t e = allow_max_smem((const void *)kern)) return e;
+    return launch(kern, grid, p->threads, p->smem, p->S, st, args, items, count, queue, bind);
 }
 
 // ---- transform multiplication without allocation ------------------------
@@ -681,17 +980,18 @@ namespace {
 
 constexpr size_t kNoAllocScratchWords = BN_NOALLOC_SCRATCH_BYTES / 8;
 // Largest table set: two primes at N = 16384 split into two 8192-point
-// halves, each prime holding twf + twi (2 L) and both folds (2 N) words.
-constexpr size_t kNoAllocTableWords = 2 * (2 * 8192 + 2 * 16384);
-static_assert(kNoAllocTableWords >= 2 * 8192 + 2 * 32768, "one prime at N = 32768 fits");
+// halves, each prime holding twf + twi (2 L) and both folds (2 N) entries.
+constexpr size_t kNoAllocTableEntries = 2 * (2 * 8192 + 2 * 16384);
+static_assert(kNoAllocTableEntries >= 2 * 8192 + 2 * 32768, "one prime at N = 32768 fits");
 
 static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocScratchWords];
-static __device__ __align__(256) uint64_t g_noalloc_tables[kNoAllocTableWords];
+static __device__ __align__(256) Tw64 g_noalloc_tables[kNoAllocTableEntries];
 
 constexpr int kNoAllocMaxDevices = 64;
 struct NoAllocDevice {
     bool ready = false;
-    uint64_t *scratch = nullptr, *tables = nullptr;  // device addresses of the arrays
+    uint64_t *scratch = nullptr;  // device addresses of the arrays
+    Tw64 *tables = nullptr;
     int sms = 0;
     bool have_tables = false;  // the table array holds (crt, N)
     bool crt = false;
@@ -704,76 +1004,93 @@ struct NoAllocDevice {
 NoAllocDevice g_noalloc_devices[kNoAllocMaxDevices];
 std::mutex g_noalloc_mutex;
 
+// x^e in Montgomery form (x and one in Montgomery form).
 template <class F>
 __device__ uint64_t form_pow(uint64_t base, uint64_t e, uint64_t one) {
     uint64_t r = one;
     while (e) {
-        if (e & 1) r = F::mul(r, base);
-        base = F::mul(base, base);
+        if (e & 1) r = F::mont(r, base);
+        base = F::mont(base, base);
         e >>= 1;
     }
     return r;
 }
 
-// One prime's tables (layout twf[L] | twi[L] | ffold[S L] | ifold[S L]), the
-// same values the plans build on the host; all inputs are in twiddle form.
+// Shoup pair of the Montgomery-form value xf: w = xf / R canonical (a
+// Montgomery product by 1), and floor(w 2^64 / P) by binary long division
+// (w < P < 2^62, so the running remainder doubled stays below 2^63).
 template <class F>
-__global__ void k_noalloc_tables(uint64_t *tab, uint32_t L, uint32_t S, uint64_t one, uint64_t wL,
+__device__ Tw64 shoup_of_form(uint64_t xf) {
+    const uint64_t w = F::canon(F::mont(xf, 1));
+    uint64_t r = w, q = 0;
+    for (int i = 0; i < 64; ++i) {
+        r <<= 1;
+        q <<= 1;
+        if (r >= F::P_VALUE) {
+            r -= F::P_VALUE;
+            q |= 1;
+        }
+    }
+    return make_ulonglong2(w, q);
+}
+
+// One prime's tables (layout twf[L] | twi[L] | ffold[S L] | ifold[S L]), the
+// same values the plans build on the host; inputs in Montgomery form.
+template <class F>
+__global__ void k_noalloc_tables(Tw64 *tab, uint32_t L, uint32_t S, uint64_t one, uint64_t wL,
                                  uint64_t wLi, uint64_t wN, uint64_t wNi, uint64_t scale) {
     const uint32_t total = 2 * L + (S > 1 ? 2 * S * L : 0);
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += gridDim.x * blockDim.x) {
+        uint64_t v;
         if (idx < 2 * L) {
             const uint32_t inv = idx >= L, i = idx - inv * L;
-            uint64_t v = 0;
+            v = 0;
             if (i > 0) {
                 const uint32_t h = 1u << (31 - __clz(i)), j = i - h;
                 v = form_pow<F>(form_pow<F>(inv ? wLi : wL, L / (2 * h), one), j, one);
             }
-            tab[idx] = F::canon(v);
         } else {
             const uint32_t k = idx - 2 * L, inv = k >= S * L, r = k - inv * S * L;
             const uint32_t sidx = r / L, j = r - sidx * L;
             const uint64_t w = form_pow<F>(inv ? wNi : wN, (uint64_t)j * sidx, one);
-            tab[idx] = F::canon(inv ? F::mul(scale, w) : w);
+            v = inv ? F::mont(scale, w) : w;
         }
+        tab[idx] = shoup_of_form<F>(v);
     }
 }
 
-// Host constants of one prime for (N, S), in twiddle form; no allocation.
+// Host constants of one prime for (N, S); no allocation.
 struct NoAllocPrime {
-    uint64_t one, wL, wLi, wN, wNi, scale;
+    uint64_t one, wL, wLi, wN, wNi, scale;  // Montgomery form, for the generator
     PrimeTab tab;
 };
 
-NoAllocPrime noalloc_prime(const HostField &f, uint32_t N, uint32_t S, uint64_t *dtab) {
+NoAllocPrime noalloc_prime(const HostField &f, uint32_t N, uint32_t S, Tw64 *dtab) {
     NoAllocPrime c{};
     const uint32_t L = N / S;
     const uint64_t wN = root_of_unity(f, N), wL = hpow(wN, S, f.p);
-    const uint64_t R = f.montgomery ? (uint64_t)(((u128)1 << 64) % f.p) : 1;
-    const uint64_t scale = hmul(hinv(N % f.p, f.p), R, f.p);
-    c.one = to_form(f, 1);
-    c.wL = to_form(f, wL);
-    c.wLi = to_form(f, hinv(wL, f.p));
-    c.wN = to_form(f, wN);
-    c.wNi = to_form(f, hinv(wN, f.p));
-    c.scale = to_form(f, scale);
+    const uint64_t scale = final_scale(f, N);
+    c.one = mont_form(1, f.p);
+    c.wL = mont_form(wL, f.p);
+    c.wLi = mont_form(hinv(wL, f.p), f.p);
+    c.wN = mont_form(wN, f.p);
+    c.wNi = mont_form(hinv(wN, f.p), f.p);
+    c.scale = mont_form(scale, f.p);
     c.tab.twf = dtab;
     c.tab.twi = dtab + L;
     c.tab.ffold = S > 1 ? dtab + 2 * L : nullptr;
     c.tab.ifold = S > 1 ? dtab + 2 * L + (size_t)S * L : nullptr;
-    c.tab.scale = c.scale;
+    c.tab.scale = shoup_pair(scale, f.p);
     if (S > 1) {
-        const uint64_t wS = hpow(wN, N / S, f.p), wSi = hinv(wS, f.p);
-        for (uint32_t k = 0; k < S; ++k) {
-            c.tab.ws[k] = to_form(f, hpow(wS, k, f.p));
-            c.tab.iws[k] = to_form(f, hpow(wSi, k, f.p));
-        }
+        const uint64_t w4 = hpow(wN, N / 4, f.p);
+        c.tab.w4 = shoup_pair(w4, f.p);
+        c.tab.iw4 = shoup_pair(hinv(w4, f.p), f.p);
     }
     return c;
 }
 
-size_t noalloc_prime_words(uint32_t N, uint32_t S) {
+size_t noalloc_prime_entries(uint32_t N, uint32_t S) {
     return 2 * (N / S) + (S > 1 ? 2 * (size_t)N : 0);
 }
 
@@ -810,21 +1127,13 @@ extern "C" bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, ui
     }
     const bool crt = crt_flag != 0;
     cudaStream_t st = (cudaStream_t)stream;
-    auto *kern = crt ? k_mul_ntt<true> : k_mul_ntt<false>;
-
-    // Geometry, as for a plan.
-    const uint32_t digits = crt ? nout : 2 * nout;
-    const uint32_t N = next_pow2(digits < 2 ? 2 : digits);
-    const uint32_t S = N > kMaxSubLength ? N / kMaxSubLength : 1;
-    const uint32_t L = N / S;
-    uint32_t logL = 0;
-    while ((1u << logL) < L) ++logL;
-    uint32_t T = L / 8;
-    if (T < 32) T = 32;
-    if (T > 1024) T = 1024;
-    const uint32_t Lp2 = (phys_words(L) + 1) & ~1u;
-    const uint32_t smem = 8u * (2u * Lp2 + T) + 4u * 32u;
-    const uint64_t stride = (S > 1 ? 2ull * N : 0ull) + (crt ? (uint64_t)N : 0ull);
+    // Geometry, as for a plan; the first prime's coefficients of a two-prime
+    // product go to the scratch array unless the transform is split.
+    const Geometry g = geometry(crt, na, nb, 0);
+    const PlainKernel kern = plain_kernel(crt, g.S);
+    const uint32_t zk_smem = crt && g.S > 1 ? 1u : 0u;
+    const uint32_t smem = smem_bytes(g.L, zk_smem ? 3 : 2, g.T);
+    const uint64_t stride = crt && !zk_smem ? buf_words(g.L) : 0;
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -851,40 +1160,39 @@ extern "C" bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, ui
         if (e == cudaSuccess) e = cudaGetSymbolAddress(&pt, g_noalloc_tables);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_mul_ntt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_mul_ntt<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        const PlainKernel all[] = {plain_kernel(false, 1), plain_kernel(false, 2), plain_kernel(false, 4),
+                                   plain_kernel(true, 1), plain_kernel(true, 2)};
+        for (PlainKernel k : all)
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         if (e != cudaSuccess) {
             record_error("bn_mul_ntt_noalloc device set-up failed");
             return BN_ECUDA;
         }
         d.scratch = static_cast<uint64_t *>(ps);
-        d.tables = static_cast<uint64_t *>(pt);
+        d.tables = static_cast<Tw64 *>(pt);
         d.ready = true;
     }
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)T, smem);
-    if (e != cudaSuccess || per_sm == 0) {
+    uint32_t max_grid = 0;
+    e = max_grid_of((const void *)kern, g, smem, d.sms, &max_grid);
+    if (e != cudaSuccess || max_grid == 0) {
         record_error("bn_mul_ntt_noalloc: kernel does not fit on this device");
         return BN_ECUDA;
     }
-    uint64_t max_grid = (uint64_t)d.sms * per_sm;
-    if (stride > 0 && kNoAllocScratchWords / stride < max_grid) max_grid = kNoAllocScratchWords / stride;
+    if (stride > 0 && kNoAllocScratchWords / stride < max_grid) max_grid = (uint32_t)(kNoAllocScratchWords / stride);
 
-    const NoAllocPrime c1 = noalloc_prime(field_p1(), N, S, d.tables);
-    const NoAllocPrime c2 = noalloc_prime(field_p2(), N, S, d.tables + noalloc_prime_words(N, S));
+    const NoAllocPrime c1 = noalloc_prime(field_p1(), g.N, g.S, d.tables);
+    const NoAllocPrime c2 = noalloc_prime(field_p2(), g.N, g.S, d.tables + noalloc_prime_entries(g.N, g.S));
     // A captured call records its own table kernel (replays regenerate the
     // tables they read) and leaves the host's record of the table contents
     // unusable for every later call.
     if (capturing) d.captured = true;
-    if (capturing || d.captured || !d.have_tables || d.crt != crt || d.N != N) {
-        const uint32_t words = (uint32_t)noalloc_prime_words(N, S);
-        const unsigned blocks = (words + 255) / 256 < 1024 ? (words + 255) / 256 : 1024;
-        k_noalloc_tables<FieldP1><<<blocks, 256, 0, st>>>(d.tables, L, S, c1.one, c1.wL, c1.wLi,
+    if (capturing || d.captured || !d.have_tables || d.crt != crt || d.N != g.N) {
+        const uint32_t entries = (uint32_t)noalloc_prime_entries(g.N, g.S);
+        const unsigned blocks = (entries + 255) / 256 < 1024 ? (entries + 255) / 256 : 1024;
+        k_noalloc_tables<FieldP1><<<blocks, 256, 0, st>>>(d.tables, g.L, g.S, c1.one, c1.wL, c1.wLi,
                                                            c1.wN, c1.wNi, c1.scale);
         if (crt)
-            k_noalloc_tables<FieldP2><<<blocks, 256, 0, st>>>(d.tables + words, L, S, c2.one, c2.wL,
+            k_noalloc_tables<FieldP2><<<blocks, 256, 0, st>>>(d.tables + entries, g.L, g.S, c2.one, c2.wL,
                                                                c2.wLi, c2.wN, c2.wNi, c2.scale);
         if ((e = cudaGetLastError()) != cudaSuccess) {
             d.have_tables = false;
@@ -893,7 +1201,7 @@ extern "C" bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, ui
         }
         d.have_tables = !d.captured;
         d.crt = crt;
-        d.N = N;
+        d.N = g.N;
     }
 
     NttArgs args{};
@@ -903,21 +1211,22 @@ extern "C" bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, ui
     args.na = na;
     args.nb = nb;
     args.nout = nout;
-    args.N = N;
-    args.L = L;
-    args.logL = logL;
-    args.S = S;
+    args.N = g.N;
+    args.L = g.L;
+    args.logL = g.logL;
+    args.S = g.S;
     args.digit_bits = crt ? 32 : 16;
+    args.zk_smem = zk_smem;
     args.batch = batch;
     args.scratch = d.scratch;
     args.scratch_stride = stride;
-    args.garner_inv = to_form(field_p2(), hinv(field_p1().p % field_p2().p, field_p2().p));
+    args.garner = shoup_pair(hinv(field_p1().p % field_p2().p, field_p2().p), field_p2().p);
     args.t1 = c1.tab;
     args.t2 = c2.tab;
-    const uint64_t grid = batch < max_grid ? batch : max_grid;
-    if (crt) k_mul_ntt<true><<<(unsigned)grid, T, smem, st>>>(args);
-    else k_mul_ntt<false><<<(unsigned)grid, T, smem, st>>>(args);
-    if ((e = cudaGetLastError()) != cudaSuccess) {
+    const uint64_t ctas = batch * g.S;
+    const uint32_t grid = (uint32_t)(ctas < max_grid ? ctas : max_grid);
+    e = launch(kern, grid, g.T, smem, g.S, st, args);
+    if (e != cudaSuccess) {
         record_error("bn_mul_ntt_noalloc kernel launch failed");
         return BN_ECUDA;
     }

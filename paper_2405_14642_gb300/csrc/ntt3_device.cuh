@@ -57,6 +57,24 @@ struct MontField32 {
         return a * w.x - q * P;
     }
     __device__ static __forceinline__ uint32_t twiddle_lazy(uint32_t a, uint2 w) { return twiddle(a, w); }
+    // Butterflies on [0, 2P): the difference u - v + 2P (< 4P) goes to the
+    // twiddle product unreduced.
+    __device__ static __forceinline__ void dif(uint32_t &u, uint32_t &v, uint2 w) {
+        const uint32_t x = u, y = v;
+        u = add(x, y);
+        v = twiddle(x + TWO_P - y, w);
+    }
+    __device__ static __forceinline__ void dif1(uint32_t &u, uint32_t &v) {
+        const uint32_t x = u, y = v;
+        u = add(x, y);
+        v = sub(x, y);
+    }
+    __device__ static __forceinline__ void dit(uint32_t &u, uint32_t &v, uint2 w) {
+        const uint32_t x = u, t = twiddle_lazy(v, w);
+        u = add(x, t);
+        v = sub(x, t);
+    }
+    __device__ static __forceinline__ void dit1(uint32_t &u, uint32_t &v) { dif1(u, v); }
 };
 
 using F0 = MontField32<469762049u, 0x1bffffffu>;  // 7 * 2^26 + 1

@@ -4,11 +4,14 @@
 // transforms, and the normalisation of convolution coefficients into limbs.
 //
 // A field type F provides Elem (the word type of its elements), Tw (the type
-// of a twiddle table entry), TWO_P, and on lazily reduced elements in [0, 2P):
-//   add, sub, canon, mul(a, b) for a, b < 2P,
-//   twiddle(a, w)      = a * (the twiddle w) for any a < 4P,
-//   twiddle_lazy(a, w) = the same for a < 2P (may be cheaper),
-// all returning a value in [0, 2P).
+// of a twiddle table entry) and the two butterflies on lazily reduced
+// elements, in place on (u, v):
+//   dif(u, v, w):  (u + v, (u - v) w)    decimation in frequency,
+//   dit(u, v, w):  (u + v w, u - v w)    decimation in time,
+// and dif1 / dit1, the same with the twiddle 1.  Each field states the range
+// its elements keep between passes; the forward passes start from values
+// below 2P, and whatever range the inverse passes end in, the field's final
+// scaling maps it back.
 #pragma once
 #include "bn_device.cuh"
 
@@ -86,8 +89,7 @@ __device__ __forceinline__ uint32_t tw_index(uint32_t base, uint32_t m, uint32_t
 
 // KK decimation-in-frequency stages with half-sizes H, H/2, ..., H >> (KK-1).
 // UNIT: the group step is 1, so the last stage's twiddle is 1, and so is that
-// of every group's element 0 in the other stages.  The
-// difference u - v + 2P (< 4P) goes to the twiddle multiply unreduced.
+// of every group's element 0 in the other stages.
 template <class F, int KK, bool UNIT>
 __device__ __forceinline__ void dif_pass(typename F::Elem *buf, uint32_t L, uint32_t H,
                                          const typename F::Tw *tw) {
@@ -117,9 +119,8 @@ __device__ __forceinline__ void dif_pass(typename F::Elem *buf, uint32_t L, uint
                 if (m & hm) continue;
                 // UNIT: base is a multiple of E, so element m's twiddle is w_{2h}^(m mod hm): 1 for m mod hm = 0
                 const bool one = UNIT && (m & (hm - 1)) == 0;
-                const T u = x[m], v = x[m + hm];
-                x[m] = F::add(u, v);
-                x[m + hm] = one ? F::sub(u, v) : F::twiddle(u + F::TWO_P - v, w[m & (hm - 1)]);
+                if (one) F::dif1(x[m], x[m + hm]);
+                else F::dif(x[m], x[m + hm], w[m & (hm - 1)]);
             }
         }
         if constexpr (UNIT) store_run<T, E>(buf, base, x);
@@ -161,10 +162,8 @@ __device__ __forceinline__ void dit_pass(typename F::Elem *buf, uint32_t L, uint
             for (int m = 0; m < E; ++m) {
                 if (m & hm) continue;
                 const bool one = UNIT && (m & (hm - 1)) == 0;  // twiddle w_{2h}^0 = 1 (as in dif_pass)
-                const T u = x[m];
-                const T v = one ? x[m + hm] : F::twiddle_lazy(x[m + hm], w[m & (hm - 1)]);
-                x[m] = F::add(u, v);
-                x[m + hm] = F::sub(u, v);
+                if (one) F::dit1(x[m], x[m + hm]);
+                else F::dit(x[m], x[m + hm], w[m & (hm - 1)]);
             }
         }
         if constexpr (UNIT) store_run<T, E>(buf, base, x);
@@ -310,14 +309,11 @@ __device__ __forceinline__ void pass_c(typename F::Elem *buf, const typename F::
                 // UNIT: j0 = 0, so element m's twiddle is tw[hm + m mod hm]: 1 for m mod hm = 0
                 const bool one = UNIT && (m & (hm - 1)) == 0;
                 if constexpr (DIF) {
-                    const T u = x[m], v = x[m + hm];
-                    x[m] = F::add(u, v);
-                    x[m + hm] = one ? F::sub(u, v) : F::twiddle(u + F::TWO_P - v, w[m & (hm - 1)]);
+                    if (one) F::dif1(x[m], x[m + hm]);
+                    else F::dif(x[m], x[m + hm], w[m & (hm - 1)]);
                 } else {
-                    const T u = x[m];
-                    const T v = one ? x[m + hm] : F::twiddle_lazy(x[m + hm], w[m & (hm - 1)]);
-                    x[m] = F::add(u, v);
-                    x[m + hm] = F::sub(u, v);
+                    if (one) F::dit1(x[m], x[m + hm]);
+                    else F::dit(x[m], x[m + hm], w[m & (hm - 1)]);
                 }
             }
         }

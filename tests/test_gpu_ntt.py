@@ -52,12 +52,15 @@ def test_ntt_plan_properties():
     torch_cuda()
     import paper_2405_14642_gb300 as bn
     # 16-bit digits: N = next pow2 of 2 (na + nb); 32-bit digits: of na + nb.
+    # Split transforms run on CTA clusters and hold no scratch (the two-prime
+    # form keeps the first prime's coefficients in global scratch only where
+    # a third shared buffer would lower occupancy).
     with bn.Plan(bn.BN_OP_MUL_NTT64, 8192, 8192, 4) as p:
-        assert p.transform_length == 32768 and p.scratch_bytes > 0
+        assert p.transform_length == 32768 and p.scratch_bytes == 0
     with bn.Plan(bn.BN_OP_MUL_NTT64, 512, 512, 4) as p:
         assert p.transform_length == 2048 and p.scratch_bytes == 0
     with bn.Plan(bn.BN_OP_MUL_NTT_CRT, 8192, 8192, 4) as p:
-        assert p.transform_length == 16384
+        assert p.transform_length == 16384 and p.scratch_bytes == 0
     with pytest.raises(bn.BnError) as e:
         bn.Plan(bn.BN_OP_MUL_NTT64, 8193, 16, 1)
     assert e.value.status == 4
