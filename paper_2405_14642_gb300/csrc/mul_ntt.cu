@@ -28,20 +28,21 @@
 // loads 8 elements, runs 3 stages in registers, stores them back: one
 // barrier per 3 stages).  A persistent grid walks the batch.
 //
-// Longer transforms (N = S*L, S in {2, 4}, L = 8192) run on a cluster of S
-// CTAs that share their shared memory.  CTA s of the cluster owns
-// sub-problem s: the first radix-S decimation-in-frequency stage is folded
-// into its digit load (y_s[j] = w_N^{js} sum_r x[j + rL] w_S^{rs}, from the
-// operand rows in global memory), then its forward transforms, pointwise
-// product and inverse run as above, and the last radix-S inverse stage's
-// factor N^-1 w_N^{-js} is applied in place.  The remaining radix-S
-// butterfly is evaluated during the normalisation: CTA r owns the
-// coefficients rL .. rL + L - 1, each the sum over s of w_S^{-rs} z_s[j],
-// read from the S CTAs' shared memory.  Nothing goes through global scratch.
-// The two-prime form keeps the first prime's coefficients in a third
-// shared buffer while the second prime runs (in global scratch, L2-resident,
-// only for short one-CTA transforms, where a third buffer would cost
-// occupancy).
+// Longer transforms (N = S*L, S in {2, 4}, L = 8192) are split into S
+// sub-problems and run on a cluster of two CTAs that share their shared
+// memory; each CTA owns S/2 sub-problems.  For sub-problem s the first
+// radix-S decimation-in-frequency stage is folded into the digit load (y_s[j]
+// = w_N^{js} sum_r x[j + rL] w_S^{rs}, from the operand rows in global
+// memory), then its forward transforms, pointwise product and inverse run as
+// above, and the last radix-S inverse stage's factor N^-1 w_N^{-js} is
+// applied to its result z_s.  A CTA with two sub-problems keeps the first
+// one's result in a third shared buffer.  The remaining radix-S butterfly,
+// sum over s of w_S^{-qs} z_s[j] for output quarter q, is evaluated by the
+// CTA that owns position j (half of the positions each), reading z_s[j] from
+// both CTAs.  Nothing goes through global scratch.  The two-prime form keeps
+// the first prime's coefficients in the third buffer while the second prime
+// runs (in global scratch, L2-resident, only for short one-CTA transforms,
+// where a third buffer would cost occupancy).
 //
 // Normalisation (Section 4.2's splitFftReg/baddRegMul2Fft, here with whole
 // 16/32-bit digits).  Each thread folds the coefficients of its window of
@@ -67,6 +68,9 @@ using namespace ntt;
 
 constexpr uint32_t kMaxSubLength = 8192;  // both spectra in shared memory
 constexpr uint32_t kMaxSplit = 4;         // N <= 32768
+
+// CTAs per product: a split transform runs on a cluster of two.
+__host__ __device__ constexpr uint32_t cluster_of(uint32_t S) { return S > 1 ? 2u : 1u; }
 
 // ---- clusters ---------------------------------------------------------------
 
@@ -115,7 +119,7 @@ __device__ __forceinline__ uint32_t ld_dsmem_u32(uint32_t addr) {
 typedef ulonglong2 Tw64;
 
 // Z_P for a prime P = k 2^m + 1 with m >= 32 (so P's low 32-bit word is 1)
-// and P < 2^62 (so 4P < 2^64).
+// and P < 2^62 (so 4P + 2^48 < 2^64).
 //   * shoup(x, (w, w')): for any 64-bit x, q = hi64(x w') and x w - q P lies
 //     in [0, 2P) and is x w mod P up to one P (Shoup; exact in 64-bit
 //     arithmetic since the result is below 2^64).
@@ -125,11 +129,19 @@ typedef ulonglong2 Tw64;
 //     (mod 2^64), so the quotient m = t_lo (P - 2) has words (-x0, x0*P_hi -
 //     x1 - borrow); m*P needs two more multiply-adds since P's low word is 1;
 //     the result is < 2P because 4P < 2^64.
-//   * Butterflies (Harvey's lazy ranges): dif on u, v < 2P gives u + v
-//     reduced into [0, 2P) and (u - v + 2P) w by Shoup, in [0, 2P); dit on
-//     u, v < 4P reduces u into [0, 2P), takes t = v w in [0, 2P) and gives
-//     u + t and u - t + 2P, both in [0, 4P).  One conditional subtraction
-//     each.
+//   * Forward (decimation-in-frequency) butterflies keep Harvey's range
+//     [0, 2P): dif gives u + v reduced into [0, 2P) and (u - v + 2P) w by
+//     Shoup (< 2P).  The constant added before a subtraction must be a
+//     multiple of P that is at least the value subtracted, and only 4.4 P
+//     fit in 64 bits for p1: so these values are reduced exactly.
+//   * Inverse (decimation-in-time) butterflies: dit takes t = v w by Shoup
+//     (< 2P, exact range) and x = red(u), and gives x + t and x - t + 2P.
+//     red(r) subtracts 2P when the high word of r exceeds the high word H of
+//     2P (then r >= (H + 1) 2^32 > 2P, no wrap), else leaves r (< (H + 1)
+//     2^32 <= 2P + 2^32): one compare of one word.  From the pointwise
+//     products (< 2P) the inverse values stay below 4P + 2^32.  The twiddle-1
+//     butterfly reduces the value standing in for the product exactly
+//     (red2, into [0, 2P)).
 template <uint64_t P>
 struct Field64 {
     using Elem = uint64_t;
@@ -137,15 +149,26 @@ struct Field64 {
     static constexpr uint64_t P_VALUE = P;
     static constexpr uint32_t PH = (uint32_t)(P >> 32);
     static constexpr uint64_t TWO_P = 2 * P;
+    static constexpr uint32_t H = (uint32_t)(TWO_P >> 32);
     static_assert((P & 0xffffffffull) == 1 && P < (1ull << 62), "P = k 2^m + 1, m >= 32, P < 2^62");
+    static_assert(((uint64_t)(H + 1) << 32) >= TWO_P, "red never wraps");
+    static_assert(P < (~0ull - (1ull << 33)) / 4, "4P + 2^33 fits in 64 bits");
     // r < 4P into [0, 2P): r - 2P wraps above r exactly when r < 2P.
-    __device__ static __forceinline__ uint64_t red(uint64_t r) {
+    __device__ static __forceinline__ uint64_t rexact(uint64_t r) {
         const uint64_t t = r - TWO_P;
         return t < r ? t : r;
     }
-    __device__ static __forceinline__ uint64_t add(uint64_t a, uint64_t b) { return red(a + b); }
-    __device__ static __forceinline__ uint64_t sub(uint64_t a, uint64_t b) { return red(a + TWO_P - b); }
+    __device__ static __forceinline__ uint64_t red(uint64_t r) {
+        return (uint32_t)(r >> 32) > H ? r - TWO_P : r;
+    }
+    // r < 4P + 2^33 into [0, 2P).
+    __device__ static __forceinline__ uint64_t red2(uint64_t r) { return rexact(red(r)); }
+    // a, b < 2P.
+    __device__ static __forceinline__ uint64_t add(uint64_t a, uint64_t b) { return rexact(a + b); }
+    __device__ static __forceinline__ uint64_t sub(uint64_t a, uint64_t b) { return rexact(a + TWO_P - b); }
+    // a mod P for a < 2P, and for a < 4P.
     __device__ static __forceinline__ uint64_t canon(uint64_t a) { return a >= P ? a - P : a; }
+    __device__ static __forceinline__ uint64_t exact(uint64_t a) { return canon(rexact(a)); }
     __device__ static __forceinline__ uint64_t shoup(uint64_t x, Tw64 w) {
         const uint64_t q = __umul64hi(x, w.y);
         const uint64_t qp = q + ((uint64_t)((uint32_t)q * PH) << 32);  // q * P mod 2^64
@@ -181,7 +204,7 @@ struct Field64 {
         v = x + TWO_P - t;
     }
     __device__ static __forceinline__ void dit1(uint64_t &u, uint64_t &v) {
-        const uint64_t x = red(u), t = red(v);
+        const uint64_t x = red(u), t = red2(v);
         u = x + t;
         v = x + TWO_P - t;
     }
@@ -204,9 +227,10 @@ struct NttArgs {
     uint32_t *c;
     uint32_t na, nb, nout;
     uint32_t N, L, logL, S, digit_bits;
-    uint32_t zk_smem;         // two primes: the first prime's coefficients in shared memory
+    uint32_t z_smem;          // a third shared buffer: the first prime's coefficients (two
+                              // primes) or the first sub-problem's result (S = 4)
     uint64_t batch;
-    uint64_t *scratch;        // two primes, zk_smem == 0: one slot per CTA
+    uint64_t *scratch;        // two primes, z_smem == 0: one slot per CTA
     uint64_t scratch_stride;  // u64 words per CTA
     Tw64 garner;              // p1^-1 mod p2
     PrimeTab t1, t2;
@@ -215,29 +239,28 @@ struct NttArgs {
 __host__ __device__ constexpr uint32_t buf_words(uint32_t L) { return (phys_words(L) + 1) & ~1u; }
 
 // Dynamic shared memory of one CTA: `bufs` padded length-L buffers, one
-// spill word per thread, the warp flags, the cluster carry word and the
-// batch queue slot.
+// spill word per thread, the warp flags, the cluster carry words (2 per
+// segment of the CTA) and the batch queue slot.
 __host__ __device__ constexpr uint32_t smem_bytes(uint32_t L, uint32_t bufs, uint32_t threads) {
-    return 8u * (bufs * buf_words(L) + threads) + 4u * (32u + 2u);
+    return 8u * (bufs * buf_words(L) + threads) + 4u * (32u + 2u * kMaxSplit + 2u);
 }
 
 struct Smem64 {
-    uint64_t *A, *B, *Z;  // Z: the first prime's coefficients (two primes, zk_smem)
+    uint64_t *A, *B, *Z;  // Z: the third buffer (z_smem)
     uint64_t *spill;
     uint32_t *flags, *xflag, *next;
 };
 
-template <bool CRT>
 __device__ __forceinline__ Smem64 smem64(const NttArgs &p, uint64_t *sm) {
     const uint32_t W = buf_words(p.L);
     Smem64 s;
     s.A = sm;
     s.B = sm + W;
-    s.Z = (CRT && p.zk_smem) ? sm + 2 * W : nullptr;
-    s.spill = sm + ((CRT && p.zk_smem) ? 3 : 2) * W;
+    s.Z = p.z_smem ? sm + 2 * W : nullptr;
+    s.spill = sm + (p.z_smem ? 3 : 2) * W;
     s.flags = reinterpret_cast<uint32_t *>(s.spill + blockDim.x);
     s.xflag = s.flags + 32;
-    s.next = s.xflag + 1;
+    s.next = s.xflag + 2 * kMaxSplit;
     return s;
 }
 
@@ -261,10 +284,10 @@ __device__ __forceinline__ uint64_t fold(const uint64_t (&x)[S], uint32_t s, Tw6
 // thread takes positions j, j + 1 (j even): with 16-bit digits one 32-bit
 // word of each row quarter holds both.  All global loads of U iterations
 // are issued before any is used.
-template <class F, uint32_t S>
+template <class F, uint32_t S, bool D16>
 __device__ void load_fold(const NttArgs &p, const PrimeTab &tb, const uint32_t *arow, const uint32_t *brow,
                           uint32_t s, uint64_t *A, uint64_t *B) {
-    const bool d16 = p.digit_bits == 16;
+    constexpr bool d16 = D16;
     const uint32_t wa = p.na, wb = p.nb;  // 32-bit words per row
     const uint32_t half = p.L / 2;
     // word index of digit position m; 16-bit digits: position pairs share one word
@@ -272,7 +295,7 @@ __device__ void load_fold(const NttArgs &p, const PrimeTab &tb, const uint32_t *
         const uint32_t w = d16 ? m >> 1 : m;
         return w < nw ? __ldg(row + w) : 0u;
     };
-    constexpr int U = S == 1 ? 2 : 1;
+    constexpr int U = D16 || S == 1 ? 2 : 1;
     for (uint32_t q0 = threadIdx.x; q0 < half; q0 += U * blockDim.x) {
         uint32_t ra[U][S][2], rb[U][S][2];
         Tw64 f[U][2];
@@ -316,7 +339,7 @@ __device__ void load_fold(const NttArgs &p, const PrimeTab &tb, const uint32_t *
     }
 }
 
-// Forward / inverse transforms of a sub-problem: the compile-time passes for
+// Forward transforms of a sub-problem: the compile-time passes for
 // the lengths the 16K..256K-bit range uses most (L = 4096 and 8192 with their
 // default thread counts; 7-8% faster), the runtime passes otherwise.
 template <class F>
@@ -326,12 +349,6 @@ __device__ __forceinline__ void forward_sub(const NttArgs &p, const Tw64 *tw, ui
     else forward2<F>(p.L, p.logL, tw, A, B);
 }
 
-template <class F>
-__device__ __forceinline__ void inverse_sub(const NttArgs &p, const Tw64 *tw, uint64_t *B) {
-    if (p.logL == 13 && blockDim.x == 1024) inverse_c<F, 13, 1024>(tw, B);
-    else if (p.logL == 12 && blockDim.x == 512) inverse_c<F, 12, 512>(tw, B);
-    else inverse<F>(p.L, p.logL, tw, B);
-}
 
 // Drops a per-CTA scratch region from L2 after its last read: its lines are
 // dead, and writing them back to memory when they are evicted would only add
@@ -344,25 +361,49 @@ __device__ __forceinline__ void discard_scratch(const uint64_t *ptr, uint32_t wo
         asm volatile("discard.global.L2 [%0], 128;" ::"l"(g + off) : "memory");
 }
 
+// The last inverse pass's epilogue: x -> x f (canonical), f the factor of
+// position j (TABLE: a per-position table; else one factor), also stored to
+// dest (padded layout) when dest is not null.
+template <class F, bool TABLE>
+struct ScaleEpi {
+    const Tw64 *fold;
+    Tw64 scale;
+    uint64_t *dest;
+    __device__ __forceinline__ uint64_t operator()(uint32_t j, uint64_t x) const {
+        const uint64_t v = F::canon(F::shoup(x, TABLE ? __ldg(fold + j) : scale));
+        if (dest) dest[phys(j)] = v;
+        return v;
+    }
+};
+
 // Sub-problem s of a*b mod the field's prime (n1..n4): z_s scaled by the last
 // inverse stage's factor (N^-1 R w_N^{-js}; N^-1 R when S = 1), canonical, to
-// dest (padded layout; dest may be B).  Ends with a barrier.
-template <class F, uint32_t S>
+// dest (padded layout; dest may be B).  The compile-time inverse folds the
+// scaling into its last pass.  Ends with a barrier.
+template <class F, uint32_t S, bool D16>
 __device__ void sub_product(const NttArgs &p, const PrimeTab &tb, const uint32_t *arow,
                             const uint32_t *brow, uint32_t s, uint64_t *A, uint64_t *B, uint64_t *dest) {
-    load_fold<F, S>(p, tb, arow, brow, s, A, B);  // n1: digits (and the folded first stage)
+    load_fold<F, S, D16>(p, tb, arow, brow, s, A, B);  // n1: digits (and the folded first stage)
     __syncthreads();
     forward_sub<F>(p, tb.twf, A, B);              // n2: forward transforms
     for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x)   // n3: pointwise
         B[phys(j)] = F::mont(A[phys(j)], B[phys(j)]);
     __syncthreads();
-    inverse_sub<F>(p, tb.twi, B);                 // n4: inverse transform (unscaled)
+    // n4: inverse transform and its scale
+    const ScaleEpi<F, (S > 1)> epi{S > 1 ? tb.ifold + s * p.L : nullptr, tb.scale, dest == B ? nullptr : dest};
+    if (p.logL == 13 && blockDim.x == 1024) {
+        inverse_c<F, 13, 1024>(tb.twi, B, epi);
+    } else if (p.logL == 12 && blockDim.x == 512) {
+        inverse_c<F, 12, 512>(tb.twi, B, epi);
+    } else {
+        inverse<F>(p.L, p.logL, tb.twi, B);
 #pragma unroll 4
-    for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) {
-        const Tw64 f = S > 1 ? __ldg(tb.ifold + s * p.L + j) : tb.scale;
-        dest[phys(j)] = F::canon(F::shoup(B[phys(j)], f));
+        for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x) {
+            const uint64_t v = epi(j, B[phys(j)]);
+            if (dest == B) B[phys(j)] = v;
+        }
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 // Addresses of a buffer in the shared memory of each CTA of the cluster.
@@ -376,21 +417,26 @@ __device__ __forceinline__ Remote remote(const uint64_t *buf, uint32_t S) {
     return v;
 }
 
-// Coefficient rL + j (canonical) from the sub-problems' scaled results of
-// the cluster's CTAs (S > 1): the last radix-S inverse stage,
-// sum_s w_S^{-rs} z_s[j].
+// The last radix-S inverse stage at position j, from the sub-problems'
+// scaled results of the cluster's CTAs: c[q] = sum_s w_S^{-qs} z_s[j] for
+// every q (canonical).  One read of each z_s[j].
 template <class F, uint32_t S>
-__device__ __forceinline__ uint64_t coefficient(const PrimeTab &tb, const Remote &zv, uint32_t r, uint32_t j) {
+__device__ __forceinline__ void combine(const PrimeTab &tb, const Remote &zv, uint32_t j, uint64_t (&c)[S]) {
     const uint32_t off = 8u * phys(j);
-    const uint64_t z0 = ld_dsmem_u64(zv.base[0] + off), z1 = ld_dsmem_u64(zv.base[1] + off);
-    if constexpr (S == 2) return F::canon(r == 0 ? F::add(z0, z1) : F::sub(z0, z1));
-    const uint64_t z2 = ld_dsmem_u64(zv.base[2] + off), z3 = ld_dsmem_u64(zv.base[3] + off);
-    if ((r & 1u) == 0) {
-        const uint64_t e0 = F::add(z0, z2), e1 = F::add(z1, z3);
-        return F::canon(r == 0 ? F::add(e0, e1) : F::sub(e0, e1));
+    uint64_t z[S];
+#pragma unroll
+    for (uint32_t s = 0; s < S; ++s) z[s] = ld_dsmem_u64(zv.base[s] + off);
+    if constexpr (S == 2) {
+        c[0] = F::exact(F::add(z[0], z[1]));
+        c[1] = F::exact(F::sub(z[0], z[1]));
+    } else {
+        const uint64_t e0 = F::add(z[0], z[2]), e1 = F::add(z[1], z[3]);
+        const uint64_t o0 = F::sub(z[0], z[2]), o1 = F::shoup(F::sub(z[1], z[3]), tb.iw4);
+        c[0] = F::exact(F::add(e0, e1));
+        c[2] = F::exact(F::sub(e0, e1));
+        c[1] = F::exact(F::add(o0, o1));
+        c[3] = F::exact(F::sub(o0, o1));
     }
-    const uint64_t o0 = F::sub(z0, z2), o1 = F::shoup(F::sub(z1, z3), tb.iw4);
-    return F::canon(r == 1 ? F::add(o0, o1) : F::sub(o0, o1));
 }
 
 // Garner's step: v = (r2 - r1) p1^-1 mod p2 for r1 < p1, r2 < p2 canonical;
@@ -403,159 +449,189 @@ __device__ __forceinline__ uint64_t garner_v(const NttArgs &p, uint64_t r1, uint
     return FieldP2::canon(FieldP2::shoup(d, p.garner));
 }
 
-// The carry into this thread's window: the Section 2 scan of (g, p) over the
-// CTA's threads, then over the cluster's CTAs in rank order (a carry-in to
-// the CTA enters its thread 0 and passes every thread whose prefix is all
-// ones).  S = 1 is the plain CTA-wide scan.  Every thread of the cluster.
-__device__ uint32_t cluster_carry_in(uint32_t g, uint32_t p, uint32_t rank, uint32_t S, uint32_t *flags,
-                                     uint32_t *xflag) {
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const RowFlags f{__ballot_sync(FULL_MASK, g), __ballot_sync(FULL_MASK, p)};
-    uint32_t wc;
-    row_carries(f, 0, wc);
-    if (lane == 0) flags[warp] = wc | ((f.P == FULL_MASK) << 1);
-    __syncthreads();
-    const uint32_t sw = lane < nw ? flags[lane] : 2u;  // missing warps pass a carry through
-    const RowFlags fw{__ballot_sync(FULL_MASK, sw & 1u), __ballot_sync(FULL_MASK, (sw >> 1) & 1u)};
-    uint32_t cin = 0, unused;
-    if (S > 1) {
-        uint32_t blk_g;
-        row_carries(fw, 0, blk_g);
-        if (threadIdx.x == 0) *xflag = blk_g | ((fw.P == FULL_MASK) << 1);
-        cluster_sync();
-        for (uint32_t q = 0; q < rank; ++q) {
-            const uint32_t x = ld_dsmem_u32(dsmem_addr(xflag, q));
-            cin = (x & 1u) | ((x >> 1) & cin);
-        }
-    }
-    const uint32_t wcin = (row_carries(fw, cin, unused) >> warp) & 1u;
-    return (row_carries(f, wcin, unused) >> lane) & 1u;
-}
-
-// n6 for the limbs [rank*part, rank*part + part) of the product (clipped to
-// nout): limb(k) gives the part of the product that starts in limb k.  Each
-// thread folds the limbs of its window, carrying inside the window; the
-// window's carry spills into the next window (the first window of a CTA
-// takes the last spill of the previous rank's CTA); the remaining one-bit
-// carries are resolved by cluster_carry_in.  Limbs are assembled in the
-// shared staging row out_s (limb k_lo + i at i + i/16: the windows fall in
-// distinct banks) and copied to crow.  Every thread of the cluster.
-template <class LimbFn>
-__device__ void normalize_part(uint32_t nout, uint32_t part, uint32_t rank, uint32_t S, uint32_t *crow,
-                               uint32_t *out_s, uint64_t *spill, uint32_t *flags, uint32_t *xflag,
-                               LimbFn &&limb) {
-    const uint32_t T = blockDim.x, t = threadIdx.x;
-    const uint32_t k_lo = rank * part < nout ? rank * part : nout;
-    const uint32_t k_hi = k_lo + part < nout ? k_lo + part : nout;
-    uint32_t QN = (part + T - 1) / T;
+// n6 for a product split over a cluster of NC CTAs.  Its limbs fall into
+// NQ*NC segments of `seg` limbs, in limb order sigma = q NC + r; CTA r holds
+// segments q = 0 .. NQ-1 (its positions of every output quarter q), and
+// thread group q (T/NQ threads) of the CTA normalises segment q: limb(q, k)
+// gives the part of the product that starts in limb k.  Each thread folds
+// the limbs of its window, carrying inside the window; the window's carry
+// spills into the next window (the first window of a segment takes the last
+// spill of segment sigma - 1, from another CTA); the one-bit carries left are
+// resolved by the Section 2 carry scan over the group's threads, then over
+// the segments in limb order (one warp scans all segments' (g, p) pairs,
+// read from every CTA).  Each segment is staged in out_s (segment q at
+// q (seg + seg/16 + 1), limb i at i + i/16) and copied to crow.  Every
+// thread of the cluster.
+template <uint32_t NC, uint32_t NQ, class LimbFn>
+__device__ void normalize_segments(uint32_t nout, uint32_t seg, uint32_t rank, uint32_t *crow, uint32_t *out_s,
+                                   uint64_t *spill, uint32_t *flags, uint32_t *xflag, LimbFn &&limb) {
+    static_assert(NC * NQ <= 32 && NQ <= kMaxSplit, "one warp scans the segments");
+    const uint32_t T = blockDim.x, t = threadIdx.x, G = T / NQ;
+    const uint32_t q = t / G, i = t - q * G;  // group (segment) and thread within it
+    const uint32_t lane = t & 31, warp = t >> 5, wpg = G >> 5, wig = warp - q * wpg;
+    const uint32_t s_lo = (q * NC + rank) * seg;
+    const uint32_t k_lo = s_lo < nout ? s_lo : nout;
+    const uint32_t k_hi = s_lo + seg < nout ? s_lo + seg : nout;
+    uint32_t *stage = out_s + q * (seg + seg / 16 + 1);
+    uint32_t QN = (seg + G - 1) / G;
     if (QN < 2) QN = 2;  // a window must absorb a two-word spill
-    const uint32_t k0 = k_lo + t * QN < k_hi ? k_lo + t * QN : k_hi;
+    const uint32_t k0 = k_lo + i * QN < k_hi ? k_lo + i * QN : k_hi;
     const uint32_t k1 = k0 + QN < k_hi ? k0 + QN : k_hi;
     u128 carry = 0;
     for (uint32_t k = k0; k < k1; ++k) {
-        const u128 v = limb(k) + carry;
-        out_s[stage_index(k - k_lo)] = (uint32_t)v;
+        const u128 v = limb(q, k) + carry;
+        stage[stage_index(k - k_lo)] = (uint32_t)v;
         carry = v >> 32;
     }
     spill[t] = (uint64_t)carry;  // < 2^64: the coefficients are below 2^96
-    __syncthreads();
-    if (S > 1) cluster_sync();
-    uint64_t c = t > 0 ? spill[t - 1] : (rank > 0 ? ld_dsmem_u64(dsmem_addr(spill + T - 1, rank - 1)) : 0);
+    cluster_sync();
+    uint64_t c = 0;
+    if (i > 0) c = spill[t - 1];
+    else if (rank > 0) c = ld_dsmem_u64(dsmem_addr(spill + q * G + G - 1, rank - 1));
+    else if (q > 0) c = ld_dsmem_u64(dsmem_addr(spill + (q - 1) * G + G - 1, NC - 1));
     uint32_t all = 0xffffffffu;
     for (uint32_t k = k0; k < k1; ++k) {
-        const uint64_t v = (uint64_t)out_s[stage_index(k - k_lo)] + (c & 0xffffffffu);
-        out_s[stage_index(k - k_lo)] = (uint32_t)v;
+        const uint64_t v = (uint64_t)stage[stage_index(k - k_lo)] + (c & 0xffffffffu);
+        stage[stage_index(k - k_lo)] = (uint32_t)v;
         c = (c >> 32) + (v >> 32);
         all &= (uint32_t)v;
     }
     const bool owns = k0 < k1;
-    const uint32_t cin = cluster_carry_in(owns && c != 0, owns && all == 0xffffffffu, rank, S, flags, xflag);
+    // Carry scan: warps, then the group's warps, then the segments.
+    const RowFlags f{__ballot_sync(FULL_MASK, owns && c != 0), __ballot_sync(FULL_MASK, owns && all == 0xffffffffu)};
+    uint32_t wc, unused;
+    row_carries(f, 0, wc);
+    if (lane == 0) flags[warp] = wc | ((f.P == FULL_MASK) << 1);
+    __syncthreads();
+    const uint32_t sw = lane < wpg ? flags[q * wpg + lane] : 2u;  // lanes past the group pass a carry through
+    const RowFlags fw{__ballot_sync(FULL_MASK, sw & 1u), __ballot_sync(FULL_MASK, (sw >> 1) & 1u)};
+    if (wig == 0 && lane == 0) {
+        uint32_t gg;
+        row_carries(fw, 0, gg);
+        xflag[q] = gg | ((fw.P == FULL_MASK) << 1);
+    }
+    cluster_sync();
+    if (warp == 0) {  // lane sigma: segment sigma's pair, from CTA sigma mod NC
+        const uint32_t x = lane < NC * NQ ? ld_dsmem_u32(dsmem_addr(xflag + lane / NC, lane % NC)) : 2u;
+        const RowFlags fs{__ballot_sync(FULL_MASK, x & 1u), __ballot_sync(FULL_MASK, (x >> 1) & 1u)};
+        const uint32_t into = row_carries(fs, 0, unused);  // bit sigma: the carry into segment sigma
+        if (lane < NQ) xflag[NQ + lane] = (into >> (lane * NC + rank)) & 1u;
+    }
+    __syncthreads();
+    const uint32_t wcin = (row_carries(fw, xflag[NQ + q], unused) >> wig) & 1u;
+    const uint32_t cin = (row_carries(f, wcin, unused) >> lane) & 1u;
     if (cin)
         for (uint32_t k = k0; k < k1; ++k)
-            if (++out_s[stage_index(k - k_lo)] != 0) break;
+            if (++stage[stage_index(k - k_lo)] != 0) break;
     __syncthreads();
-    for (uint32_t x = k_lo + t; x < k_hi; x += T) st_stream(crow + x, out_s[stage_index(x - k_lo)]);
-    __syncthreads();
+    for (uint32_t x = k_lo + i; x < k_hi; x += G) st_stream(crow + x, stage[stage_index(x - k_lo)]);
 }
 
-// One product by a CTA (S = 1) or a cluster of S CTAs (this one of rank
+// One product by a CTA (S = 1) or a cluster of two CTAs (this one of rank
 // `rank`).  zk: where the first prime's coefficients go (two primes).
 //
-// In a cluster, CTA r first gathers its coefficients rL .. rL + L - 1 into
-// its own A (thread-consecutive positions, so each warp reads whole runs of
-// the other CTAs' buffers); two primes: the first prime's into A, then
-// Garner's v into its Z.  Only then is it normalised, from local memory,
-// with B (no longer read by any CTA) as the staging row.
+// In a cluster, CTA r owns the positions j in [rL/2, (r+1)L/2) of every
+// output quarter: it reads z_s[j] of all S sub-problems once (thread-
+// consecutive j, so each warp reads whole runs of both CTAs' buffers),
+// evaluates the last radix-S stage for all quarters into its own A; 16-bit
+// digits: as limb values c[j] + c[j+1] 2^16 (quarter q at q L/4); two primes:
+// the first prime's coefficients (quarter q at q L/2), then Garner's v into
+// its Z.  Only then is it normalised, from local memory, with B (no longer
+// read by the other CTA) as the staging row.
 template <bool CRT, uint32_t S>
 __device__ void pair_product(const NttArgs &p, const uint32_t *arow, const uint32_t *brow, uint32_t *crow,
                              const Smem64 &s, uint64_t *zk, uint32_t rank) {
+    constexpr uint32_t C = cluster_of(S), SP = S / C;  // CTAs, sub-problems per CTA
     if constexpr (CRT) {
-        sub_product<FieldP1, S>(p, p.t1, arow, brow, rank, s.A, s.B, zk);
-        sub_product<FieldP2, S>(p, p.t2, arow, brow, rank, s.A, s.B, s.B);
+        static_assert(SP == 1, "two primes split at most in two");
+        sub_product<FieldP1, S, false>(p, p.t1, arow, brow, rank, s.A, s.B, zk);
+        sub_product<FieldP2, S, false>(p, p.t2, arow, brow, rank, s.A, s.B, s.B);
+    } else if constexpr (SP == 2) {
+        sub_product<FieldP1, S, true>(p, p.t1, arow, brow, 2 * rank, s.A, s.B, s.Z);
+        sub_product<FieldP1, S, true>(p, p.t1, arow, brow, 2 * rank + 1, s.A, s.B, s.B);
     } else {
-        sub_product<FieldP1, S>(p, p.t1, arow, brow, rank, s.A, s.B, s.B);
+        sub_product<FieldP1, S, true>(p, p.t1, arow, brow, rank, s.A, s.B, s.B);
     }
-    const uint32_t r = rank;
-    // c1 / v: the (first prime's) coefficients and Garner's v of this CTA's
-    // part, in padded layout; out_s: the staging row.
-    const uint64_t *c1 = CRT ? zk : s.B;
-    const uint64_t *gv = s.B;
-    uint32_t *out_s = reinterpret_cast<uint32_t *>(s.A);
-    if constexpr (S > 1) {
+    if constexpr (S == 1) {
+        uint32_t *out_s = reinterpret_cast<uint32_t *>(s.A);
+        if constexpr (!CRT) {
+            // 16-bit digits: limb k holds coefficients 2k and 2k + 1 (< 2^46 + 2^62).
+            normalize_limbs(p.nout, crow, out_s, s.spill, s.flags, [&](uint32_t k) {
+                return (u128)(s.B[phys(2 * k)] + (s.B[phys(2 * k + 1)] << 16));
+            });
+        } else {
+            normalize_limbs(p.nout, crow, out_s, s.spill, s.flags, [&](uint32_t k) {
+                const uint64_t r1 = zk[phys(k)];
+                return (u128)r1 + (u128)garner_v(p, r1, s.B[phys(k)]) * FieldP1::P_VALUE;
+            });
+            if (!p.z_smem) discard_scratch(zk, buf_words(p.L));  // consumed
+        }
+        return;
+    } else {
+        const uint32_t Q = p.L / C, j0 = rank * Q;  // this CTA's positions
         cluster_sync();  // every sub-problem's result is in place
         if constexpr (!CRT) {
-            const Remote zb = remote(s.B, S);
+            // sub-problem s: in CTA s / SP, in Z for the first of two, else in B
+            Remote zb;
+#pragma unroll
+            for (uint32_t t = 0; t < S; ++t)
+                zb.base[t] = dsmem_addr(SP == 2 && t % 2 == 0 ? s.Z : s.B, t / SP);
 #pragma unroll 2
-            for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x)
-                s.A[phys(j)] = coefficient<FieldP1, S>(p.t1, zb, r, j);
+            for (uint32_t h = threadIdx.x; h < Q / 2; h += blockDim.x) {
+                uint64_t c0[S], c1[S];
+                combine<FieldP1, S>(p.t1, zb, j0 + 2 * h, c0);
+                combine<FieldP1, S>(p.t1, zb, j0 + 2 * h + 1, c1);
+#pragma unroll
+                for (uint32_t q = 0; q < S; ++q) s.A[phys(q * (Q / 2) + h)] = c0[q] + (c1[q] << 16);
+            }
         } else {
             const Remote z1 = remote(zk, S), z2 = remote(s.B, S);
-#pragma unroll 2
-            for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x)
-                s.A[phys(j)] = coefficient<FieldP1, S>(p.t1, z1, r, j);
-            cluster_sync();  // no CTA reads Z any more: it takes Garner's v
-#pragma unroll 2
-            for (uint32_t j = threadIdx.x; j < p.L; j += blockDim.x)
-                zk[phys(j)] = garner_v(p, s.A[phys(j)], coefficient<FieldP2, S>(p.t2, z2, r, j));
+            for (uint32_t j = threadIdx.x; j < Q; j += blockDim.x) {
+                uint64_t c[S];
+                combine<FieldP1, S>(p.t1, z1, j0 + j, c);
+#pragma unroll
+                for (uint32_t q = 0; q < S; ++q) s.A[phys(q * Q + j)] = c[q];
+            }
+            cluster_sync();  // the other CTA reads Z no more: it takes Garner's v
+            for (uint32_t j = threadIdx.x; j < Q; j += blockDim.x) {
+                uint64_t c[S];
+                combine<FieldP2, S>(p.t2, z2, j0 + j, c);
+#pragma unroll
+                for (uint32_t q = 0; q < S; ++q) zk[phys(q * Q + j)] = garner_v(p, s.A[phys(q * Q + j)], c[q]);
+            }
         }
-        cluster_sync();  // no CTA reads B any more: it becomes the staging row
-        c1 = s.A;
-        gv = zk;
-        out_s = reinterpret_cast<uint32_t *>(s.B);
+        cluster_sync();  // the other CTA reads B no more: it becomes the staging row
+        uint32_t *out_s = reinterpret_cast<uint32_t *>(s.B);
+        const uint64_t *c1 = s.A, *gv = zk;
+        if constexpr (!CRT) {
+            // limb k of segment (q, rank) starts at A[q Q/2 + k - its first limb]
+            normalize_segments<C, S>(p.nout, Q / 2, rank, crow, out_s, s.spill, s.flags, s.xflag,
+                                     [&](uint32_t q, uint32_t k) {
+                                         return (u128)c1[phys(q * (Q / 2) + k - (q * C + rank) * (Q / 2))];
+                                     });
+        } else {
+            normalize_segments<C, S>(p.nout, Q, rank, crow, out_s, s.spill, s.flags, s.xflag,
+                                     [&](uint32_t q, uint32_t k) {
+                                         const uint32_t x = q * Q + k - (q * C + rank) * Q;
+                                         return (u128)c1[phys(x)] + (u128)gv[phys(x)] * FieldP1::P_VALUE;
+                                     });
+        }
+        cluster_sync();  // no CTA reuses its buffers while the other may read them
     }
-    const uint32_t base = r * p.L;
-    if constexpr (!CRT) {
-        // 16-bit digits: limb k holds coefficients 2k and 2k + 1 (< 2^46 + 2^62).
-        const uint32_t part = S > 1 ? p.L / 2 : p.nout;
-        normalize_part(p.nout, part, r, S, crow, out_s, s.spill, s.flags, s.xflag, [&](uint32_t k) {
-            const uint32_t j = 2 * k - base;
-            return (u128)(c1[phys(j)] + (c1[phys(j + 1)] << 16));
-        });
-    } else {
-        const uint32_t part = S > 1 ? p.L : p.nout;
-        normalize_part(p.nout, part, r, S, crow, out_s, s.spill, s.flags, s.xflag, [&](uint32_t k) {
-            const uint32_t j = k - base;
-            const uint64_t r1 = c1[phys(j)];
-            const uint64_t v = S > 1 ? gv[phys(j)] : garner_v(p, r1, s.B[phys(j)]);
-            return (u128)r1 + (u128)v * FieldP1::P_VALUE;
-        });
-        if (!p.zk_smem) discard_scratch(zk, buf_words(p.L));  // consumed
-    }
-    if constexpr (S > 1) cluster_sync();  // no CTA reuses its buffers while another may read them
 }
 
 template <bool CRT>
 __device__ __forceinline__ uint64_t *zk_slot(const NttArgs &p, const Smem64 &s) {
     if constexpr (!CRT) return nullptr;
-    return p.zk_smem ? s.Z : p.scratch + blockIdx.x * p.scratch_stride;
+    return p.z_smem ? s.Z : p.scratch + blockIdx.x * p.scratch_stride;
 }
 
 template <bool CRT, uint32_t S>
 __global__ void __launch_bounds__(1024) k_mul_ntt(NttArgs p) {
     extern __shared__ __align__(16) uint64_t sm64[];
-    const Smem64 s = smem64<CRT>(p, sm64);
+    const Smem64 s = smem64(p, sm64);
     uint64_t *zk = zk_slot<CRT>(p, s);
-    constexpr bool cl = S > 1;
+    constexpr bool cl = S > 1;  // a cluster of cluster_of(S) CTAs per product
     const uint32_t rank = cl ? cluster_rank() : 0u;
     const uint64_t first = cl ? cluster_index() : blockIdx.x, stride = cl ? cluster_count() : gridDim.x;
     for (uint64_t inst = first; inst < p.batch; inst += stride)
@@ -571,7 +647,7 @@ __global__ void __launch_bounds__(1024)
     k_mul_ntt_batch(NttArgs p, const BatchItem *items, uint32_t count, uint32_t *queue,
                     const BatchBinding *bind) {
     extern __shared__ __align__(16) uint64_t sm64[];
-    const Smem64 s = smem64<CRT>(p, sm64);
+    const Smem64 s = smem64(p, sm64);
     uint64_t *zk = zk_slot<CRT>(p, s);
     constexpr bool cl = S > 1;
     const uint32_t rank = cl ? cluster_rank() : 0u;
@@ -723,8 +799,8 @@ BatchKernel batch_kernel(bool crt, uint32_t S) {
     return S == 1 ? k_mul_ntt_batch<false, 1> : (S == 2 ? k_mul_ntt_batch<false, 2> : k_mul_ntt_batch<false, 4>);
 }
 
-// Largest co-resident grid of the plain kernel for the geometry (a multiple
-// of S); 0 if it does not fit.
+// Largest co-resident grid of the plain kernel for the geometry (whole
+// clusters); 0 if it does not fit.
 cudaError_t max_grid_of(const void *kern, const Geometry &g, uint32_t smem, int sms, uint32_t *grid) {
     *grid = 0;
     if (g.S == 1) {
@@ -735,22 +811,23 @@ cudaError_t max_grid_of(const void *kern, const Geometry &g, uint32_t smem, int 
     }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
+    const uint32_t C = cluster_of(g.S);
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = g.S;
+    attr[0].val.clusterDim.x = C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(g.S * (uint32_t)sms, 1, 1);
+    cfg.gridDim = dim3(C * (uint32_t)sms, 1, 1);
     cfg.blockDim = dim3(g.T, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
     const cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
-    if (e == cudaSuccess) *grid = (uint32_t)clusters * g.S;
+    if (e == cudaSuccess) *grid = (uint32_t)clusters * C;
     return e;
 }
 
-// Launch with a cluster of S CTAs when S > 1.
+// Launch with clusters of cluster_of(S) CTAs when S > 1.
 template <class... Args>
 cudaError_t launch(void (*kern)(Args...), uint32_t grid, uint32_t threads, uint32_t smem, uint32_t S,
                    cudaStream_t st, Args... args) {
@@ -762,7 +839,7 @@ cudaError_t launch(void (*kern)(Args...), uint32_t grid, uint32_t threads, uint3
     cfg.stream = st;
     if (S > 1) {
         attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = S;
+        attr[0].val.clusterDim.x = cluster_of(S);
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
@@ -776,7 +853,7 @@ cudaError_t launch(void (*kern)(Args...), uint32_t grid, uint32_t threads, uint3
 struct NttPlan {
     bool crt = false;
     uint32_t na = 0, nb = 0, nout = 0, N = 0, L = 0, logL = 0, S = 1, threads = 0;
-    uint32_t smem = 0, max_grid = 0, zk_smem = 0;
+    uint32_t smem = 0, max_grid = 0, z_smem = 0;
     uint64_t scratch_stride = 0;
     size_t scratch_bytes = 0;
     void *dev = nullptr;          // tables followed by scratch
@@ -814,23 +891,24 @@ bn_status ntt_create(NttPlan **out, bool crt, uint32_t na, uint32_t nb, const bn
     int dev = 0, sms = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // Two primes: the first prime's coefficients stay in shared memory when a
-    // third buffer costs no occupancy (and always in a cluster).
+    // A third shared buffer: for S = 4 (two sub-problems per CTA); for two
+    // primes in a cluster, and for one-CTA two-prime products when it costs
+    // no occupancy (else the first prime's coefficients go to scratch).
     uint32_t grid2 = 0, grid3 = 0;
     if (e == cudaSuccess) e = max_grid_of(kern, g, smem_bytes(g.L, 2, g.T), sms, &grid2);
-    if (e == cudaSuccess && crt) e = max_grid_of(kern, g, smem_bytes(g.L, 3, g.T), sms, &grid3);
+    if (e == cudaSuccess) e = max_grid_of(kern, g, smem_bytes(g.L, 3, g.T), sms, &grid3);
     if (e != cudaSuccess) {
         delete p;
         return BN_ECUDA;
     }
-    p->zk_smem = crt && (g.S > 1 || grid3 >= grid2) ? 1u : 0u;
-    p->smem = smem_bytes(g.L, p->zk_smem ? 3 : 2, g.T);
-    p->max_grid = p->zk_smem ? grid3 : grid2;
+    p->z_smem = (g.S == 4 || (crt && (g.S > 1 || grid3 >= grid2))) ? 1u : 0u;
+    p->smem = smem_bytes(g.L, p->z_smem ? 3 : 2, g.T);
+    p->max_grid = p->z_smem ? grid3 : grid2;
     if (p->max_grid == 0) {
         delete p;
         return BN_EUNSUPPORTED;
     }
-    p->scratch_stride = crt && !p->zk_smem ? buf_words(g.L) : 0;
+    p->scratch_stride = crt && !p->z_smem ? buf_words(g.L) : 0;
 
     // Tables for each prime, then scratch, in one allocation.
     std::vector<HostTables> tabs;
@@ -901,7 +979,7 @@ NttArgs plan_args(const NttPlan *p) {
     args.logL = p->logL;
     args.S = p->S;
     args.digit_bits = p->crt ? 32 : 16;
-    args.zk_smem = p->zk_smem;
+    args.z_smem = p->z_smem;
     args.scratch = p->scratch;
     args.scratch_stride = p->scratch_stride;
     args.garner = p->garner;
@@ -912,7 +990,7 @@ NttArgs plan_args(const NttPlan *p) {
 
 // Grid for `units` products: persistent, at most max_grid CTAs, whole clusters.
 uint32_t grid_for(const NttPlan *p, uint64_t units) {
-    const uint64_t ctas = units * p->S;
+    const uint64_t ctas = units * cluster_of(p->S);
     return (uint32_t)(ctas < p->max_grid ? ctas : p->max_grid);
 }
 
@@ -940,7 +1018,7 @@ cudaError_t ntt_launch_sized(NttPlan *p, uint32_t na, uint32_t nb, const uint32_
     args.nb = nb;
     args.nout = na + nb;
     args.batch = 1;
-    return launch(plain_kernel(p->crt, p->S), p->S, p->threads, p->smem, p->S, st, args);
+    return launch(plain_kernel(p->crt, p->S), cluster_of(p->S), p->threads, p->smem, p->S, st, args);
 }
 
 bn_status ntt_batch_plan(NttPlan **out, bool crt, uint32_t N) {
@@ -1131,9 +1209,9 @@ extern "C" bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, ui
     // product go to the scratch array unless the transform is split.
     const Geometry g = geometry(crt, na, nb, 0);
     const PlainKernel kern = plain_kernel(crt, g.S);
-    const uint32_t zk_smem = crt && g.S > 1 ? 1u : 0u;
-    const uint32_t smem = smem_bytes(g.L, zk_smem ? 3 : 2, g.T);
-    const uint64_t stride = crt && !zk_smem ? buf_words(g.L) : 0;
+    const uint32_t z_smem = g.S == 4 || (crt && g.S > 1) ? 1u : 0u;
+    const uint32_t smem = smem_bytes(g.L, z_smem ? 3 : 2, g.T);
+    const uint64_t stride = crt && !z_smem ? buf_words(g.L) : 0;
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1216,14 +1294,14 @@ extern "C" bn_status bn_mul_ntt_noalloc(const uint32_t *a, const uint32_t *b, ui
     args.logL = g.logL;
     args.S = g.S;
     args.digit_bits = crt ? 32 : 16;
-    args.zk_smem = zk_smem;
+    args.z_smem = z_smem;
     args.batch = batch;
     args.scratch = d.scratch;
     args.scratch_stride = stride;
     args.garner = shoup_pair(hinv(field_p1().p % field_p2().p, field_p2().p), field_p2().p);
     args.t1 = c1.tab;
     args.t2 = c2.tab;
-    const uint64_t ctas = batch * g.S;
+    const uint64_t ctas = batch * cluster_of(g.S);
     const uint32_t grid = (uint32_t)(ctas < max_grid ? ctas : max_grid);
     e = launch(kern, grid, g.T, smem, g.S, st, args);
     if (e != cudaSuccess) {

@@ -13,6 +13,8 @@
 // below 2P, and whatever range the inverse passes end in, the field's final
 // scaling maps it back.
 #pragma once
+#include <type_traits>
+
 #include "bn_device.cuh"
 
 namespace bn {
@@ -274,8 +276,15 @@ __host__ __device__ constexpr uint32_t pidx_c(uint32_t i) {
 // STEP*E/2 .. STEP (decimation in frequency), else STEP .. STEP*E/2
 // (decimation in time).  UNIT (STEP = 1): the trivial stage has twiddle 1, and
 // so has element 0 of every group in the other stages.
-template <class F, int KK, bool UNIT, uint32_t STEP, uint32_t L, uint32_t NT, bool DIF>
-__device__ __forceinline__ void pass_c(typename F::Elem *buf, const typename F::Tw *tw) {
+// A pass's epilogue: epi(i, x) is stored at logical index i instead of x
+// (the last inverse pass folds a final scaling in this way).
+struct NoEpi {
+    template <class T>
+    __device__ __forceinline__ T operator()(uint32_t, T x) const { return x; }
+};
+
+template <class F, int KK, bool UNIT, uint32_t STEP, uint32_t L, uint32_t NT, bool DIF, class Epi = NoEpi>
+__device__ __forceinline__ void pass_c(typename F::Elem *buf, const typename F::Tw *tw, const Epi &epi = Epi{}) {
     using T = typename F::Elem;
     using W = typename F::Tw;
     constexpr int E = 1 << KK;
@@ -316,6 +325,10 @@ __device__ __forceinline__ void pass_c(typename F::Elem *buf, const typename F::
                     else F::dit(x[m], x[m + hm], w[m & (hm - 1)]);
                 }
             }
+        }
+        if constexpr (!std::is_same<Epi, NoEpi>::value) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) x[m] = epi(base + m * STEP, x[m]);
         }
         if constexpr (UNIT) {
             store_run<T, E>(buf, base, x);
@@ -361,26 +374,32 @@ __device__ void forward2_c(const typename F::Tw *tw, typename F::Elem *A, typena
     __syncthreads();
 }
 
-template <class F, uint32_t L, uint32_t NT, uint32_t H0, uint32_t LEFT>
-__device__ __forceinline__ void dit_rest_c(typename F::Elem *B, const typename F::Tw *tw) {
-    if constexpr (LEFT >= 3) {
+template <class F, uint32_t L, uint32_t NT, uint32_t H0, uint32_t LEFT, class Epi>
+__device__ __forceinline__ void dit_rest_c(typename F::Elem *B, const typename F::Tw *tw, const Epi &epi) {
+    if constexpr (LEFT > 3) {
         pass_c<F, 3, false, H0, L, NT, false>(B, tw);
         __syncthreads();
-        dit_rest_c<F, L, NT, H0 * 8, LEFT - 3>(B, tw);
+        dit_rest_c<F, L, NT, H0 * 8, LEFT - 3>(B, tw, epi);
     } else if constexpr (LEFT > 0) {
-        pass_c<F, (int)LEFT, false, H0, L, NT, false>(B, tw);
+        pass_c<F, (int)LEFT, false, H0, L, NT, false>(B, tw, epi);
         __syncthreads();
     }
 }
 
-// Unscaled inverse transform of B of length 2^LOGL; ends with a barrier.
-template <class F, uint32_t LOGL, uint32_t NT>
-__device__ void inverse_c(const typename F::Tw *tw, typename F::Elem *B) {
+// Inverse transform of B of length 2^LOGL, unscaled, or with the last
+// pass's outputs passed through epi; ends with a barrier.
+template <class F, uint32_t LOGL, uint32_t NT, class Epi = NoEpi>
+__device__ void inverse_c(const typename F::Tw *tw, typename F::Elem *B, const Epi &epi = Epi{}) {
     constexpr uint32_t L = 1u << LOGL;
     constexpr uint32_t first = LOGL >= 3 ? 3 : LOGL;
-    pass_c<F, (int)first, true, 1, L, NT, false>(B, tw);
-    __syncthreads();
-    dit_rest_c<F, L, NT, (1u << first), LOGL - first>(B, tw);
+    if constexpr (LOGL == first) {
+        pass_c<F, (int)first, true, 1, L, NT, false>(B, tw, epi);
+        __syncthreads();
+    } else {
+        pass_c<F, (int)first, true, 1, L, NT, false>(B, tw);
+        __syncthreads();
+        dit_rest_c<F, L, NT, (1u << first), LOGL - first>(B, tw, epi);
+    }
 }
 
 // Normalisation (Section 4.2's splitFftReg/baddRegMul2Fft, with whole
