@@ -408,6 +408,23 @@ const char *bn_last_error(void);
 /* Library version as 10000*major + 100*minor + patch. */
 int bn_version(void);
 
+/* ---- debug build -----------------------------------------------------------
+ * The library also builds as a debug variant (compiled with BN_DEBUG) in
+ * which the kernels check what a correct run never sees, without trapping:
+ * a word of a product at or beyond na + nb that is not zero, or a carry
+ * leaving the product (the exact product has na + nb limbs, Section 3.2,
+ * Fig. 5; BN_DEBUG_SPILL), and a shared-memory index outside its region
+ * (BN_DEBUG_INDEX).  Schoolbook, tensor-core schoolbook and transform
+ * products are checked.
+ * bn_debug_word synchronises the device and returns the OR of the bits set
+ * since the last call, clearing them; ~0u if the synchronisation failed.
+ * The regular build compiles the checks out and always returns 0.
+ * bn_debug_build returns 1 in the debug build, 0 otherwise. */
+#define BN_DEBUG_SPILL 1u
+#define BN_DEBUG_INDEX 2u
+uint32_t bn_debug_word(void);
+int bn_debug_build(void);
+
 #ifdef __cplusplus
 }
 #endif

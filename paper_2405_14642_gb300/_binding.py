@@ -110,6 +110,8 @@ def load(build_if_missing: bool = False):
         "bn_status_str": ([ctypes.c_int], ctypes.c_char_p),
         "bn_last_error": ([], ctypes.c_char_p),
         "bn_version": ([], ctypes.c_int),
+        "bn_debug_word": ([], ctypes.c_uint32),
+        "bn_debug_build": ([], ctypes.c_int),
         "bn_mul_ntt_noalloc": ([u32p, u32p, u32p, u32, u32, u64, ctypes.c_int, vp], st),
         "bn_mul_low": ([u32p, u32p, u32p, u32, u64, vp], st),
         "bn_poly": ([u32p, u32p, u32p, u32, u64, vp], st),

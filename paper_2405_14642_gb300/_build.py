@@ -1,9 +1,12 @@
-"""Builds the CUDA library ``_lib/libbn_gb300.so`` for sm_103a with nvcc.
+"""Builds the CUDA library ``_lib/libbn_gb300.so`` for sm_103a with nvcc, and
+its debug variant ``_lib/libbn_gb300_debug.so`` (compiled with BN_DEBUG: the
+kernels' spill, carry and index checks, read through bn_debug_word).
 
-Each ``csrc/*.cu`` translation unit compiles in parallel; the objects are
-linked into one shared library exporting the C ABI of ``include/bn.h``.
-A stamp records the host architecture and a hash of the sources and flags,
-so a copy of the tree moved to another machine rebuilds itself.
+Each ``csrc/*.cu`` translation unit compiles in parallel (both variants in
+one pool); the objects are linked into one shared library per variant,
+exporting the C ABI of ``include/bn.h``.  A stamp records the host
+architecture and a hash of the sources and flags, so a copy of the tree
+moved to another machine rebuilds itself.
 """
 from __future__ import annotations
 
@@ -21,6 +24,8 @@ CSRC = PKG / "csrc"
 LIB_DIR = PKG / "_lib"
 OBJ_DIR = ROOT / "_build" / "bn"
 LIB_NAME = "libbn_gb300.so"
+DEBUG_LIB_NAME = "libbn_gb300_debug.so"
+DEBUG_FLAGS = ["-DBN_DEBUG"]
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 
@@ -40,10 +45,10 @@ def sources():
     return sorted(CSRC.glob("*.cu"))
 
 
-def _stamp() -> str:
+def _stamp(debug: bool = False) -> str:
     h = hashlib.sha256()
     h.update(platform.machine().encode())
-    h.update(" ".join(ARCH_FLAGS + NVCC_FLAGS).encode())
+    h.update(" ".join(ARCH_FLAGS + NVCC_FLAGS + (DEBUG_FLAGS if debug else [])).encode())
     for f in sorted(list(CSRC.glob("*")) + [ROOT / "include" / "bn.h"]):
         if f.is_file():
             h.update(f.name.encode())
@@ -51,49 +56,64 @@ def _stamp() -> str:
     return h.hexdigest()
 
 
-def library_path() -> Path:
-    return LIB_DIR / LIB_NAME
+def library_path(debug: bool = False) -> Path:
+    return LIB_DIR / (DEBUG_LIB_NAME if debug else LIB_NAME)
 
 
-def is_current() -> bool:
-    stamp = LIB_DIR / "stamp.txt"
-    return library_path().exists() and stamp.exists() and stamp.read_text() == _stamp()
+def _stamp_path(debug: bool) -> Path:
+    return LIB_DIR / ("stamp_debug.txt" if debug else "stamp.txt")
 
 
-def build(force: bool = False, verbose: bool = False) -> Path:
-    """Compile and link the library if it is missing or stale; return its path."""
-    if not force and is_current():
-        return library_path()
-    nvcc = nvcc_path()
-    OBJ_DIR.mkdir(parents=True, exist_ok=True)
-    LIB_DIR.mkdir(parents=True, exist_ok=True)
+def is_current(debug: bool = False) -> bool:
+    stamp = _stamp_path(debug)
+    return library_path(debug).exists() and stamp.exists() and stamp.read_text() == _stamp(debug)
 
-    def compile_one(src: Path) -> Path:
-        obj = OBJ_DIR / (src.stem + ".o")
-        cmd = [nvcc, *ARCH_FLAGS, *NVCC_FLAGS, "-c", str(src), "-o", str(obj)]
-        if verbose:
-            cmd.insert(1, "-Xptxas=-v")
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed on {src.name}:\n{r.stderr}")
-        if verbose and r.stderr:
-            print(r.stderr)
-        return obj
 
-    srcs = sources()
-    with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    out = library_path()
-    tmp = out.with_name(out.name + f".tmp{os.getpid()}")
-    libdir = cuda_lib_dir(nvcc)
-    cmd = [nvcc, *ARCH_FLAGS, "-shared", "-cudart", "shared", *map(str, objs), "-o", str(tmp),
-           "-Xlinker", f"-rpath,{libdir}"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, out)
-    (LIB_DIR / "stamp.txt").write_text(_stamp())
-    return out
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> Path:
+    """Compile and link the library (or its debug variant) if it is missing or
+    stale; return its path."""
+    return build_variants((debug,), force, verbose)[0]
+
+
+def build_variants(variants=(False, True), force: bool = False, verbose: bool = False):
+    """Compile the stale variants' translation units in one parallel pool,
+    link each; return the libraries' paths in the order asked."""
+    todo = [d for d in variants if force or not is_current(d)]
+    if todo:
+        nvcc = nvcc_path()
+        LIB_DIR.mkdir(parents=True, exist_ok=True)
+
+        def compile_one(job):
+            src, debug = job
+            odir = OBJ_DIR.with_name(OBJ_DIR.name + ("_debug" if debug else ""))
+            odir.mkdir(parents=True, exist_ok=True)
+            obj = odir / (src.stem + ".o")
+            cmd = [nvcc, *ARCH_FLAGS, *NVCC_FLAGS, *(DEBUG_FLAGS if debug else []), "-c", str(src),
+                   "-o", str(obj)]
+            if verbose:
+                cmd.insert(1, "-Xptxas=-v")
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"nvcc failed on {src.name}{' (debug)' if debug else ''}:\n{r.stderr}")
+            if verbose and r.stderr:
+                print(r.stderr)
+            return debug, obj
+
+        jobs = [(src, d) for d in todo for src in sources()]
+        with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+            objs = list(ex.map(compile_one, jobs))
+        libdir = cuda_lib_dir(nvcc)
+        for d in todo:
+            out = library_path(d)
+            tmp = out.with_name(out.name + f".tmp{os.getpid()}")
+            cmd = [nvcc, *ARCH_FLAGS, "-shared", "-cudart", "shared", *[str(o) for dd, o in objs if dd == d],
+                   "-o", str(tmp), "-Xlinker", f"-rpath,{libdir}"]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"link failed:\n{r.stderr}")
+            os.replace(tmp, out)
+            _stamp_path(d).write_text(_stamp(d))
+    return [library_path(d) for d in variants]
 
 
 if __name__ == "__main__":

@@ -407,4 +407,18 @@ const char *bn_last_error(void) { return g_last_error; }
 
 int bn_version(void) { return 100; }
 
+uint32_t bn_debug_word(void) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return ~0u;
+    return bn::debug_word_quad() | bn::debug_word_quad_tc() | bn::debug_word_ntt() |
+           bn::debug_word_ntt3_small() | bn::debug_word_ntt3_mid() | bn::debug_word_ntt3_large();
+}
+
+int bn_debug_build(void) {
+#ifdef BN_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 }  // extern "C"

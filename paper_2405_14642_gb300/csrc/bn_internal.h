@@ -17,6 +17,15 @@ cudaError_t allow_max_smem(const void *kernel);
 // Records `what` as this host thread's bn_last_error() text.
 void record_error(const char *what);
 
+// Debug build (-DBN_DEBUG): each kernel translation unit's check bits, read
+// and cleared (bn_debug.cuh); 0 in the regular build.
+uint32_t debug_word_quad();
+uint32_t debug_word_quad_tc();
+uint32_t debug_word_ntt();
+uint32_t debug_word_ntt3_small();
+uint32_t debug_word_ntt3_mid();
+uint32_t debug_word_ntt3_large();
+
 // ---- mixed-size batches ----------------------------------------------------
 // One operation of a batch: operands at the given limb offsets of the flat
 // a and b buffers, result at off_c of the flat c buffer.

@@ -497,6 +497,8 @@ __device__ void normalize_segments(uint32_t nout, uint32_t seg, uint32_t rank, u
         all &= (uint32_t)v;
     }
     const bool owns = k0 < k1;
+    BN_DEBUG_CHECK(!(owns && k1 == nout) || c == 0, kDbgSpill);  // nothing leaves the product
+    BN_DEBUG_CHECK(owns || c == 0, kDbgSpill);
     // Carry scan: warps, then the group's warps, then the segments.
     const RowFlags f{__ballot_sync(FULL_MASK, owns && c != 0), __ballot_sync(FULL_MASK, owns && all == 0xffffffffu)};
     uint32_t wc, unused;
@@ -520,6 +522,7 @@ __device__ void normalize_segments(uint32_t nout, uint32_t seg, uint32_t rank, u
     __syncthreads();
     const uint32_t wcin = (row_carries(fw, xflag[NQ + q], unused) >> wig) & 1u;
     const uint32_t cin = (row_carries(f, wcin, unused) >> lane) & 1u;
+    BN_DEBUG_CHECK(!(owns && k1 == nout && cin && all == 0xffffffffu), kDbgSpill);
     if (cin)
         for (uint32_t k = k0; k < k1; ++k)
             if (++stage[stage_index(k - k_lo)] != 0) break;
@@ -582,7 +585,10 @@ __device__ void pair_product(const NttArgs &p, const uint32_t *arow, const uint3
                 combine<FieldP1, S>(p.t1, zb, j0 + 2 * h, c0);
                 combine<FieldP1, S>(p.t1, zb, j0 + 2 * h + 1, c1);
 #pragma unroll
-                for (uint32_t q = 0; q < S; ++q) s.A[phys(q * (Q / 2) + h)] = c0[q] + (c1[q] << 16);
+                for (uint32_t q = 0; q < S; ++q) {
+                    BN_DEBUG_CHECK(phys(q * (Q / 2) + h) < buf_words(p.L), kDbgIndex);
+                    s.A[phys(q * (Q / 2) + h)] = c0[q] + (c1[q] << 16);
+                }
             }
         } else {
             const Remote z1 = remote(zk, S), z2 = remote(s.B, S);
@@ -616,7 +622,11 @@ __device__ void pair_product(const NttArgs &p, const uint32_t *arow, const uint3
                                          return (u128)c1[phys(x)] + (u128)gv[phys(x)] * FieldP1::P_VALUE;
                                      });
         }
-        cluster_sync();  // no CTA reuses its buffers while the other may read them
+        // No barrier here: the other CTA reads this one's B and Z only before
+        // the barrier above, and its spill and carry words only before it
+        // reaches the next product's first barrier, which this CTA must reach
+        // too before it writes them again.  The kernels hold a last barrier
+        // before exit.
     }
 }
 
@@ -636,6 +646,7 @@ __global__ void __launch_bounds__(1024) k_mul_ntt(NttArgs p) {
     const uint64_t first = cl ? cluster_index() : blockIdx.x, stride = cl ? cluster_count() : gridDim.x;
     for (uint64_t inst = first; inst < p.batch; inst += stride)
         pair_product<CRT, S>(p, p.a + inst * p.na, p.b + inst * p.nb, p.c + inst * p.nout, s, zk, rank);
+    if constexpr (cl) cluster_sync();  // no CTA exits while the other may read its shared memory
 }
 
 // Mixed-size batch of products that share the transform length N (and so
@@ -667,6 +678,7 @@ __global__ void __launch_bounds__(1024)
         q.batch = 1;
         pair_product<CRT, S>(q, bind->a + it.off_a, bind->b + it.off_b, bind->c + it.off_c, s, zk, rank);
     }
+    if constexpr (cl) cluster_sync();  // no CTA exits while the other may read its shared memory
 }
 
 // ---- host side: fields, tables, plan ----------------------------------------
@@ -849,6 +861,8 @@ cudaError_t launch(void (*kern)(Args...), uint32_t grid, uint32_t threads, uint3
 }
 
 }  // namespace
+
+BN_DEBUG_ACCESSOR(debug_word_ntt)
 
 struct NttPlan {
     bool crt = false;

@@ -4,6 +4,8 @@
 
 namespace bn {
 
+BN_DEBUG_ACCESSOR(debug_word_ntt3_large)
+
 ntt3::Kernels3 ntt3_kernels_large(uint32_t log_n) {
     switch (log_n) {
     case 13: return ntt3::kernels3<13>();

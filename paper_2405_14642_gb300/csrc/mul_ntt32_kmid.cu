@@ -4,6 +4,8 @@
 
 namespace bn {
 
+BN_DEBUG_ACCESSOR(debug_word_ntt3_mid)
+
 ntt3::Kernels3 ntt3_kernels_mid(uint32_t log_n) {
     switch (log_n) {
     case 11: return ntt3::kernels3<11>();

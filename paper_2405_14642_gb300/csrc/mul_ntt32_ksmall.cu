@@ -4,6 +4,8 @@
 
 namespace bn {
 
+BN_DEBUG_ACCESSOR(debug_word_ntt3_small)
+
 ntt3::Kernels3 ntt3_kernels_small(uint32_t log_n) {
     switch (log_n) {
     case 1: return ntt3::kernels3<1>();

@@ -89,12 +89,14 @@ __device__ __forceinline__ void quad_instance(const QuadArgs &p, uint64_t inst, 
             u = Unit{k0, k0 - p.nbp, R - r, k1, k1 - p.nbp, r + 1};
         }
         conv_unit<Q>(As, Bs, u, [&](uint32_t k, const uint32_t (&acc)[Q + 2]) {
+            BN_DEBUG_CHECK(k + Q <= p.nap + p.nbp && p.l_offset + phys(k + Q - 1) < p.hc_offset, kDbgIndex);
             st_words<Q>(Ls, k, acc);
             *reinterpret_cast<uint2 *>(Hc + 2 * (k / Q)) = make_uint2(acc[Q], acc[Q + 1]);
         });
     } else if (t < p.units) {
         uint32_t acc[Q + 2];
         auto publish = [&](uint32_t k) {
+            BN_DEBUG_CHECK(k + Q <= p.nap + p.nbp && p.l_offset + phys(k + Q - 1) < p.hc_offset, kDbgIndex);
             st_words<Q>(Ls, k, acc);
             *reinterpret_cast<uint2 *>(Hc + 2 * (k / Q)) = make_uint2(acc[Q], acc[Q + 1]);
         };
@@ -158,6 +160,14 @@ __device__ __forceinline__ void quad_instance(const QuadArgs &p, uint64_t inst, 
             carry = (uint32_t)(v >> 32);
         }
         st_words<W2>(Ls, base, s);
+        // The exact product has na + nb words: every word of L + H from there
+        // to its end nw is zero, and no carry leaves it (Fig. 5).  (When nw
+        // is an odd number of windows, the last thread's 2Q words run past nw
+        // into the spent H words of its own instance: those are not product
+        // words.)
+#pragma unroll
+        for (int q = 0; q < W2; ++q) BN_DEBUG_CHECK(base + q < p.nout || base + q >= nw || s[q] == 0, kDbgSpill);
+        BN_DEBUG_CHECK(base + W2 != nw || carry == 0, kDbgSpill);
     }
     __syncthreads();
     if (!live) return;
@@ -238,6 +248,8 @@ uint32_t default_q(uint32_t na, uint32_t nb) {
 }
 
 }  // namespace
+
+BN_DEBUG_ACCESSOR(debug_word_quad)
 
 bn_status quad_configure(QuadConfig &cfg, uint32_t na, uint32_t nb, const bn_tuning *t) {
     if (na == 0 || nb == 0) return BN_EINVAL;

@@ -636,6 +636,8 @@ TcGeometry geometry(uint32_t na, uint32_t nb) {
 
 }  // namespace
 
+BN_DEBUG_ACCESSOR(debug_word_quad_tc)
+
 struct QuadTcPlan {
     TcGeometry geo;
     uint32_t nout = 0, ctas = 0;

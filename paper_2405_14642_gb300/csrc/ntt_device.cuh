@@ -15,6 +15,7 @@
 #pragma once
 #include <type_traits>
 
+#include "bn_debug.cuh"
 #include "bn_device.cuh"
 
 namespace bn {
@@ -441,8 +442,13 @@ __device__ void normalize_limbs(uint32_t nout, uint32_t *crow, uint32_t *out_s, 
         all &= (uint32_t)v;
     }
     const bool owns = k0 < k1;
+    // nothing may spill past the product: not out of its top window, not into
+    // a thread with no limbs
+    BN_DEBUG_CHECK(!(owns && k1 == nout) || c == 0, kDbgSpill);
+    BN_DEBUG_CHECK(owns || c == 0, kDbgSpill);
     // (c) resolve the carries across windows (Section 2 carry scan)
     const uint32_t cin = group_carry_in(owns && c != 0, owns && all == 0xffffffffu, T, flags);
+    BN_DEBUG_CHECK(!(owns && k1 == nout && cin && all == 0xffffffffu), kDbgSpill);
     if (cin)
         for (uint32_t k = k0; k < k1; ++k)
             if (++out_s[stage_index(k)] != 0) break;

@@ -3,6 +3,7 @@
 // multiply-accumulate chains and the window loop.  See mul_quad.cu for the
 // partition they implement.
 #pragma once
+#include "bn_debug.cuh"
 #include "bn_device.cuh"
 
 namespace bn {
