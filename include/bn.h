@@ -213,11 +213,13 @@ bn_status bn_mul(const uint32_t *a, const uint32_t *b, uint32_t *c,
  * caller-owned device memory; crt selects the two-prime form).  Instead of
  * plan-owned memory it uses two file-scope device arrays that every GPU which
  * loads the library holds until the process exits:
- *   scratch   BN_NOALLOC_SCRATCH_BYTES (32 MiB), which caps the number of
- *             CTAs (at 256K bits: 64 CTAs, so large sizes run slower than
- *             bn_mul_ntt), and
- *   tables    768 KiB of twiddle tables, regenerated on the device (on
- *             `stream`) whenever the transform length or field changes.
+ *   scratch   BN_NOALLOC_SCRATCH_BYTES (32 MiB): the first prime's
+ *             coefficients of two-prime products short enough to run on
+ *             one CTA (longer transforms keep everything in shared memory);
+ *             large enough for a full grid at every size, and
+ *   tables    1.5 MiB of twiddle tables (Shoup pairs), regenerated on the
+ *             device (on `stream`) whenever the transform length or field
+ *             changes.
  * Operand sizes above BN_NOALLOC_MAX_LIMBS return BN_EUNSUPPORTED with a
  * bn_last_error() text saying so.  No call allocates host or device memory.
  *
