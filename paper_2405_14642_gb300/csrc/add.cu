@@ -14,6 +14,12 @@
 // Every thread keeps its R chunks in registers (efficient sequentialization,
 // Section 2): the limbs are read once and written once, so the kernel is
 // bound by HBM bandwidth.
+//
+// Aligned 256K-bit rows (one team of 8 warps per instance) run a
+// persistent, double-buffered form instead: each thread copies its own
+// chunks of the CTA's next instance into a private shared-memory stage with
+// cp.async while it adds the current one, so a full instance per SM is
+// always in flight to HBM whatever the registers allow.
 #include "bn_device.cuh"
 #include "bn_internal.h"
 
@@ -142,6 +148,111 @@ __device__ __forceinline__ void add_team_instance(const AddArgs &p, uint64_t ins
             store_chunk<VEC>(row, j, s[r]);
         }
     }
+}
+
+// ---- the streaming form ------------------------------------------------------
+
+constexpr uint32_t kStreamThreads = 256;  // one team of 8 warps per CTA
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Instances of exactly chunks = 256 R 16-byte chunks (na = nb = n, aligned
+// rows), CTA i taking instances i, i + gridDim.x, ...  Shared memory:
+// buf[stage][r][operand][thread], 16 bytes each: thread t only ever reads
+// the pieces it copied itself, so cp.async.wait_group (its own copies) is
+// the only synchronisation the data needs; the warp flags of the carry scan
+// alternate between two sets, so one barrier per instance suffices.
+template <int R>
+__global__ void __launch_bounds__(kStreamThreads) k_add_stream(AddArgs p) {
+    extern __shared__ __align__(16) uint4 buf[];
+    __shared__ uint32_t warp_flags[2][kStreamThreads / 32];
+    const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint32_t j0 = w * R * 32 + lane;
+    auto piece = [&](int stage, int r, int op) -> uint4 * {
+        return buf + ((stage * R + r) * 2 + op) * kStreamThreads + tid;
+    };
+    auto issue = [&](uint64_t inst, int stage) {
+        const uint32_t *ar = p.a + inst * p.na, *br = p.b + inst * p.nb;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t j = j0 + r * 32;
+            cp_async16(piece(stage, r, 0), ar + 4 * j);
+            cp_async16(piece(stage, r, 1), br + 4 * j);
+        }
+        cp_async_commit();
+    };
+    int stage = 0;
+    uint64_t inst = blockIdx.x;
+    if (inst < p.batch) issue(inst, 0);
+    for (; inst < p.batch; inst += gridDim.x, stage ^= 1) {
+        const uint64_t next = inst + gridDim.x;
+        if (next < p.batch) {
+            issue(next, stage ^ 1);
+            cp_async_wait<1>();  // this instance's pieces are in
+        } else {
+            cp_async_wait<0>();
+        }
+        uint32_t s[R][4];
+        uint32_t gbits = 0, pbits = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {  // step 1: map
+            const uint4 av = *piece(stage, r, 0), bv = *piece(stage, r, 1);
+            const uint32_t a[4] = {av.x, av.y, av.z, av.w}, b[4] = {bv.x, bv.y, bv.z, bv.w};
+            gbits |= chunk_add<4>(a, b, s[r]) << r;
+            pbits |= chunk_all_ones<4>(s[r]) << r;
+        }
+        uint32_t wg = 0, wp = 1;  // step 2a: rows, then warp
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const RowFlags f{__ballot_sync(FULL_MASK, (gbits >> r) & 1u), __ballot_sync(FULL_MASK, (pbits >> r) & 1u)};
+            uint32_t rg;
+            row_carries(f, 0, rg);
+            carry_compose(wg, wp, rg, f.P == FULL_MASK);
+        }
+        if (lane == 0) warp_flags[stage][w] = wg | (wp << 1);
+        __syncthreads();
+        // step 2b: the 8 warps' summaries
+        const uint32_t sw = lane < kStreamThreads / 32 ? warp_flags[stage][lane] : 0u;
+        const RowFlags fw{__ballot_sync(FULL_MASK, sw & 1u), __ballot_sync(FULL_MASK, (sw >> 1) & 1u)};
+        uint32_t unused;
+        uint32_t cin = (row_carries(fw, 0, unused) >> w) & 1u;
+        uint32_t *row = p.c + inst * p.nout;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {  // step 3: map, row by row
+            const RowFlags f{__ballot_sync(FULL_MASK, (gbits >> r) & 1u), __ballot_sync(FULL_MASK, (pbits >> r) & 1u)};
+            uint32_t cout;
+            const uint32_t ci = (row_carries(f, cin, cout) >> lane) & 1u;
+            cin = cout;
+            const uint32_t j = j0 + r * 32;
+            if (j == p.chunks - 1) st_stream(row + p.n, ((gbits >> r) & 1u) | (((pbits >> r) & 1u) & ci));
+            chunk_inc<4>(s[r], ci);
+            store_chunk<4>(row, j, s[r]);
+        }
+    }
+}
+
+template <int R>
+cudaError_t launch_stream(const AddArgs &args, cudaStream_t st) {
+    const uint32_t smem = 2u * R * 2u * kStreamThreads * 16u;
+    cudaError_t e = allow_max_smem((const void *)k_add_stream<R>);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_add_stream<R>, kStreamThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const uint64_t ctas = (uint64_t)sms * per_sm;
+    const uint32_t grid = (uint32_t)(args.batch < ctas ? args.batch : ctas);
+    k_add_stream<R><<<grid, kStreamThreads, smem, st>>>(args);
+    return cudaGetLastError();
 }
 
 template <int VEC, int R>
@@ -289,6 +400,12 @@ cudaError_t add_launch(const AddConfig &cfg, const uint32_t *a, const uint32_t *
         }
     }
     if (W > kTeamMaxThreads / 32) return cudaErrorInvalidConfiguration;
+    // Aligned 256K-bit rows (one 8-warp team of 8 rows, registers for two
+    // CTAs per SM): the streaming form.  At 64K and 128K bits the team kernel
+    // keeps more loads in flight and stays faster (measured on GB300).
+    if (vec == 4 && !cfg.limbs_per_thread && !cfg.cta_threads && cfg.na == cfg.nb && W == 8 &&
+        R == 8 && args.chunks == 256 * R)
+        return launch_stream<8>(args, st);
     args.warps_per_team = W;
     args.team = 32 * W;
     uint32_t target = cfg.cta_threads ? cfg.cta_threads : 256;

@@ -46,6 +46,19 @@ def test_add_unaligned_rows(n):
     assert_limbs_equal(to_host(bn.bn_add(ta, tb)), oracle.add(a, b), "add unaligned")
 
 
+@pytest.mark.parametrize("n", [2048, 4096, 8192])
+def test_add_streaming_rounds(n):
+    """Aligned equal-length rows of 64K-256K bits take the persistent,
+    double-buffered kernel: enough instances for several rounds per CTA and
+    a ragged last round, 5% carry-chain edge cases, every row checked."""
+    torch_cuda()
+    import paper_2405_14642_gb300 as bn
+    batch = 3 * 152 * 3 + 17
+    a, b = workloads.pair_batch(batch, n, n, seed=workloads.seed_for(12, n))
+    got = to_host(bn.bn_add(to_dev(a), to_dev(b)))
+    assert_limbs_equal(got, oracle.add(a, b), f"stream {n}")
+
+
 def test_add_full_carry_chains():
     torch_cuda()
     import paper_2405_14642_gb300 as bn
