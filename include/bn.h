@@ -108,8 +108,12 @@ typedef struct bn_tuning {
     uint32_t cta_threads;       /* threads per CTA (multiple of 32, <= 1024); the three-prime
                                    transform's kernels are compiled for one count per
                                    length (N/8 within 32..1024) and refuse any other */
-    uint32_t variant;           /* quad: 1 = carry-chain accumulation, 2 = per-column
-                                   64-bit sums with carry counts; other ops: 0 */
+    uint32_t variant;           /* quad: 1 = carry-chain accumulation by thread groups,
+                                   2 = per-column 64-bit sums with carry counts, 3 = one
+                                   product per thread (operands up to 128 limbs, no
+                                   other tuning field); 0 = 3 for operands up to 96
+                                   limbs and batches of at least 4864, else 1;
+                                   other ops: 0 */
     uint32_t reserved;          /* must be zero */
 } bn_tuning;
 

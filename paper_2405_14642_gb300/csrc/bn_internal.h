@@ -77,6 +77,8 @@ struct QuadConfig {
     uint32_t na = 0, nb = 0, nout = 0;
     uint32_t q = 0;        // result limbs per window
     bool cols = false;     // per-column 64-bit sums instead of carry chains
+    bool lane = false;     // one product per thread (operands up to 128 limbs)
+    bool lane_auto = false;  // the lane form for batches of at least a warp per SM
     uint32_t threads = 0;  // threads per instance group
     uint32_t cta_threads = 0;
 };

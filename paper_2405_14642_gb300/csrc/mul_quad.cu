@@ -29,6 +29,8 @@
 // apart, so L and H are each written once per word.  c = L + H is then an
 // ordinary addition done with the Section 2 carry scan over threads in
 // memory order (2Q words per thread), and the result is copied out.
+#include <utility>
+
 #include "bn_internal.h"
 #include "quad_device.cuh"
 
@@ -238,6 +240,199 @@ __global__ void __launch_bounds__(kQuadMaxThreads)
     }
 }
 
+// ---- lane form: one product per thread ------------------------------------
+//
+// For operands of at most kLaneMaxLimbs words a thread computes a whole
+// product.  Its windows of Q columns run in order k = 0, Q, 2Q, ...; each
+// window starts from the previous one's two top words, so its low Q words are
+// final when it ends and go straight to memory: no L + H pass, no carry scan
+// and no barrier.  The 32 lanes of a warp take 32 consecutive instances, so
+// they run the same windows and blocks without divergence, which lets the
+// two triangular blocks at the ends of a window (the Q x Q corners of the
+// parallelogram where the B index leaves [0, nb)) run as shortened chains
+// instead of multiplying zero padding.  Block (I, J) of window K pairs A's
+// word block I with B's blocks J - 1 and J, J = K - I:
+//   J = nb/Q   only block J - 1 (its top words): the falling triangle,
+//   1 .. nb/Q - 1   a full block,
+//   J = 0      only block 0 (its low words): the rising triangle.
+// Operands sit in shared memory, one row per lane at a stride of an odd
+// number of 16-byte units (conflict-free vector reads), staged by the warp
+// with coalesced loads.
+constexpr uint32_t kLaneQ = 8;
+constexpr uint32_t kLaneThreads = 128;
+constexpr uint32_t kLaneMaxLimbs = 128;     // longer operand, any form request
+constexpr uint32_t kLaneAutoLimbs = 96;     // default form up to this size (faster than the
+                                            // thread-group form at 8-96 limbs, slower at 128)
+constexpr uint64_t kLaneMinBatch = 32 * 152;
+
+struct LaneArgs {
+    const uint32_t *a, *b;  // a is the longer operand (na >= nb)
+    uint32_t *c;
+    uint32_t na, nb, nap, nbp, nout;  // nap, nbp: rounded up to Q
+    uint32_t stride;                  // shared words per lane row
+    uint32_t vec_a, vec_b, vec_c;
+    uint64_t batch;
+};
+
+__host__ __device__ inline uint32_t lane_stride(uint32_t nap, uint32_t nbp) {
+    uint32_t s = roundup(nap + nbp, 4);
+    if ((s / 4) % 2 == 0) s += 4;
+    return s;
+}
+
+// Rows 0 .. nrows-1 of `rows` (n words each, contiguous in global memory) to
+// shared rows S + r * stride + off, coalesced: unit x (a 16-byte vector, or a
+// word) of the block is unit o of row r, x = r d + o, and (r, o) steps with x
+// by 32 = (32 / d) d + 32 % d without a division per unit.
+__device__ __forceinline__ void lane_stage(uint32_t *S, uint32_t stride, uint32_t off, const uint32_t *rows,
+                                           uint32_t n, uint32_t nrows, bool vec, uint32_t lane) {
+    const uint32_t d = vec ? n / 4 : n, total = nrows * d;
+    const uint32_t sr = 32 / d, so = 32 - sr * d;
+    uint32_t r = lane / d, o = lane - r * d;
+    for (uint32_t x = lane; x < total; x += 32) {
+        BN_DEBUG_CHECK(r < nrows && o < d, kDbgIndex);
+        if (vec)
+            *reinterpret_cast<uint4 *>(S + r * stride + off + 4 * o) = ld_stream_v4(rows + 4 * (uint64_t)x);
+        else
+            S[r * stride + off + o] = ld_stream(rows + x);
+        r += sr;
+        o += so;
+        if (o >= d) {
+            o -= d;
+            ++r;
+        }
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void ld_lane(const uint32_t *S, uint32_t (&v)[N]) {
+#pragma unroll
+    for (int j = 0; j < N / 4; ++j) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(S + 4 * j);
+        v[4 * j] = t.x; v[4 * j + 1] = t.y; v[4 * j + 2] = t.z; v[4 * j + 3] = t.w;
+    }
+}
+
+// A full block: steps s = 0 .. Q-1 with A word A[s] and the B window
+// (lo[s..Q), hi[0..s)) reversed into place, as window_block does.
+template <int Q>
+__device__ __forceinline__ void lane_block(const uint32_t *A, const uint32_t (&lo)[Q], const uint32_t (&hi)[Q],
+                                           uint32_t (&acc)[Q + 2], uint32_t &cnt) {
+    uint32_t av[Q];
+    ld_lane<Q>(A, av);
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+        uint32_t w[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int idx = Q - s + q;
+            w[q] = idx < Q ? lo[idx] : hi[idx - Q];
+        }
+        mac<Q>(acc, cnt, av[s], w);
+    }
+}
+
+// Full blocks I = i0 .. i0+n-1 of a window (B blocks J0 = K - i0 downwards).
+template <int Q>
+__device__ __forceinline__ void lane_full(const uint32_t *A, const uint32_t *B, uint32_t n,
+                                          uint32_t (&acc)[Q + 2], uint32_t &cnt) {
+    uint32_t c0[Q], c1[Q];
+    ld_lane<Q>(B, c1);
+    for (uint32_t m = 0; m + 1 < n; m += 2) {
+        ld_lane<Q>(B - Q, c0);
+        lane_block<Q>(A, c0, c1, acc, cnt);
+        ld_lane<Q>(B - 2 * Q, c1);
+        lane_block<Q>(A + Q, c1, c0, acc, cnt);
+        A += 2 * Q;
+        B -= 2 * Q;
+    }
+    if (n & 1) {
+        ld_lane<Q>(B - Q, c0);
+        lane_block<Q>(A, c0, c1, acc, cnt);
+    }
+}
+
+// Rising triangle (J = 0): step s multiplies A[s] by B[0 .. Q-s) into window
+// words s .. Q-1 (low halves) and s+1 .. Q (high halves).
+template <int Q, int... S>
+__device__ __forceinline__ void lane_rising(const uint32_t *A, const uint32_t *B, uint32_t (&acc)[Q + 2],
+                                            uint32_t &cnt, std::integer_sequence<int, S...>) {
+    uint32_t av[Q], b[Q];
+    ld_lane<Q>(A, av);
+    ld_lane<Q>(B, b);
+    ((lo_chain<Q - S>(acc + S, cnt, av[S], b), hi_chain<Q - S>(acc + S + 1, acc[Q + 1], av[S], b)), ...);
+}
+
+// Falling triangle (J = nb/Q, lo = B's last block): step s >= 1 multiplies
+// A[s] by lo[Q-s .. Q) into window words 0 .. s-1 (low halves) and 1 .. s
+// (high halves); each chain's carry out is held for its word and all are
+// added in at the end.
+template <int Q, int... S>
+__device__ __forceinline__ void lane_falling(const uint32_t *A, const uint32_t *Blast, uint32_t (&acc)[Q + 2],
+                                             std::integer_sequence<int, S...>) {
+    static_assert(Q == 8, "the pending-carry fold is written for Q = 8");
+    uint32_t av[Q], lo[Q], pend[Q + 1];
+    ld_lane<Q>(A, av);
+    ld_lane<Q>(Blast, lo);
+#pragma unroll
+    for (int q = 0; q <= Q; ++q) pend[q] = 0;
+    ((lo_chain<S + 1>(acc, pend[S + 1], av[S + 1], lo + Q - 1 - S),
+      hi_chain<S + 1>(acc + 1, pend[S + 2], av[S + 1], lo + Q - 1 - S)), ...);
+    fold_pending8(acc, pend);
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kLaneThreads) k_mul_quad_lane(LaneArgs p) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t inst0 = ((uint64_t)blockIdx.x * (kLaneThreads / 32) + warp) * 32;
+    if (inst0 >= p.batch) return;  // the whole warp is past the batch (no CTA barrier follows)
+    const uint32_t nrows = p.batch - inst0 < 32 ? (uint32_t)(p.batch - inst0) : 32u;
+    uint32_t *S = smem + warp * 32 * p.stride;
+    lane_stage(S, p.stride, 0, p.a + inst0 * p.na, p.na, nrows, p.vec_a, lane);
+    lane_stage(S, p.stride, p.nap, p.b + inst0 * p.nb, p.nb, nrows, p.vec_b, lane);
+    uint32_t *A = S + lane * p.stride, *B = A + p.nap;
+    for (uint32_t x = p.na; x < p.nap; ++x) A[x] = 0;
+    for (uint32_t x = p.nb; x < p.nbp; ++x) B[x] = 0;
+    __syncwarp();
+
+    const uint32_t NA = p.nap / Q, NB = p.nbp / Q, KW = (p.nout + Q - 1) / Q;
+    const bool live = lane < nrows;
+    uint32_t *crow = p.c + (inst0 + lane) * p.nout;
+    uint32_t acc[Q + 2];
+#pragma unroll
+    for (int q = 0; q < Q + 2; ++q) acc[q] = 0;
+    for (uint32_t K = 0; K < KW; ++K) {
+        // Carry in the previous window's two top words.
+        acc[0] = acc[Q];
+        acc[1] = acc[Q + 1];
+#pragma unroll
+        for (int q = 2; q < Q + 2; ++q) acc[q] = 0;
+        uint32_t cnt = 0;
+        if (K >= NB) lane_falling<Q>(A + (K - NB) * Q, B + (NB - 1) * Q, acc, std::make_integer_sequence<int, Q - 1>{});
+        const uint32_t i0 = K + 1 > NB ? K + 1 - NB : 0, i1 = K < NA ? K : NA;
+        if (i1 > i0) lane_full<Q>(A + i0 * Q, B + (K - i0) * Q, i1 - i0, acc, cnt);
+        if (K < NA) lane_rising<Q>(A + K * Q, B, acc, cnt, std::make_integer_sequence<int, Q>{});
+        fold_count<Q>(acc, cnt);
+        const uint32_t k = K * Q;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) BN_DEBUG_CHECK(k + q < p.nout || acc[q] == 0, kDbgSpill);
+        if (!live) continue;
+        if (p.vec_c) {
+#pragma unroll
+            for (int j = 0; j < Q / 4; ++j)
+                if (k + 4 * j < p.nout)
+                    st_stream_v4(crow + k + 4 * j, make_uint4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]));
+        } else {
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                if (k + q < p.nout) st_stream(crow + k + q, acc[q]);
+        }
+    }
+    // The exact product has nout words: nothing is carried out of the last window.
+    BN_DEBUG_CHECK(acc[Q] == 0 && acc[Q + 1] == 0, kDbgSpill);
+}
+
 // Window size: 8 at every size.  Timed on GB300 against 4 over the sweep
 // (1K-256K bits, CTA targets 128/256/512): 8 wins by 13-22% everywhere; 4
 // stays available through bn_tuning.
@@ -260,15 +455,25 @@ bn_status quad_configure(QuadConfig &cfg, uint32_t na, uint32_t nb, const bn_tun
     cfg.nout = na + nb;
     const uint32_t hi = na > nb ? na : nb, lo = na > nb ? nb : na;
     cfg.q = default_q(hi, lo);
+    cfg.lane_auto = hi <= kLaneAutoLimbs;
     if (t) {
-        if (t->reserved || t->variant > 2) return BN_EINVAL;
-        if (t->variant) cfg.cols = t->variant == 2;
+        if (t->reserved || t->variant > 3) return BN_EINVAL;
+        if (t->variant) {
+            cfg.cols = t->variant == 2;
+            cfg.lane = t->variant == 3;
+            cfg.lane_auto = false;
+        }
+        if (cfg.lane && (hi > kLaneMaxLimbs || t->limbs_per_thread || t->cta_threads)) return BN_EUNSUPPORTED;
         if (t->limbs_per_thread) {
             if (t->limbs_per_thread != 4 && t->limbs_per_thread != 8) return BN_EINVAL;
             cfg.q = t->limbs_per_thread;
         }
         if (t->cta_threads && (t->cta_threads % 32 || t->cta_threads > 1024)) return BN_EINVAL;
         cfg.cta_threads = t->cta_threads;
+    }
+    if (cfg.lane) {
+        cfg.threads = 1;
+        return BN_OK;
     }
     const Geometry g = geometry(hi, lo, cfg.q, cfg.cta_threads ? cfg.cta_threads : 256);
     if (g.group > kQuadMaxThreads) return BN_EUNSUPPORTED;  // needs a larger window
@@ -284,6 +489,26 @@ cudaError_t quad_launch(const QuadConfig &cfg, const uint32_t *a, const uint32_t
     if (na < nb) {  // the product is symmetric; make a the longer operand
         const uint32_t *tp = a; a = b; b = tp;
         const uint32_t tn = na; na = nb; nb = tn;
+    }
+    if (cfg.lane || (cfg.lane_auto && batch >= kLaneMinBatch)) {
+        LaneArgs la{};
+        la.a = a; la.b = b; la.c = c;
+        la.na = na; la.nb = nb;
+        la.nap = roundup(na, kLaneQ);
+        la.nbp = roundup(nb, kLaneQ);
+        la.nout = na + nb;
+        la.stride = lane_stride(la.nap, la.nbp);
+        la.vec_a = (na % 4 == 0) && ((uintptr_t)a % 16 == 0);
+        la.vec_b = (nb % 4 == 0) && ((uintptr_t)b % 16 == 0);
+        la.vec_c = (la.nout % 4 == 0) && ((uintptr_t)c % 16 == 0);
+        la.batch = batch;
+        const uint64_t grid = (batch + kLaneThreads - 1) / kLaneThreads;
+        if (grid > 0x7fffffffull) return cudaErrorInvalidConfiguration;
+        const uint32_t smem = kLaneThreads * la.stride * 4;
+        cudaError_t e = allow_max_smem((const void *)k_mul_quad_lane<kLaneQ>);
+        if (e != cudaSuccess) return e;
+        k_mul_quad_lane<kLaneQ><<<(unsigned)grid, kLaneThreads, smem, st>>>(la);
+        return cudaGetLastError();
     }
     const Geometry g = geometry(na, nb, cfg.q, cfg.cta_threads ? cfg.cta_threads : 256);
     QuadArgs args{};

@@ -109,6 +109,216 @@ __device__ __forceinline__ void fold_count(uint32_t (&acc)[Q + 2], uint32_t &cnt
     cnt = 0;
 }
 
+// Partial carry chains for the triangular blocks of the lane form:
+// x[0..M) += the low (lo_chain) or high (hi_chain) words of a * w[0..M), the
+// chain's carry out added to c.  One asm statement per chain (the carry flag
+// does not survive between statements).
+template <int M>
+__device__ __forceinline__ void lo_chain(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w);
+template <int M>
+__device__ __forceinline__ void hi_chain(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w);
+
+template <>
+__device__ __forceinline__ void lo_chain<1>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\t"
+        "addc.u32 %1, %1, 0;"
+        : "+r"(x[0]), "+r"(c)
+        : "r"(a), "r"(w[0]));
+}
+
+template <>
+__device__ __forceinline__ void lo_chain<2>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+        "madc.lo.cc.u32 %1, %3, %5, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(c)
+        : "r"(a), "r"(w[0]), "r"(w[1]));
+}
+
+template <>
+__device__ __forceinline__ void lo_chain<3>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.lo.cc.u32 %0, %4, %5, %0;\n\t"
+        "madc.lo.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %4, %7, %2;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(c)
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]));
+}
+
+template <>
+__device__ __forceinline__ void lo_chain<4>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.lo.cc.u32 %0, %5, %6, %0;\n\t"
+        "madc.lo.cc.u32 %1, %5, %7, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %8, %2;\n\t"
+        "madc.lo.cc.u32 %3, %5, %9, %3;\n\t"
+        "addc.u32 %4, %4, 0;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(c)
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]));
+}
+
+template <>
+__device__ __forceinline__ void lo_chain<5>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.lo.cc.u32 %0, %6, %7, %0;\n\t"
+        "madc.lo.cc.u32 %1, %6, %8, %1;\n\t"
+        "madc.lo.cc.u32 %2, %6, %9, %2;\n\t"
+        "madc.lo.cc.u32 %3, %6, %10, %3;\n\t"
+        "madc.lo.cc.u32 %4, %6, %11, %4;\n\t"
+        "addc.u32 %5, %5, 0;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(x[4]), "+r"(c)
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]));
+}
+
+template <>
+__device__ __forceinline__ void lo_chain<6>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.lo.cc.u32 %0, %7, %8, %0;\n\t"
+        "madc.lo.cc.u32 %1, %7, %9, %1;\n\t"
+        "madc.lo.cc.u32 %2, %7, %10, %2;\n\t"
+        "madc.lo.cc.u32 %3, %7, %11, %3;\n\t"
+        "madc.lo.cc.u32 %4, %7, %12, %4;\n\t"
+        "madc.lo.cc.u32 %5, %7, %13, %5;\n\t"
+        "addc.u32 %6, %6, 0;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(x[4]), "+r"(x[5]), "+r"(c)
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]));
+}
+
+template <>
+__device__ __forceinline__ void lo_chain<7>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.lo.cc.u32 %0, %8, %9, %0;\n\t"
+        "madc.lo.cc.u32 %1, %8, %10, %1;\n\t"
+        "madc.lo.cc.u32 %2, %8, %11, %2;\n\t"
+        "madc.lo.cc.u32 %3, %8, %12, %3;\n\t"
+        "madc.lo.cc.u32 %4, %8, %13, %4;\n\t"
+        "madc.lo.cc.u32 %5, %8, %14, %5;\n\t"
+        "madc.lo.cc.u32 %6, %8, %15, %6;\n\t"
+        "addc.u32 %7, %7, 0;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(x[4]), "+r"(x[5]), "+r"(x[6]), "+r"(c)
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]));
+}
+
+template <>
+__device__ __forceinline__ void lo_chain<8>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.lo.cc.u32 %0, %9, %10, %0;\n\t"
+        "madc.lo.cc.u32 %1, %9, %11, %1;\n\t"
+        "madc.lo.cc.u32 %2, %9, %12, %2;\n\t"
+        "madc.lo.cc.u32 %3, %9, %13, %3;\n\t"
+        "madc.lo.cc.u32 %4, %9, %14, %4;\n\t"
+        "madc.lo.cc.u32 %5, %9, %15, %5;\n\t"
+        "madc.lo.cc.u32 %6, %9, %16, %6;\n\t"
+        "madc.lo.cc.u32 %7, %9, %17, %7;\n\t"
+        "addc.u32 %8, %8, 0;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(x[4]), "+r"(x[5]), "+r"(x[6]), "+r"(x[7]), "+r"(c)
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]));
+}
+
+template <>
+__device__ __forceinline__ void hi_chain<1>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.hi.cc.u32 %0, %2, %3, %0;\n\t"
+        "addc.u32 %1, %1, 0;"
+        : "+r"(x[0]), "+r"(c)
+        : "r"(a), "r"(w[0]));
+}
+
+template <>
+__device__ __forceinline__ void hi_chain<2>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.hi.cc.u32 %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %5, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(c)
+        : "r"(a), "r"(w[0]), "r"(w[1]));
+}
+
+template <>
+__device__ __forceinline__ void hi_chain<3>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.hi.cc.u32 %0, %4, %5, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(c)
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]));
+}
+
+template <>
+__device__ __forceinline__ void hi_chain<4>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.hi.cc.u32 %0, %5, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %5, %7, %1;\n\t"
+        "madc.hi.cc.u32 %2, %5, %8, %2;\n\t"
+        "madc.hi.cc.u32 %3, %5, %9, %3;\n\t"
+        "addc.u32 %4, %4, 0;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(c)
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]));
+}
+
+template <>
+__device__ __forceinline__ void hi_chain<5>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.hi.cc.u32 %0, %6, %7, %0;\n\t"
+        "madc.hi.cc.u32 %1, %6, %8, %1;\n\t"
+        "madc.hi.cc.u32 %2, %6, %9, %2;\n\t"
+        "madc.hi.cc.u32 %3, %6, %10, %3;\n\t"
+        "madc.hi.cc.u32 %4, %6, %11, %4;\n\t"
+        "addc.u32 %5, %5, 0;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(x[4]), "+r"(c)
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]));
+}
+
+template <>
+__device__ __forceinline__ void hi_chain<6>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.hi.cc.u32 %0, %7, %8, %0;\n\t"
+        "madc.hi.cc.u32 %1, %7, %9, %1;\n\t"
+        "madc.hi.cc.u32 %2, %7, %10, %2;\n\t"
+        "madc.hi.cc.u32 %3, %7, %11, %3;\n\t"
+        "madc.hi.cc.u32 %4, %7, %12, %4;\n\t"
+        "madc.hi.cc.u32 %5, %7, %13, %5;\n\t"
+        "addc.u32 %6, %6, 0;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(x[4]), "+r"(x[5]), "+r"(c)
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]));
+}
+
+template <>
+__device__ __forceinline__ void hi_chain<7>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.hi.cc.u32 %0, %8, %9, %0;\n\t"
+        "madc.hi.cc.u32 %1, %8, %10, %1;\n\t"
+        "madc.hi.cc.u32 %2, %8, %11, %2;\n\t"
+        "madc.hi.cc.u32 %3, %8, %12, %3;\n\t"
+        "madc.hi.cc.u32 %4, %8, %13, %4;\n\t"
+        "madc.hi.cc.u32 %5, %8, %14, %5;\n\t"
+        "madc.hi.cc.u32 %6, %8, %15, %6;\n\t"
+        "addc.u32 %7, %7, 0;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(x[4]), "+r"(x[5]), "+r"(x[6]), "+r"(c)
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]));
+}
+
+template <>
+__device__ __forceinline__ void hi_chain<8>(uint32_t *x, uint32_t &c, uint32_t a, const uint32_t *w) {
+    asm("mad.hi.cc.u32 %0, %9, %10, %0;\n\t"
+        "madc.hi.cc.u32 %1, %9, %11, %1;\n\t"
+        "madc.hi.cc.u32 %2, %9, %12, %2;\n\t"
+        "madc.hi.cc.u32 %3, %9, %13, %3;\n\t"
+        "madc.hi.cc.u32 %4, %9, %14, %4;\n\t"
+        "madc.hi.cc.u32 %5, %9, %15, %5;\n\t"
+        "madc.hi.cc.u32 %6, %9, %16, %6;\n\t"
+        "madc.hi.cc.u32 %7, %9, %17, %7;\n\t"
+        "addc.u32 %8, %8, 0;"
+        : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(x[4]), "+r"(x[5]), "+r"(x[6]), "+r"(x[7]), "+r"(c)
+        : "r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]));
+}
+
+// acc[1..8] += pend[1..8], the carry out into acc[9].
+__device__ __forceinline__ void fold_pending8(uint32_t (&acc)[10], const uint32_t (&pend)[9]) {
+    asm("add.cc.u32  %0, %0, %9;\n\t"
+        "addc.cc.u32 %1, %1, %10;\n\t"
+        "addc.cc.u32 %2, %2, %11;\n\t"
+        "addc.cc.u32 %3, %3, %12;\n\t"
+        "addc.cc.u32 %4, %4, %13;\n\t"
+        "addc.cc.u32 %5, %5, %14;\n\t"
+        "addc.cc.u32 %6, %6, %15;\n\t"
+        "addc.cc.u32 %7, %7, %16;\n\t"
+        "addc.u32    %8, %8, 0;"
+        : "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3]), "+r"(acc[4]), "+r"(acc[5]), "+r"(acc[6]),
+          "+r"(acc[7]), "+r"(acc[8]), "+r"(acc[9])
+        : "r"(pend[1]), "r"(pend[2]), "r"(pend[3]), "r"(pend[4]), "r"(pend[5]), "r"(pend[6]),
+          "r"(pend[7]), "r"(pend[8]));
+}
+
 // Column form (Section 3.2's accumulate step): column q keeps a 64-bit sum
 // and a carry count.  One mad.wide adds the full 64-bit product; the sum
 // wrapped exactly when its high word decreased, since a product's high word

@@ -82,3 +82,46 @@ def test_quad_full_size_sampled(point):
     rows = np.random.default_rng(point.seed).choice(point.batch, k, replace=False)
     rows = np.union1d(rows, [19, 39, point.batch - 1])
     assert_limbs_equal(got[rows], oracle.mul(a[rows], b[rows]), f"quad {point.bits} sampled")
+
+
+LANE_SHAPES = [(1, 1), (1, 2), (3, 3), (4, 4), (5, 7), (8, 8), (9, 9), (17, 15), (31, 32), (32, 32),
+               (33, 33), (24, 40), (64, 64), (65, 63), (100, 3), (3, 100), (64, 1), (128, 128), (127, 1)]
+
+
+@pytest.mark.parametrize("batch", [1, 37, 5000])
+@pytest.mark.parametrize("na,nb", LANE_SHAPES)
+def test_quad_lane_form(na, nb, batch):
+    """One product per thread (variant 3): every size it holds, batches that
+    fill one lane, part of a warp, and many warps with a ragged last one."""
+    torch_cuda()
+    import paper_2405_14642_gb300 as bn
+    a, b = workloads.pair_batch(batch, na, nb, seed=workloads.seed_for(6, 7000 + 3 * na + nb + batch))
+    a[0] = 0xFFFFFFFF
+    b[0] = 0xFFFFFFFF
+    with bn.Plan(bn.BN_OP_MUL_QUAD, na, nb, batch, variant=3) as plan:
+        got = to_host(plan.execute(to_dev(a), to_dev(b)))
+    assert_limbs_equal(got, oracle.mul(a, b), f"quad lane {na}x{nb} batch {batch}")
+
+
+@pytest.mark.parametrize("na,nb", [(32, 32), (12, 20), (33, 7)])
+def test_quad_lane_form_unaligned_rows(na, nb):
+    """Operand and result rows off the 16-byte boundary take the word-wise staging and stores."""
+    torch = torch_cuda()
+    import paper_2405_14642_gb300 as bn
+    batch = 70
+    a, b = workloads.pair_batch(batch, na, nb, seed=workloads.seed_for(6, 7500 + na + nb))
+    ta = torch.empty(batch * na + 1, dtype=torch.int32, device="cuda")[1:].view(batch, na)
+    ta.copy_(to_dev(a))
+    out = torch.empty(batch * (na + nb) + 1, dtype=torch.int32, device="cuda")[1:].view(batch, na + nb)
+    with bn.Plan(bn.BN_OP_MUL_QUAD, na, nb, batch, variant=3) as plan:
+        got = to_host(plan.execute(ta, to_dev(b), out=out))
+    assert_limbs_equal(got, oracle.mul(a, b), f"quad lane unaligned {na}x{nb}")
+
+
+def test_quad_lane_form_limits():
+    torch_cuda()
+    import paper_2405_14642_gb300 as bn
+    with pytest.raises(bn.BnError):
+        bn.Plan(bn.BN_OP_MUL_QUAD, 129, 8, 4, variant=3)
+    with pytest.raises(bn.BnError):
+        bn.Plan(bn.BN_OP_MUL_QUAD, 32, 32, 4, variant=3, limbs_per_thread=4)
