@@ -31,14 +31,17 @@
 // bytes.  D = 2^23 + v with v < 2^23, so its bit pattern minus 0x4b000000 is
 // v, which the epilogue warps add into per-thread integer column sums (four
 // warps per group of 32 tensor-memory lanes, each a quarter of D's columns)
-// and publish to a per-CTA scratch row.  Two kernels, by the width of D:
+// and publish to a per-CTA scratch row.  Three kernels, by the width of D:
 //  * k_mul_quad_tc (ma > 128): two D slots of 256 columns; warps 1-7 build
 //    W_J in shared memory (the MMA's A operand) into one of two slots, warps
 //    8-23 read D, warp 0 issues the MMAs;
-//  * k_mul_quad_tc_tw (ma <= 128): W in tensor memory, built by the 16
-//    epilogue warps; three D slots of 128 columns and two W slots, or, when
-//    ma <= 64, four of each with 64-column D slots and the steps issued in
-//    interleaved pairs (see there).
+//  * k_mul_quad_tc_tw (64 < ma16 <= 128): W in tensor memory, built by the 16
+//    epilogue warps; three D slots of 128 columns and two W slots;
+//  * k_mul_quad_tc_tall (ma16 <= 64): every MMA's A operand is a window of
+//    one Toeplitz matrix in shared memory, D takes all of tensor memory in
+//    slots of 32 or 64 columns, up to eight accumulation chains in flight,
+//    the epilogue stores D's starting value instead of a bias MMA, and the
+//    staging and the carry into limbs overlap the MMAs (see there).
 // Warp 0 polls its mbarriers without sleeping (its wake-up is on the
 // critical path).  Every wait is bounded; a timeout raises a device flag
 // (bn_tc_check).
@@ -77,6 +80,8 @@ struct TcArgs {
     uint64_t scratch_stride;  // words per CTA
     uint32_t xs;              // bytes per K-chunk row of XX: (2 ma + ma16 - ma) * 16
     uint32_t w_off, ca_off, cb_off, braw_off, spill_off, flags_off, bar_off;  // shared-memory offsets
+    uint32_t x1_off;          // k_mul_quad_tc_tall: the second XX buffer
+    uint32_t t_off, t_bytes;  // k_mul_quad_tc_tall: the two T buffers
 };
 
 // Row r of W_J, words 16 u .. 16 u + 15 (K-chunks 4 u .. 4 u + 3), into the
@@ -380,20 +385,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
 // issues the MMAs; warps 1-16, four per group of 32 tensor-memory lanes, each
 // build a quarter of their lanes' W rows (16 columns), read 32 columns of D
 // (one load) and keep those columns' sums.
-//
-// DW = 64 (ma <= 64, up to 64K bits): four D slots of 64 columns and four W
-// slots, and the MMA warp issues the steps in pairs (J, J + 1), their MMAs
-// interleaved: two accumulation chains in flight instead of one, while the
-// epilogue warps build the next pair's W's.
 constexpr uint32_t kThreadsTw = 544;
 constexpr uint32_t kWColsTw = 64;  // tensor-memory columns per W slot
 
-template <uint32_t DW>
 __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
-    constexpr uint32_t kDSlotsTw = DW == 128 ? 3 : 4, kWSlotsTw = DW == 128 ? 2 : 4;
-    constexpr uint32_t kDColsTw = DW;       // tensor-memory columns per D slot
-    constexpr uint32_t kCW = DW / 4;        // D columns per epilogue warp
-    constexpr bool kPair = DW == 64;        // MMAs of two steps interleaved
+    constexpr uint32_t kDSlotsTw = 3, kWSlotsTw = 2;
+    constexpr uint32_t kDColsTw = 128;      // tensor-memory columns per D slot
+    constexpr uint32_t kCW = kDColsTw / 4;  // D columns per epilogue warp
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *X = sm;  // XX doubles as the normalisation's staging row
     uint32_t *braw = reinterpret_cast<uint32_t *>(sm + g.braw_off);
@@ -459,40 +457,26 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
             const uint32_t idesc = tc::idesc_f16_f32(128, g.ma16);
             const uint64_t bstep = (2 * g.xs) >> 4;
             const uint64_t cad = tc::smem_desc(x_s + g.ca_off, 128, 0), cbd = tc::smem_desc(x_s + g.cb_off, 128, 0);
-            constexpr uint32_t kStepsPerIssue = kPair ? 2 : 1;
-            for (uint32_t J = 0; J < S; J += kStepsPerIssue) {
-                const uint32_t n = J + 1 < S ? kStepsPerIssue : 1;  // steps issued together
-                bool ok = true;
-                for (uint32_t h = 0; h < n && ok; ++h) {
-                    const uint32_t gh = gs + h, ud = gh / kDSlotsTw;
-                    ok = tc::mbar_wait_spin(&wfull[gh % kWSlotsTw], (gh / kWSlotsTw) & 1u, kWaitNs, abortf);
-                    if (ok && ud > 0)
-                        ok = tc::mbar_wait_spin(&dempty[gh % kDSlotsTw], (ud - 1) & 1u, kWaitNs, abortf);
-                }
+            for (uint32_t J = 0; J < S; ++J) {
+                const uint32_t ud = gs / kDSlotsTw;
+                bool ok = tc::mbar_wait_spin(&wfull[gs % kWSlotsTw], (gs / kWSlotsTw) & 1u, kWaitNs, abortf);
+                if (ok && ud > 0) ok = tc::mbar_wait_spin(&dempty[gs % kDSlotsTw], (ud - 1) & 1u, kWaitNs, abortf);
                 if (!__all_sync(FULL_MASK, ok)) {
                     *abortf = 1;
                     break;
                 }
                 tc::fence_after_sync();
-                const uint32_t d0 = gs % kDSlotsTw, d1 = (gs + 1) % kDSlotsTw;
-                const uint32_t dt0 = tbase + kDColsTw * d0, dt1 = tbase + kDColsTw * d1;
-                const uint32_t at0 = wbase + kWColsTw * (gs % kWSlotsTw);
-                const uint32_t at1 = wbase + kWColsTw * ((gs + 1) % kWSlotsTw);
-                const uint64_t bd0 = tc::smem_desc(x_s + (g.ma - J) * 16, g.xs, 128);  // XX from block ma - J
-                const uint64_t bd1 = bd0 - 1;  // step J + 1: one block (16 bytes) lower
+                const uint32_t dt = tbase + kDColsTw * (gs % kDSlotsTw);
+                const uint32_t at = wbase + kWColsTw * (gs % kWSlotsTw);
+                const uint64_t bd = tc::smem_desc(x_s + (g.ma - J) * 16, g.xs, 128);  // XX from block ma - J
                 if (tc::elect_one()) {
-                    tc::mma_f16_ss(dt0, cad, cbd, idesc, 0);  // D = 2^23
-                    if (n == 2) tc::mma_f16_ss(dt1, cad, cbd, idesc, 0);
+                    tc::mma_f16_ss(dt, cad, cbd, idesc, 0);  // D = 2^23
 #pragma unroll
-                    for (uint32_t kk = 0; kk < 8; ++kk) {
-                        tc::mma_f16_ts(dt0, at0 + 8 * kk, bd0 + kk * bstep, idesc, 1);
-                        if (n == 2) tc::mma_f16_ts(dt1, at1 + 8 * kk, bd1 + kk * bstep, idesc, 1);
-                    }
-                    tc::mma_commit(&dfull[d0]);
-                    if (n == 2) tc::mma_commit(&dfull[d1]);
+                    for (uint32_t kk = 0; kk < 8; ++kk) tc::mma_f16_ts(dt, at + 8 * kk, bd + kk * bstep, idesc, 1);
+                    tc::mma_commit(&dfull[gs % kDSlotsTw]);
                 }
                 __syncwarp();
-                gs += n;
+                ++gs;
             }
         } else {
             // column quarter m: D columns [kCW m, kCW m + kCW), W columns [16 m, 16 m + 16)
@@ -532,8 +516,7 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
                 }
                 if (n0 < g.ma) {  // the warp's kCW columns of D in one load
                     uint32_t v[kCW];
-                    if constexpr (kCW == 32) tc::tmem_ld32(tbase + lane_off + kDColsTw * d + n0, v);
-                    else tc::tmem_ld16(tbase + lane_off + kDColsTw * d + n0, v);
+                    tc::tmem_ld32(tbase + lane_off + kDColsTw * d + n0, v);
 #pragma unroll
                     for (int j = 0; j < (int)kCW; ++j) acc[0][j] += v[j] - kBiasBits;
                 }
@@ -544,11 +527,7 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
                 // over as block J + ma
                 const uint32_t f = J - n0;  // warp-uniform
                 if (J < g.mb && f < kCW) {
-                    if constexpr (kCW == 32) {
-                        switch (f) { BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) BN_TC_FLUSH8(16) BN_TC_FLUSH8(24) }
-                    } else {
-                        switch (f) { BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) }
-                    }
+                    switch (f) { BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) BN_TC_FLUSH8(16) BN_TC_FLUSH8(24) }
                 }
             }
             // publish: column n < mb went on to block n + ma after step n (two
@@ -584,14 +563,450 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
 }
+// ---- up to 64K bits: the Toeplitz rows in shared memory --------------------
+//
+// At N = ma16 <= 64 one MMA carries little work (128 x N x 16 products), and a
+// single accumulation chain completes one only every ~140 SM clocks whatever
+// N; the tensor pipe needs several independent chains in flight.  K-chunk kk
+// of W_J (its columns 16 kk .. 16 kk + 15) is the 128-row window starting at
+// row R0 = 128 J - 16 kk of one tall matrix T[R][c] = b-byte (R - c), c < 16:
+//     W_J[r][16 kk + c] = b-byte (128 J + r - 16 kk - c) = T[R0 + r][c].
+// So every MMA takes its A operand from a window of T in shared memory (a
+// descriptor offset), and all of tensor memory holds D: 512 / DW slots.  The
+// steps run in groups of half that many, their MMAs interleaved (as many
+// accumulation chains in flight), each group's D in one half of the slots
+// while the other half is read.
+//
+// Three roles, so that nothing but MMAs sits on the tensor pipe's critical
+// path:
+//  * warp 0 issues the MMAs (group g reads T buffer g % 2 and D half g % 2,
+//    product p reads XX buffer p % 2);
+//  * warps 1-8 (epilogue) read D, keep the column sums and publish them,
+//    per product, into one of two column-sum rows;
+//  * warps 9-16 (producer) stage each product's XX and b's bytes, build each
+//    group's rows of T: R in [128 J - 112, 128 (J + n)), in the A operand's
+//    layout (K-major, no swizzle: row i, K-half h at (i / 8) * 256 + h * 128
+//    + (i % 8) * 16, i.e. LBO = 128, SBO = 256), and carry the previous
+//    product's column sums into limbs once its own first two groups are
+//    built, while the tensor pipe runs them.
+// mbarriers link them (tfull/tempty per T buffer, xfull/xempty per XX
+// buffer, dfull/dempty per D slot, cfull/cempty per column-sum row; the
+// producer's own barrier is an mbarrier too), and every wait is bounded and
+// watches the CTA's abort flag.
+constexpr uint32_t kTallRowBytes = 32;  // 16 fp16
+constexpr uint32_t kTallLbo = 128, kTallSbo = 256;
+constexpr uint32_t kTallLead = 112;     // rows of T below 128 J that step J's window reaches
+constexpr uint32_t kEpiTall = 8;    // two per group of 32 tensor-memory lanes
+constexpr uint32_t kProdWarps = 8;
+constexpr uint32_t kThreadsTall = 32 * (1 + kEpiTall + kProdWarps);
+
+// Row R of T (words k = 0..7: the fp16 pair (b-byte (R - 2k), b-byte (R - 2k - 1)))
+// from braw (b's bytes at offset 128 + index, zero outside b; R >= -112).
+__device__ __forceinline__ void tall_row(const uint32_t *braw, int32_t R, uint32_t (&w)[8]) {
+    const uint32_t e = (uint32_t)(113 + R);  // braw byte of b-byte (R - 15)
+    const uint32_t *bw = braw + (e >> 2);
+    const uint32_t sh = e & 3u;
+    uint32_t wv[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) wv[j] = bw[j];
+    // x_m holds b-bytes R - 4m, R - 4m - 1, R - 4m - 2, R - 4m - 3 (bytes 0..3)
+    const uint32_t sel = (sh + 3) | ((sh + 2) << 4) | ((sh + 1) << 8) | (sh << 12);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const uint32_t x = __byte_perm(wv[3 - m], wv[4 - m], sel);
+        w[2 * m] = tc::bytes01_f16x2(x);
+        w[2 * m + 1] = tc::bytes23_f16x2(x);
+    }
+}
+
+// A barrier among the warps of one role: each warp's lane 0 arrives on an
+// mbarrier counting those warps (release: the warp's earlier writes, shared
+// or global, are visible to a thread that sees the phase complete), then
+// every thread waits for the phase (bounded, watching the abort flag).
+__device__ __forceinline__ bool role_sync(uint64_t *bar, uint32_t &phase, volatile uint32_t *abortf) {
+    __threadfence_block();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) tc::mbar_arrive(bar);
+    const bool ok = __all_sync(FULL_MASK, tc::mbar_wait(bar, phase, kWaitNs, abortf));
+    phase ^= 1u;
+    if (!ok) *abortf = 1;
+    return ok;
+}
+
+// normalize_limbs for the NW warps of one role (thread t of NT = 32 NW),
+// synchronised by role_sync: column sums -> limbs, carry scan, copy-out.
+template <uint32_t NW, class LimbFn>
+__device__ bool normalize_role(uint32_t nout, uint32_t *crow, uint32_t *out_s, uint64_t *spill, uint32_t *flags,
+                               uint32_t t, uint64_t *bar, uint32_t &phase, volatile uint32_t *abortf,
+                               LimbFn &&limb) {
+    constexpr uint32_t NT = 32 * NW;
+    const uint32_t lane = t & 31, w = t >> 5;
+    uint32_t QN = (nout + NT - 1) / NT;
+    if (QN < 2) QN = 2;  // a window must absorb a two-word spill
+    const uint32_t k0 = t * QN;
+    const uint32_t k1 = k0 + QN < nout ? k0 + QN : nout;
+    // (a) this window's limbs, carrying within the window
+    ntt::u128 carry = 0;
+    for (uint32_t k = k0; k < k1; ++k) {
+        const ntt::u128 v = limb(k) + carry;
+        out_s[ntt::stage_index(k)] = (uint32_t)v;
+        carry = v >> 32;
+    }
+    spill[t] = (uint64_t)carry;
+    if (!role_sync(bar, phase, abortf)) return false;
+    // (b) add the previous window's spill
+    uint64_t c = t > 0 ? spill[t - 1] : 0;
+    uint32_t all = 0xffffffffu;
+    for (uint32_t k = k0; k < k1; ++k) {
+        const uint64_t v = (uint64_t)out_s[ntt::stage_index(k)] + (c & 0xffffffffu);
+        out_s[ntt::stage_index(k)] = (uint32_t)v;
+        c = (c >> 32) + (v >> 32);
+        all &= (uint32_t)v;
+    }
+    const bool owns = k0 < k1;
+    BN_DEBUG_CHECK(!(owns && k1 == nout) || c == 0, kDbgSpill);
+    BN_DEBUG_CHECK(owns || c == 0, kDbgSpill);
+    // (c) carry scan over the NT windows in memory order (Section 2)
+    const RowFlags f{__ballot_sync(FULL_MASK, owns && c != 0), __ballot_sync(FULL_MASK, owns && all == 0xffffffffu)};
+    uint32_t wc;
+    row_carries(f, 0, wc);
+    if (lane == 0) flags[w] = wc | ((f.P == FULL_MASK) << 1);
+    if (!role_sync(bar, phase, abortf)) return false;
+    const uint32_t sw = lane < NW ? flags[lane] : 0u;
+    const RowFlags fw{__ballot_sync(FULL_MASK, sw & 1u), __ballot_sync(FULL_MASK, (sw >> 1) & 1u)};
+    uint32_t unused;
+    const uint32_t wcin = (row_carries(fw, 0, unused) >> w) & 1u;
+    const uint32_t cin = (row_carries(f, wcin, unused) >> lane) & 1u;
+    BN_DEBUG_CHECK(!(owns && k1 == nout && cin && all == 0xffffffffu), kDbgSpill);
+    if (cin)
+        for (uint32_t k = k0; k < k1; ++k)
+            if (++out_s[ntt::stage_index(k)] != 0) break;
+    if (!role_sync(bar, phase, abortf)) return false;
+    // (d) coalesced copy-out; the staging row and flags are free again after the barrier
+    for (uint32_t x = t; x < nout; x += NT) st_stream(crow + x, out_s[ntt::stage_index(x)]);
+    return role_sync(bar, phase, abortf);
+}
+
+// Whole warp: NC (16 or 32) columns of this warp's tensor-memory lanes at
+// taddr set to 2^23 (bit pattern kBiasBits), where a D slot's sums start.
+template <uint32_t NC>
+__device__ __forceinline__ void bias_columns(uint32_t taddr) {
+    uint32_t v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = kBiasBits;
+#pragma unroll
+    for (uint32_t c = 0; c < NC; c += 16) tc::tmem_st16(taddr + c, v);
+}
+
+template <uint32_t DW>
+__global__ void __launch_bounds__(kThreadsTall, 1) k_mul_quad_tc_tall(TcArgs g) {
+    constexpr uint32_t kDS = kTmemCols / DW;  // D slots
+    constexpr uint32_t kC = kDS / 2;          // steps per group (chains in flight)
+    constexpr uint32_t kCW = DW / 2;          // D columns per epilogue warp
+    extern __shared__ __align__(1024) uint8_t sm[];
+    // XX buffers at 0 and g.x1_off, T buffers at g.t_off and g.t_off + g.t_bytes, the
+    // normalisation's staging row at g.spill_off followed by its spill words
+    uint8_t *const X0 = sm, *const X1 = sm + g.x1_off;
+    uint32_t *const braw0 = reinterpret_cast<uint32_t *>(sm + g.braw_off);
+    uint32_t *const braw1 = braw0 + (32 * (g.mb + 2) + 4);
+    uint32_t *out_s = reinterpret_cast<uint32_t *>(sm + g.spill_off);
+    uint64_t *spill = reinterpret_cast<uint64_t *>(sm + g.spill_off + ((4 * ntt::stage_index(g.nout) + 16 + 15) & ~15u));
+    uint32_t *flags = reinterpret_cast<uint32_t *>(sm + g.flags_off);
+    uint64_t *dfull = reinterpret_cast<uint64_t *>(sm + g.bar_off);  // [kDS] MMA commits
+    uint64_t *dempty = dfull + kDS;                                    // [kDS] one arrival per epilogue warp
+    uint64_t *tfull = dempty + kDS;    // [2] one arrival per producer warp
+    uint64_t *tempty = tfull + 2;      // [2] MMA commits
+    uint64_t *xfull = tempty + 2;      // [2] one arrival per producer warp
+    uint64_t *xempty = xfull + 2;      // [2] MMA commits
+    uint64_t *cfull = xempty + 2;      // [2] one arrival per epilogue warp
+    uint64_t *cempty = cfull + 2;      // [2] one arrival per producer warp
+    uint64_t *pbar = cempty + 2;       // the producer warps' own barrier
+    uint32_t *slot = reinterpret_cast<uint32_t *>(pbar + 1);
+    volatile uint32_t *abortf = slot + 1;
+
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tc::tmem_alloc(slot, kTmemCols);
+    if (tid == 0) {
+        for (uint32_t k = 0; k < kDS; ++k) {
+            tc::mbar_init(&dfull[k], 1);
+            tc::mbar_init(&dempty[k], kEpiTall);
+        }
+        for (uint32_t k = 0; k < 2; ++k) {
+            tc::mbar_init(&tfull[k], kProdWarps);
+            tc::mbar_init(&tempty[k], 1);
+            tc::mbar_init(&xfull[k], kProdWarps);
+            tc::mbar_init(&xempty[k], 1);
+            tc::mbar_init(&cfull[k], kEpiTall);
+            tc::mbar_init(&cempty[k], kProdWarps);
+        }
+        tc::mbar_init(pbar, kProdWarps);
+        *abortf = 0;
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *slot, S = g.mb + 1;  // steps J = 0..mb of a product
+    if (warp >= 1 && warp <= kEpiTall) {  // every D slot starts at 2^23 (the epilogue restores it after each read)
+        const uint32_t lq = warp & 3, n0 = (DW / 2) * ((warp - 1) >> 2);
+        for (uint32_t d = 0; d < kDS; ++d) bias_columns<DW / 2>(tbase + ((32 * lq) << 16) + DW * d + n0);
+        tc::tmem_st_wait();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // this CTA's two column-sum rows (product p uses row p % 2)
+    uint32_t *const cols0 = g.scratch + blockIdx.x * g.scratch_stride;
+    uint32_t *const cols1 = cols0 + g.scratch_stride / 2;
+
+    if (warp == 0) {
+        // ---- MMA warp
+        const uint32_t idesc = tc::idesc_f16_f32(128, g.ma16);
+        const uint64_t bstep = (2 * g.xs) >> 4;
+        const uint32_t s0 = tc::smem_u32(sm);
+        uint32_t gs = 0, gg = 0, pi = 0;  // steps, groups, products issued by this CTA
+        bool ok = true;
+        for (uint64_t inst = blockIdx.x; inst < g.batch && ok; inst += gridDim.x, ++pi) {
+            const uint32_t xb = pi & 1u, x_s = s0 + (xb ? g.x1_off : 0u);
+            ok = __all_sync(FULL_MASK, tc::mbar_wait_spin(&xfull[xb], (pi >> 1) & 1u, kWaitNs, abortf));
+            for (uint32_t J = 0; J < S && ok; J += kC, ++gg) {
+                const uint32_t n = J + kC <= S ? kC : S - J;  // steps of this group
+                const uint32_t tb = gg & 1u, t_s = s0 + g.t_off + tb * g.t_bytes;
+                for (uint32_t h = 0; h < n && ok; ++h) {
+                    const uint32_t gh = gs + h, ud = gh / kDS;
+                    if (ud > 0) ok = tc::mbar_wait_spin(&dempty[gh % kDS], (ud - 1) & 1u, kWaitNs, abortf);
+                }
+                if (ok) ok = tc::mbar_wait_spin(&tfull[tb], (gg >> 1) & 1u, kWaitNs, abortf);
+                ok = __all_sync(FULL_MASK, ok);
+                if (!ok) break;
+                tc::fence_after_sync();
+                if (tc::elect_one()) {
+                    // step J + h: its D slot, its T window at K-chunk 0 (row 128 h + 112
+                    // of the group's rows) and its XX window (block ma - J - h);
+                    // K-chunk kk moves T 16 rows up and XX two K-chunks on
+                    uint32_t dt[kC];
+                    uint64_t ad[kC], bd[kC];
+#pragma unroll
+                    for (uint32_t h = 0; h < kC; ++h) {
+                        const uint32_t hh = h < n ? h : 0;  // (unused beyond n)
+                        dt[h] = tbase + DW * ((gs + hh) % kDS);
+                        ad[h] = tc::smem_desc(t_s + (kBlk * hh + kTallLead) * kTallRowBytes, kTallLbo, kTallSbo);
+                        bd[h] = tc::smem_desc(x_s + (g.ma - J - hh) * 16, g.xs, 128);
+                    }
+                    uint64_t bk = 0;
+#pragma unroll
+                    for (uint32_t kk = 0; kk < 8; ++kk, bk += bstep)
+#pragma unroll
+                        for (uint32_t h = 0; h < kC; ++h)
+                            if (h < n)
+                                tc::mma_f16_ss(dt[h], ad[h] - kk * (16 * kTallRowBytes / 16), bd[h] + bk, idesc, 1);
+                    for (uint32_t h = 0; h < n; ++h) tc::mma_commit(&dfull[(gs + h) % kDS]);
+                    tc::mma_commit(&tempty[tb]);                // T buffer tb may be rebuilt
+                    if (J + n == S) tc::mma_commit(&xempty[xb]);  // XX buffer xb may be restaged
+                }
+                __syncwarp();
+                gs += n;
+            }
+        }
+        if (!ok) *abortf = 1;
+        // the MMAs issued last finish before tensor memory is freed (bounded; at once
+        // when the epilogue has already seen them)
+        if (lane == 0 && gs > 0) tc::mbar_wait(&dfull[(gs - 1) % kDS], ((gs - 1) / kDS) & 1u, kWaitNs);
+        __syncwarp();
+    } else if (warp > kEpiTall) {
+        // ---- producer warps: XX and b's bytes of each product, T's rows of each
+        // group, and the previous product's limbs
+        const uint32_t pt = tid - 32 * (1 + kEpiTall);
+        constexpr uint32_t PT = 32 * kProdWarps;
+        uint32_t gg = 0, pi = 0, pph = 0;
+        bool ok = true;
+        // column sums of product q (instance `inst`) -> limbs
+        auto finish = [&](uint32_t q, uint64_t inst) -> bool {
+            const uint32_t cb = q & 1u;
+            const uint32_t *cols = cb ? cols1 : cols0;
+            if (!__all_sync(FULL_MASK, tc::mbar_wait(&cfull[cb], (q >> 1) & 1u, kWaitNs, abortf))) return false;
+            const bool done = normalize_role<kProdWarps>(
+                g.nout, g.c + inst * g.nout, out_s, spill, flags, pt, pbar, pph, abortf, [&](uint32_t k) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(cols + 4 * k);
+                    return (ntt::u128)((uint64_t)v.x + ((uint64_t)v.y << 8) + ((uint64_t)v.z << 16) +
+                                       ((uint64_t)v.w << 24));
+                });
+            __syncwarp();
+            if (done && lane == 0) tc::mbar_arrive(&cempty[cb]);
+            return done;
+        };
+        for (uint64_t inst = blockIdx.x; inst < g.batch && ok; inst += gridDim.x, ++pi) {
+            const uint32_t xb = pi & 1u;
+            uint8_t *const X = xb ? X1 : X0;
+            uint32_t *const braw = xb ? braw1 : braw0;
+            const uint32_t *arow = g.a + inst * g.na, *brow = g.b + inst * g.nb;
+            if (pi >= 2) ok = __all_sync(FULL_MASK, tc::mbar_wait(&xempty[xb], ((pi - 2) >> 1) & 1u, kWaitNs, abortf));
+            if (!ok) break;
+            // XX: a-block I at blocks I and I + ma, zero blocks up to D's width
+            for (uint32_t x = pt; x < 16 * g.ma; x += PT) {
+                const uint32_t I = x >> 4, q = x & 15, w0 = 32 * I + 2 * q;
+                const uint32_t u = w0 < g.na ? __ldg(arow + w0) : 0u;
+                const uint32_t v = w0 + 1 < g.na ? __ldg(arow + w0 + 1) : 0u;
+                const uint4 f = make_uint4(tc::bytes01_f16x2(u), tc::bytes23_f16x2(u), tc::bytes01_f16x2(v),
+                                           tc::bytes23_f16x2(v));
+                *reinterpret_cast<uint4 *>(X + q * g.xs + I * 16) = f;
+                *reinterpret_cast<uint4 *>(X + q * g.xs + (I + g.ma) * 16) = f;
+            }
+            const uint32_t zb = g.ma16 - g.ma;
+            for (uint32_t x = pt; x < 16 * zb; x += PT)
+                *reinterpret_cast<uint4 *>(X + (x / zb) * g.xs + (2 * g.ma + x % zb) * 16) = make_uint4(0, 0, 0, 0);
+            const uint32_t bwords = 32 * (g.mb + 2) + 4;
+            for (uint32_t x = pt; x < bwords; x += PT) braw[x] = (x >= 32 && x - 32 < g.nb) ? __ldg(brow + x - 32) : 0u;
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&xfull[xb]);
+            if (!role_sync(pbar, pph, abortf)) {  // b's bytes are read by every producer thread's rows
+                ok = false;
+                break;
+            }
+            uint32_t k = 0;  // group of this product
+            for (uint32_t J = 0; J < S && ok; J += kC, ++gg, ++k) {
+                const uint32_t n = J + kC <= S ? kC : S - J, tb = gg & 1u;
+                uint8_t *const Tb = sm + g.t_off + tb * g.t_bytes;
+                if (gg >= 2) ok = __all_sync(FULL_MASK, tc::mbar_wait(&tempty[tb], ((gg - 2) >> 1) & 1u, kWaitNs, abortf));
+                if (!ok) break;
+                const int32_t Rbase = (int32_t)(kBlk * J) - (int32_t)kTallLead;
+                const uint32_t nrows = kBlk * n + kTallLead;
+                for (uint32_t i = pt; i < nrows; i += PT) {
+                    uint32_t w[8];
+                    tall_row(braw, Rbase + (int32_t)i, w);
+                    uint8_t *row = Tb + (i >> 3) * kTallSbo + (i & 7) * 16;
+                    *reinterpret_cast<uint4 *>(row) = make_uint4(w[0], w[1], w[2], w[3]);
+                    *reinterpret_cast<uint4 *>(row + kTallLbo) = make_uint4(w[4], w[5], w[6], w[7]);
+                }
+                tc::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&tfull[tb]);
+                // both T buffers hold this product's work: finish the previous product
+                if (pi > 0 && (k == 1 || J + n == S && k == 0)) ok = finish(pi - 1, inst - gridDim.x);
+            }
+        }
+        if (ok && pi > 0) ok = finish(pi - 1, blockIdx.x + (uint64_t)(pi - 1) * gridDim.x);
+        if (!ok) *abortf = 1;
+    } else {
+        // ---- epilogue warps: column half m, D columns [kCW m, kCW m + kCW)
+        const uint32_t lq = warp & 3;  // the tensor-memory lanes this warp may move
+        const uint32_t m = (warp - 1) >> 2, n0 = kCW * m, r = 32 * lq + lane;
+        const uint32_t lane_off = (32 * lq) << 16;
+        uint32_t gs = 0, pi = 0, dprev = 0;
+        bool ok = true;
+        // D slot d is free again once this warp's stores of its starting values have landed
+        auto release = [&](uint32_t d) {
+            tc::tmem_st_wait();
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&dempty[d]);
+        };
+        for (uint64_t inst = blockIdx.x; inst < g.batch && ok; inst += gridDim.x, ++pi) {
+            const uint32_t cb = pi & 1u;
+            uint32_t *const colr = (cb ? cols1 : cols0) + r;  // this thread's row of every column block
+            if (pi >= 2) ok = __all_sync(FULL_MASK, tc::mbar_wait(&cempty[cb], ((pi - 2) >> 1) & 1u, kWaitNs, abortf));
+            if (!ok) break;
+            uint32_t acc[kCW / 32 + (kCW % 32 != 0)][kCW < 32 ? kCW : 32];
+#pragma unroll
+            for (int i = 0; i < (int)kCW; ++i) acc[i >> 5][i & 31] = 0;
+            for (uint32_t J = 0; J < S; ++J, ++gs) {
+                const uint32_t d = gs % kDS;
+                ok = __all_sync(FULL_MASK, tc::mbar_wait(&dfull[d], (gs / kDS) & 1u, kWaitNs, abortf));
+                if (!ok) break;
+                tc::fence_after_sync();
+                if (n0 < g.ma) {  // the warp's kCW columns of D in one load
+                    if constexpr (kCW == 32) {  // two loads of 16 (fewer live registers)
+#pragma unroll
+                        for (int hf = 0; hf < 2; ++hf) {
+                            uint32_t v[16];
+                            tc::tmem_ld16(tbase + lane_off + DW * d + n0 + 16 * hf, v);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) acc[0][16 * hf + j] += v[j] - kBiasBits;
+                        }
+                    } else {
+                        uint32_t v[16];
+                        tc::tmem_ld16(tbase + lane_off + DW * d + n0, v);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) acc[0][j] += v[j] - kBiasBits;
+                    }
+                }
+                // the previous slot's starting values have landed: release it; this
+                // slot starts over at 2^23 (its store lands while the next step waits)
+                if (J > 0) release(dprev);
+                bias_columns<kCW>(tbase + lane_off + DW * d + n0);
+                dprev = d;
+                // column J now holds all of block J: store it and start the column
+                // over as block J + ma
+                const uint32_t f = J - n0;  // warp-uniform
+                if (J < g.mb && f < kCW) {
+                    if constexpr (kCW == 32) {
+                        switch (f) { BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) BN_TC_FLUSH8(16) BN_TC_FLUSH8(24) }
+                    } else {
+                        switch (f) { BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) }
+                    }
+                }
+            }
+            if (!ok) break;
+            release(dprev);
+            // publish: column n < mb went on to block n + ma after step n
+#pragma unroll
+            for (int j = 0; j < (int)kCW; ++j)
+                if (n0 + j >= g.mb && n0 + j < g.ma) colr[kBlk * (n0 + j)] = acc[j >> 5][j & 31];
+            uint32_t *const colr_hi = colr + kBlk * g.ma;
+#pragma unroll
+            for (int j = 0; j < (int)kCW; ++j)
+                if (n0 + j < g.mb) colr_hi[kBlk * (n0 + j)] = acc[j >> 5][j & 31];
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&cfull[cb]);  // the producer carries them into limbs
+        }
+        if (!ok) *abortf = 1;
+    }
+    if (tid == 0 && *abortf) atomicOr(&g_tc_fault, 1u);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
+}
 #undef BN_TC_FLUSH8
 #undef BN_TC_FLUSH
 
 struct TcGeometry {
     uint32_t na, nb, ma, mb, ma16, xs, w_off, ca_off, cb_off, braw_off, spill_off, flags_off, bar_off, smem;
-    bool swap, tw;  // tw: W in tensor memory (k_mul_quad_tc_tw, ma <= 128)
-    uint32_t dw;    // its D slot width: 64 (ma <= 64) or 128
+    bool swap, tw;  // tw: W in tensor memory (k_mul_quad_tc_tw, 64 < ma16 <= 128)
+    bool tall;      // the rows of T in shared memory (k_mul_quad_tc_tall, ma16 <= 64)
+    uint32_t dw;    // D slot width: 32 or 64 (tall), 128 (tw)
+    uint32_t x1_off, t_off, t_bytes;
 };
+
+constexpr uint32_t kSmemMax = 227 * 1024;  // dynamic shared memory per CTA (opt-in)
+
+// k_mul_quad_tc_tall's layout: two XX buffers, two T buffers (one group of
+// steps each), the normalisation's staging row and spill words, two copies
+// of b's bytes, the flags and the mbarriers.
+void tall_geometry(TcGeometry &q, uint32_t nout) {
+    q.tall = true;
+    q.tw = false;
+    q.dw = q.ma16 <= 32 ? 32 : 64;
+    const uint32_t dslots = kTmemCols / q.dw, group = dslots / 2;
+    const uint32_t xbytes = (16 * q.xs + 1023) & ~1023u;
+    q.x1_off = xbytes;
+    q.t_off = 2 * xbytes;
+    q.t_bytes = ((kBlk * group + kTallLead) * kTallRowBytes + 1023) & ~1023u;
+    uint32_t off = q.t_off + 2 * q.t_bytes;
+    q.spill_off = off;  // staging row (stage_index(nout) words + 16 bytes), then 8 bytes per epilogue thread
+    off += ((4 * (nout + (nout >> 4)) + 16 + 15) & ~15u) + 8 * 32 * kProdWarps;
+    q.ca_off = q.cb_off = 0;  // no bias MMA: the epilogue stores D's starting value
+    q.braw_off = off;
+    off += 2 * 4 * (32 * (q.mb + 2) + 4);
+    off = (off + 15) & ~15u;
+    q.flags_off = off;
+    off += 4 * kEpiWarps;
+    q.bar_off = (off + 15) & ~15u;
+    q.smem = q.bar_off + 8 * (2 * dslots + 13) + 16;  // mbarriers, then the tensor-memory slot and abort flag
+    if (q.smem < kMinSmem) q.smem = kMinSmem;  // one CTA per SM: each takes all of tensor memory
+    q.w_off = 0;
+}
 
 TcGeometry geometry(uint32_t na, uint32_t nb) {
     TcGeometry q{};
@@ -606,6 +1021,10 @@ TcGeometry geometry(uint32_t na, uint32_t nb) {
     q.xs = (2 * q.ma + (q.ma16 - q.ma)) * 16;
     const uint32_t nout = q.na + q.nb;
     const uint32_t stage_bytes = 4 * ((nout - 1) + ((nout - 1) >> 4) + 1);
+    if (q.ma16 <= 64) {
+        tall_geometry(q, nout);
+        return q;
+    }
     q.w_off = 16 * q.xs;  // a multiple of 256
     uint32_t off;
     if (q.tw) {  // no W in shared memory; the spill words after the staging row
@@ -653,18 +1072,25 @@ bn_status quad_tc_create(QuadTcPlan **out, uint32_t na, uint32_t nb) {
     if (!p) return BN_ENOMEM;
     p->geo = geometry(na, nb);
     p->nout = na + nb;
+    if (p->geo.smem > kSmemMax) {
+        delete p;
+        return BN_EUNSUPPORTED;
+    }
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc);
-    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc_tw<128>);
-    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc_tw<64>);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc_tw);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc_tall<32>);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)k_mul_quad_tc_tall<64>);
     if (e != cudaSuccess) {
         delete p;
         return BN_ECUDA;
     }
     p->ctas = (uint32_t)sms;
-    p->stride = (uint64_t)kBlk * (p->geo.ma + p->geo.mb);
+    // column sums per CTA: one row, or two for k_mul_quad_tc_tall (one product's
+    // sums are carried into limbs while the next product's accumulate)
+    p->stride = (uint64_t)kBlk * (p->geo.ma + p->geo.mb) * (p->geo.tall ? 2 : 1);
     e = cudaMalloc(&p->scratch, p->stride * 4ull * p->ctas);
     if (e != cudaSuccess) {
         delete p;
@@ -707,11 +1133,16 @@ cudaError_t quad_tc_launch(QuadTcPlan *p, const uint32_t *a, const uint32_t *b, 
     g.spill_off = q.spill_off;
     g.flags_off = q.flags_off;
     g.bar_off = q.bar_off;
+    g.x1_off = q.x1_off;
+    g.t_off = q.t_off;
+    g.t_bytes = q.t_bytes;
     const uint32_t grid = batch < p->ctas ? (uint32_t)batch : p->ctas;
-    if (q.tw && q.dw == 64)
-        k_mul_quad_tc_tw<64><<<grid, kThreadsTw, q.smem, st>>>(g);
+    if (q.tall && q.dw == 32)
+        k_mul_quad_tc_tall<32><<<grid, kThreadsTall, q.smem, st>>>(g);
+    else if (q.tall)
+        k_mul_quad_tc_tall<64><<<grid, kThreadsTall, q.smem, st>>>(g);
     else if (q.tw)
-        k_mul_quad_tc_tw<128><<<grid, kThreadsTw, q.smem, st>>>(g);
+        k_mul_quad_tc_tw<<<grid, kThreadsTw, q.smem, st>>>(g);
     else
         k_mul_quad_tc<<<grid, kThreads, q.smem, st>>>(g);
     return cudaGetLastError();

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 SHAPES = {
     "bn_mul_quad": [(1, 1, 5), (7, 3, 9), (33, 17, 20), (128, 128, 41), (513, 257, 6), (1000, 999, 4),
                     (32, 32, 4864), (64, 9, 5000), (13, 6, 4900)],             # the last three: one per thread
-    "bn_mul_quad_tc": [(1, 1, 5), (100, 37, 7), (1024, 1024, 3), (4224, 100, 2)],
+    "bn_mul_quad_tc": [(1, 1, 5), (100, 37, 7), (1024, 1024, 3), (1500, 700, 3), (2048, 2048, 3), (4224, 100, 2)],
     "bn_mul_ntt3": [(5, 3, 9), (512, 512, 6), (8192, 8192, 2)],
     "ntt64": [(3, 2, 9), (500, 600, 7), (3000, 2500, 3), (8192, 8192, 2)],      # unsplit, S = 2, S = 4
     "crt": [(3, 2, 9), (1024, 1024, 5), (8192, 5000, 2), (8192, 8192, 2)],      # unsplit, S = 2

@@ -17,7 +17,9 @@ SHAPES = [(1, 1), (1, 2), (2, 1), (3, 5), (31, 33), (32, 32), (33, 31), (64, 64)
           (3, 100), (128, 128), (129, 130), (500, 20), (777, 1000), (1024, 1024), (2047, 2049),
           (2048, 2048), (4096, 4096), (4097, 4000), (5000, 3001), (8192, 8192), (8192, 1),
           (1, 8192), (8192, 100), (100, 8192), (4097, 4097), (4500, 4500), (6000, 5000),
-          (8000, 300), (8191, 8191), (8192, 4097), (7777, 8000), (8192, 32), (8192, 33)]
+          (8000, 300), (8191, 8191), (8192, 4097), (7777, 8000), (8192, 32), (8192, 33),
+          # up to 64 blocks: the Toeplitz-rows form, one chunk (<= 32 blocks) or two (64 blocks)
+          (2048, 1), (1, 2048), (1500, 1500), (1025, 1023), (1000, 2048), (2048, 2047), (2000, 64)]
 
 
 def _tc(a, b):

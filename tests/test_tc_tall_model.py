@@ -1,0 +1,126 @@
+"""CPU model of the tensor-core schoolbook's form up to 64K bits, where every
+MMA's A operand is a 128-row window of one tall Toeplitz matrix
+T[R][c] = b-byte (R - c), c < 16, kept in shared memory (Section 3, Eq. 1's
+column sums on bytes).
+
+It checks the indexing the kernel relies on, not the oracle: K-chunk kk of
+W_J (W_J[r][c] = b-byte (128 J + r - c)) equals rows R0 = 128 J - 16 kk ..
+R0 + 127 of T for every step of every chunk, from the chunk's first stored
+row 128 J0 - 112; the row builder's byte selection (five words of b's bytes,
+byte_perm with the kernel's selector) yields exactly b-bytes R, R-1, ..., R-15
+in its eight fp16 pairs without reading outside the staged words; and the
+double-buffered shared-memory layout stays inside the 227 KB a CTA may hold.
+A planted slip (the window one K-chunk off, the selector one byte off)
+must fail."""
+import numpy as np
+import pytest
+
+BLK, LEAD, ROWB = 128, 112, 32
+SMEM_MAX = 227 * 1024
+
+
+def byte_perm(x, y, s):
+    v = (y << 32) | x
+    return sum(((v >> (8 * ((s >> (4 * i)) & 7))) & 0xFF) << (8 * i) for i in range(4))
+
+
+def staged_b(bbytes, mb):
+    """braw: b's bytes at byte offset 128, zeros around, 32 (mb + 2) + 4 words."""
+    words = 32 * (mb + 2) + 4
+    raw = np.zeros(4 * words, np.int64)
+    raw[128:128 + bbytes.size] = bbytes
+    w = [int(raw[4 * i]) | int(raw[4 * i + 1]) << 8 | int(raw[4 * i + 2]) << 16 | int(raw[4 * i + 3]) << 24
+         for i in range(words)]
+    return w
+
+
+def tall_row(braw, R, slip=0):
+    """The kernel's row builder: returns the 16 bytes (c = 0..15) it converts."""
+    e = 113 + R
+    assert e >= 0
+    w0, sh = e >> 2, e & 3
+    assert w0 + 4 < len(braw), "reads past the staged words"
+    wv = braw[w0:w0 + 5]
+    sel = (sh + 3 + slip) | ((sh + 2) << 4) | ((sh + 1) << 8) | (sh << 12)
+    out = []
+    for m in range(4):
+        x = byte_perm(wv[3 - m], wv[4 - m], sel)
+        out += [x & 0xFF, (x >> 8) & 0xFF, (x >> 16) & 0xFF, (x >> 24) & 0xFF]
+    return out
+
+
+def chunk_of(mb, ma16, na_limbs, nb_limbs):
+    """Steps per T buffer (one group: half the D slots) and the end of the
+    shared-memory layout, as the kernel's geometry lays them out."""
+    ma = -(-na_limbs // 32)
+    xs = (2 * ma + (ma16 - ma)) * 16
+    nout = na_limbs + nb_limbs
+    dw = 32 if ma16 <= 32 else 64
+    dslots = 512 // dw
+    group = dslots // 2
+    xbytes = (16 * xs + 1023) & ~1023
+    t_bytes = ((BLK * group + LEAD) * ROWB + 1023) & ~1023
+    off = 2 * xbytes + 2 * t_bytes
+    off += ((4 * (nout + (nout >> 4)) + 16 + 15) & ~15) + 8 * 256
+    off += 2 * 4 * (32 * (mb + 2) + 4)
+    off = (off + 15) & ~15
+    off += 4 * 16
+    off = (off + 15) & ~15
+    end = off + 8 * (2 * dslots + 13) + 16
+    assert (BLK * group + LEAD) * ROWB <= t_bytes
+    return group, end
+
+
+@pytest.mark.parametrize("nb_limbs", [1, 31, 32, 33, 1000, 1024, 2048])
+def test_windows_of_T_are_the_K_chunks_of_W(nb_limbs):
+    rng = np.random.default_rng(nb_limbs)
+    bb = rng.integers(0, 256, 4 * nb_limbs)
+    mb = -(-bb.size // BLK)
+    bpad = np.zeros(BLK * (mb + 3), np.int64)
+    bpad[BLK:BLK + bb.size] = bb                       # b-byte i at BLK + i
+    na_limbs = max(nb_limbs, 1024 if nb_limbs <= 1024 else 2048)
+    ma16 = (-(-na_limbs // 32) + 15) & ~15
+    chunk, end = chunk_of(mb, ma16, na_limbs, nb_limbs)
+    assert end <= SMEM_MAX
+    braw = staged_b(bb, mb)
+    r = np.arange(BLK)[:, None]
+    c = np.arange(16)[None, :]
+    for J0 in range(0, mb + 1, chunk):
+        J1 = min(mb + 1, J0 + chunk)
+        Rbase, nrows = BLK * J0 - LEAD, BLK * (J1 - J0) + LEAD
+        T = np.array([tall_row(braw, Rbase + i) for i in range(nrows)])
+        Rs = Rbase + np.arange(nrows)[:, None]
+        assert np.array_equal(T, bpad[BLK + Rs - c] * ((Rs - c) >= 0))
+        for J in range(J0, J1):
+            for kk in range(8):
+                i0 = BLK * (J - J0) + LEAD - 16 * kk
+                assert 0 <= i0 and i0 + BLK <= nrows and i0 % 8 == 0
+                W_chunk = bpad[BLK + BLK * J + r - 16 * kk - c]
+                assert np.array_equal(T[i0:i0 + BLK], W_chunk)
+
+
+def test_planted_slips_fail():
+    bb = np.random.default_rng(1).integers(1, 256, 4 * 64)
+    mb = 2
+    braw = staged_b(bb, mb)
+    bpad = np.zeros(BLK * (mb + 3), np.int64)
+    bpad[BLK:BLK + bb.size] = bb
+    R = 200
+    want = [int(bpad[BLK + R - cc]) for cc in range(16)]
+    assert tall_row(braw, R) == want
+    assert tall_row(braw, R, slip=1) != want
+    # a window one K-chunk off is another matrix
+    T = np.array([tall_row(braw, -LEAD + i) for i in range(BLK * 3 + LEAD)])
+    r = np.arange(BLK)[:, None]
+    c = np.arange(16)[None, :]
+    J, kk = 1, 3
+    i0 = BLK * J + LEAD - 16 * (kk + 1)
+    assert not np.array_equal(T[i0:i0 + BLK], bpad[BLK + BLK * J + r - 16 * kk - c])
+
+
+@pytest.mark.parametrize("limbs", [32 * k for k in range(1, 65)])
+def test_layout_fits_at_every_size(limbs):
+    ma = mb = -(-limbs // 32)
+    ma16 = (ma + 15) & ~15
+    chunk, end = chunk_of(mb, ma16, limbs, limbs)
+    assert chunk >= 1 and end <= SMEM_MAX
