@@ -241,6 +241,35 @@ def imad_peak(torch, bn, dev):
             "probe": res}
 
 
+MMA_PROBE_CASES = ((32, 1, 1 << 30), (32, 2, 1 << 30), (32, 4, 1 << 30), (32, 8, 1 << 30), (32, 8, 8),
+                   (64, 4, 8), (64, 8, 1 << 30), (128, 2, 8), (128, 4, 1 << 30), (256, 2, 1 << 30))
+
+
+def mma_probe(torch, bn, dev):
+    """SM clocks per tensor-core MMA (kind::f16, M = 128, K = 16, N = n, operands
+    in shared memory at moving windows) for a number of independent
+    accumulation chains, each restarted every chain_len of its MMAs; one CTA
+    per SM issues them from one thread (bn_probe_mma_throughput)."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = []
+    for n, chains, chain_len in MMA_PROBE_CASES:
+        iters = 16384
+        bn.bn_probe_mma_throughput(n, chains, chain_len, 64, sms, status)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bn.bn_probe_mma_throughput(n, chains, chain_len, iters, sms, status)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out.append({"n": n, "chains": chains, "chain_len": chain_len if chain_len < (1 << 30) else None,
+                    "clocks_per_mma": round(ms * 1e-3 * SM_MAX_MHZ_NOMINAL * 1e6 / iters, 1)})
+    if int(status.item()):
+        raise RuntimeError("the tensor-core probe's wait timed out")
+    return out
+
+
 def kernel_traffic(op_label: str):
     """DRAM bytes per launch from the committed ncu capture of this op, if none
     of the kernel's source files changed since the capture (else None)."""
@@ -337,6 +366,7 @@ def run_gpu(args, rank, world, local_rank):
         step()
     torch.cuda.synchronize()
     peak_info = imad_peak(torch, bn, dev) if rank == 0 else None
+    mma_info = mma_probe(torch, bn, dev) if rank == 0 and not args.quick else None
 
     evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
             for _ in ops] for _ in range(args.steps)]
@@ -412,7 +442,7 @@ def run_gpu(args, rank, world, local_rank):
         "config": workload_config(ops, world),
         "add_gbs": round(add_gbs, 1) if add_gbs else None,
         "roofline": roof, "rooflines": rooflines, "breakdown": rows,
-        "imad_probe": peak_info, "clocks": clocks, "gpu_launches": gpu_launches,
+        "imad_probe": peak_info, "mma_probe": mma_info, "clocks": clocks, "gpu_launches": gpu_launches,
         "e2e": e2e, "cpu_baseline": cpu, "impl": "ours", "skipped_ops": skipped,
         "mixed": mixed, "serving": serving, "fused": fused, "forms": forms,
     }

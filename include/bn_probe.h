@@ -1,5 +1,5 @@
 /*
- * bn_probe.h - measurement helper for the integer-multiply roofline.
+ * bn_probe.h - measurement helpers for the integer-multiply and tensor-core rooflines.
  *
  * The multiplication kernels are bound by the integer multiply-add pipe, and
  * no peak for it is recorded for this GPU.  This entry point runs a
@@ -35,6 +35,20 @@ typedef enum bn_probe_kind {
  * not a multiple of 32, unknown kind), BN_ECUDA. */
 bn_status bn_probe_int_throughput(int kind, uint32_t blocks, uint32_t threads, uint32_t iters,
                                   uint32_t *out, uint64_t *ops_per_thread, void *stream);
+
+/* Enqueue the tensor-core chain probe: `ctas` CTAs (one per SM: each holds
+ * 130 KB of shared memory) each issue `iters` MMAs (tcgen05.mma kind::f16,
+ * M = 128, K = 16, N = n, operands in shared memory at windows that move with
+ * every MMA, as the tensor-core schoolbook's do) from one thread, round-robin
+ * over `chains` accumulators of n tensor-memory columns, each restarted
+ * (accumulate = 0) every `chain_len` of its MMAs.  Timing it gives the SM
+ * clocks per MMA of a given number of independent accumulation chains.  The
+ * operands are zero.  *status (device memory) is set to 1 if the wait for the
+ * MMAs timed out (after 2 s; the kernel then frees its tensor memory and
+ * returns).  Errors: BN_EINVAL (null status, zero sizes, n not a multiple of
+ * 16 in [16, 256], n * chains > 512), BN_ECUDA. */
+bn_status bn_probe_mma_throughput(uint32_t n, uint32_t chains, uint32_t chain_len, uint32_t iters,
+                                  uint32_t ctas, uint32_t *status, void *stream);
 
 #ifdef __cplusplus
 }

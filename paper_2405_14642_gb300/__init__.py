@@ -29,11 +29,11 @@ from ._binding import (COMPLETION_DTYPE, REQUEST_DTYPE, Server, device_to_host,
                        BN_OP_MUL_NTT_CRT, BN_OP_MUL_NTT3, BN_OP_MUL_QUAD, BN_OP_MUL_QUAD_TC, BN_ETIMEOUT, BnError, Plan, bn_add,
                        bn_mul, bn_mul_ntt, bn_mul_ntt3, bn_mul_quad_tc, bn_tc_check, bn_tc_wait_selftest,
                        bn_add6, bn_mul_low, bn_mul_ntt_noalloc, bn_mul_quad, bn_poly,
-                       bn_probe_int_throughput, library_path, load)
+                       bn_probe_int_throughput, bn_probe_mma_throughput, library_path, load)
 
 __all__ = ["bn_add", "bn_mul_quad", "bn_mul_ntt", "Plan", "BnError", "load", "library_path",
            "BN_OP_ADD", "BN_OP_MUL_QUAD", "BN_OP_MUL_NTT64", "BN_OP_MUL_NTT_CRT",
-           "BN_ADD_MAX_LIMBS", "BN_MUL_MAX_LIMBS", "bn_probe_int_throughput",
+           "BN_ADD_MAX_LIMBS", "BN_MUL_MAX_LIMBS", "bn_probe_int_throughput", "bn_probe_mma_throughput",
            "bn_mul_ntt_noalloc", "Batch", "BATCH_ITEM_DTYPE", "BN_BATCH_AUTOTUNE", "BN_BATCH_PLAIN", "BN_BATCH_PLAIN_CLASSES",
            "BN_OP_MUL_AUTO", "Server", "REQUEST_DTYPE", "COMPLETION_DTYPE", "device_to_host",
            "bn_mul_low", "bn_poly", "bn_add6", "bn_mul_ntt3", "BN_OP_MUL_NTT3", "bn_mul",

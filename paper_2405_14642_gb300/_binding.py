@@ -130,6 +130,7 @@ def load(build_if_missing: bool = False):
         "bn_batch_destroy": ([vp], st),
         "bn_probe_int_throughput": ([ctypes.c_int, u32, u32, u32, u32p,
                                      ctypes.POINTER(ctypes.c_uint64), vp], st),
+        "bn_probe_mma_throughput": ([u32, u32, u32, u32, u32, u32p, vp], st),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -325,6 +326,14 @@ def bn_probe_int_throughput(kind: int, blocks: int, threads: int, iters: int, ou
     _check(lib.bn_probe_int_throughput(kind, blocks, threads, iters, _ptr(out), ctypes.byref(ops),
                                        _stream_handle(stream, out.device)), "bn_probe_int_throughput")
     return ops.value
+
+
+def bn_probe_mma_throughput(n: int, chains: int, chain_len: int, iters: int, ctas: int, status,
+                            stream=None) -> None:
+    """Enqueue the tensor-core chain probe; status: a 1-element int32 device tensor."""
+    lib = load()
+    _check(lib.bn_probe_mma_throughput(n, chains, chain_len, iters, ctas, _ptr(status),
+                                       _stream_handle(stream, status.device)), "bn_probe_mma_throughput")
 
 
 class Plan:

@@ -1,7 +1,9 @@
-// Register-only integer multiply-add throughput probe (include/bn_probe.h).
+// Throughput probes (include/bn_probe.h): register-only integer multiply-adds,
+// and chains of small tensor-core MMAs.
 #include <cuda_runtime.h>
 
 #include "../../include/bn_probe.h"
+#include "tc_device.cuh"
 
 namespace {
 
@@ -79,6 +81,68 @@ __global__ void __launch_bounds__(1024) k_probe(uint32_t iters, uint32_t *out) {
     if ((threadIdx.x & 31) == 0) atomicXor(out + blockIdx.x, s);
 }
 
+
+// One CTA per SM; one elected thread of warp 0 issues `iters` MMAs of
+// kind::f16, M = 128, K = 16, N = n over `chains` accumulators of n columns
+// (MMA i goes to accumulator i % chains and restarts it, accumulate = 0,
+// every chain_len MMAs of that accumulator), A and B from shared memory
+// windows that move with every MMA as the tensor-core schoolbook's do (A: a
+// 128-row window of a tall K-major matrix stepping 512 bytes; B: an n-row
+// window stepping 16 bytes with a 1 KB K-chunk stride).  The operands are
+// zero: only the time matters.  One commit at the end; the wait for it is
+// bounded, and a timeout sets *status.
+constexpr uint32_t kProbeA = 98304, kProbeB = 32768, kProbeSmem = kProbeA + kProbeB + 128;
+
+__global__ void __launch_bounds__(128, 1) k_probe_mma(uint32_t n, uint32_t chains, uint32_t chain_len,
+                                                      uint32_t iters, uint32_t ncols, uint32_t *status) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kProbeA + kProbeB);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(sm + kProbeA + kProbeB + 64);
+    for (uint32_t i = threadIdx.x; i < (kProbeA + kProbeB) / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
+    const uint32_t warp = threadIdx.x >> 5;
+    if (warp == 0) bn::tc::tmem_alloc(slot, ncols);
+    if (threadIdx.x == 0) {
+        bn::tc::mbar_init(bar, 1);
+        bn::tc::fence_mbar_init();
+    }
+    bn::tc::fence_proxy_async();
+    bn::tc::fence_before_sync();
+    __syncthreads();
+    bn::tc::fence_after_sync();
+    const uint32_t taddr = *slot;
+    if (warp == 0) {
+        if (bn::tc::elect_one()) {
+            const uint32_t s0 = bn::tc::smem_u32(sm);
+            const uint64_t ad = bn::tc::smem_desc(s0, 128, 256), bd = bn::tc::smem_desc(s0 + kProbeA, 1024, 128);
+            const uint32_t idesc = bn::tc::idesc_f16_f32(128, n);
+            // counters stepped without divisions, so that issuing stays well ahead of the pipe:
+            // A window ia of 185 positions x 512 bytes (the last ends at 94208 + 4096 = kProbeA),
+            // B window ib of 32 positions x 16 bytes (n <= 256 rows: 4 KB per K-chunk, ends below
+            // kProbeB), accumulator c, and r = this round's place in its chain
+            uint32_t c = 0, r = 0, ia = 0, ib = 0;
+            for (uint32_t i = 0; i < iters; ++i) {
+                bn::tc::mma_f16_ss(taddr + n * c, ad + 32 * ia, bd + ib, idesc, r != 0);
+                ia = ia == 184 ? 0 : ia + 1;
+                ib = (ib + 1) & 31;
+                if (++c == chains) {
+                    c = 0;
+                    r = r + 1 == chain_len ? 0 : r + 1;
+                }
+            }
+            bn::tc::mma_commit(bar);
+            if (!bn::tc::mbar_wait(bar, 0, 2000000000ull)) {
+                atomicExch(status, 1u);
+                bn::tc::mbar_wait(bar, 0, 2000000000ull);  // the MMAs in flight, bounded again
+            }
+        }
+        __syncwarp();
+    }
+    bn::tc::fence_before_sync();
+    __syncthreads();
+    bn::tc::fence_after_sync();
+    if (warp == 0) bn::tc::tmem_dealloc(taddr, ncols);
+}
 }  // namespace
 
 extern "C" bn_status bn_probe_int_throughput(int kind, uint32_t blocks, uint32_t threads,
@@ -95,5 +159,17 @@ extern "C" bn_status bn_probe_int_throughput(int kind, uint32_t blocks, uint32_t
     default: return BN_EINVAL;
     }
     *ops_per_thread = (uint64_t)iters * (kind == BN_PROBE_MAC_CHAIN ? 32u : 8u);
+    return cudaGetLastError() == cudaSuccess ? BN_OK : BN_ECUDA;
+}
+
+extern "C" bn_status bn_probe_mma_throughput(uint32_t n, uint32_t chains, uint32_t chain_len, uint32_t iters,
+                                             uint32_t ctas, uint32_t *status, void *stream) {
+    if (!status || ctas == 0 || iters == 0 || chains == 0 || chain_len == 0) return BN_EINVAL;
+    if (n < 16 || n > 256 || n % 16 || n * chains > 512) return BN_EINVAL;
+    uint32_t ncols = 32;
+    while (ncols < n * chains) ncols <<= 1;
+    if (cudaFuncSetAttribute(k_probe_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kProbeSmem) != cudaSuccess)
+        return BN_ECUDA;
+    k_probe_mma<<<ctas, 128, kProbeSmem, (cudaStream_t)stream>>>(n, chains, chain_len, iters, ncols, status);
     return cudaGetLastError() == cudaSuccess ? BN_OK : BN_ECUDA;
 }

@@ -115,3 +115,18 @@ def test_tc_bounded_wait_gives_up():
     assert status == bn.BN_ETIMEOUT
     assert elapsed < 5.0  # not the second waiter's own 10 s limit
     bn.bn_tc_check()      # the self-test leaves the flag clear
+
+
+def test_mma_probe_runs_and_checks_arguments():
+    """The tensor-core chain probe (bn_probe.h) completes within its bounded
+    wait and refuses shapes that do not fit tensor memory or the MMA."""
+    torch = torch_cuda()
+    import paper_2405_14642_gb300 as bn
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for n, chains, chain_len in [(32, 8, 8), (64, 4, 1000), (256, 2, 3), (16, 1, 1)]:
+        bn.bn_probe_mma_throughput(n, chains, chain_len, 300, 4, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    for bad in [(64, 16, 8), (24, 1, 8), (272, 1, 8), (32, 0, 8), (32, 1, 0)]:
+        with pytest.raises(bn.BnError):
+            bn.bn_probe_mma_throughput(*bad, 10, 1, status)
