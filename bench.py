@@ -630,10 +630,34 @@ def run_mixed(args, torch, bn, dev, rank):
     identical = bool(torch.equal(results["batched"], results["plain_class"])
                      and torch.equal(results["batched"], results["plain_item"]))
     del results
+    # The graph's fixed cost: the same kind of batch at 1/10 and 1/100 of the
+    # items (every class still present at 1/100 here); a straight line through
+    # (items, ms) meets the axis at the cost of launching the per-class
+    # persistent kernels with nothing to do, which is all that one kernel over
+    # every class could save on the launch structure.
+    scaling = [{"items": len(items), "ms": out["batched"]["ms"], "classes": out["batched"]["classes"]}]
+    for every in (10, 100):
+        sub = items[::every]
+        batch = bn.Batch(sub, bn.BN_BATCH_AUTOTUNE)
+        batch.execute(ta, tb, tc, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.mixed_steps):
+            batch.execute(ta, tb, tc, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        scaling.append({"items": len(sub), "ms": round(e0.elapsed_time(e1) / args.mixed_steps, 3),
+                        "classes": batch.info["classes"]})
+        batch.close()
+    xs = np.array([r["items"] for r in scaling], float)
+    ys = np.array([r["ms"] for r in scaling], float)
+    slope, icpt = np.polyfit(xs, ys, 1)
     return {"workload": f"{len(items)} ops, 70% mul (auto quad/NTT) / 30% add, limbs log-uniform "
                         "32..8192 per operand, 5% edge cases",
             "batched": out["batched"], "plain_class": out["plain_class"],
             "plain_item": out["plain_item"],
+            "graph_scaling": scaling, "graph_fixed_ms": round(float(icpt), 4),
             "speedup_vs_class": round(out["plain_class"]["ms"] / out["batched"]["ms"], 2),
             "speedup_vs_item": round(out["plain_item"]["ms"] / out["batched"]["ms"], 2),
             "results_identical": identical}
@@ -902,6 +926,7 @@ def compact(full: dict) -> dict:
                         "plain_item_ms": m["plain_item"]["ms"],
                         "speedup_vs_class": m["speedup_vs_class"],
                         "speedup_vs_item": m["speedup_vs_item"],
+                        "graph_fixed_ms": m.get("graph_fixed_ms"),
                         "results_identical": m["results_identical"]}
     sv = full.get("serving")
     if sv:
