@@ -793,13 +793,16 @@ __global__ void __launch_bounds__(kThreadsTall, 1) k_mul_quad_tc_tall(TcArgs g) 
                         ad[h] = tc::smem_desc(t_s + (kBlk * hh + kTallLead) * kTallRowBytes, kTallLbo, kTallSbo);
                         bd[h] = tc::smem_desc(x_s + (g.ma - J - hh) * 16, g.xs, 128);
                     }
-                    uint64_t bk = 0;
+                    // step by step, K-chunks from 7 down to 0: each MMA's T window sits 16 rows
+                    // above the one before, also from one step to the next, so consecutive MMAs
+                    // share 7/8 of their A operand
 #pragma unroll
-                    for (uint32_t kk = 0; kk < 8; ++kk, bk += bstep)
+                    for (uint32_t h = 0; h < kC; ++h) {
+                        if (h >= n) break;
 #pragma unroll
-                        for (uint32_t h = 0; h < kC; ++h)
-                            if (h < n)
-                                tc::mma_f16_ss(dt[h], ad[h] - kk * (16 * kTallRowBytes / 16), bd[h] + bk, idesc, 1);
+                        for (int kk = 7; kk >= 0; --kk)
+                            tc::mma_f16_ss(dt[h], ad[h] - kk * (16 * kTallRowBytes / 16), bd[h] + kk * bstep, idesc, 1);
+                    }
                     for (uint32_t h = 0; h < n; ++h) tc::mma_commit(&dfull[(gs + h) % kDS]);
                     tc::mma_commit(&tempty[tb]);                // T buffer tb may be rebuilt
                     if (J + n == S) tc::mma_commit(&xempty[xb]);  // XX buffer xb may be restaged
