@@ -33,8 +33,9 @@
 // warps per group of 32 tensor-memory lanes, each a quarter of D's columns)
 // and publish to a per-CTA scratch row.  Three kernels, by the width of D:
 //  * k_mul_quad_tc (ma > 128): two D slots of 256 columns; warps 1-7 build
-//    W_J in shared memory (the MMA's A operand) into one of two slots, warps
-//    8-23 read D, warp 0 issues the MMAs;
+//    each step's Toeplitz rows (below) in shared memory, whose windows are the
+//    MMAs' A operands, into one of two slots; warps 8-23 read D, warp 0 issues
+//    the MMAs;
 //  * k_mul_quad_tc_tw (64 < ma16 <= 128): W in tensor memory, built by the 16
 //    epilogue warps; three D slots of 128 columns and two W slots;
 //  * k_mul_quad_tc_tall (ma16 <= 64): every MMA's A operand is a window of
@@ -65,8 +66,7 @@ constexpr uint32_t kEpiWarps = 16;   // four per group of 32 tensor-memory lanes
 constexpr uint32_t kBlk = 128;       // bytes per block: rows of W, K of a step
 constexpr uint32_t kTmemCols = 512;  // the D slots
 constexpr uint32_t kWSlotsMax = 4, kDSlotsMax = 4;  // mbarrier room for any of the kernels
-constexpr uint32_t kWBytes = 128 * 128 * 2;     // one W_J in fp16: 16 K-chunks x 16 row groups x 128 B
-constexpr uint32_t kWLbo = 2048, kWSbo = 128;   // W: K-chunk stride, 8-row-group stride
+constexpr uint32_t kTSlotBytes = 8192;          // one step's 240 Toeplitz rows (7.5 KB) in k_mul_quad_tc
 constexpr uint64_t kWaitNs = 1000000000ull;     // 1 s per wait
 constexpr uint32_t kMinSmem = 116 * 1024;       // one CTA per SM (the whole tensor memory each)
 
@@ -84,34 +84,10 @@ struct TcArgs {
     uint32_t t_off, t_bytes;  // k_mul_quad_tc_tall: the two T buffers
 };
 
-// Row r of W_J, words 16 u .. 16 u + 15 (K-chunks 4 u .. 4 u + 3), into the
-// W slot at `w` (shared memory, the MMA's A operand: K-major without swizzle,
-// the 16-byte piece of row r and K-chunk q at (r / 8) * 128 + q * 2048 +
-// (r % 8) * 16).  Word k of row r holds the fp16 pair (W_J[r][2k], W_J[r][2k+1])
-// = (b-byte (v - 2k), b-byte (v - 2k - 1)), v = 128 J + r; braw holds b's
-// bytes at offset 128 + index, zero outside b (bytes are denser in shared
-// memory than fp16, which halves these reads).
-__device__ __forceinline__ void build_w(const uint32_t *braw, uint32_t J, uint32_t r, uint32_t u, uint8_t *w) {
-    const uint32_t e = 97 + 128 * J + r - 32 * u;  // lowest byte offset this thread reads
-    const uint32_t *bw = braw + (e >> 2);
-    const uint32_t sh = e & 3u;
-    uint32_t wv[9];
-#pragma unroll
-    for (int j = 0; j < 9; ++j) wv[j] = bw[j];
-    // words 2g, 2g + 1: bytes at offsets e + 31 - 4g, e + 30 - 4g, e + 29 - 4g, e + 28 - 4g
-    const uint32_t sel = (sh + 3) | ((sh + 2) << 4) | ((sh + 1) << 8) | (sh << 12);
-    uint8_t *row = w + (r >> 3) * kWSbo + (r & 7) * 16 + 4 * u * kWLbo;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const uint32_t r0 = __byte_perm(wv[7 - 2 * q], wv[8 - 2 * q], sel);
-        const uint32_t r1 = __byte_perm(wv[6 - 2 * q], wv[7 - 2 * q], sel);
-        *reinterpret_cast<uint4 *>(row + q * kWLbo) =
-            make_uint4(tc::bytes01_f16x2(r0), tc::bytes23_f16x2(r0), tc::bytes01_f16x2(r1), tc::bytes23_f16x2(r1));
-    }
-}
-
-// Quarter u of row r of W_J (words 16 u .. 16 u + 15, the same values as
-// build_w) into registers, for a store to tensor memory.
+// Quarter u of row r of W_J (words 16 u .. 16 u + 15) into registers, for a
+// store to tensor memory.  Word k of row r holds the fp16 pair (W_J[r][2k],
+// W_J[r][2k+1]) = (b-byte (v - 2k), b-byte (v - 2k - 1)), v = 128 J + r; braw
+// holds b's bytes at offset 128 + index, zero outside b.
 __device__ __forceinline__ void build_w_regs(const uint32_t *braw, uint32_t J, uint32_t r, uint32_t u,
                                              uint32_t (&out)[16]) {
     const uint32_t e = 97 + 128 * J + r - 32 * u;  // lowest byte offset this thread reads
@@ -132,33 +108,6 @@ __device__ __forceinline__ void build_w_regs(const uint32_t *braw, uint32_t J, u
     }
 }
 
-// build_w for the quarter rows x0 and x1 (row = x & 127, quarter = x >> 7),
-// both rows' source words loaded before either is converted and stored.
-__device__ __forceinline__ void build_w2(const uint32_t *braw, uint32_t J, uint32_t x0, uint32_t x1, uint8_t *w) {
-    uint32_t wv[2][9], sel[2];
-    uint8_t *row[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const uint32_t x = i ? x1 : x0, r = x & 127, u = x >> 7;
-        const uint32_t e = 97 + 128 * J + r - 32 * u;
-        const uint32_t *bw = braw + (e >> 2);
-        const uint32_t sh = e & 3u;
-#pragma unroll
-        for (int j = 0; j < 9; ++j) wv[i][j] = bw[j];
-        sel[i] = (sh + 3) | ((sh + 2) << 4) | ((sh + 1) << 8) | (sh << 12);
-        row[i] = w + (r >> 3) * kWSbo + (r & 7) * 16 + 4 * u * kWLbo;
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t r0 = __byte_perm(wv[i][7 - 2 * q], wv[i][8 - 2 * q], sel[i]);
-            const uint32_t r1 = __byte_perm(wv[i][6 - 2 * q], wv[i][7 - 2 * q], sel[i]);
-            *reinterpret_cast<uint4 *>(row[i] + q * kWLbo) = make_uint4(
-                tc::bytes01_f16x2(r0), tc::bytes23_f16x2(r0), tc::bytes01_f16x2(r1), tc::bytes23_f16x2(r1));
-        }
-}
-
 // Every D starts at 2^23 (a first MMA multiplies 2048 by 4096 into each
 // element); the byte products add an integer v < 2^23, so D = 2^23 + v is
 // exact in f32 and, having exponent 23, its bit pattern is 0x4b000000 + v.
@@ -175,16 +124,50 @@ constexpr uint32_t kBiasBytes = 256;  // each bias operand: one core matrix per 
     BN_TC_FLUSH(x) BN_TC_FLUSH(x + 1) BN_TC_FLUSH(x + 2) BN_TC_FLUSH(x + 3) BN_TC_FLUSH(x + 4) \
         BN_TC_FLUSH(x + 5) BN_TC_FLUSH(x + 6) BN_TC_FLUSH(x + 7)
 
+// ---- Toeplitz rows ----------------------------------------------------------
+//
+// K-chunk kk of W_J (its columns 16 kk .. 16 kk + 15) is the 128-row window
+// starting at row R0 = 128 J - 16 kk of one tall matrix T[R][c] = b-byte (R - c),
+// c < 16:  W_J[r][16 kk + c] = b-byte (128 J + r - 16 kk - c) = T[R0 + r][c].
+// An MMA can therefore take its A operand from a window of T in shared memory
+// (a descriptor offset) instead of a whole W_J: a step needs T's 240 rows
+// 128 J - 112 .. 128 J + 127 (7.5 KB) where W_J takes 32 KB, and consecutive
+// K-chunks' windows overlap by 7/8.  Layout of the A operand (K-major, no
+// swizzle): row i, K-half h at (i / 8) * 256 + h * 128 + (i % 8) * 16, i.e.
+// LBO = 128, SBO = 256.
+constexpr uint32_t kTallRowBytes = 32;  // 16 fp16
+constexpr uint32_t kTallLbo = 128, kTallSbo = 256;
+constexpr uint32_t kTallLead = 112;     // rows of T below 128 J that step J's window reaches
+
+// Row R of T (words k = 0..7: the fp16 pair (b-byte (R - 2k), b-byte (R - 2k - 1)))
+// from braw (b's bytes at offset 128 + index, zero outside b; R >= -112).
+__device__ __forceinline__ void tall_row(const uint32_t *braw, int32_t R, uint32_t (&w)[8]) {
+    const uint32_t e = (uint32_t)(113 + R);  // braw byte of b-byte (R - 15)
+    const uint32_t *bw = braw + (e >> 2);
+    const uint32_t sh = e & 3u;
+    uint32_t wv[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) wv[j] = bw[j];
+    // x_m holds b-bytes R - 4m, R - 4m - 1, R - 4m - 2, R - 4m - 3 (bytes 0..3)
+    const uint32_t sel = (sh + 3) | ((sh + 2) << 4) | ((sh + 1) << 8) | (sh << 12);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const uint32_t x = __byte_perm(wv[3 - m], wv[4 - m], sel);
+        w[2 * m] = tc::bytes01_f16x2(x);
+        w[2 * m + 1] = tc::bytes23_f16x2(x);
+    }
+}
+
 // Products whose longer operand has more than 128 blocks: two D slots of
 // SLOTC = 256 columns; an epilogue warp owns 64 columns of its 32 lanes.
 __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
     constexpr uint32_t SLOTC = 256;
     constexpr uint32_t kDS = kTmemCols / SLOTC;  // D slots
     constexpr uint32_t kCPW = SLOTC / 128;       // 32-column chunks per epilogue warp
-    constexpr uint32_t kWS = 2;                  // W slots (two leave room for XX at 256K bits)
+    constexpr uint32_t kWS = 2;                  // slots of Toeplitz rows
     extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t *X = sm;  // XX and the W slots double as the normalisation's staging row
-    uint8_t *W = sm + g.w_off;
+    uint8_t *X = sm;  // XX and the T slots double as the normalisation's staging row
+    uint8_t *W = sm + g.w_off;  // two slots of Toeplitz rows
     uint32_t *braw = reinterpret_cast<uint32_t *>(sm + g.braw_off);
     uint64_t *spill = reinterpret_cast<uint64_t *>(sm + g.spill_off);
     uint32_t *flags = reinterpret_cast<uint32_t *>(sm + g.flags_off);
@@ -252,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
             // they stay in uniform registers); one elected lane issues the
             // MMAs and commits them
             const uint32_t idesc = tc::idesc_f16_f32(128, g.ma16);
-            const uint64_t bstep = (2 * g.xs) >> 4, astep = (2 * kWLbo) >> 4;
+            const uint64_t bstep = (2 * g.xs) >> 4;
             for (uint32_t J = 0; J < S; ++J, ++gs) {
                 const uint32_t k = gs % kWS, d = gs % kDS, ud = gs / kDS;
                 bool ok = tc::mbar_wait_spin(&wfull[k], (gs / kWS) & 1u, kWaitNs, abortf);
@@ -263,23 +246,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
                 }
                 tc::fence_after_sync();
                 const uint32_t dt = tbase + SLOTC * d;
-                const uint64_t ad = tc::smem_desc(w_s + k * kWBytes, kWLbo, kWSbo);
+                // T's rows of step J in slot k; K-chunk kk's window from row 112 - 16 kk
+                const uint64_t ad = tc::smem_desc(w_s + k * kTSlotBytes + kTallLead * kTallRowBytes, kTallLbo, kTallSbo);
                 const uint64_t bd = tc::smem_desc(x_s + (g.ma - J) * 16, g.xs, 128);  // XX from block ma - J
                 // the bias operands' core matrix repeats over all row groups (stride 0)
                 const uint64_t cad = tc::smem_desc(x_s + g.ca_off, 128, 0);
                 const uint64_t cbd = tc::smem_desc(x_s + g.cb_off, 128, 0);
                 if (tc::elect_one()) {
                     tc::mma_f16_ss(dt, cad, cbd, idesc, 0);  // D = 2^23
+                    // K-chunks descending: each window sits 16 rows above the previous one
 #pragma unroll
-                    for (uint32_t kk = 0; kk < 8; ++kk) tc::mma_f16_ss(dt, ad + kk * astep, bd + kk * bstep, idesc, 1);
+                    for (int kk = 7; kk >= 0; --kk)
+                        tc::mma_f16_ss(dt, ad - kk * (16 * kTallRowBytes / 16), bd + kk * bstep, idesc, 1);
                     tc::mma_commit(&dfull[d]);
                     tc::mma_commit(&wempty[k]);
                 }
                 __syncwarp();
             }
         } else if (warp <= kBuildWarps) {
-            // builders: W of each step into a W slot once the MMA that last read
-            // it is done; the 512 quarter rows are spread over the builder threads
+            // builders: T's 240 rows of each step (128 J - 112 .. 128 J + 127) into a
+            // slot once the MMAs that last read it are done
             const uint32_t bt = tid - 32;
             for (uint32_t J = 0; J < S; ++J, ++gs) {
                 const uint32_t k = gs % kWS, use = gs / kWS;
@@ -288,10 +274,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
                     *abortf = 1;
                     break;
                 }
-                uint8_t *wk = W + k * kWBytes;
-                uint32_t x = bt;
-                for (; x + 32 * kBuildWarps < 512; x += 64 * kBuildWarps) build_w2(braw, J, x, x + 32 * kBuildWarps, wk);
-                if (x < 512) build_w(braw, J, x & 127, x >> 7, wk);
+                uint8_t *wk = W + k * kTSlotBytes;
+                const int32_t Rbase = (int32_t)(kBlk * J) - (int32_t)kTallLead;
+                for (uint32_t i = bt; i < kBlk + kTallLead; i += 32 * kBuildWarps) {
+                    uint32_t w[8];
+                    tall_row(braw, Rbase + (int32_t)i, w);
+                    uint8_t *row = wk + (i >> 3) * kTallSbo + (i & 7) * 16;
+                    *reinterpret_cast<uint4 *>(row) = make_uint4(w[0], w[1], w[2], w[3]);
+                    *reinterpret_cast<uint4 *>(row + kTallLbo) = make_uint4(w[4], w[5], w[6], w[7]);
+                }
                 tc::fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&wfull[k]);
@@ -565,17 +556,13 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
 }
 // ---- up to 64K bits: the Toeplitz rows in shared memory --------------------
 //
-// At N = ma16 <= 64 one MMA carries little work (128 x N x 16 products), and a
-// single accumulation chain completes one only every ~140 SM clocks whatever
-// N; the tensor pipe needs several independent chains in flight.  K-chunk kk
-// of W_J (its columns 16 kk .. 16 kk + 15) is the 128-row window starting at
-// row R0 = 128 J - 16 kk of one tall matrix T[R][c] = b-byte (R - c), c < 16:
-//     W_J[r][16 kk + c] = b-byte (128 J + r - 16 kk - c) = T[R0 + r][c].
-// So every MMA takes its A operand from a window of T in shared memory (a
-// descriptor offset), and all of tensor memory holds D: 512 / DW slots.  The
-// steps run in groups of half that many, their MMAs interleaved (as many
-// accumulation chains in flight), each group's D in one half of the slots
-// while the other half is read.
+// At N = ma16 <= 64 one MMA carries little work (128 x N x 16 products) and its
+// cost is set by the operands it reads from shared memory.  Every MMA takes
+// its A operand from a window of T (the Toeplitz rows above): no W is built
+// per step, a step's eight MMAs run back to back with K-chunks descending so
+// that each window sits 16 rows above the previous one (also from one step to
+// the next), and all of tensor memory holds D: 512 / DW slots, used by groups
+// of half that many steps while the other half is read.
 //
 // Three roles, so that nothing but MMAs sits on the tensor pipe's critical
 // path:
@@ -593,31 +580,9 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
 // buffer, dfull/dempty per D slot, cfull/cempty per column-sum row; the
 // producer's own barrier is an mbarrier too), and every wait is bounded and
 // watches the CTA's abort flag.
-constexpr uint32_t kTallRowBytes = 32;  // 16 fp16
-constexpr uint32_t kTallLbo = 128, kTallSbo = 256;
-constexpr uint32_t kTallLead = 112;     // rows of T below 128 J that step J's window reaches
 constexpr uint32_t kEpiTall = 8;    // two per group of 32 tensor-memory lanes
 constexpr uint32_t kProdWarps = 8;
 constexpr uint32_t kThreadsTall = 32 * (1 + kEpiTall + kProdWarps);
-
-// Row R of T (words k = 0..7: the fp16 pair (b-byte (R - 2k), b-byte (R - 2k - 1)))
-// from braw (b's bytes at offset 128 + index, zero outside b; R >= -112).
-__device__ __forceinline__ void tall_row(const uint32_t *braw, int32_t R, uint32_t (&w)[8]) {
-    const uint32_t e = (uint32_t)(113 + R);  // braw byte of b-byte (R - 15)
-    const uint32_t *bw = braw + (e >> 2);
-    const uint32_t sh = e & 3u;
-    uint32_t wv[5];
-#pragma unroll
-    for (int j = 0; j < 5; ++j) wv[j] = bw[j];
-    // x_m holds b-bytes R - 4m, R - 4m - 1, R - 4m - 2, R - 4m - 3 (bytes 0..3)
-    const uint32_t sel = (sh + 3) | ((sh + 2) << 4) | ((sh + 1) << 8) | (sh << 12);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const uint32_t x = __byte_perm(wv[3 - m], wv[4 - m], sel);
-        w[2 * m] = tc::bytes01_f16x2(x);
-        w[2 * m + 1] = tc::bytes23_f16x2(x);
-    }
-}
 
 // A barrier among the warps of one role: each warp's lane 0 arrives on an
 // mbarrier counting those warps (release: the warp's earlier writes, shared
@@ -1036,8 +1001,8 @@ TcGeometry geometry(uint32_t na, uint32_t nb) {
         q.spill_off = off;
         off += 8 * kThreadsTw;
     } else {
-        q.spill_off = q.w_off;  // the normalisation's spill words reuse the W slots
-        off = q.w_off + 2 * kWBytes;
+        q.spill_off = q.w_off;  // the normalisation's spill words reuse the T slots
+        off = q.w_off + 2 * kTSlotBytes;
         if (off < stage_bytes) off = stage_bytes;
     }
     off = (off + 15) & ~15u;

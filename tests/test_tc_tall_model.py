@@ -124,3 +124,23 @@ def test_layout_fits_at_every_size(limbs):
     ma16 = (ma + 15) & ~15
     chunk, end = chunk_of(mb, ma16, limbs, limbs)
     assert chunk >= 1 and end <= SMEM_MAX
+
+
+@pytest.mark.parametrize("nb_limbs", [4097, 6000, 8192])
+def test_per_step_slots_of_the_256K_kernel(nb_limbs):
+    """The 256K-bit kernel builds T's 240 rows of one step at a time (rows
+    128 J - 112 .. 128 J + 127): its eight K-chunk windows are W_J's, and the
+    row builder stays inside the staged bytes up to the last step."""
+    rng = np.random.default_rng(nb_limbs)
+    bb = rng.integers(0, 256, 4 * nb_limbs)
+    mb = -(-bb.size // BLK)
+    bpad = np.zeros(BLK * (mb + 3), np.int64)
+    bpad[BLK:BLK + bb.size] = bb
+    braw = staged_b(bb, mb)
+    r = np.arange(BLK)[:, None]
+    c = np.arange(16)[None, :]
+    for J in (0, 1, mb // 2, mb - 1, mb):
+        T = np.array([tall_row(braw, BLK * J - LEAD + i) for i in range(BLK + LEAD)])
+        for kk in range(8):
+            i0 = LEAD - 16 * kk
+            assert np.array_equal(T[i0:i0 + BLK], bpad[BLK + BLK * J + r - 16 * kk - c])
