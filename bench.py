@@ -741,8 +741,8 @@ def run_e2e(args, torch, bn, ops, hosts, dev, world=1):
     """Same metric through the host-buffer entry point with pinned host
     buffers: every op copies its operands in and its result out inside the
     timed region (bn_plan_execute_host_async), the ops spread round-robin over
-    three streams so that copies of one op overlap kernels of another; the
-    timed region ends when all streams are synchronised."""
+    --e2e-streams streams so that copies of one op overlap kernels of another;
+    the timed region ends when all streams are synchronised."""
     pinned_in, pinned_out, plans = {}, {}, {}
     for o in ops:
         if o.bits not in pinned_in:
@@ -755,7 +755,7 @@ def run_e2e(args, torch, bn, ops, hosts, dev, world=1):
             pinned_out[key] = torch.empty((o.batch, o.nout), dtype=torch.int32).pin_memory()
         opcode = OPCODES[o.name](bn)
         plans[o.label] = bn.Plan(opcode, o.na, o.nb, o.batch)
-    streams = [torch.cuda.Stream(dev) for _ in range(3)]
+    streams = [torch.cuda.Stream(dev) for _ in range(args.e2e_streams)]
 
     def step():
         for i, o in enumerate(ops):
@@ -782,9 +782,9 @@ def run_e2e(args, torch, bn, ops, hosts, dev, world=1):
     d2h = sum(4 * o.nout * o.batch for o in ops)
     return {"value": world * mults * steps / el, "unit": UNIT, "h2d_bytes_per_step": world * h2d,
             "d2h_bytes_per_step": world * d2h, "steps": steps, "ms_per_step": round(el / steps * 1e3, 3),
-            "ranks": world,
-            "api": "bn_plan_execute_host_async on 3 streams (pinned host buffers, copies "
-                   "inside the timed region)"}
+            "ranks": world, "streams": args.e2e_streams,
+            "api": f"bn_plan_execute_host_async on {args.e2e_streams} streams (pinned host buffers, "
+                   "copies inside the timed region)"}
 
 
 # ---- CPU oracle ------------------------------------------------------------
@@ -912,7 +912,7 @@ def compact(full: dict) -> dict:
     out = {k: full[k] for k in keep if k in full}
     if isinstance(out.get("e2e"), dict) and "api" in out["e2e"]:
         out["e2e"] = dict(out["e2e"], api="bn_plan_execute_host_async, pinned host buffers, "
-                                          "3 streams")
+                                          "%d streams" % full["e2e"].get("streams", 8))
     if isinstance(out.get("roofline"), dict):
         out["roofline"] = dict(out["roofline"])
     if full.get("rooflines"):
@@ -1000,6 +1000,8 @@ def main(argv=None):
     ap.add_argument("--integer-schoolbook", action="store_true",
                     help="the integer-pipe schoolbook at every size (for profiling that kernel)")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-streams", type=int, default=8,
+                    help="streams the end-to-end pass spreads the ops over")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-step-budget", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
