@@ -49,6 +49,7 @@
 #include <cuda_runtime.h>
 
 #include <new>
+#include <type_traits>
 
 #include "bn_internal.h"
 #include "ntt_device.cuh"
@@ -561,28 +562,39 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
 // its A operand from a window of T (the Toeplitz rows above): no W is built
 // per step, a step's eight MMAs run back to back with K-chunks descending so
 // that each window sits 16 rows above the previous one (also from one step to
-// the next), and all of tensor memory holds D: 512 / DW slots, used by groups
-// of half that many steps while the other half is read.
+// the next), and all of tensor memory holds D: 512 / DW slots in two halves,
+// group g of steps (half as many steps as slots) writing half g % 2 while the
+// other half is read.  The first MMA of a step overwrites its slot, so D holds
+// that step's column sums v < 2^23 exactly; the epilogue takes the integer
+// from the bit pattern of v + 2^23 (0x4b000000 + v).
 //
-// Three roles, so that nothing but MMAs sits on the tensor pipe's critical
-// path:
-//  * warp 0 issues the MMAs (group g reads T buffer g % 2 and D half g % 2,
-//    product p reads XX buffer p % 2);
-//  * warps 1-8 (epilogue) read D, keep the column sums and publish them,
-//    per product, into one of two column-sum rows;
-//  * warps 9-16 (producer) stage each product's XX and b's bytes, build each
-//    group's rows of T: R in [128 J - 112, 128 (J + n)), in the A operand's
-//    layout (K-major, no swizzle: row i, K-half h at (i / 8) * 256 + h * 128
-//    + (i % 8) * 16, i.e. LBO = 128, SBO = 256), and carry the previous
-//    product's column sums into limbs once its own first two groups are
-//    built, while the tensor pipe runs them.
-// mbarriers link them (tfull/tempty per T buffer, xfull/xempty per XX
-// buffer, dfull/dempty per D slot, cfull/cempty per column-sum row; the
-// producer's own barrier is an mbarrier too), and every wait is bounded and
-// watches the CTA's abort flag.
+// Roles, so that nothing but MMAs sits on the tensor pipe's critical path:
+//  * warp 0 issues the MMAs (group g reads T buffer g % 3 and D half g % 2,
+//    product p reads XX buffer p % 2) and commits once per group;
+//  * warps 1-8 (epilogue) read each group's D half once the group has
+//    completed, keep the column sums, store each finished column, publish the
+//    rest per product into one of two column-sum rows, and free the half;
+//  * warps 9-16 (producer) stage each product's XX and b's bytes from a copy
+//    of the product's rows fetched (cp.async) while the previous product ran,
+//    and build each group's rows of T: R in [128 J - 112, 128 (J + n)), in
+//    the A operand's layout (K-major, no swizzle: row i, K-half h at
+//    (i / 8) * 256 + h * 128 + (i % 8) * 16, i.e. LBO = 128, SBO = 256), up to
+//    three groups ahead of the tensor pipe;
+//  * the column sums of each product are carried into limbs by four more
+//    warps at DW = 64 (17-20), or by the producer once three groups of the
+//    next product are built at DW = 32.
+// mbarriers link them (tfull/tempty per T buffer, the latter also telling the
+// epilogue that the group's D half is complete; dempty per D half; xfull/
+// xempty per XX buffer; cfull/cempty per column-sum row; the producer's and
+// the normalising warps' own barriers are mbarriers too), and every wait is
+// bounded and watches the CTA's abort flag.
 constexpr uint32_t kEpiTall = 8;    // two per group of 32 tensor-memory lanes
 constexpr uint32_t kProdWarps = 8;
-constexpr uint32_t kThreadsTall = 32 * (1 + kEpiTall + kProdWarps);
+constexpr uint32_t kTBufs = 3;      // T buffers: the producer builds up to three groups ahead
+template <uint32_t DW>
+constexpr uint32_t norm_warps() { return DW == 64 ? 4u : 0u; }
+template <uint32_t DW>
+constexpr uint32_t threads_tall() { return 32 * (1 + kEpiTall + kProdWarps + norm_warps<DW>()); }
 
 // A barrier among the warps of one role: each warp's lane 0 arrives on an
 // mbarrier counting those warps (release: the warp's earlier writes, shared
@@ -599,7 +611,10 @@ __device__ __forceinline__ bool role_sync(uint64_t *bar, uint32_t &phase, volati
 }
 
 // normalize_limbs for the NW warps of one role (thread t of NT = 32 NW),
-// synchronised by role_sync: column sums -> limbs, carry scan, copy-out.
+// synchronised by role_sync: column sums -> limbs, carry scan, copy-out.  A
+// byte column holds at most 8192 byte products (64K bits), so its sum is
+// below 2^29 and a limb (four columns) below 2^54: a 64-bit running carry
+// suffices.  The limbs' loads go out eight at a time.
 template <uint32_t NW, class LimbFn>
 __device__ bool normalize_role(uint32_t nout, uint32_t *crow, uint32_t *out_s, uint64_t *spill, uint32_t *flags,
                                uint32_t t, uint64_t *bar, uint32_t &phase, volatile uint32_t *abortf,
@@ -611,13 +626,20 @@ __device__ bool normalize_role(uint32_t nout, uint32_t *crow, uint32_t *out_s, u
     const uint32_t k0 = t * QN;
     const uint32_t k1 = k0 + QN < nout ? k0 + QN : nout;
     // (a) this window's limbs, carrying within the window
-    ntt::u128 carry = 0;
-    for (uint32_t k = k0; k < k1; ++k) {
-        const ntt::u128 v = limb(k) + carry;
-        out_s[ntt::stage_index(k)] = (uint32_t)v;
-        carry = v >> 32;
+    uint64_t carry = 0;
+    for (uint32_t k = k0; k < k1; k += 8) {
+        uint64_t lv[8];
+#pragma unroll
+        for (uint32_t j = 0; j < 8; ++j) lv[j] = k + j < k1 ? limb(k + j) : 0;
+#pragma unroll
+        for (uint32_t j = 0; j < 8; ++j)
+            if (k + j < k1) {
+                const uint64_t v = lv[j] + carry;
+                out_s[ntt::stage_index(k + j)] = (uint32_t)v;
+                carry = v >> 32;
+            }
     }
-    spill[t] = (uint64_t)carry;
+    spill[t] = carry;
     if (!role_sync(bar, phase, abortf)) return false;
     // (b) add the previous window's spill
     uint64_t c = t > 0 ? spill[t - 1] : 0;
@@ -652,59 +674,64 @@ __device__ bool normalize_role(uint32_t nout, uint32_t *crow, uint32_t *out_s, u
     return role_sync(bar, phase, abortf);
 }
 
-// Whole warp: NC (16 or 32) columns of this warp's tensor-memory lanes at
-// taddr set to 2^23 (bit pattern kBiasBits), where a D slot's sums start.
-template <uint32_t NC>
-__device__ __forceinline__ void bias_columns(uint32_t taddr) {
-    uint32_t v[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = kBiasBits;
-#pragma unroll
-    for (uint32_t c = 0; c < NC; c += 16) tc::tmem_st16(taddr + c, v);
+// Limb k of a column-sum row (four byte columns per limb).
+__device__ __forceinline__ uint64_t limb_of(const uint32_t *cols, uint32_t k) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(cols + 4 * k);
+    return (uint64_t)v.x + ((uint64_t)v.y << 8) + ((uint64_t)v.z << 16) + ((uint64_t)v.w << 24);
 }
 
+// Four-byte asynchronous copy global -> shared (completes at cp_async_wait_all).
+__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <uint32_t DW>
-__global__ void __launch_bounds__(kThreadsTall, 1) k_mul_quad_tc_tall(TcArgs g) {
+__global__ void __launch_bounds__(threads_tall<DW>(), 1) k_mul_quad_tc_tall(TcArgs g) {
     constexpr uint32_t kDS = kTmemCols / DW;  // D slots
-    constexpr uint32_t kC = kDS / 2;          // steps per group (chains in flight)
+    constexpr uint32_t kC = kDS / 2;          // steps per group: one D half
     constexpr uint32_t kCW = DW / 2;          // D columns per epilogue warp
+    constexpr uint32_t kNW = norm_warps<DW>();
     extern __shared__ __align__(1024) uint8_t sm[];
-    // XX buffers at 0 and g.x1_off, T buffers at g.t_off and g.t_off + g.t_bytes, the
-    // normalisation's staging row at g.spill_off followed by its spill words
+    // XX buffers at 0 and g.x1_off, T buffers from g.t_off (g.t_bytes each), a's
+    // words of the next product at g.ca_off, b's bytes (two copies) at g.braw_off,
+    // the normalisation's staging row at g.spill_off followed by its spill words
     uint8_t *const X0 = sm, *const X1 = sm + g.x1_off;
+    uint32_t *const araw = reinterpret_cast<uint32_t *>(sm + g.ca_off);
     uint32_t *const braw0 = reinterpret_cast<uint32_t *>(sm + g.braw_off);
     uint32_t *const braw1 = braw0 + (32 * (g.mb + 2) + 4);
     uint32_t *out_s = reinterpret_cast<uint32_t *>(sm + g.spill_off);
     uint64_t *spill = reinterpret_cast<uint64_t *>(sm + g.spill_off + ((4 * ntt::stage_index(g.nout) + 16 + 15) & ~15u));
     uint32_t *flags = reinterpret_cast<uint32_t *>(sm + g.flags_off);
-    uint64_t *dfull = reinterpret_cast<uint64_t *>(sm + g.bar_off);  // [kDS] MMA commits
-    uint64_t *dempty = dfull + kDS;                                    // [kDS] one arrival per epilogue warp
-    uint64_t *tfull = dempty + kDS;    // [2] one arrival per producer warp
-    uint64_t *tempty = tfull + 2;      // [2] MMA commits
-    uint64_t *xfull = tempty + 2;      // [2] one arrival per producer warp
-    uint64_t *xempty = xfull + 2;      // [2] MMA commits
-    uint64_t *cfull = xempty + 2;      // [2] one arrival per epilogue warp
-    uint64_t *cempty = cfull + 2;      // [2] one arrival per producer warp
-    uint64_t *pbar = cempty + 2;       // the producer warps' own barrier
-    uint32_t *slot = reinterpret_cast<uint32_t *>(pbar + 1);
+    uint64_t *tfull = reinterpret_cast<uint64_t *>(sm + g.bar_off);  // [kTBufs] one arrival per producer warp
+    uint64_t *tempty = tfull + kTBufs;  // [kTBufs] MMA commits: the group has completed
+    uint64_t *dempty = tempty + kTBufs; // [2] one arrival per epilogue warp: the D half is free
+    uint64_t *xfull = dempty + 2;       // [2] one arrival per producer warp
+    uint64_t *xempty = xfull + 2;       // [2] MMA commits
+    uint64_t *cfull = xempty + 2;       // [2] one arrival per epilogue warp
+    uint64_t *cempty = cfull + 2;       // [2] one arrival per normalising warp
+    uint64_t *pbar = cempty + 2;        // the producer warps' own barrier
+    uint64_t *nbar = pbar + 1;          // the normalising warps' own barrier
+    uint32_t *slot = reinterpret_cast<uint32_t *>(nbar + 1);
     volatile uint32_t *abortf = slot + 1;
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) tc::tmem_alloc(slot, kTmemCols);
     if (tid == 0) {
-        for (uint32_t k = 0; k < kDS; ++k) {
-            tc::mbar_init(&dfull[k], 1);
-            tc::mbar_init(&dempty[k], kEpiTall);
-        }
-        for (uint32_t k = 0; k < 2; ++k) {
+        for (uint32_t k = 0; k < kTBufs; ++k) {
             tc::mbar_init(&tfull[k], kProdWarps);
             tc::mbar_init(&tempty[k], 1);
+        }
+        for (uint32_t k = 0; k < 2; ++k) {
+            tc::mbar_init(&dempty[k], kEpiTall);
             tc::mbar_init(&xfull[k], kProdWarps);
             tc::mbar_init(&xempty[k], 1);
             tc::mbar_init(&cfull[k], kEpiTall);
-            tc::mbar_init(&cempty[k], kProdWarps);
+            tc::mbar_init(&cempty[k], kNW ? kNW : kProdWarps);
         }
         tc::mbar_init(pbar, kProdWarps);
+        tc::mbar_init(nbar, kNW ? kNW : 1);
         *abortf = 0;
         tc::fence_mbar_init();
     }
@@ -712,109 +739,117 @@ __global__ void __launch_bounds__(kThreadsTall, 1) k_mul_quad_tc_tall(TcArgs g) 
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = *slot, S = g.mb + 1;  // steps J = 0..mb of a product
-    if (warp >= 1 && warp <= kEpiTall) {  // every D slot starts at 2^23 (the epilogue restores it after each read)
-        const uint32_t lq = warp & 3, n0 = (DW / 2) * ((warp - 1) >> 2);
-        for (uint32_t d = 0; d < kDS; ++d) bias_columns<DW / 2>(tbase + ((32 * lq) << 16) + DW * d + n0);
-        tc::tmem_st_wait();
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
     // this CTA's two column-sum rows (product p uses row p % 2)
     uint32_t *const cols0 = g.scratch + blockIdx.x * g.scratch_stride;
     uint32_t *const cols1 = cols0 + g.scratch_stride / 2;
+    // column sums of product q (instance inst) -> limbs, by the NW warps of a role
+    auto finish = [&](uint32_t q, uint64_t inst, uint32_t t, uint64_t *bar, uint32_t &ph, auto nw) -> bool {
+        const uint32_t cb = q & 1u;
+        const uint32_t *cols = cb ? cols1 : cols0;
+        if (!__all_sync(FULL_MASK, tc::mbar_wait(&cfull[cb], (q >> 1) & 1u, kWaitNs, abortf))) return false;
+        const bool done = normalize_role<decltype(nw)::value>(g.nout, g.c + inst * g.nout, out_s, spill, flags, t,
+                                                               bar, ph, abortf,
+                                                               [&](uint32_t k) { return limb_of(cols, k); });
+        __syncwarp();
+        if (done && lane == 0) tc::mbar_arrive(&cempty[cb]);
+        return done;
+    };
 
     if (warp == 0) {
         // ---- MMA warp
         const uint32_t idesc = tc::idesc_f16_f32(128, g.ma16);
         const uint64_t bstep = (2 * g.xs) >> 4;
         const uint32_t s0 = tc::smem_u32(sm);
-        uint32_t gs = 0, gg = 0, pi = 0;  // steps, groups, products issued by this CTA
+        uint32_t gg = 0, pi = 0;  // groups, products issued by this CTA
         bool ok = true;
         for (uint64_t inst = blockIdx.x; inst < g.batch && ok; inst += gridDim.x, ++pi) {
             const uint32_t xb = pi & 1u, x_s = s0 + (xb ? g.x1_off : 0u);
             ok = __all_sync(FULL_MASK, tc::mbar_wait_spin(&xfull[xb], (pi >> 1) & 1u, kWaitNs, abortf));
             for (uint32_t J = 0; J < S && ok; J += kC, ++gg) {
                 const uint32_t n = J + kC <= S ? kC : S - J;  // steps of this group
-                const uint32_t tb = gg & 1u, t_s = s0 + g.t_off + tb * g.t_bytes;
-                for (uint32_t h = 0; h < n && ok; ++h) {
-                    const uint32_t gh = gs + h, ud = gh / kDS;
-                    if (ud > 0) ok = tc::mbar_wait_spin(&dempty[gh % kDS], (ud - 1) & 1u, kWaitNs, abortf);
-                }
-                if (ok) ok = tc::mbar_wait_spin(&tfull[tb], (gg >> 1) & 1u, kWaitNs, abortf);
+                const uint32_t tb = gg % kTBufs, dh = gg & 1u, t_s = s0 + g.t_off + tb * g.t_bytes;
+                if (gg >= 2) ok = tc::mbar_wait_spin(&dempty[dh], ((gg - 2) >> 1) & 1u, kWaitNs, abortf);
+                if (ok) ok = tc::mbar_wait_spin(&tfull[tb], (gg / kTBufs) & 1u, kWaitNs, abortf);
                 ok = __all_sync(FULL_MASK, ok);
                 if (!ok) break;
                 tc::fence_after_sync();
                 if (tc::elect_one()) {
-                    // step J + h: its D slot, its T window at K-chunk 0 (row 128 h + 112
-                    // of the group's rows) and its XX window (block ma - J - h);
-                    // K-chunk kk moves T 16 rows up and XX two K-chunks on
+                    // step J + h: D slot kC dh + h, its T window at K-chunk 0 (row 128 h + 112
+                    // of the group's rows) and its XX window (block ma - J - h); K-chunk kk
+                    // moves T 16 rows up and XX two K-chunks on
                     uint32_t dt[kC];
                     uint64_t ad[kC], bd[kC];
 #pragma unroll
                     for (uint32_t h = 0; h < kC; ++h) {
                         const uint32_t hh = h < n ? h : 0;  // (unused beyond n)
-                        dt[h] = tbase + DW * ((gs + hh) % kDS);
+                        dt[h] = tbase + DW * (kC * dh + hh);
                         ad[h] = tc::smem_desc(t_s + (kBlk * hh + kTallLead) * kTallRowBytes, kTallLbo, kTallSbo);
                         bd[h] = tc::smem_desc(x_s + (g.ma - J - hh) * 16, g.xs, 128);
                     }
                     // step by step, K-chunks from 7 down to 0: each MMA's T window sits 16 rows
                     // above the one before, also from one step to the next, so consecutive MMAs
-                    // share 7/8 of their A operand
+                    // share 7/8 of their A operand; a step's first MMA overwrites its slot
 #pragma unroll
                     for (uint32_t h = 0; h < kC; ++h) {
                         if (h >= n) break;
 #pragma unroll
                         for (int kk = 7; kk >= 0; --kk)
-                            tc::mma_f16_ss(dt[h], ad[h] - kk * (16 * kTallRowBytes / 16), bd[h] + kk * bstep, idesc, 1);
+                            tc::mma_f16_ss(dt[h], ad[h] - kk * (16 * kTallRowBytes / 16), bd[h] + kk * bstep, idesc,
+                                           kk != 7);
                     }
-                    for (uint32_t h = 0; h < n; ++h) tc::mma_commit(&dfull[(gs + h) % kDS]);
-                    tc::mma_commit(&tempty[tb]);                // T buffer tb may be rebuilt
+                    tc::mma_commit(&tempty[tb]);                // the group's D half is complete, T buffer tb free
                     if (J + n == S) tc::mma_commit(&xempty[xb]);  // XX buffer xb may be restaged
                 }
                 __syncwarp();
-                gs += n;
             }
         }
         if (!ok) *abortf = 1;
         // the MMAs issued last finish before tensor memory is freed (bounded; at once
         // when the epilogue has already seen them)
-        if (lane == 0 && gs > 0) tc::mbar_wait(&dfull[(gs - 1) % kDS], ((gs - 1) / kDS) & 1u, kWaitNs);
+        if (lane == 0 && gg > 0) tc::mbar_wait(&tempty[(gg - 1) % kTBufs], ((gg - 1) / kTBufs) & 1u, kWaitNs);
         __syncwarp();
+    } else if (kNW && warp > kEpiTall + kProdWarps) {
+        // ---- normalising warps: each product's column sums -> limbs
+        const uint32_t nt = tid - 32 * (1 + kEpiTall + kProdWarps);
+        uint32_t nph = 0, pi = 0;
+        bool ok = true;
+        for (uint64_t inst = blockIdx.x; inst < g.batch && ok; inst += gridDim.x, ++pi)
+            ok = finish(pi, inst, nt, nbar, nph, std::integral_constant<uint32_t, (kNW ? kNW : 1)>{});
+        if (!ok) *abortf = 1;
     } else if (warp > kEpiTall) {
         // ---- producer warps: XX and b's bytes of each product, T's rows of each
-        // group, and the previous product's limbs
+        // group (and, at DW = 32, the previous product's limbs)
         const uint32_t pt = tid - 32 * (1 + kEpiTall);
         constexpr uint32_t PT = 32 * kProdWarps;
+        const uint32_t bwords = 32 * (g.mb + 2) + 4;
         uint32_t gg = 0, pi = 0, pph = 0;
         bool ok = true;
-        // column sums of product q (instance `inst`) -> limbs
-        auto finish = [&](uint32_t q, uint64_t inst) -> bool {
-            const uint32_t cb = q & 1u;
-            const uint32_t *cols = cb ? cols1 : cols0;
-            if (!__all_sync(FULL_MASK, tc::mbar_wait(&cfull[cb], (q >> 1) & 1u, kWaitNs, abortf))) return false;
-            const bool done = normalize_role<kProdWarps>(
-                g.nout, g.c + inst * g.nout, out_s, spill, flags, pt, pbar, pph, abortf, [&](uint32_t k) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(cols + 4 * k);
-                    return (ntt::u128)((uint64_t)v.x + ((uint64_t)v.y << 8) + ((uint64_t)v.z << 16) +
-                                       ((uint64_t)v.w << 24));
-                });
-            __syncwarp();
-            if (done && lane == 0) tc::mbar_arrive(&cempty[cb]);
-            return done;
+        // a's and b's words of product inst into araw and braw (asynchronously)
+        auto prefetch = [&](uint64_t inst, uint32_t *braw) {
+            const uint32_t *arow = g.a + inst * g.na, *brow = g.b + inst * g.nb;
+            for (uint32_t x = pt; x < g.na; x += PT) cp_async4(araw + x, arow + x);
+            for (uint32_t x = pt; x < g.nb; x += PT) cp_async4(braw + 32 + x, brow + x);
+            cp_async_commit();
         };
+        // araw beyond na and braw outside b stay zero
+        for (uint32_t x = pt; x < 32 * g.ma; x += PT) araw[x] = 0;
+        for (uint32_t x = pt; x < bwords; x += PT) braw0[x] = braw1[x] = 0;
+        ok = role_sync(pbar, pph, abortf);
+        if (ok && blockIdx.x < g.batch) prefetch(blockIdx.x, braw0);
         for (uint64_t inst = blockIdx.x; inst < g.batch && ok; inst += gridDim.x, ++pi) {
             const uint32_t xb = pi & 1u;
             uint8_t *const X = xb ? X1 : X0;
             uint32_t *const braw = xb ? braw1 : braw0;
-            const uint32_t *arow = g.a + inst * g.na, *brow = g.b + inst * g.nb;
             if (pi >= 2) ok = __all_sync(FULL_MASK, tc::mbar_wait(&xempty[xb], ((pi - 2) >> 1) & 1u, kWaitNs, abortf));
-            if (!ok) break;
+            cp_async_wait_all();
+            if (!ok || !role_sync(pbar, pph, abortf)) {  // every thread's copies have landed
+                ok = false;
+                break;
+            }
             // XX: a-block I at blocks I and I + ma, zero blocks up to D's width
             for (uint32_t x = pt; x < 16 * g.ma; x += PT) {
                 const uint32_t I = x >> 4, q = x & 15, w0 = 32 * I + 2 * q;
-                const uint32_t u = w0 < g.na ? __ldg(arow + w0) : 0u;
-                const uint32_t v = w0 + 1 < g.na ? __ldg(arow + w0 + 1) : 0u;
+                const uint32_t u = araw[w0], v = araw[w0 + 1];
                 const uint4 f = make_uint4(tc::bytes01_f16x2(u), tc::bytes23_f16x2(u), tc::bytes01_f16x2(v),
                                            tc::bytes23_f16x2(v));
                 *reinterpret_cast<uint4 *>(X + q * g.xs + I * 16) = f;
@@ -823,20 +858,23 @@ __global__ void __launch_bounds__(kThreadsTall, 1) k_mul_quad_tc_tall(TcArgs g) 
             const uint32_t zb = g.ma16 - g.ma;
             for (uint32_t x = pt; x < 16 * zb; x += PT)
                 *reinterpret_cast<uint4 *>(X + (x / zb) * g.xs + (2 * g.ma + x % zb) * 16) = make_uint4(0, 0, 0, 0);
-            const uint32_t bwords = 32 * (g.mb + 2) + 4;
-            for (uint32_t x = pt; x < bwords; x += PT) braw[x] = (x >= 32 && x - 32 < g.nb) ? __ldg(brow + x - 32) : 0u;
             tc::fence_proxy_async();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&xfull[xb]);
-            if (!role_sync(pbar, pph, abortf)) {  // b's bytes are read by every producer thread's rows
+            // araw has been read by every thread, and the other braw copy (the product
+            // before this one) is no longer read: fetch the next product's rows
+            if (!role_sync(pbar, pph, abortf)) {
                 ok = false;
                 break;
             }
+            if (inst + gridDim.x < g.batch) prefetch(inst + gridDim.x, xb ? braw0 : braw1);
             uint32_t k = 0;  // group of this product
             for (uint32_t J = 0; J < S && ok; J += kC, ++gg, ++k) {
-                const uint32_t n = J + kC <= S ? kC : S - J, tb = gg & 1u;
+                const uint32_t n = J + kC <= S ? kC : S - J, tb = gg % kTBufs;
                 uint8_t *const Tb = sm + g.t_off + tb * g.t_bytes;
-                if (gg >= 2) ok = __all_sync(FULL_MASK, tc::mbar_wait(&tempty[tb], ((gg - 2) >> 1) & 1u, kWaitNs, abortf));
+                if (gg >= kTBufs)
+                    ok = __all_sync(FULL_MASK,
+                                    tc::mbar_wait(&tempty[tb], ((gg - kTBufs) / kTBufs) & 1u, kWaitNs, abortf));
                 if (!ok) break;
                 const int32_t Rbase = (int32_t)(kBlk * J) - (int32_t)kTallLead;
                 const uint32_t nrows = kBlk * n + kTallLead;
@@ -850,84 +888,85 @@ __global__ void __launch_bounds__(kThreadsTall, 1) k_mul_quad_tc_tall(TcArgs g) 
                 tc::fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&tfull[tb]);
-                // both T buffers hold this product's work: finish the previous product
-                if (pi > 0 && (k == 1 || J + n == S && k == 0)) ok = finish(pi - 1, inst - gridDim.x);
+                // every T buffer holds this product's work: finish the previous product
+                if (!kNW && pi > 0 && (k == kTBufs - 1 || (J + n == S && k < kTBufs - 1)))
+                    ok = finish(pi - 1, inst - gridDim.x, pt, pbar, pph, std::integral_constant<uint32_t, kProdWarps>{});
             }
         }
-        if (ok && pi > 0) ok = finish(pi - 1, blockIdx.x + (uint64_t)(pi - 1) * gridDim.x);
+        cp_async_wait_all();  // nothing in flight into shared memory at exit
+        if (!kNW && ok && pi > 0)
+            ok = finish(pi - 1, blockIdx.x + (uint64_t)(pi - 1) * gridDim.x, pt, pbar, pph,
+                        std::integral_constant<uint32_t, kProdWarps>{});
         if (!ok) *abortf = 1;
     } else {
         // ---- epilogue warps: column half m, D columns [kCW m, kCW m + kCW)
         const uint32_t lq = warp & 3;  // the tensor-memory lanes this warp may move
         const uint32_t m = (warp - 1) >> 2, n0 = kCW * m, r = 32 * lq + lane;
         const uint32_t lane_off = (32 * lq) << 16;
-        uint32_t gs = 0, pi = 0, dprev = 0;
+        uint32_t eg = 0, pi = 0;  // groups read, products
         bool ok = true;
-        // D slot d is free again once this warp's stores of its starting values have landed
-        auto release = [&](uint32_t d) {
-            tc::tmem_st_wait();
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&dempty[d]);
-        };
         for (uint64_t inst = blockIdx.x; inst < g.batch && ok; inst += gridDim.x, ++pi) {
             const uint32_t cb = pi & 1u;
             uint32_t *const colr = (cb ? cols1 : cols0) + r;  // this thread's row of every column block
             if (pi >= 2) ok = __all_sync(FULL_MASK, tc::mbar_wait(&cempty[cb], ((pi - 2) >> 1) & 1u, kWaitNs, abortf));
             if (!ok) break;
-            uint32_t acc[kCW / 32 + (kCW % 32 != 0)][kCW < 32 ? kCW : 32];
+            uint32_t acc[kCW];
 #pragma unroll
-            for (int i = 0; i < (int)kCW; ++i) acc[i >> 5][i & 31] = 0;
-            for (uint32_t J = 0; J < S; ++J, ++gs) {
-                const uint32_t d = gs % kDS;
-                ok = __all_sync(FULL_MASK, tc::mbar_wait(&dfull[d], (gs / kDS) & 1u, kWaitNs, abortf));
-                if (!ok) break;
+            for (uint32_t i = 0; i < kCW; ++i) acc[i] = 0;
+            // step J: wait for its group at the group's first step, add the step's D
+            // columns, free the D half after the group's last step
+            auto step = [&](uint32_t J) -> bool {
+                const uint32_t jh = J % kC;
+                if (jh == 0 && !__all_sync(FULL_MASK, tc::mbar_wait(&tempty[eg % kTBufs], (eg / kTBufs) & 1u,
+                                                                    kWaitNs, abortf)))
+                    return false;
                 tc::fence_after_sync();
-                if (n0 < g.ma) {  // the warp's kCW columns of D in one load
-                    if constexpr (kCW == 32) {  // two loads of 16 (fewer live registers)
+                if (n0 < g.ma) {
+                    uint32_t v[kCW];
+                    const uint32_t ta = tbase + lane_off + DW * (kC * (eg & 1u) + jh) + n0;
+                    tc::tmem_ld16_async(ta, v);
+                    if constexpr (kCW == 32) tc::tmem_ld16_async(ta + 16, v + 16);
+                    tc::tmem_ld_wait();
 #pragma unroll
-                        for (int hf = 0; hf < 2; ++hf) {
-                            uint32_t v[16];
-                            tc::tmem_ld16(tbase + lane_off + DW * d + n0 + 16 * hf, v);
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) acc[0][16 * hf + j] += v[j] - kBiasBits;
-                        }
-                    } else {
-                        uint32_t v[16];
-                        tc::tmem_ld16(tbase + lane_off + DW * d + n0, v);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) acc[0][j] += v[j] - kBiasBits;
-                    }
+                    for (uint32_t j = 0; j < kCW; ++j)
+                        acc[j] += __float_as_uint(__uint_as_float(v[j]) + 8388608.0f) - kBiasBits;
                 }
-                // the previous slot's starting values have landed: release it; this
-                // slot starts over at 2^23 (its store lands while the next step waits)
-                if (J > 0) release(dprev);
-                bias_columns<kCW>(tbase + lane_off + DW * d + n0);
-                dprev = d;
-                // column J now holds all of block J: store it and start the column
-                // over as block J + ma
-                const uint32_t f = J - n0;  // warp-uniform
-                if (J < g.mb && f < kCW) {
-                    if constexpr (kCW == 32) {
-                        switch (f) { BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) BN_TC_FLUSH8(16) BN_TC_FLUSH8(24) }
-                    } else {
-                        switch (f) { BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) }
-                    }
+                if (jh == kC - 1 || J == S - 1) {  // the group's D half may be overwritten
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&dempty[eg & 1u]);
+                    ++eg;
                 }
+                return true;
+            };
+            // three runs of steps: before this warp's columns, the run in which step J
+            // completes column J - n0 of this warp (unrolled, so that the column is a
+            // register: store it and start it over as block J + ma), and the rest
+            const uint32_t jb = n0 < g.mb ? n0 : g.mb;
+            const uint32_t je = n0 + kCW < g.mb ? n0 + kCW : g.mb;
+            uint32_t J = 0;
+            for (; J < jb && ok; ++J) ok = step(J);
+#pragma unroll
+            for (uint32_t x = 0; x < kCW; ++x) {
+                if (!ok || n0 + x >= je) break;
+                ok = step(n0 + x);
+                colr[kBlk * (n0 + x)] = acc[x];
+                acc[x] = 0;
             }
+            if (J < je) J = je;
+            for (; J < S && ok; ++J) ok = step(J);
             if (!ok) break;
-            release(dprev);
             // publish: column n < mb went on to block n + ma after step n
 #pragma unroll
-            for (int j = 0; j < (int)kCW; ++j)
-                if (n0 + j >= g.mb && n0 + j < g.ma) colr[kBlk * (n0 + j)] = acc[j >> 5][j & 31];
+            for (uint32_t j = 0; j < kCW; ++j)
+                if (n0 + j >= g.mb && n0 + j < g.ma) colr[kBlk * (n0 + j)] = acc[j];
             uint32_t *const colr_hi = colr + kBlk * g.ma;
 #pragma unroll
-            for (int j = 0; j < (int)kCW; ++j)
-                if (n0 + j < g.mb) colr_hi[kBlk * (n0 + j)] = acc[j >> 5][j & 31];
+            for (uint32_t j = 0; j < kCW; ++j)
+                if (n0 + j < g.mb) colr_hi[kBlk * (n0 + j)] = acc[j];
             __threadfence_block();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&cfull[cb]);  // the producer carries them into limbs
+            if (lane == 0) tc::mbar_arrive(&cfull[cb]);  // the normalising warps carry them into limbs
         }
         if (!ok) *abortf = 1;
     }
@@ -949,29 +988,31 @@ struct TcGeometry {
 
 constexpr uint32_t kSmemMax = 227 * 1024;  // dynamic shared memory per CTA (opt-in)
 
-// k_mul_quad_tc_tall's layout: two XX buffers, two T buffers (one group of
-// steps each), the normalisation's staging row and spill words, two copies
-// of b's bytes, the flags and the mbarriers.
+// k_mul_quad_tc_tall's layout: two XX buffers, three T buffers (one group of
+// steps each), the normalisation's staging row and spill words, a's words of
+// the next product, two copies of b's bytes, the flags and the mbarriers.
 void tall_geometry(TcGeometry &q, uint32_t nout) {
     q.tall = true;
     q.tw = false;
     q.dw = q.ma16 <= 32 ? 32 : 64;
-    const uint32_t dslots = kTmemCols / q.dw, group = dslots / 2;
+    const uint32_t group = kTmemCols / q.dw / 2;
     const uint32_t xbytes = (16 * q.xs + 1023) & ~1023u;
     q.x1_off = xbytes;
     q.t_off = 2 * xbytes;
     q.t_bytes = ((kBlk * group + kTallLead) * kTallRowBytes + 1023) & ~1023u;
-    uint32_t off = q.t_off + 2 * q.t_bytes;
-    q.spill_off = off;  // staging row (stage_index(nout) words + 16 bytes), then 8 bytes per epilogue thread
+    uint32_t off = q.t_off + kTBufs * q.t_bytes;
+    q.spill_off = off;  // staging row (stage_index(nout) words + 16 bytes), then 8 bytes per normalising thread
     off += ((4 * (nout + (nout >> 4)) + 16 + 15) & ~15u) + 8 * 32 * kProdWarps;
-    q.ca_off = q.cb_off = 0;  // no bias MMA: the epilogue stores D's starting value
+    q.ca_off = off;  // a's words of the next product: 32 per block, zero from na on
+    off += 128 * q.ma;
+    q.cb_off = 0;
     q.braw_off = off;
     off += 2 * 4 * (32 * (q.mb + 2) + 4);
     off = (off + 15) & ~15u;
     q.flags_off = off;
     off += 4 * kEpiWarps;
     q.bar_off = (off + 15) & ~15u;
-    q.smem = q.bar_off + 8 * (2 * dslots + 13) + 16;  // mbarriers, then the tensor-memory slot and abort flag
+    q.smem = q.bar_off + 8 * (2 * kTBufs + 12) + 16;  // mbarriers, then the tensor-memory slot and abort flag
     if (q.smem < kMinSmem) q.smem = kMinSmem;  // one CTA per SM: each takes all of tensor memory
     q.w_off = 0;
 }
@@ -1106,9 +1147,9 @@ cudaError_t quad_tc_launch(QuadTcPlan *p, const uint32_t *a, const uint32_t *b, 
     g.t_bytes = q.t_bytes;
     const uint32_t grid = batch < p->ctas ? (uint32_t)batch : p->ctas;
     if (q.tall && q.dw == 32)
-        k_mul_quad_tc_tall<32><<<grid, kThreadsTall, q.smem, st>>>(g);
+        k_mul_quad_tc_tall<32><<<grid, threads_tall<32>(), q.smem, st>>>(g);
     else if (q.tall)
-        k_mul_quad_tc_tall<64><<<grid, kThreadsTall, q.smem, st>>>(g);
+        k_mul_quad_tc_tall<64><<<grid, threads_tall<64>(), q.smem, st>>>(g);
     else if (q.tw)
         k_mul_quad_tc_tw<<<grid, kThreadsTw, q.smem, st>>>(g);
     else

@@ -56,17 +56,17 @@ def chunk_of(mb, ma16, na_limbs, nb_limbs):
     xs = (2 * ma + (ma16 - ma)) * 16
     nout = na_limbs + nb_limbs
     dw = 32 if ma16 <= 32 else 64
-    dslots = 512 // dw
-    group = dslots // 2
+    group = 512 // dw // 2
     xbytes = (16 * xs + 1023) & ~1023
     t_bytes = ((BLK * group + LEAD) * ROWB + 1023) & ~1023
-    off = 2 * xbytes + 2 * t_bytes
+    off = 2 * xbytes + 3 * t_bytes                     # three T buffers
     off += ((4 * (nout + (nout >> 4)) + 16 + 15) & ~15) + 8 * 256
+    off += 128 * ma                                    # a's words of the next product
     off += 2 * 4 * (32 * (mb + 2) + 4)
     off = (off + 15) & ~15
     off += 4 * 16
     off = (off + 15) & ~15
-    end = off + 8 * (2 * dslots + 13) + 16
+    end = off + 8 * (2 * 3 + 12) + 16                  # 18 mbarriers, the slot, the abort flag
     assert (BLK * group + LEAD) * ROWB <= t_bytes
     return group, end
 
