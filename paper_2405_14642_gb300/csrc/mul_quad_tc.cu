@@ -40,9 +40,10 @@
 //    epilogue warps; three D slots of 128 columns and two W slots;
 //  * k_mul_quad_tc_tall (ma16 <= 64): every MMA's A operand is a window of
 //    one Toeplitz matrix in shared memory, D takes all of tensor memory in
-//    slots of 32 or 64 columns, up to eight accumulation chains in flight,
-//    the epilogue stores D's starting value instead of a bias MMA, and the
-//    staging and the carry into limbs overlap the MMAs (see there).
+//    slots of 32 or 64 columns in two halves, three buffers of Toeplitz rows,
+//    no bias MMA (a step's first MMA overwrites D and the epilogue adds the
+//    2^23 in f32), and the staging and the carry into limbs overlap the MMAs
+//    (see there).
 // Warp 0 polls its mbarriers without sleeping (its wake-up is on the
 // critical path).  Every wait is bounded; a timeout raises a device flag
 // (bn_tc_check).
