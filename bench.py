@@ -81,7 +81,7 @@ OPCODES = {"add": lambda bn: bn.BN_OP_ADD, "quad": lambda bn: bn.BN_OP_MUL_QUAD,
 # The schoolbook product runs on the integer pipes below this size and on the
 # tensor cores (byte digits, exact f32 sums) from it up, where that kernel is
 # the faster schoolbook on GB300; both compute every word product.
-TC_MIN_BITS = 32768
+TC_MIN_BITS = 16384
 # fp16-equivalent FLOP of one 32x32-bit word product on the tensor cores:
 # 16 byte products, 2 FLOP each.
 TC_FLOP_PER_WORD_PRODUCT = 32
@@ -130,7 +130,7 @@ def workload_config(ops, world: int):
     bits = sorted({o.bits for o in ops})
     return {
         "workload": "size sweep 1K-256K bits: add + schoolbook mul at every size (integer-pipe "
-                    "kernel below 32K bits, tensor-core kernel from 32K bits), NTT mul "
+                    "kernel below 16K bits, tensor-core kernel from 16K bits), NTT mul "
                     "(1x64-bit prime/16-bit digits, 2x64-bit primes CRT/32-bit digits, "
                     "3x32-bit primes/32-bit digits) at 16K-256K; 64 MiB of u32 operand limbs "
                     "per side per size",

@@ -28,11 +28,11 @@ def test_ops_and_algorithmic_work():
     assert labels[:2] == ["add@1K", "quad@1K"] and labels[-2:] == ["crt@256K", "ntt3@256K"]
     add = next(o for o in ops if o.label == "add@256K")
     assert add.bytes == 4 * (3 * 8192 + 1) * 2048 and add.mults == 0
-    # the schoolbook runs on the tensor cores from 32K bits up
-    assert next(o for o in ops if o.label == "quad@16K").name == "quad"
+    # the schoolbook runs on the tensor cores from 16K bits up
+    assert next(o for o in ops if o.label == "quad@8K").name == "quad"
     quad = next(o for o in ops if o.label == "quadtc@256K")
     assert quad.prods == 8192 * 8192 * 2048 and quad.nout == 16384
-    assert [o.bits for o in ops if o.name == "quadtc"] == [1 << e for e in range(15, 19)]
+    assert [o.bits for o in ops if o.name == "quadtc"] == [1 << e for e in range(14, 19)]
     ntt = next(o for o in ops if o.label == "ntt64@256K")
     assert ntt.prods == 4 * bench.ntt_lengths(8192)[2] * 2048
     # three primes of 32 bits at N = 16384: 3 * (3 * 8192 * 14 + 2 * 16384) word products
