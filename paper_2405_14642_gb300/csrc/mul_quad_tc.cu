@@ -117,14 +117,23 @@ constexpr uint32_t kBiasBits = 0x4b000000u;
 constexpr uint16_t kF16_2048 = 0x6800u, kF16_4096 = 0x6c00u;
 constexpr uint32_t kBiasBytes = 256;  // each bias operand: one core matrix per K-chunk (8 rows, then zeros)
 
-#define BN_TC_FLUSH(x)                                   \
-    case x:                                              \
-        colr[kBlk * (n0 + (x))] = acc[(x) >> 5][(x) & 31]; \
-        acc[(x) >> 5][(x) & 31] = 0;                     \
-        break;
-#define BN_TC_FLUSH8(x)                                                                      \
-    BN_TC_FLUSH(x) BN_TC_FLUSH(x + 1) BN_TC_FLUSH(x + 2) BN_TC_FLUSH(x + 3) BN_TC_FLUSH(x + 4) \
-        BN_TC_FLUSH(x + 5) BN_TC_FLUSH(x + 6) BN_TC_FLUSH(x + 7)
+// Column f (warp-uniform, f < N of the M accumulators) stored to dst[stride f]
+// and started over at zero, by a tree of uniform branches on f: a switch
+// compiles to an indirect jump, which measured slower in these epilogues.
+template <uint32_t LO, uint32_t N, uint32_t M>
+__device__ __forceinline__ void flush_tree(uint32_t (&acc)[M], uint32_t f, uint32_t *dst, uint32_t stride) {
+    if constexpr (N == 1) {
+        dst[stride * LO] = acc[LO];
+        acc[LO] = 0;
+    } else {
+        if (f < LO + N / 2) flush_tree<LO, N / 2, M>(acc, f, dst, stride);
+        else flush_tree<LO + N / 2, N / 2, M>(acc, f, dst, stride);
+    }
+}
+template <uint32_t M>
+__device__ __forceinline__ void flush_column(uint32_t (&acc)[M], uint32_t f, uint32_t *dst, uint32_t stride) {
+    flush_tree<0, M, M>(acc, f, dst, stride);
+}
 
 // ---- Toeplitz rows ----------------------------------------------------------
 //
@@ -295,11 +304,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
             const uint32_t m = (warp - 1 - kBuildWarps) >> 2, n0 = 32 * kCPW * m;
             const uint32_t chi = (g.ma + 31) >> 5;        // chunks that hold D's ma columns
             uint32_t *const colr = cols + 32 * lq + lane;  // this thread's row of every column block
-            uint32_t acc[kCPW][32];
+            uint32_t acc[kCPW * 32];
 #pragma unroll
-            for (int c = 0; c < (int)kCPW; ++c)
-#pragma unroll
-                for (int i = 0; i < 32; ++i) acc[c][i] = 0;
+            for (int i = 0; i < (int)(kCPW * 32); ++i) acc[i] = 0;
             for (uint32_t J = 0; J < S; ++J, ++gs) {
                 const uint32_t d = gs % kDS;
                 if (!__all_sync(FULL_MASK, tc::mbar_wait(&dfull[d], (gs / kDS) & 1u, kWaitNs, abortf))) {
@@ -317,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
                             uint32_t v[8];
                             tc::tmem_ld8(ta + 8 * hh, v);
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) acc[c][8 * hh + j] += v[j] - kBiasBits;
+                            for (int j = 0; j < 8; ++j) acc[32 * c + 8 * hh + j] += v[j] - kBiasBits;
                         }
                     }
                 }
@@ -328,12 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
                 // over as block J + ma (after the last step, J = mb, every column
                 // is published below instead)
                 const uint32_t f = J - n0;  // warp-uniform
-                if (J < g.mb && f < 32 * kCPW) {
-                    switch (f) {
-                        BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) BN_TC_FLUSH8(16) BN_TC_FLUSH8(24)
-                        BN_TC_FLUSH8(32) BN_TC_FLUSH8(40) BN_TC_FLUSH8(48) BN_TC_FLUSH8(56)
-                    }
-                }
+                if (J < g.mb && f < 32 * kCPW) flush_column(acc, f, colr + kBlk * n0, kBlk);
             }
             // publish: column n < mb went on to block n + ma after step n
 #pragma unroll
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mul_quad_tc(TcArgs g) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const uint32_t n = n0 + 32 * c + j;
-                    if (n < g.ma) colr[kBlk * (n < g.mb ? n + g.ma : n)] = acc[c][j];
+                    if (n < g.ma) colr[kBlk * (n < g.mb ? n + g.ma : n)] = acc[32 * c + j];
                 }
         }
         __syncthreads();
@@ -519,9 +521,7 @@ __global__ void __launch_bounds__(kThreadsTw, 1) k_mul_quad_tc_tw(TcArgs g) {
                 // column J now holds all of block J: store it and start the column
                 // over as block J + ma
                 const uint32_t f = J - n0;  // warp-uniform
-                if (J < g.mb && f < kCW) {
-                    switch (f) { BN_TC_FLUSH8(0) BN_TC_FLUSH8(8) BN_TC_FLUSH8(16) BN_TC_FLUSH8(24) }
-                }
+                if (J < g.mb && f < kCW) flush_column(acc[0], f, colr + kBlk * n0, kBlk);
             }
             // publish: column n < mb went on to block n + ma after step n (two
             // loops with one destination each: this form compiles without spills)
@@ -976,8 +976,6 @@ __global__ void __launch_bounds__(threads_tall<DW>(), 1) k_mul_quad_tc_tall(TcAr
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
 }
-#undef BN_TC_FLUSH8
-#undef BN_TC_FLUSH
 
 struct TcGeometry {
     uint32_t na, nb, ma, mb, ma16, xs, w_off, ca_off, cb_off, braw_off, spill_off, flags_off, bar_off, smem;

@@ -130,3 +130,15 @@ def test_mma_probe_runs_and_checks_arguments():
     for bad in [(64, 16, 8), (24, 1, 8), (272, 1, 8), (32, 0, 8), (32, 1, 0)]:
         with pytest.raises(bn.BnError):
             bn.bn_probe_mma_throughput(*bad, 10, 1, status)
+
+
+@pytest.mark.parametrize("batch", [1, 2, 151, 152, 153, 305])
+@pytest.mark.parametrize("na,nb", [(1024, 1024), (2048, 1500), (500, 20), (4096, 4000)])
+def test_quad_tc_batch_around_the_grid(batch, na, nb):
+    """Batches of one pair, around one pair per SM (152) and past two, at
+    32- and 64-column slots of the Toeplitz-window kernel (each CTA fetches its
+    next pair's rows ahead, so the last pair of a CTA, a CTA without a second
+    pair and a grid smaller than the SM count all occur) and at 128K bits."""
+    torch_cuda()
+    a, b = workloads.pair_batch(batch, na, nb, seed=workloads.seed_for(9, 9000 + batch * 5 + na), edges=True)
+    assert_limbs_equal(_tc(a, b), oracle.mul(a, b), f"quad_tc batch {batch} {na}x{nb}")
