@@ -423,12 +423,20 @@ __device__ void normalize_limbs(uint32_t nout, uint32_t *crow, uint32_t *out_s, 
     if (QN < 2) QN = 2;  // a window must absorb a two-word spill
     const uint32_t k0 = t * QN;
     const uint32_t k1 = k0 + QN < nout ? k0 + QN : nout;
-    // (a) this window's limbs, carrying within the window
+    // (a) this window's limbs, carrying within the window (their loads four at
+    // a time, so that a limb read from L2 does not wait for the one before)
     u128 carry = 0;
-    for (uint32_t k = k0; k < k1; ++k) {
-        const u128 v = limb(k) + carry;
-        out_s[stage_index(k)] = (uint32_t)v;
-        carry = v >> 32;
+    for (uint32_t k = k0; k < k1; k += 4) {
+        u128 lv[4];
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) lv[j] = k + j < k1 ? limb(k + j) : (u128)0;
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j)
+            if (k + j < k1) {
+                const u128 v = lv[j] + carry;
+                out_s[stage_index(k + j)] = (uint32_t)v;
+                carry = v >> 32;
+            }
     }
     spill[t] = (uint64_t)carry;  // < 2^64: the coefficients are below 2^96
     __syncthreads();
