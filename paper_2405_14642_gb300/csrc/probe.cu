@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(128, 1) k_probe_mma(uint32_t n, uint32_t chain
             // counters stepped without divisions, so that issuing stays well ahead of the pipe:
             // A window ia of 185 positions x 512 bytes (the last ends at 94208 + 4096 = kProbeA),
             // B window ib of 32 positions x 16 bytes (n <= 256 rows: 4 KB per K-chunk, ends below
-            // kProbeB), accumulator c, and r = this round's place in its chain
+            // kProbeB), accumulator c, and r = this MMA's place in its chain
             uint32_t c = 0, r = 0, ia = 0, ib = 0;
             for (uint32_t i = 0; i < iters; ++i) {
                 bn::tc::mma_f16_ss(taddr + n * c, ad + 32 * ia, bd + ib, idesc, r != 0);
