@@ -144,3 +144,126 @@ def test_per_step_slots_of_the_256K_kernel(nb_limbs):
         for kk in range(8):
             i0 = LEAD - 16 * kk
             assert np.array_equal(T[i0:i0 + BLK], bpad[BLK + BLK * J + r - 16 * kk - c])
+
+
+# ---- the Toeplitz-window kernel's hand-over protocol --------------------------
+#
+# The roles of k_mul_quad_tc_tall in program order, as generators of actions on
+# mbarriers: ("wait", bar, k) waits for the k-th completion of bar with the parity
+# k % 2 (mbarrier try_wait.parity), ("arrive", bar) completes a phase (each role
+# stands for all its warps), ("commit", bar) queues an arrival that the tensor
+# pipe delivers after every MMA issued before it.  A random scheduler runs them;
+# a parity wait is only correct if, when its parity test passes, exactly k + 1
+# phases have completed (a barrier two phases ahead would make it wait forever,
+# one behind would let it through early).
+
+def _tall_roles(S, kC, products, normalizer):
+    groups = [min(kC, S - J) for J in range(0, S, kC)]
+
+    def mma():
+        gg = 0
+        for pi in range(products):
+            yield ("wait", ("xfull", pi % 2), pi // 2)
+            for k, n in enumerate(groups):
+                if gg >= 2:
+                    yield ("wait", ("dempty", gg % 2), (gg - 2) // 2)
+                yield ("wait", ("tfull", gg % 3), gg // 3)
+                yield ("commit", ("tempty", gg % 3))
+                if k == len(groups) - 1:
+                    yield ("commit", ("xempty", pi % 2))
+                gg += 1
+        if gg:
+            yield ("wait", ("tempty", (gg - 1) % 3), (gg - 1) // 3)
+
+    def epilogue():
+        eg = 0
+        for pi in range(products):
+            if pi >= 2:
+                yield ("wait", ("cempty", pi % 2), (pi - 2) // 2)
+            for n in groups:
+                yield ("wait", ("tempty", eg % 3), eg // 3)
+                yield ("arrive", ("dempty", eg % 2))
+                eg += 1
+            yield ("arrive", ("cfull", pi % 2))
+
+    def finish(q):
+        yield ("wait", ("cfull", q % 2), q // 2)
+        yield ("arrive", ("cempty", q % 2))
+
+    def producer():
+        gg = 0
+        for pi in range(products):
+            if pi >= 2:
+                yield ("wait", ("xempty", pi % 2), (pi - 2) // 2)
+            yield ("arrive", ("xfull", pi % 2))
+            for k, n in enumerate(groups):
+                if gg >= 3:
+                    yield ("wait", ("tempty", gg % 3), (gg - 3) // 3)
+                yield ("arrive", ("tfull", gg % 3))
+                last = k == len(groups) - 1
+                if not normalizer and pi > 0 and (k == 2 or (last and k < 2)):
+                    yield from finish(pi - 1)
+                gg += 1
+        if not normalizer and products:
+            yield from finish(products - 1)
+
+    def normalizing():
+        for pi in range(products):
+            yield from finish(pi)
+
+    roles = [mma(), epilogue(), producer()]
+    if normalizer:
+        roles.append(normalizing())
+    return roles
+
+
+def _run_protocol(S, kC, products, normalizer, seed):
+    rng = np.random.default_rng(seed)
+    done = {}        # completed phases per barrier
+    fifo = []        # commits the tensor pipe has yet to deliver
+    roles = _tall_roles(S, kC, products, normalizer)
+    pending = [next(r, None) for r in roles]
+    waits = 0
+    while True:
+        ready = []
+        for i, act in enumerate(pending):
+            if act is None:
+                continue
+            if act[0] == "wait":
+                c, k = done.get(act[1], 0), act[2]
+                assert c <= k + 1, f"{act[1]} ran {c - k} phases past a wait for completion {k}"
+                if c % 2 != k % 2:           # the parity test passes ...
+                    assert c == k + 1, f"{act[1]}: wait for completion {k} passed at {c}"
+                    ready.append(i)
+            else:
+                ready.append(i)
+        if fifo:
+            ready.append(-1)
+        if not ready:
+            assert all(a is None for a in pending), f"deadlock: {pending}"
+            return waits
+        i = ready[rng.integers(len(ready))]
+        if i == -1:
+            bar = fifo.pop(0)
+            done[bar] = done.get(bar, 0) + 1
+            continue
+        act = pending[i]
+        if act[0] == "arrive":
+            done[act[1]] = done.get(act[1], 0) + 1
+        elif act[0] == "commit":
+            fifo.append(act[1])
+        else:
+            waits += 1
+        pending[i] = next(roles[i], None)
+
+
+@pytest.mark.parametrize("S,kC,normalizer", [(17, 8, False), (33, 8, False), (9, 8, False), (2, 8, False),
+                                             (65, 4, True), (33, 4, True), (5, 4, True), (1, 4, True)])
+@pytest.mark.parametrize("products", [1, 2, 3, 5])
+def test_hand_over_protocol_under_random_schedules(S, kC, normalizer, products):
+    """Steps per product S (tail groups included), 8 steps per group with the
+    producer carrying the limbs (32-column slots) or 4 with four normalising
+    warps (64-column slots), 1-5 products per CTA: in 150 random interleavings
+    every wait completes on its own phase and no role is left waiting."""
+    for seed in range(150):
+        assert _run_protocol(S, kC, products, normalizer, seed) > 0
