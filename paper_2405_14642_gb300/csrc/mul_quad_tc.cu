@@ -81,9 +81,11 @@ struct TcArgs {
     uint32_t *scratch;        // per CTA: 128 (ma + mb) byte-column sums
     uint64_t scratch_stride;  // words per CTA
     uint32_t xs;              // bytes per K-chunk row of XX: (2 ma + ma16 - ma) * 16
-    uint32_t w_off, ca_off, cb_off, braw_off, spill_off, flags_off, bar_off;  // shared-memory offsets
+    // shared-memory offsets (ca_off, cb_off: the bias MMA's operands; in k_mul_quad_tc_tall
+    // ca_off holds a's words of the next product)
+    uint32_t w_off, ca_off, cb_off, braw_off, spill_off, flags_off, bar_off;
     uint32_t x1_off;          // k_mul_quad_tc_tall: the second XX buffer
-    uint32_t t_off, t_bytes;  // k_mul_quad_tc_tall: the two T buffers
+    uint32_t t_off, t_bytes;  // k_mul_quad_tc_tall: the kTBufs T buffers
 };
 
 // Quarter u of row r of W_J (words 16 u .. 16 u + 15) into registers, for a
